@@ -1,0 +1,99 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the
+pins of test_oracle_closed_forms.py catch each one."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.asp_oracle as OA
+import tests.test_oracle_closed_forms as pins
+
+
+def _patch(monkeypatch, name, fn):
+    monkeypatch.setattr(OA, name, fn)
+    monkeypatch.setattr(O, name, fn)
+
+
+def test_flipped_jacobian_sign_is_caught(monkeypatch):
+    orig = OA.model_and_jacobian
+
+    def bad(theta, xs, ys):
+        m, J = orig(theta, xs, ys)
+        J = J.copy()
+        J[:, 1::4] *= -1.0          # d/dx0 with the wrong sign
+        return m, J
+
+    _patch(monkeypatch, "model_and_jacobian", bad)
+    with pytest.raises(AssertionError):
+        pins.test_jacobian_against_central_differences()
+
+
+def test_missing_factor_two_in_width_is_caught(monkeypatch):
+    def bad(theta, xs, ys):
+        theta = np.asarray(theta, float)
+        out = np.zeros(np.broadcast(xs, ys).shape)
+        for k in range(len(theta) // 4):
+            a, x0, y0, w = theta[4 * k: 4 * k + 4]
+            out += a * np.exp(-((xs - x0) ** 2 + (ys - y0) ** 2) / (w * w))
+        return out
+
+    _patch(monkeypatch, "gauss_model", bad)
+    with pytest.raises(AssertionError):
+        pins.test_model_against_python_loop()
+
+
+def test_widths_added_instead_of_subtracted_is_caught(monkeypatch):
+    def bad(a_ic, w_ic, alpha_b, omega_b):
+        F = a_ic * w_ic * w_ic / (alpha_b * omega_b * omega_b)
+        wi = math.sqrt(w_ic * w_ic + omega_b * omega_b)
+        return F, F / (2 * math.pi * wi * wi), wi, False
+
+    _patch(monkeypatch, "deconvolve", bad)
+    with pytest.raises(AssertionError):
+        pins.test_eq7_eq8_against_numerical_convolution(0.3, 2.0, 1.0, 1.5)
+
+
+def test_transposed_psf_index_is_caught(monkeypatch):
+    orig = OA.subtract_terms
+
+    def bad(R, B, terms):
+        return orig(R, np.asarray(B)[::-1, ::-1], terms)   # B(q - p) instead of B(p - q)
+
+    _patch(monkeypatch, "subtract_terms", bad)
+    with pytest.raises(AssertionError):
+        pins.test_subtraction_separable_against_definition(9, 11)
+
+
+def test_unit_sum_smoothing_kernel_is_caught(monkeypatch):
+    def bad(s):
+        m = int(math.ceil(4.0 * s))
+        u = np.arange(-m, m + 1, dtype=np.float64)
+        e = np.exp(-u * u / (2.0 * s * s))
+        return e / e.sum()
+
+    _patch(monkeypatch, "smoothing_kernel_1d", bad)
+    with pytest.raises(AssertionError):
+        pins.test_smoothing_init_recovers_gaussian_scale_and_amplitude()
+
+
+def test_signed_argmax_is_caught(monkeypatch):
+    def bad(R):
+        flat = np.asarray(R).ravel()
+        i = int(np.argmax(flat))
+        return i, float(flat[i])
+
+    _patch(monkeypatch, "peak_simple", bad)
+    with pytest.raises(AssertionError):
+        pins.test_argmax_against_python_scan_with_ties()
+
+
+def test_gain_on_wrong_side_is_caught(monkeypatch):
+    orig = OA.MinorCycle._component_from_fit
+
+    def bad(self, a, x, y, w, gain=1.0):
+        return orig(self, a, x, y, w, gain=1.0 / gain if gain != 1.0 else 1.0)
+
+    monkeypatch.setattr(OA.MinorCycle, "_component_from_fit", bad)
+    with pytest.raises(AssertionError):
+        pins.test_first_iteration_on_point_source_gaussian_psf()
