@@ -1,0 +1,231 @@
+/*
+ * libasp -- the Asp-Clean2016 minor cycle on one GB300 GPU (sm_103a).
+ *
+ * Zhang, Bhatnagar, Rau & Zhang (2016), "Efficient implementation of the
+ * adaptive scale pixel decomposition algorithm".  The PSF is approximated by a
+ * single Gaussian (alpha_b, omega_b) (Sect. 3), so each candidate component is
+ * fitted as a PSF-convolved Gaussian directly to the residual image (Eq. 6) by
+ * Levenberg-Marquardt, then deconvolved analytically (Eqs. 7-8); the residual
+ * is updated with the full PSF (Sect. 2 step 3) and initial values come from a
+ * peak search, simple or multi-scale smoothed (Sect. 2 step 1, Sect. 3).
+ *
+ * Conventions for every call:
+ *  - Images are FP32, row-major, y the slow axis; pixel centres sit at integer
+ *    coordinates (x = column, y = row); flat index = y * W + x.
+ *  - The PSF is a 2H x 2W FP32 array whose zero lag is at [H, W] (so
+ *    B[p - q + (H, W)] exists for every pair of image pixels p, q).
+ *  - "_dev" pointers are device pointers of the current CUDA device; "_host"
+ *    pointers are host memory (pageable or pinned).  The library copies what
+ *    it is given: it never keeps a caller pointer after a call returns.
+ *  - Every call enqueues its work on the context's stream; calls that return
+ *    values synchronise that stream before returning.
+ *  - Errors are returned, never thrown; nothing aborts.  After ASP_ERR_CUDA or
+ *    ASP_ERR_TIMEOUT the context answers ASP_ERR_STATE to everything except
+ *    asp_destroy and the getters of the last error.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef ASP_H
+#define ASP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct asp_ctx asp_ctx;
+
+typedef enum {
+    ASP_OK = 0,
+    ASP_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter */
+    ASP_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    ASP_ERR_OOM = 3,           /* device allocation failed */
+    ASP_ERR_NAN = 4,           /* non-finite input or result */
+    ASP_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    ASP_ERR_NOT_CONVERGED = 6, /* reserved: fits report status in asp_fit_info */
+    ASP_ERR_STATE = 7,         /* context unusable after an earlier failure */
+    ASP_ERR_UNSUPPORTED = 8,   /* size beyond a compiled-in limit */
+    ASP_ERR_CAPACITY = 9       /* component list full */
+} asp_status;
+
+/* Initial-value modes (Sect. 3): AUTO applies the 5 % area switch. */
+typedef enum { ASP_INIT_AUTO = 0, ASP_INIT_SIMPLE = 1, ASP_INIT_SMOOTH = 2 } asp_init_mode;
+/* Peak-search modes for asp_find_peak. */
+typedef enum { ASP_PEAK_SIMPLE = 0, ASP_PEAK_SMOOTH = 1 } asp_peak_mode;
+/* Levenberg-Marquardt termination codes (asp_fit_info.status). */
+typedef enum { ASP_LM_CONVERGED = 0, ASP_LM_CAP = 1, ASP_LM_STALLED = 2 } asp_lm_status;
+/* Why a minor cycle stopped (asp_cycle_stats.stop_reason). */
+typedef enum {
+    ASP_STOP_NONE = 0, ASP_STOP_ITER = 1, ASP_STOP_NOISE = 2, ASP_STOP_CAPACITY = 3
+} asp_stop_reason;
+
+/* Largest active set one fit accepts (members fitted jointly). */
+#define ASP_KMAX 32
+
+/* A PSF-convolved Gaussian a exp(-((x-x0)^2+(y-y0)^2)/(2 w^2)): the fitted
+ * function of Eq. 6, (alpha_ic, x_ic, y_ic, omega_ic). */
+typedef struct { double amp, x, y, width; } asp_gauss;
+
+/* A deconvolved model component (Eqs. 7-8): flux F = 2 pi alpha omega^2 (for a
+ * point: F itself), amplitude alpha, centre, width omega (0 for a point). */
+typedef struct {
+    double flux, amp, x, y, width;
+    int32_t is_point;
+    int32_t reserved;
+} asp_component;
+
+/* Peak-search result.  SIMPLE: the largest |R| (lowest index on ties), init
+ * (R(p*), x*, y*, omega_b).  SMOOTH: the largest |S_j| over scales and pixels
+ * (ties: lower scale, then lower index); init (S/(sqrt(pi) s), x*, y*,
+ * max(s, omega_b)). */
+typedef struct {
+    int64_t index;
+    int32_t x, y;
+    float value;          /* R(p*) or S_j*(p*) */
+    float scale;          /* s_j* (SMOOTH) or 0 */
+    int32_t mode;         /* asp_peak_mode */
+    int32_t scale_index;  /* j* or -1 */
+    double a0, x0, y0, w0;
+} asp_peak;
+
+/* Outcome of one Levenberg-Marquardt fit. */
+typedef struct {
+    int32_t iters;        /* damped solves (accepted or rejected) */
+    int32_t passes;       /* pixel passes over the window (1 + valid trials) */
+    int32_t status;       /* asp_lm_status */
+    int32_t k;            /* members fitted */
+    int32_t x0, x1, y0, y1; /* fit window (inclusive) */
+    double chi2_init, chi2_final, lambda;
+    int64_t pixel_evals;  /* passes x window pixels */
+} asp_fit_info;
+
+/* Minor-cycle parameters.  Defaults from asp_default_params. */
+typedef struct {
+    float gain;           /* loop gain for a new component (Sect. 4: 0.35) */
+    int32_t k_max;        /* active-set cap (1..ASP_KMAX) */
+    int32_t lm_max_iter;  /* damped solves per fit (50) */
+    double lm_lambda0;    /* 1e-3 */
+    double lm_rtol;       /* predicted / actual relative chi2 decrease (1e-7) */
+    double lm_xtol;       /* relative step size (1e-7) */
+    float noise_sigma;    /* <= 0: 1.4826 x MAD of the dirty image */
+    float stop_ksigma;    /* stop when max|R| < stop_ksigma * noise_sigma (3) */
+    int32_t n_scales;     /* smoothing scales omega_b 2^j, j < n_scales (6) */
+    float area_frac;      /* simple-method switch threshold (Sect. 3: 0.05) */
+    int32_t init_mode;    /* asp_init_mode */
+    double tau;           /* active-set retention threshold (1e-3) */
+    int32_t retained_cap; /* retained-list cap (0: 8 x k_max) */
+    int32_t max_components; /* component-list capacity (0: 65536) */
+} asp_params;
+
+/* Totals of asp_minor_cycle since asp_init (or the last asp_set_state). */
+typedef struct {
+    int64_t iterations;   /* minor-cycle iterations done */
+    int64_t components;   /* components in the model */
+    int64_t pixel_evals;  /* LM pixel evaluations (window pixels x passes) */
+    int64_t lm_iters;     /* damped solves */
+    int64_t lm_passes;    /* pixel passes */
+    double peak_abs;      /* current max |R| */
+    int32_t stop_reason;  /* asp_stop_reason of the last call */
+    int32_t reserved;
+} asp_cycle_stats;
+
+/* One minor-cycle iteration as recorded on the device. */
+typedef struct {
+    int32_t t, mode, k, status;
+    int32_t iters, passes, x0, x1, y0, y1;
+    int32_t new_index, n_terms;
+    float peak_value, init_scale;
+    double chi2_init, chi2_final;
+    double a0, x0_init, y0_init, w0;
+} asp_iter_record;
+
+const char* asp_status_string(asp_status s);
+void asp_default_params(asp_params* p);
+
+/* Create a context: copies dirty (H x W) and psf (2H x 2W) from device
+ * memory, fits the single-Gaussian beam (alpha_b, omega_b) to the PSF main
+ * lobe (Sect. 3) and finds the first peak.  stream: a cudaStream_t (NULL:
+ * the legacy default stream).  On error *out is NULL. */
+asp_status asp_init(const asp_params* p, int H, int W, const float* dirty_dev, const float* psf_dev,
+                    void* stream, asp_ctx** out);
+/* Same as asp_init with host-memory inputs (the copy is part of the call). */
+asp_status asp_init_host(const asp_params* p, int H, int W, const float* dirty_host,
+                         const float* psf_host, void* stream, asp_ctx** out);
+asp_status asp_destroy(asp_ctx* ctx);
+/* Last error message of this context ("" if none). */
+const char* asp_last_error(const asp_ctx* ctx);
+
+/* Beam (alpha_b, omega_b) and the fitted centre (PSF array coordinates). */
+asp_status asp_get_beam(asp_ctx* ctx, double* alpha_b, double* omega_b, double* x_b, double* y_b);
+
+/* Peak search on the current residual (Sect. 2 step 1; Sect. 3 simple
+ * method).  mode: asp_peak_mode. */
+asp_status asp_find_peak(asp_ctx* ctx, int mode, asp_peak* out);
+
+/* Joint LM fit of n Gaussians (Eq. 6) to the current residual.  The last
+ * n_old members are taken as already subtracted: their initial Gaussians are
+ * added back to form the target T = R + sum_old g(init).  The window is the
+ * bounding box of the members' boxes (half-width max(5, ceil(4 w)) around the
+ * rounded centre), clipped to the image.  Writes n fitted Gaussians to out
+ * (host) and the fit outcome to info (host).  1 <= n <= k_max. */
+asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_old,
+                              asp_gauss* out, asp_fit_info* info);
+
+/* Normal equations of the Eq. 6 objective at theta over a given window
+ * (inclusive bounds, clipped), target T = R + sum of the last n_old members:
+ * A = J^T J (4n x 4n, row-major, full), g = J^T r, chi2 = r^T r.  Host
+ * outputs.  This is the LM pixel pass on its own. */
+asp_status asp_eval_normal_equations(asp_ctx* ctx, const asp_gauss* theta, int n, int n_old,
+                                     int x0, int x1, int y0, int y1,
+                                     double* A_host, double* g_host, double* chi2_host);
+
+/* R -= B * (gain * sum_i c_i) with the full PSF (Sect. 2 step 3); c_i is
+ * component i sampled on the grid (a flux-normalised Gaussian on the box
+ * |q - centre|_inf <= ceil(5 w) + 1 if w >= 0.5 px and not a point, else a
+ * bilinear deposit).  A negative flux adds the component back.  n <= 2 x
+ * ASP_KMAX. */
+asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float gain);
+
+/* Run up to n_iter minor-cycle iterations (Sect. 2 steps 1-4 with the
+ * Sect. 3 objective, deconvolution and initial-value switch); the loop stops
+ * early when max|R| < stop_ksigma * noise_sigma.  Totals to out (may be NULL). */
+asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out);
+
+/* Multi-scale smoothed residual S_j (unit-L2 Gaussian of scale s_j, zero
+ * padding) written to out_dev (H x W, device).  scale_index < asp_num_scales. */
+asp_status asp_smooth(asp_ctx* ctx, int scale_index, float* out_dev);
+asp_status asp_num_scales(asp_ctx* ctx, int* n, double* scales_host /* >= n entries or NULL */);
+
+/* Residual access.  asp_residual_ptr: borrowed device pointer, valid until
+ * asp_destroy; writes through it are the caller's responsibility (call
+ * asp_refresh_peak afterwards). */
+asp_status asp_residual_ptr(asp_ctx* ctx, float** residual_dev);
+asp_status asp_copy_residual(asp_ctx* ctx, float* dst, int dst_on_host);
+asp_status asp_set_residual(asp_ctx* ctx, const float* src, int src_on_host);
+asp_status asp_refresh_peak(asp_ctx* ctx);
+
+/* Model access.  asp_get_components copies min(cap, count) components to
+ * host memory and sets *count to the total. */
+asp_status asp_get_components(asp_ctx* ctx, asp_component* out_host, int cap, int* count);
+asp_status asp_get_history(asp_ctx* ctx, asp_iter_record* out_host, int cap, int* count);
+asp_status asp_get_stats(asp_ctx* ctx, asp_cycle_stats* out);
+
+/* Minor-cycle state beyond the residual: the component list, the retained
+ * (active) list most recent first, the iteration counter and the last
+ * iteration's (omega_i, omega_0) used by the init-mode switch.  All host. */
+asp_status asp_get_state(asp_ctx* ctx, asp_component* comps, int comp_cap, int* n_comp,
+                         int* retained, int ret_cap, int* n_ret, int64_t* t,
+                         double* last_wi, double* last_w0);
+asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp,
+                         const int* retained, int n_ret, int64_t t, double last_wi,
+                         double last_w0);
+/* Checkpoint the whole minor-cycle state (residual included) to a file, or
+ * restore it into a context of the same size. */
+asp_status asp_save_state(asp_ctx* ctx, const char* path);
+asp_status asp_load_state(asp_ctx* ctx, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASP_H */

@@ -216,8 +216,8 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
 
     1. evaluate A, g, chi^2 at the current point;
     2. solve the damped normal equations (one iteration per solve);
-    3. stop as converged if the predicted decrease ``2 d.g - d.A.d`` is
-       below ``rtol * chi^2``;
+    3. stop as converged if the predicted decrease ``2 d.g - d.A.d`` (=
+       ``d.g + lambda d.D.d`` for the damped step) is below ``rtol * chi^2``;
     4. evaluate chi^2 (with A, g) at the trial point; accept iff chi^2
        strictly decreases (lambda /= 10), else lambda *= 10;
     5. on an accepted step stop if the relative decrease is below rtol or
@@ -246,7 +246,11 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
                 status = LM_STALLED
                 break
             continue
-        pred = 2.0 * float(delta @ g) - float(delta @ A @ delta)
+        # predicted decrease 2 d.g - d.A.d of the linearised model; by the
+        # damped normal equations (A + lam D) d = g it equals d.g + lam d.D.d
+        dd = np.diag(A).copy()
+        dd[~(dd > 0)] = 1.0
+        pred = float(delta @ g) + lam * float(delta @ (dd * delta))
         if pred <= lm.rtol * chi2:
             status = LM_CONVERGED
             break

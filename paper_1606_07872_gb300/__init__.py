@@ -1,0 +1,360 @@
+"""GB300-native Asp-Clean2016 minor cycle (Zhang, Bhatnagar, Rau & Zhang 2016).
+
+Thin Python binding of ``libasp.so`` (C-ABI in ``include/asp.h``).  The
+functions carry the C names (``asp_init``, ``asp_find_peak``,
+``asp_fit_active_set``, ``asp_subtract``, ``asp_minor_cycle``, ...) and only
+marshal arguments; PyTorch provides device memory and streams.  There is no
+CPU path: without the built library, importing the binding's calls raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    ASP_INIT_AUTO, ASP_INIT_SIMPLE, ASP_INIT_SMOOTH, ASP_KMAX, ASP_LM_CAP, ASP_LM_CONVERGED, ASP_LM_STALLED,
+    ASP_PEAK_SIMPLE, ASP_PEAK_SMOOTH, ASP_STOP_CAPACITY, ASP_STOP_ITER, ASP_STOP_NOISE, ASP_STOP_NONE,
+    asp_component, asp_cycle_stats, asp_fit_info, asp_gauss, asp_iter_record, asp_params, asp_peak,
+)
+
+__all__ = [
+    "AspError", "lib", "default_params", "asp_init", "asp_init_host", "asp_destroy", "asp_get_beam",
+    "asp_find_peak", "asp_fit_active_set", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
+    "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
+    "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
+    "Context",
+]
+
+_LIB: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libasp.so (raises ImportError if it is not built)."""
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+class AspError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        name = _lib.STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {name}" + (f" ({message})" if message else ""))
+
+
+def _check(status: int, where: str, handle=None):
+    if status != 0:
+        msg = ""
+        if handle:
+            raw = lib().asp_last_error(handle)
+            msg = raw.decode() if raw else ""
+        raise AspError(status, where, msg)
+
+
+def default_params(**overrides) -> asp_params:
+    """asp_params with the library defaults, then ``overrides`` applied."""
+    p = asp_params()
+    lib().asp_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _cuda_f32(t, shape, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _host_f32(a, shape, name):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.shape != tuple(shape):
+        raise ValueError(f"{name} has shape {a.shape}, expected {tuple(shape)}")
+    return a
+
+
+# ----------------------------------------------------------------- C-named calls
+
+def asp_init(params: asp_params, dirty, psf, stream=None):
+    """asp_init: dirty (H x W) and psf (2H x 2W) as float32 CUDA tensors."""
+    H, W = int(dirty.shape[0]), int(dirty.shape[1])
+    dp = _cuda_f32(dirty, (H, W), "dirty")
+    pp = _cuda_f32(psf, (2 * H, 2 * W), "psf")
+    h = C.c_void_p()
+    _check(lib().asp_init(C.byref(params), H, W, dp, pp, _stream_handle(stream), C.byref(h)), "asp_init")
+    return h
+
+
+def asp_init_host(params: asp_params, dirty, psf, stream=None):
+    """asp_init_host: dirty and psf as host arrays (copied inside the call)."""
+    d = _host_f32(dirty, np.shape(dirty), "dirty")
+    H, W = d.shape
+    p = _host_f32(psf, (2 * H, 2 * W), "psf")
+    h = C.c_void_p()
+    _check(lib().asp_init_host(C.byref(params), H, W, d.ctypes.data, p.ctypes.data, _stream_handle(stream),
+                               C.byref(h)), "asp_init_host")
+    return h
+
+
+def asp_destroy(h):
+    _check(lib().asp_destroy(h), "asp_destroy")
+
+
+def asp_get_beam(h):
+    v = [C.c_double() for _ in range(4)]
+    _check(lib().asp_get_beam(h, *[C.byref(x) for x in v]), "asp_get_beam", h)
+    return tuple(x.value for x in v)
+
+
+def asp_find_peak(h, mode: int = ASP_PEAK_SIMPLE) -> dict:
+    out = asp_peak()
+    _check(lib().asp_find_peak(h, int(mode), C.byref(out)), "asp_find_peak", h)
+    return {f: getattr(out, f) for f, _ in asp_peak._fields_}
+
+
+def _gauss_array(rows):
+    rows = np.asarray(rows, dtype=np.float64).reshape(-1, 4)
+    arr = (asp_gauss * len(rows))()
+    for i, (a, x, y, w) in enumerate(rows):
+        arr[i] = asp_gauss(a, x, y, w)
+    return arr, len(rows)
+
+
+def asp_fit_active_set(h, init, n_old: int = 0):
+    """Joint LM fit; ``init`` rows (a, x, y, w).  Returns (fitted rows, info)."""
+    arr, n = _gauss_array(init)
+    out = (asp_gauss * n)()
+    info = asp_fit_info()
+    _check(lib().asp_fit_active_set(h, arr, n, int(n_old), out, C.byref(info)), "asp_fit_active_set", h)
+    res = np.array([[g.amp, g.x, g.y, g.width] for g in out])
+    return res, {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_}
+
+
+def asp_eval_normal_equations(h, theta, n_old: int, window):
+    arr, n = _gauss_array(theta)
+    P = 4 * n
+    A = np.zeros((P, P))
+    g = np.zeros(P)
+    chi2 = np.zeros(1)
+    x0, x1, y0, y1 = (int(v) for v in window)
+    _check(lib().asp_eval_normal_equations(h, arr, n, int(n_old), x0, x1, y0, y1, A.ctypes.data, g.ctypes.data,
+                                           chi2.ctypes.data), "asp_eval_normal_equations", h)
+    return A, g, float(chi2[0])
+
+
+def _component_array(rows):
+    rows = np.asarray(rows, dtype=np.float64).reshape(-1, 6)
+    arr = (asp_component * len(rows))()
+    for i, (F, a, x, y, w, pt) in enumerate(rows):
+        arr[i] = asp_component(F, a, x, y, w, int(pt), 0)
+    return arr, len(rows)
+
+
+def asp_subtract(h, comps, gain: float = 1.0):
+    """R -= B * (gain * sum of components); rows (flux, amp, x, y, width, is_point)."""
+    arr, n = _component_array(comps)
+    _check(lib().asp_subtract(h, arr, n, float(gain)), "asp_subtract", h)
+
+
+def _stats_dict(s: asp_cycle_stats) -> dict:
+    return {f: getattr(s, f) for f, _ in asp_cycle_stats._fields_ if f != "reserved"}
+
+
+def asp_minor_cycle(h, n_iter: int) -> dict:
+    s = asp_cycle_stats()
+    _check(lib().asp_minor_cycle(h, int(n_iter), C.byref(s)), "asp_minor_cycle", h)
+    return _stats_dict(s)
+
+
+def asp_get_stats(h) -> dict:
+    s = asp_cycle_stats()
+    _check(lib().asp_get_stats(h, C.byref(s)), "asp_get_stats", h)
+    return _stats_dict(s)
+
+
+def asp_num_scales(h):
+    n = C.c_int()
+    _check(lib().asp_num_scales(h, C.byref(n), None), "asp_num_scales", h)
+    sc = np.zeros(max(n.value, 1))
+    _check(lib().asp_num_scales(h, C.byref(n), sc.ctypes.data), "asp_num_scales", h)
+    return sc[: n.value]
+
+
+def asp_smooth(h, scale_index: int, out):
+    """Smoothed residual of one scale into ``out`` (float32 CUDA tensor H x W)."""
+    _check(lib().asp_smooth(h, int(scale_index), out.data_ptr()), "asp_smooth", h)
+    return out
+
+
+def asp_copy_residual(h, out):
+    """Residual into ``out``: a float32 CUDA tensor or a numpy float32 array."""
+    if isinstance(out, np.ndarray):
+        assert out.dtype == np.float32 and out.flags.c_contiguous
+        _check(lib().asp_copy_residual(h, out.ctypes.data, 1), "asp_copy_residual", h)
+    else:
+        _check(lib().asp_copy_residual(h, out.data_ptr(), 0), "asp_copy_residual", h)
+    return out
+
+
+def asp_set_residual(h, src):
+    if isinstance(src, np.ndarray):
+        a = np.ascontiguousarray(src, dtype=np.float32)
+        _check(lib().asp_set_residual(h, a.ctypes.data, 1), "asp_set_residual", h)
+    else:
+        _check(lib().asp_set_residual(h, src.data_ptr(), 0), "asp_set_residual", h)
+
+
+def _comp_rows(arr, n):
+    return np.array([[c.flux, c.amp, c.x, c.y, c.width, c.is_point] for c in arr[:n]]).reshape(-1, 6)
+
+
+def asp_get_components(h) -> np.ndarray:
+    """Component list as rows (flux, amp, x, y, width, is_point)."""
+    n = C.c_int()
+    _check(lib().asp_get_components(h, None, 0, C.byref(n)), "asp_get_components", h)
+    arr = (asp_component * max(n.value, 1))()
+    _check(lib().asp_get_components(h, arr, n.value, C.byref(n)), "asp_get_components", h)
+    return _comp_rows(arr, n.value)
+
+
+def asp_get_history(h) -> list:
+    n = C.c_int()
+    _check(lib().asp_get_history(h, None, 0, C.byref(n)), "asp_get_history", h)
+    arr = (asp_iter_record * max(n.value, 1))()
+    _check(lib().asp_get_history(h, arr, n.value, C.byref(n)), "asp_get_history", h)
+    return [{f: getattr(r, f) for f, _ in asp_iter_record._fields_} for r in arr[: n.value]]
+
+
+def asp_get_state(h) -> dict:
+    nc, nr = C.c_int(), C.c_int()
+    t = C.c_int64()
+    wi, w0 = C.c_double(), C.c_double()
+    _check(lib().asp_get_state(h, None, 0, C.byref(nc), None, 0, C.byref(nr), C.byref(t), C.byref(wi),
+                               C.byref(w0)), "asp_get_state", h)
+    comps = (asp_component * max(nc.value, 1))()
+    ret = (C.c_int * max(nr.value, 1))()
+    _check(lib().asp_get_state(h, comps, nc.value, C.byref(nc), ret, nr.value, C.byref(nr), C.byref(t),
+                               C.byref(wi), C.byref(w0)), "asp_get_state", h)
+    return dict(comps=_comp_rows(comps, nc.value), retained=[ret[i] for i in range(nr.value)], t=t.value,
+                last_wi=wi.value, last_w0=w0.value)
+
+
+def asp_set_state(h, comps, retained: Sequence[int], t: int, last_wi: float, last_w0: float):
+    arr, n = _component_array(comps if len(comps) else np.zeros((0, 6)))
+    ret = (C.c_int * max(len(retained), 1))(*retained)
+    _check(lib().asp_set_state(h, arr, n, ret, len(retained), int(t), float(last_wi), float(last_w0)),
+           "asp_set_state", h)
+
+
+def asp_save_state(h, path: str):
+    _check(lib().asp_save_state(h, os.fsencode(path)), "asp_save_state", h)
+
+
+def asp_load_state(h, path: str):
+    _check(lib().asp_load_state(h, os.fsencode(path)), "asp_load_state", h)
+
+
+# ----------------------------------------------------------------- convenience
+
+class Context:
+    """Owns one libasp context.  ``dirty``/``psf``: float32 CUDA tensors
+    (device inputs) or numpy arrays (host inputs, copied in the call)."""
+
+    def __init__(self, dirty, psf, params: Optional[asp_params] = None, stream=None, **overrides):
+        self.params = params if params is not None else default_params(**overrides)
+        if isinstance(dirty, np.ndarray):
+            self.h = asp_init_host(self.params, dirty, psf, stream)
+            self.H, self.W = np.shape(dirty)
+        else:
+            self.h = asp_init(self.params, dirty, psf, stream)
+            self.H, self.W = int(dirty.shape[0]), int(dirty.shape[1])
+
+    def close(self):
+        if self.h:
+            asp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def beam(self):
+        return asp_get_beam(self.h)
+
+    def find_peak(self, mode=ASP_PEAK_SIMPLE):
+        return asp_find_peak(self.h, mode)
+
+    def fit(self, init, n_old=0):
+        return asp_fit_active_set(self.h, init, n_old)
+
+    def normal_equations(self, theta, n_old, window):
+        return asp_eval_normal_equations(self.h, theta, n_old, window)
+
+    def subtract(self, comps, gain=1.0):
+        asp_subtract(self.h, comps, gain)
+
+    def minor_cycle(self, n_iter):
+        return asp_minor_cycle(self.h, n_iter)
+
+    def stats(self):
+        return asp_get_stats(self.h)
+
+    def residual(self) -> np.ndarray:
+        out = np.empty((self.H, self.W), dtype=np.float32)
+        return asp_copy_residual(self.h, out)
+
+    def residual_device(self):
+        import torch
+        out = torch.empty((self.H, self.W), dtype=torch.float32, device="cuda")
+        return asp_copy_residual(self.h, out)
+
+    def set_residual(self, src):
+        asp_set_residual(self.h, src)
+
+    def components(self):
+        return asp_get_components(self.h)
+
+    def history(self):
+        return asp_get_history(self.h)
+
+    def state(self):
+        return asp_get_state(self.h)
+
+    def set_state(self, comps, retained, t, last_wi, last_w0):
+        asp_set_state(self.h, comps, retained, t, last_wi, last_w0)
+
+    def smooth(self, j):
+        import torch
+        out = torch.empty((self.H, self.W), dtype=torch.float32, device="cuda")
+        return asp_smooth(self.h, j, out)
+
+    def scales(self):
+        return asp_num_scales(self.h)

@@ -1,0 +1,803 @@
+// C-ABI of libasp: context life cycle, argument checking, device memory, and
+// the launch sequence of the minor cycle (captured once into a CUDA graph and
+// replayed; every step runs in the kernels of asp_fit.cu, asp_image.cu and
+// asp_cycle.cu).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "asp_dev.cuh"
+#include "asp_internal.h"
+
+using namespace aspd;
+
+namespace aspd {
+cudaError_t launch_beam_init(FitDesc* desc, const float* B, int H, int W, int g_max, cudaStream_t s);
+cudaError_t launch_radix_median(const float* v, long long n, int abs_dev_from, double center, unsigned long long* hist,
+                                double* out, cudaStream_t s);
+}
+
+struct asp_ctx {
+    int dev = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    asp_params p{};
+    Params dp{};
+    int H = 0, W = 0;
+    long long N = 0;
+    float* R = nullptr;
+    float* B = nullptr;
+    double alpha_b = 0, omega_b = 0, xb = 0, yb = 0;
+    double noise = 0;
+    CycleState* st = nullptr;
+    asp_component* comps = nullptr;
+    asp_component* comp_stage = nullptr;
+    asp_iter_record* hist = nullptr;
+    float* wbuf = nullptr;
+    float* T1 = nullptr;
+    int terms_cap = 0;
+    float* S1 = nullptr;
+    float* taps_dev = nullptr;
+    SmoothTaps taps{};
+    double* partials = nullptr;
+    double* sums = nullptr;
+    unsigned* bar = nullptr;
+    float* Tg = nullptr;
+    ArgRes* part = nullptr;
+    unsigned* ticket = nullptr;
+    unsigned long long* hist256 = nullptr;
+    double* dscalar = nullptr;
+    int g_max = 1, tpt = 1, grid_img = 1;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_unroll = 8;
+    int graph_state = 0;   // 0 untried, 1 usable, -1 unavailable (direct launches)
+    int broken = 0;
+    std::string err;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+asp_status fail(asp_ctx* c, asp_status s, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (s == ASP_ERR_CUDA || s == ASP_ERR_TIMEOUT) c->broken = 1;
+    }
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? ASP_ERR_OOM : ASP_ERR_CUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+#define CHECK_CTX()                                                                                \
+    do {                                                                                           \
+        if (!ctx) return ASP_ERR_INVALID_ARG;                                                      \
+        if (ctx->broken) return ASP_ERR_STATE;                                                     \
+        cudaSetDevice(ctx->dev);                                                                   \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(asp_ctx* ctx, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) return e;
+    ctx->allocs.push_back(q);
+    *p = reinterpret_cast<T*>(q);
+    return cudaSuccess;
+}
+
+LMConst lmconst_from(const asp_params& p, int max_iter_override = -1) {
+    LMConst l{};
+    l.lambda0 = p.lm_lambda0;
+    l.lambda_up = 10.0;
+    l.lambda_down = 10.0;
+    l.lambda_min = 1e-12;
+    l.lambda_max = 1e12;
+    l.rtol = p.lm_rtol;
+    l.xtol = p.lm_xtol;
+    l.max_iter = max_iter_override >= 0 ? max_iter_override : p.lm_max_iter;
+    const char* env = getenv("ASP_FIT_PX_PER_CTA");
+    l.px_per_cta = env ? atoi(env) : 0;
+    return l;
+}
+
+asp_status validate_params(const asp_params* p) {
+    if (!p) return ASP_ERR_INVALID_ARG;
+    if (!(p->gain > 0.f && p->gain <= 1.f)) return ASP_ERR_INVALID_ARG;
+    if (p->k_max < 1) return ASP_ERR_INVALID_ARG;
+    if (p->k_max > ASP_KMAX) return ASP_ERR_UNSUPPORTED;
+    if (p->lm_max_iter < 0 || p->n_scales < 1 || p->n_scales > MAX_SCALES) return ASP_ERR_INVALID_ARG;
+    if (!(p->lm_lambda0 > 0) || !(p->lm_rtol >= 0) || !(p->lm_xtol >= 0)) return ASP_ERR_INVALID_ARG;
+    if (p->init_mode < 0 || p->init_mode > 2) return ASP_ERR_INVALID_ARG;
+    if (p->retained_cap < 0 || p->retained_cap > RET_MAX) return ASP_ERR_UNSUPPORTED;
+    if (p->max_components < 0) return ASP_ERR_INVALID_ARG;
+    return ASP_OK;
+}
+
+asp_status read_state(asp_ctx* ctx, CycleState* h) {
+    CK(cudaMemcpyAsync(h, ctx->st, sizeof(CycleState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+// Field-wise host->device update of the control block.
+template <class T>
+asp_status put_field(asp_ctx* ctx, T* dev_field, const T& v) {
+    CK(cudaMemcpyAsync(dev_field, &v, sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+asp_status refresh_peak(asp_ctx* ctx) {
+    CK(launch_argmax(ctx->R, ctx->N, ctx->grid_img, ctx->part, ctx->ticket, &ctx->st->peak, &ctx->st->nonfinite,
+                     nullptr, ctx->stream));
+    return ASP_OK;
+}
+
+// One minor-cycle iteration as a fixed launch sequence (device-side gating).
+asp_status enqueue_iteration(asp_ctx* ctx) {
+    const int H = ctx->H, W = ctx->W;
+    CK(launch_cycle_begin(ctx->st, ctx->dp, H, W, ctx->stream));
+    CK(launch_smooth(ctx->R, H, W, ctx->taps, ctx->st, &ctx->st->skip_smooth, -1, ctx->S1, nullptr, ctx->grid_img,
+                     ctx->part, ctx->ticket, ctx->stream));
+    CK(launch_select(ctx->st, ctx->comps, ctx->dp, H, W, ctx->g_max, ctx->stream));
+    CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &ctx->st->fit, ctx->dp.lm, &ctx->st->fout, ctx->partials,
+                     ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
+    CK(launch_update(ctx->st, ctx->comps, ctx->hist, ctx->dp, H, W, ctx->wbuf, ctx->stream));
+    CK(launch_subtract(ctx->B, ctx->R, H, W, ctx->st, &ctx->st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img,
+                       ctx->part, ctx->ticket, ctx->stream));
+    return ASP_OK;
+}
+
+asp_status build_graph(asp_ctx* ctx) {
+    if (ctx->graph_state != 0) return ASP_OK;
+    if (getenv("ASP_NO_GRAPH")) { ctx->graph_state = -1; return ASP_OK; }
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cs;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    asp_status s = ASP_OK;
+    if (ok) {
+        for (int i = 0; i < ctx->graph_unroll && s == ASP_OK; ++i) s = enqueue_iteration(ctx);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        ok = (s == ASP_OK) && e == cudaSuccess && g != nullptr;
+    }
+    ctx->stream = saved;
+    ctx->broken = 0;
+    ctx->err.clear();
+    if (ok && cudaGraphInstantiate(&ctx->gexec, g, 0) == cudaSuccess) {
+        ctx->graph_state = 1;
+    } else {
+        ctx->graph_state = -1;
+        cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return ASP_OK;
+}
+
+void host_member_box(double x, double y, double w, long long* b) { member_box(x, y, w, b); }
+
+}  // namespace
+
+// =====================================================================
+extern "C" {
+
+const char* asp_status_string(asp_status s) {
+    switch (s) {
+        case ASP_OK: return "ok";
+        case ASP_ERR_INVALID_ARG: return "invalid argument";
+        case ASP_ERR_CUDA: return "CUDA error";
+        case ASP_ERR_OOM: return "out of device memory";
+        case ASP_ERR_NAN: return "non-finite value";
+        case ASP_ERR_TIMEOUT: return "device wait timed out";
+        case ASP_ERR_NOT_CONVERGED: return "not converged";
+        case ASP_ERR_STATE: return "context unusable after an earlier error";
+        case ASP_ERR_UNSUPPORTED: return "size beyond a compiled-in limit";
+        case ASP_ERR_CAPACITY: return "component list full";
+    }
+    return "unknown status";
+}
+
+void asp_default_params(asp_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->gain = 0.35f;
+    p->k_max = 5;
+    p->lm_max_iter = 50;
+    p->lm_lambda0 = 1e-3;
+    p->lm_rtol = 1e-7;
+    p->lm_xtol = 1e-7;
+    p->noise_sigma = 0.f;
+    p->stop_ksigma = 3.f;
+    p->n_scales = 6;
+    p->area_frac = 0.05f;
+    p->init_mode = ASP_INIT_AUTO;
+    p->tau = 1e-3;
+    p->retained_cap = 0;
+    p->max_components = 0;
+}
+
+const char* asp_last_error(const asp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static asp_status init_common(const asp_params* pin, int H, int W, const float* dirty, const float* psf, int on_host,
+                              void* stream, asp_ctx** out) {
+    if (!out) return ASP_ERR_INVALID_ARG;
+    *out = nullptr;
+    asp_status vs = validate_params(pin);
+    if (vs != ASP_OK) return vs;
+    if (H < 1 || W < 1 || !dirty || !psf) return ASP_ERR_INVALID_ARG;
+    if ((long long)H * W > (1LL << 31) / 4 || H > (1 << 20) || W > (1 << 20)) return ASP_ERR_UNSUPPORTED;
+    asp_ctx* ctx = new asp_ctx();
+    ctx->p = *pin;
+    if (ctx->p.retained_cap == 0) ctx->p.retained_cap = std::min(RET_MAX, 8 * ctx->p.k_max);
+    if (ctx->p.max_components == 0) ctx->p.max_components = 65536;
+    ctx->H = H;
+    ctx->W = W;
+    ctx->N = (long long)H * W;
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    asp_status s = ASP_OK;
+    auto bail = [&](asp_status st) { asp_destroy(ctx); return st; };
+    if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(ASP_ERR_CUDA);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->dev) != cudaSuccess) return bail(ASP_ERR_CUDA);
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->grid_img = ctx->num_sms * 4;
+    ctx->tpt = fit_tpt_for(ctx->p.k_max);
+    int bps = 0;
+    if (fit_configure(ctx->tpt, &bps) != cudaSuccess || bps < 1) return bail(ASP_ERR_CUDA);
+    ctx->g_max = ctx->num_sms * bps;
+
+    // device parameters
+    ctx->dp.gain = ctx->p.gain;
+    ctx->dp.area_frac = ctx->p.area_frac;
+    ctx->dp.k_max = ctx->p.k_max;
+    ctx->dp.init_mode = ctx->p.init_mode;
+    ctx->dp.retained_cap = ctx->p.retained_cap;
+    ctx->dp.n_scales = ctx->p.n_scales;
+    ctx->dp.tau = ctx->p.tau;
+    ctx->dp.lm = lmconst_from(ctx->p);
+
+    const long long N = ctx->N;
+    ctx->terms_cap = std::max(2 * ctx->p.k_max - 1, 1);
+    const int cap = ctx->p.max_components;
+#define AL(ptr, n) if (dalloc(ctx, &(ptr), (size_t)(n)) != cudaSuccess) return bail(ASP_ERR_OOM)
+    AL(ctx->R, N);
+    AL(ctx->B, 4 * N);
+    AL(ctx->st, 1);
+    AL(ctx->comps, cap);
+    AL(ctx->comp_stage, MAX_TERMS);
+    AL(ctx->hist, cap);
+    AL(ctx->wbuf, (size_t)MAX_TERMS * (W + H));
+    AL(ctx->T1, (size_t)ctx->terms_cap * (2 * H - 1) * W);
+    AL(ctx->partials, (size_t)ctx->g_max * NACC_MAX);
+    AL(ctx->sums, 2 * NACC_MAX);
+    AL(ctx->bar, 1);
+    AL(ctx->Tg, 4 * N);   // window targets beyond shared memory (image or PSF windows)
+    AL(ctx->part, std::max(ctx->grid_img, ctx->g_max));
+    AL(ctx->ticket, 1);
+    AL(ctx->hist256, 260);
+    AL(ctx->dscalar, 4);
+#undef AL
+    cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(ctx->R, dirty, N * sizeof(float), kind, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->B, psf, 4 * N * sizeof(float), kind, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->st, 0, sizeof(CycleState), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream) != cudaSuccess)
+        return bail(ASP_ERR_CUDA);
+
+    // ---- beam: LM fit of one Gaussian to the PSF main lobe (Sect. 3)
+    if (launch_beam_init(&ctx->st->fit, ctx->B, H, W, ctx->g_max, ctx->stream) != cudaSuccess)
+        return bail(ASP_ERR_CUDA);
+    if (cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream) != cudaSuccess) return bail(ASP_ERR_CUDA);
+    if (launch_lm_fit(ctx->tpt, ctx->g_max, ctx->B, 2 * W, &ctx->st->fit, ctx->dp.lm, &ctx->st->fout, ctx->partials,
+                      ctx->sums, ctx->bar, ctx->Tg, ctx->stream) != cudaSuccess)
+        return bail(ASP_ERR_CUDA);
+    FitOut fo;
+    if (cudaMemcpyAsync(&fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return bail(ASP_ERR_CUDA);
+    if (fo.error) { ctx->err = "beam fit: device wait timed out"; return bail(ASP_ERR_TIMEOUT); }
+    ctx->alpha_b = fo.theta[0];
+    ctx->xb = fo.theta[1];
+    ctx->yb = fo.theta[2];
+    ctx->omega_b = fo.theta[3];
+    if (!(ctx->omega_b > 0) || !std::isfinite(ctx->alpha_b) || ctx->alpha_b == 0.0) return bail(ASP_ERR_NAN);
+
+    // ---- smoothing scales s_j = omega_b 2^j, kept while s_j <= min(H, W) / 8
+    {
+        std::vector<float> taps;
+        SmoothTaps& t = ctx->taps;
+        t.n = 0;
+        for (int j = 0; j < ctx->p.n_scales; ++j) {
+            double s_j = ctx->omega_b * std::ldexp(1.0, j);
+            if (j > 0 && s_j > std::min(H, W) / 8.0) continue;
+            int m = (int)std::ceil(4.0 * s_j);
+            std::vector<double> e(2 * m + 1);
+            double ss = 0;
+            for (int u = -m; u <= m; ++u) { e[u + m] = std::exp(-(double)u * u / (2.0 * s_j * s_j)); ss += e[u + m] * e[u + m]; }
+            double inv = 1.0 / std::sqrt(ss);
+            t.off[t.n] = (int)taps.size();
+            t.m[t.n] = m;
+            t.scale[t.n] = s_j;
+            for (double v : e) taps.push_back((float)(v * inv));
+            t.n++;
+        }
+        if (dalloc(ctx, &ctx->taps_dev, taps.size()) != cudaSuccess) return bail(ASP_ERR_OOM);
+        if (dalloc(ctx, &ctx->S1, (size_t)t.n * N) != cudaSuccess) return bail(ASP_ERR_OOM);
+        if (cudaMemcpy(ctx->taps_dev, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(ASP_ERR_CUDA);
+        t.k = ctx->taps_dev;
+    }
+
+    // ---- noise level: given, or 1.4826 x MAD of the dirty image
+    if (ctx->p.noise_sigma > 0.f) {
+        ctx->noise = ctx->p.noise_sigma;
+    } else {
+        double med = 0, mad = 0;
+        if (launch_radix_median(ctx->R, N, 0, 0.0, ctx->hist256, ctx->dscalar, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&med, ctx->dscalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return bail(ASP_ERR_CUDA);
+        if (launch_radix_median(ctx->R, N, 1, med, ctx->hist256, ctx->dscalar, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&mad, ctx->dscalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            return bail(ASP_ERR_CUDA);
+        ctx->noise = 1.4826 * mad;
+    }
+
+    // ---- control block
+    CycleState h;
+    memset(&h, 0, sizeof(h));
+    h.cap_comp = cap;
+    h.thr = (double)ctx->p.stop_ksigma * ctx->noise;
+    h.alpha_b = ctx->alpha_b;
+    h.omega_b = ctx->omega_b;
+    h.t_stop = 0;
+    if (cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return bail(ASP_ERR_CUDA);
+    s = refresh_peak(ctx);
+    if (s != ASP_OK) return bail(s);
+    CycleState chk;
+    s = read_state(ctx, &chk);
+    if (s != ASP_OK) return bail(s);
+    if (chk.nonfinite) { ctx->err = "non-finite value in the dirty image"; return bail(ASP_ERR_NAN); }
+    *out = ctx;
+    return ASP_OK;
+}
+
+asp_status asp_init(const asp_params* p, int H, int W, const float* dirty_dev, const float* psf_dev, void* stream,
+                    asp_ctx** out) {
+    return init_common(p, H, W, dirty_dev, psf_dev, 0, stream, out);
+}
+
+asp_status asp_init_host(const asp_params* p, int H, int W, const float* dirty_host, const float* psf_host,
+                         void* stream, asp_ctx** out) {
+    return init_common(p, H, W, dirty_host, psf_host, 1, stream, out);
+}
+
+asp_status asp_destroy(asp_ctx* ctx) {
+    if (!ctx) return ASP_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->dev);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (void* q : ctx->allocs) cudaFree(q);
+    delete ctx;
+    return ASP_OK;
+}
+
+asp_status asp_get_beam(asp_ctx* ctx, double* alpha_b, double* omega_b, double* x_b, double* y_b) {
+    CHECK_CTX();
+    if (alpha_b) *alpha_b = ctx->alpha_b;
+    if (omega_b) *omega_b = ctx->omega_b;
+    if (x_b) *x_b = ctx->xb;
+    if (y_b) *y_b = ctx->yb;
+    return ASP_OK;
+}
+
+asp_status asp_find_peak(asp_ctx* ctx, int mode, asp_peak* out) {
+    CHECK_CTX();
+    if (!out || (mode != ASP_PEAK_SIMPLE && mode != ASP_PEAK_SMOOTH)) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    if (mode == ASP_PEAK_SIMPLE) {
+        asp_status s = refresh_peak(ctx);
+        if (s != ASP_OK) return s;
+        s = read_state(ctx, &h);
+        if (s != ASP_OK) return s;
+        out->index = h.peak.idx;
+        out->x = (int32_t)(h.peak.idx % ctx->W);
+        out->y = (int32_t)(h.peak.idx / ctx->W);
+        out->value = h.peak.val;
+        out->scale = 0.f;
+        out->mode = ASP_PEAK_SIMPLE;
+        out->scale_index = -1;
+        out->a0 = h.peak.val;
+        out->x0 = out->x;
+        out->y0 = out->y;
+        out->w0 = ctx->omega_b;
+        return ASP_OK;
+    }
+    CK(launch_smooth(ctx->R, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, -1, ctx->S1, nullptr, ctx->grid_img,
+                     ctx->part, ctx->ticket, ctx->stream));
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    out->index = h.speak.idx;
+    out->x = (int32_t)(h.speak.idx % ctx->W);
+    out->y = (int32_t)(h.speak.idx / ctx->W);
+    out->value = h.speak.val;
+    out->scale = (float)ctx->taps.scale[h.speak.j];
+    out->mode = ASP_PEAK_SMOOTH;
+    out->scale_index = h.speak.j;
+    out->a0 = h.init[0];
+    out->x0 = h.init[1];
+    out->y0 = h.init[2];
+    out->w0 = h.init[3];
+    return ASP_OK;
+}
+
+static asp_status run_fit(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, int x0, int x1, int y0, int y1,
+                          int max_iter, FitOut* fo) {
+    FitDesc d;
+    memset(&d, 0, sizeof(d));
+    d.K = n;
+    d.n_old = n_old;
+    d.wx0 = x0;
+    d.wy0 = y0;
+    d.ww = x1 - x0 + 1;
+    d.wh = y1 - y0 + 1;
+    d.omega_min = 0.25 * ctx->omega_b;
+    d.bx0 = x0; d.bx1 = x1; d.by0 = y0; d.by1 = y1;
+    for (int k = 0; k < n; ++k) {
+        d.theta0[4 * k] = init[k].amp;
+        d.theta0[4 * k + 1] = init[k].x;
+        d.theta0[4 * k + 2] = init[k].y;
+        d.theta0[4 * k + 3] = init[k].width;
+    }
+    LMConst lmc = ctx->dp.lm;
+    if (max_iter >= 0) lmc.max_iter = max_iter;
+    int smem_ok = 1;
+    d.grid = fit_grid((long long)d.ww * d.wh, n, lmc.px_per_cta, ctx->g_max, &smem_ok);
+    d.smem_ok = smem_ok;
+    d.active = 1;
+    CK(cudaMemcpyAsync(&ctx->st->fit, &d, sizeof(d), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream));
+    CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, ctx->W, &ctx->st->fit, lmc, &ctx->st->fout, ctx->partials,
+                     ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
+    CK(cudaMemcpyAsync(fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (fo->error) return fail(ctx, ASP_ERR_TIMEOUT, "fit: grid barrier timed out");
+    return ASP_OK;
+}
+
+static bool gauss_ok(const asp_gauss& g) {
+    return std::isfinite(g.amp) && std::isfinite(g.x) && std::isfinite(g.y) && std::isfinite(g.width) && g.width > 0;
+}
+
+asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, asp_gauss* out,
+                              asp_fit_info* info) {
+    CHECK_CTX();
+    if (!init || !out || n < 1 || n > ctx->p.k_max || n_old < 0 || n_old > n) return ASP_ERR_INVALID_ARG;
+    long long wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!gauss_ok(init[k])) return ASP_ERR_INVALID_ARG;
+        long long b[4];
+        host_member_box(init[k].x, init[k].y, init[k].width, b);
+        if (k == 0) { wx0 = b[0]; wx1 = b[1]; wy0 = b[2]; wy1 = b[3]; }
+        wx0 = std::min(wx0, b[0]); wx1 = std::max(wx1, b[1]);
+        wy0 = std::min(wy0, b[2]); wy1 = std::max(wy1, b[3]);
+    }
+    wx0 = std::max(wx0, 0LL); wy0 = std::max(wy0, 0LL);
+    wx1 = std::min(wx1, (long long)ctx->W - 1); wy1 = std::min(wy1, (long long)ctx->H - 1);
+    if (wx0 > wx1 || wy0 > wy1) return ASP_ERR_INVALID_ARG;
+    FitOut fo;
+    asp_status s = run_fit(ctx, init, n, n_old, (int)wx0, (int)wx1, (int)wy0, (int)wy1, -1, &fo);
+    if (s != ASP_OK) return s;
+    for (int k = 0; k < n; ++k) {
+        out[k].amp = fo.theta[4 * k];
+        out[k].x = fo.theta[4 * k + 1];
+        out[k].y = fo.theta[4 * k + 2];
+        out[k].width = fo.theta[4 * k + 3];
+    }
+    if (info) {
+        info->iters = fo.iters;
+        info->passes = fo.passes;
+        info->status = fo.status;
+        info->k = n;
+        info->x0 = (int)wx0; info->x1 = (int)wx1; info->y0 = (int)wy0; info->y1 = (int)wy1;
+        info->chi2_init = fo.chi2_init;
+        info->chi2_final = fo.chi2;
+        info->lambda = fo.lambda;
+        info->pixel_evals = fo.pixel_evals;
+    }
+    return ASP_OK;
+}
+
+asp_status asp_eval_normal_equations(asp_ctx* ctx, const asp_gauss* theta, int n, int n_old, int x0, int x1, int y0,
+                                     int y1, double* A_host, double* g_host, double* chi2_host) {
+    CHECK_CTX();
+    if (!theta || n < 1 || n > ASP_KMAX || n > ctx->p.k_max || n_old < 0 || n_old > n) return ASP_ERR_INVALID_ARG;
+    x0 = std::max(x0, 0); y0 = std::max(y0, 0);
+    x1 = std::min(x1, ctx->W - 1); y1 = std::min(y1, ctx->H - 1);
+    if (x0 > x1 || y0 > y1) return ASP_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k)
+        if (!gauss_ok(theta[k])) return ASP_ERR_INVALID_ARG;
+    FitOut fo;
+    asp_status s = run_fit(ctx, theta, n, n_old, x0, x1, y0, y1, 0, &fo);
+    if (s != ASP_OK) return s;
+    // after the single pass the sums live in buffer 1
+    const int P = 4 * n, NAp = ((P + 1) + 3) & ~3, nb = NAp / 4;
+    std::vector<double> acc((size_t)fit_tiles(n) * 16);
+    CK(cudaMemcpy(acc.data(), ctx->sums + NACC_MAX, acc.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    auto at = [&](int i, int j) {
+        if (i > j) std::swap(i, j);
+        int bi = i >> 2, bj = j >> 2;
+        int t = bi * nb - bi * (bi - 1) / 2 + (bj - bi);
+        return acc[(size_t)t * 16 + (i & 3) * 4 + (j & 3)];
+    };
+    for (int i = 0; i < P; ++i) {
+        if (A_host)
+            for (int j = 0; j < P; ++j) A_host[(size_t)i * P + j] = at(i, j);
+        if (g_host) g_host[i] = at(i, P);
+    }
+    if (chi2_host) *chi2_host = at(P, P);
+    return ASP_OK;
+}
+
+asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float gain) {
+    CHECK_CTX();
+    if (!comps || n < 0 || n > ctx->terms_cap || !std::isfinite(gain)) return ASP_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(comps[i].flux) || !std::isfinite(comps[i].x) || !std::isfinite(comps[i].y) ||
+            !std::isfinite(comps[i].width) || comps[i].width < 0)
+            return ASP_ERR_INVALID_ARG;
+    if (n == 0) return ASP_OK;
+    CK(cudaMemcpyAsync(ctx->comp_stage, comps, n * sizeof(asp_component), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_terms_from_components(ctx->st, ctx->comp_stage, n, gain, ctx->H, ctx->W, ctx->wbuf, ctx->stream));
+    CK(launch_subtract(ctx->B, ctx->R, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,
+                       ctx->ticket, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
+    CHECK_CTX();
+    if (n_iter < 0) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    const int t0 = h.t;
+    struct { int t_stop, stopped, stop_reason; } ctl = {t0 + n_iter, 0, 0};
+    CK(cudaMemcpyAsync(&ctx->st->t_stop, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, ctx->stream));
+    s = build_graph(ctx);
+    if (s != ASP_OK) return s;
+    if (n_iter > 0) {
+        if (ctx->graph_state == 1) {
+            const int reps = (n_iter + ctx->graph_unroll - 1) / ctx->graph_unroll;
+            for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        } else {
+            for (int i = 0; i < n_iter; ++i) {
+                s = enqueue_iteration(ctx);
+                if (s != ASP_OK) return s;
+            }
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    if (h.error == ASP_ERR_TIMEOUT) return fail(ctx, ASP_ERR_TIMEOUT, "fit: grid barrier timed out");
+    if (h.error == ASP_ERR_NAN || h.nonfinite) return fail(ctx, ASP_ERR_NAN, "non-finite value in the residual");
+    if (out) {
+        out->iterations = h.t;
+        out->components = h.n_comp;
+        out->pixel_evals = h.pixel_evals;
+        out->lm_iters = h.lm_iters;
+        out->lm_passes = h.lm_passes;
+        out->peak_abs = std::fabs((double)h.peak.val);
+        out->stop_reason = h.stop_reason;
+        out->reserved = 0;
+    }
+    if (h.stop_reason == ASP_STOP_CAPACITY) return fail(ctx, ASP_ERR_CAPACITY, "component list full");
+    return ASP_OK;
+}
+
+asp_status asp_get_stats(asp_ctx* ctx, asp_cycle_stats* out) {
+    CHECK_CTX();
+    if (!out) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    out->iterations = h.t;
+    out->components = h.n_comp;
+    out->pixel_evals = h.pixel_evals;
+    out->lm_iters = h.lm_iters;
+    out->lm_passes = h.lm_passes;
+    out->peak_abs = std::fabs((double)h.peak.val);
+    out->stop_reason = h.stop_reason;
+    out->reserved = 0;
+    return ASP_OK;
+}
+
+asp_status asp_num_scales(asp_ctx* ctx, int* n, double* scales_host) {
+    CHECK_CTX();
+    if (!n) return ASP_ERR_INVALID_ARG;
+    *n = ctx->taps.n;
+    if (scales_host)
+        for (int j = 0; j < ctx->taps.n; ++j) scales_host[j] = ctx->taps.scale[j];
+    return ASP_OK;
+}
+
+asp_status asp_smooth(asp_ctx* ctx, int scale_index, float* out_dev) {
+    CHECK_CTX();
+    if (scale_index < 0 || scale_index >= ctx->taps.n || !out_dev) return ASP_ERR_INVALID_ARG;
+    CK(launch_smooth(ctx->R, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, scale_index, ctx->S1, out_dev, ctx->grid_img,
+                     ctx->part, ctx->ticket, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+asp_status asp_residual_ptr(asp_ctx* ctx, float** residual_dev) {
+    CHECK_CTX();
+    if (!residual_dev) return ASP_ERR_INVALID_ARG;
+    *residual_dev = ctx->R;
+    return ASP_OK;
+}
+
+asp_status asp_copy_residual(asp_ctx* ctx, float* dst, int dst_on_host) {
+    CHECK_CTX();
+    if (!dst) return ASP_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(dst, ctx->R, ctx->N * sizeof(float),
+                       dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+asp_status asp_set_residual(asp_ctx* ctx, const float* src, int src_on_host) {
+    CHECK_CTX();
+    if (!src) return ASP_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(ctx->R, src, ctx->N * sizeof(float),
+                       src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    return asp_refresh_peak(ctx);
+}
+
+asp_status asp_refresh_peak(asp_ctx* ctx) {
+    CHECK_CTX();
+    asp_status s = refresh_peak(ctx);
+    if (s != ASP_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+asp_status asp_get_components(asp_ctx* ctx, asp_component* out_host, int cap, int* count) {
+    CHECK_CTX();
+    if (!count || cap < 0 || (cap > 0 && !out_host)) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    *count = h.n_comp;
+    const int n = std::min(cap, h.n_comp);
+    if (n > 0) CK(cudaMemcpy(out_host, ctx->comps, n * sizeof(asp_component), cudaMemcpyDeviceToHost));
+    return ASP_OK;
+}
+
+asp_status asp_get_history(asp_ctx* ctx, asp_iter_record* out_host, int cap, int* count) {
+    CHECK_CTX();
+    if (!count || cap < 0 || (cap > 0 && !out_host)) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    const int total = std::min(h.t, ctx->p.max_components);
+    *count = total;
+    const int n = std::min(cap, total);
+    if (n > 0) CK(cudaMemcpy(out_host, ctx->hist, n * sizeof(asp_iter_record), cudaMemcpyDeviceToHost));
+    return ASP_OK;
+}
+
+asp_status asp_get_state(asp_ctx* ctx, asp_component* comps, int comp_cap, int* n_comp, int* retained, int ret_cap,
+                         int* n_ret, int64_t* t, double* last_wi, double* last_w0) {
+    CHECK_CTX();
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    if (n_comp) *n_comp = h.n_comp;
+    if (comps && comp_cap > 0) {
+        const int n = std::min(comp_cap, h.n_comp);
+        if (n > 0) CK(cudaMemcpy(comps, ctx->comps, n * sizeof(asp_component), cudaMemcpyDeviceToHost));
+    }
+    if (n_ret) *n_ret = h.n_ret;
+    if (retained && ret_cap > 0)
+        for (int i = 0; i < std::min(ret_cap, h.n_ret); ++i) retained[i] = h.ret[i];
+    if (t) *t = h.t;
+    if (last_wi) *last_wi = h.last_wi;
+    if (last_w0) *last_w0 = h.last_w0;
+    return ASP_OK;
+}
+
+asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp, const int* retained, int n_ret,
+                         int64_t t, double last_wi, double last_w0) {
+    CHECK_CTX();
+    if (n_comp < 0 || n_comp > ctx->p.max_components || (n_comp > 0 && !comps)) return ASP_ERR_INVALID_ARG;
+    if (n_ret < 0 || n_ret > ctx->p.retained_cap || (n_ret > 0 && !retained) || t < 0 || t > (1LL << 30))
+        return ASP_ERR_INVALID_ARG;
+    for (int i = 0; i < n_ret; ++i)
+        if (retained[i] < 0 || retained[i] >= n_comp) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    if (n_comp > 0) CK(cudaMemcpy(ctx->comps, comps, n_comp * sizeof(asp_component), cudaMemcpyHostToDevice));
+    h.n_comp = n_comp;
+    h.n_ret = n_ret;
+    for (int i = 0; i < n_ret; ++i) h.ret[i] = retained[i];
+    h.t = (int)t;
+    h.t_stop = (int)t;
+    h.last_wi = last_wi;
+    h.last_w0 = last_w0;
+    h.stopped = 0;
+    h.stop_reason = 0;
+    h.pixel_evals = h.lm_iters = h.lm_passes = 0;
+    CK(cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    return asp_refresh_peak(ctx);
+}
+
+static const uint32_t STATE_MAGIC = 0x41535031u;   // "ASP1"
+
+asp_status asp_save_state(asp_ctx* ctx, const char* path) {
+    CHECK_CTX();
+    if (!path) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    std::vector<float> R(ctx->N);
+    std::vector<asp_component> comps(h.n_comp);
+    CK(cudaMemcpy(R.data(), ctx->R, ctx->N * sizeof(float), cudaMemcpyDeviceToHost));
+    if (h.n_comp) CK(cudaMemcpy(comps.data(), ctx->comps, h.n_comp * sizeof(asp_component), cudaMemcpyDeviceToHost));
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(ctx, ASP_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    int32_t hdr[6] = {(int32_t)STATE_MAGIC, ctx->H, ctx->W, h.n_comp, h.n_ret, h.t};
+    bool ok = fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    double dd[6] = {h.last_wi, h.last_w0, ctx->alpha_b, ctx->omega_b, 0.0, 0.0};
+    ok = ok && fwrite(dd, sizeof(dd), 1, f) == 1;
+    ok = ok && fwrite(R.data(), sizeof(float), R.size(), f) == R.size();
+    if (h.n_comp) ok = ok && fwrite(comps.data(), sizeof(asp_component), comps.size(), f) == comps.size();
+    if (h.n_ret) ok = ok && fwrite(h.ret, sizeof(int), h.n_ret, f) == (size_t)h.n_ret;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? ASP_OK : fail(ctx, ASP_ERR_INVALID_ARG, "short write");
+}
+
+asp_status asp_load_state(asp_ctx* ctx, const char* path) {
+    CHECK_CTX();
+    if (!path) return ASP_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(ctx, ASP_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    int32_t hdr[6];
+    double dd[6];
+    bool ok = fread(hdr, sizeof(hdr), 1, f) == 1 && fread(dd, sizeof(dd), 1, f) == 1;
+    if (!ok || hdr[0] != (int32_t)STATE_MAGIC || hdr[1] != ctx->H || hdr[2] != ctx->W || hdr[3] < 0 ||
+        hdr[3] > ctx->p.max_components || hdr[4] < 0 || hdr[4] > RET_MAX) {
+        fclose(f);
+        return fail(ctx, ASP_ERR_INVALID_ARG, "state file does not match this context");
+    }
+    std::vector<float> R(ctx->N);
+    std::vector<asp_component> comps(hdr[3]);
+    std::vector<int> ret(hdr[4]);
+    ok = fread(R.data(), sizeof(float), R.size(), f) == R.size();
+    if (hdr[3]) ok = ok && fread(comps.data(), sizeof(asp_component), comps.size(), f) == comps.size();
+    if (hdr[4]) ok = ok && fread(ret.data(), sizeof(int), ret.size(), f) == ret.size();
+    fclose(f);
+    if (!ok) return fail(ctx, ASP_ERR_INVALID_ARG, "short read");
+    CK(cudaMemcpy(ctx->R, R.data(), ctx->N * sizeof(float), cudaMemcpyHostToDevice));
+    return asp_set_state(ctx, comps.data(), hdr[3], ret.data(), std::min(hdr[4], ctx->p.retained_cap), hdr[5], dd[0],
+                         dd[1]);
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+// Device-side control of one minor-cycle iteration (Sect. 2 steps 1-4 with
+// the Sect. 3 changes), so a whole iteration runs without a host round trip:
+//   k_cycle_begin  stopping tests (iteration cap, max|R| below the noise
+//                  threshold) and the initial-value switch (simple method iff
+//                  the last optimal component's area is < area_frac of the
+//                  last initial guess's area, Sect. 3);
+//   k_select       active set (new member + overlapping retained members) and
+//                  the joint fit window, written as a FitDesc;
+//   k_update       Eqs. 7-8 deconvolution, loop gain on the new component,
+//                  component list / retained list updates, and the separable
+//                  subtraction terms dC = gain c_new + sum_old (c'_k - c_k);
+//   k_build_weights the sampled, flux-normalised axis weights of each term.
+// These are scalar control kernels: one thread (or one block per term).
+#include "asp_dev.cuh"
+#include "asp_internal.h"
+
+namespace aspd {
+
+namespace {
+
+constexpr double TWO_PI = 6.283185307179586477;
+
+// Single-Gaussian image of a component: (alpha_b omega_b^2 F / w_ic^2, x, y,
+// w_ic) with w_ic^2 = w_i^2 + omega_b^2 (Eqs. 7-8 inverted).
+__device__ void gauss_of(const asp_component& c, double ab, double wb, double* g) {
+    double wic2 = c.width * c.width + wb * wb;
+    g[0] = ab * wb * wb * c.flux / wic2;
+    g[1] = c.x;
+    g[2] = c.y;
+    g[3] = sqrt(wic2);
+}
+
+// Eqs. 7-8 through the flux F = a_ic w_ic^2 / (alpha_b omega_b^2); a point
+// when w_ic^2 <= omega_b^2 (1 + 1e-3).
+__device__ asp_component deconvolve(double a, double x, double y, double w, double ab, double wb, double gain) {
+    asp_component c;
+    double F = a * w * w / (ab * wb * wb);
+    c.x = x;
+    c.y = y;
+    c.reserved = 0;
+    if (w * w > wb * wb * (1.0 + 1e-3)) {
+        double wi = sqrt(w * w - wb * wb);
+        c.flux = gain * F;
+        c.amp = gain * F / (TWO_PI * wi * wi);
+        c.width = wi;
+        c.is_point = 0;
+    } else {
+        c.flux = gain * F;
+        c.amp = gain * F;
+        c.width = 0.0;
+        c.is_point = 1;
+    }
+    return c;
+}
+
+// Term descriptor of component c scaled by s; returns false if its support
+// misses the image.
+__device__ bool make_term(const asp_component& c, double s, int H, int W, int slot, TermDesc& td) {
+    long long ux0, ux1, uy0, uy1;
+    if (c.is_point || c.width < 0.5) {
+        td.bilinear = 1;
+        ux0 = (long long)floor(c.x); ux1 = ux0 + 1;
+        uy0 = (long long)floor(c.y); uy1 = uy0 + 1;
+    } else {
+        td.bilinear = 0;
+        double h = ceil(5.0 * c.width) + 1.0;
+        ux0 = (long long)ceil(c.x - h); ux1 = (long long)floor(c.x + h);
+        uy0 = (long long)ceil(c.y - h); uy1 = (long long)floor(c.y + h);
+    }
+    long long qx0 = ux0 < 0 ? 0 : ux0, qx1 = ux1 > W - 1 ? W - 1 : ux1;
+    long long qy0 = uy0 < 0 ? 0 : uy0, qy1 = uy1 > H - 1 ? H - 1 : uy1;
+    if (qx0 > qx1 || qy0 > qy1) return false;
+    td.qx0 = (int)qx0; td.nx = (int)(qx1 - qx0 + 1);
+    td.qy0 = (int)qy0; td.ny = (int)(qy1 - qy0 + 1);
+    td.ux0 = (int)(ux0 < -(1LL << 30) ? -(1LL << 30) : ux0);
+    td.ux1 = (int)(ux1 > (1LL << 30) ? (1LL << 30) : ux1);
+    td.uy0 = (int)(uy0 < -(1LL << 30) ? -(1LL << 30) : uy0);
+    td.uy1 = (int)(uy1 > (1LL << 30) ? (1LL << 30) : uy1);
+    td.scale = (float)s;
+    td.cx = c.x; td.cy = c.y; td.w = c.width;
+    td.woff_x = slot * (W + H);
+    td.woff_y = slot * (W + H) + W;
+    td.r0 = H - td.qy0 - td.ny + 1;
+    td.pad = 0;
+    return true;
+}
+
+__device__ void finish_terms(CycleState* st, int H, int W) {
+    long long off = 0;
+    for (int t = 0; t < st->n_terms; ++t) {
+        st->terms[t].t1off = off;
+        off += (long long)(H + st->terms[t].ny - 1) * W;
+    }
+}
+
+}  // namespace
+
+__global__ void k_cycle_begin(CycleState* st, Params p, int H, int W) {
+    if (threadIdx.x != 0) return;
+    st->fit.active = 0;
+    st->skip_smooth = 1;
+    if (st->stopped) return;
+    if (st->nonfinite) { st->stopped = 1; st->error = ASP_ERR_NAN; return; }
+    if (st->t >= st->t_stop) { st->stopped = 1; st->stop_reason = ASP_STOP_ITER; return; }
+    if (fabs((double)st->peak.val) < st->thr) { st->stopped = 1; st->stop_reason = ASP_STOP_NOISE; return; }
+    if (st->n_comp >= st->cap_comp) { st->stopped = 1; st->stop_reason = ASP_STOP_CAPACITY; return; }
+    int mode;
+    if (p.init_mode == ASP_INIT_SIMPLE) mode = ASP_PEAK_SIMPLE;
+    else if (p.init_mode == ASP_INIT_SMOOTH) mode = ASP_PEAK_SMOOTH;
+    else mode = (st->t > 0 && st->last_wi * st->last_wi < (double)p.area_frac * st->last_w0 * st->last_w0)
+                    ? ASP_PEAK_SIMPLE : ASP_PEAK_SMOOTH;
+    st->mode = mode;
+    st->skip_smooth = mode != ASP_PEAK_SMOOTH;
+    if (mode == ASP_PEAK_SIMPLE) {
+        const long long idx = st->peak.idx;
+        st->init[0] = st->peak.val;
+        st->init[1] = (double)(idx % W);
+        st->init[2] = (double)(idx / W);
+        st->init[3] = st->omega_b;
+        st->init_scale = -1;
+        st->init_value = st->peak.val;
+        st->init_s = 0.f;
+    }
+}
+
+__global__ void k_select(CycleState* st, const asp_component* __restrict__ comps, Params p, int H, int W,
+                         int g_max) {
+    if (threadIdx.x != 0) return;
+    if (st->stopped) return;
+    FitDesc& f = st->fit;
+    const double ab = st->alpha_b, wb = st->omega_b;
+    long long nb[4];
+    member_box(st->init[1], st->init[2], st->init[3], nb);
+    long long wx0 = nb[0], wx1 = nb[1], wy0 = nb[2], wy1 = nb[3];
+    for (int i = 0; i < 4; ++i) f.theta0[i] = st->init[i];
+    st->members[0] = -1;
+    int K = 1;
+    for (int r = 0; r < st->n_ret && K < p.k_max; ++r) {
+        const int k = st->ret[r];
+        double g[4];
+        gauss_of(comps[k], ab, wb, g);
+        long long b[4];
+        member_box(g[1], g[2], g[3], b);
+        if (b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3]) {
+            for (int i = 0; i < 4; ++i) f.theta0[4 * K + i] = g[i];
+            st->members[K] = k;
+            wx0 = min(wx0, b[0]); wx1 = max(wx1, b[1]);
+            wy0 = min(wy0, b[2]); wy1 = max(wy1, b[3]);
+            ++K;
+        }
+    }
+    wx0 = max(wx0, 0LL); wy0 = max(wy0, 0LL);
+    wx1 = min(wx1, (long long)W - 1); wy1 = min(wy1, (long long)H - 1);
+    f.K = K;
+    f.n_old = K - 1;
+    f.wx0 = (int)wx0; f.wy0 = (int)wy0;
+    f.ww = (int)(wx1 - wx0 + 1); f.wh = (int)(wy1 - wy0 + 1);
+    f.use_mask = 0;
+    f.mcx = f.mcy = f.mr2 = 0.0;
+    f.omega_min = 0.25 * wb;
+    f.bx0 = (double)wx0; f.bx1 = (double)wx1; f.by0 = (double)wy0; f.by1 = (double)wy1;
+    int smem_ok = 1;
+    f.grid = fit_grid((long long)f.ww * f.wh, K, p.lm.px_per_cta, g_max, &smem_ok);
+    f.smem_ok = smem_ok;
+    f.active = 1;
+    st->K = K;
+    st->fout.error = 0;
+}
+
+__global__ void k_update(CycleState* st, asp_component* comps, asp_iter_record* hist, Params p, int H, int W) {
+    if (threadIdx.x != 0) return;
+    if (st->stopped) return;
+    const FitOut& fo = st->fout;
+    const FitDesc& f = st->fit;
+    if (fo.error) { st->stopped = 1; st->error = fo.error; st->n_terms = 0; return; }
+    const double ab = st->alpha_b, wb = st->omega_b;
+    const int K = f.K;
+    int nt = 0;
+    // new component with the loop gain (Sect. 3, after Eq. 8)
+    const int ni = st->n_comp;
+    asp_component cn = deconvolve(fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], ab, wb, (double)p.gain);
+    comps[ni] = cn;
+    st->n_comp = ni + 1;
+    if (make_term(cn, cn.flux, H, W, nt, st->terms[nt])) ++nt;
+    // old members are replaced by their refit values
+    int keep[KMAX];
+    for (int m = 1; m < K; ++m) {
+        const int k = st->members[m];
+        const asp_component old = comps[k];
+        const double* g0 = &f.theta0[4 * m];
+        const double* g1 = &fo.theta[4 * m];
+        const double tau = p.tau;
+        keep[m] = fabs(g1[0] - g0[0]) > tau * fabs(g0[0]) || fabs(g1[1] - g0[1]) > tau * g0[3] ||
+                  fabs(g1[2] - g0[2]) > tau * g0[3] || fabs(g1[3] - g0[3]) > tau * g0[3];
+        asp_component nc = deconvolve(g1[0], g1[1], g1[2], g1[3], ab, wb, 1.0);
+        comps[k] = nc;
+        if (make_term(nc, nc.flux, H, W, nt, st->terms[nt])) ++nt;
+        if (make_term(old, -old.flux, H, W, nt, st->terms[nt])) ++nt;
+    }
+    st->n_terms = nt;
+    finish_terms(st, H, W);
+    // retained list: new first, then the previous list minus members whose
+    // fit moved no parameter by more than tau
+    int nr = 0;
+    int tmp[RET_MAX];
+    tmp[nr++] = ni;
+    for (int r = 0; r < st->n_ret && nr < p.retained_cap; ++r) {
+        const int k = st->ret[r];
+        bool drop = false;
+        for (int m = 1; m < K; ++m)
+            if (st->members[m] == k && !keep[m]) drop = true;
+        if (!drop) tmp[nr++] = k;
+    }
+    for (int r = 0; r < nr; ++r) st->ret[r] = tmp[r];
+    st->n_ret = nr;
+    // history
+    asp_iter_record tmp_rec;
+    asp_iter_record& h = st->t < st->cap_comp ? hist[st->t] : tmp_rec;
+    h.t = st->t; h.mode = st->mode; h.k = K; h.status = fo.status;
+    h.iters = fo.iters; h.passes = fo.passes;
+    h.x0 = f.wx0; h.x1 = f.wx0 + f.ww - 1; h.y0 = f.wy0; h.y1 = f.wy0 + f.wh - 1;
+    h.new_index = ni; h.n_terms = nt;
+    h.peak_value = st->peak.val;
+    h.init_scale = st->init_scale >= 0 ? st->init_s : 0.f;
+    h.chi2_init = fo.chi2_init; h.chi2_final = fo.chi2;
+    h.a0 = st->init[0]; h.x0_init = st->init[1]; h.y0_init = st->init[2]; h.w0 = st->init[3];
+    // switch statistics and totals
+    st->last_wi = cn.width;
+    st->last_w0 = st->init[3];
+    st->pixel_evals += fo.pixel_evals;
+    st->lm_iters += fo.iters;
+    st->lm_passes += fo.passes;
+    st->t += 1;
+}
+
+__global__ void k_terms_from_components(CycleState* st, const asp_component* __restrict__ comps, int n, float gain,
+                                        int H, int W) {
+    if (threadIdx.x != 0) return;
+    int nt = 0;
+    for (int i = 0; i < n && nt < MAX_TERMS; ++i)
+        if (make_term(comps[i], (double)gain * comps[i].flux, H, W, nt, st->terms[nt])) ++nt;
+    st->n_terms = nt;
+    finish_terms(st, H, W);
+}
+
+// Axis weights of every term: sampled Gaussian normalised to unit sum over the
+// unclipped support (so the component's discrete flux is its F), or the
+// bilinear pair (1 - f, f).  One block per term.
+__global__ void __launch_bounds__(256)
+k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __restrict__ wbuf) {
+    if (gate && *gate) return;
+    const int t = blockIdx.x;
+    if (t >= st->n_terms) return;
+    const TermDesc td = st->terms[t];
+    __shared__ double red[256];
+    for (int axis = 0; axis < 2; ++axis) {
+        const double c = axis == 0 ? td.cx : td.cy;
+        const int q0 = axis == 0 ? td.qx0 : td.qy0;
+        const int n = axis == 0 ? td.nx : td.ny;
+        const int u0 = axis == 0 ? td.ux0 : td.uy0;
+        const int u1 = axis == 0 ? td.ux1 : td.uy1;
+        float* out = wbuf + (axis == 0 ? td.woff_x : td.woff_y);
+        if (td.bilinear) {
+            const double f0 = floor(c);
+            const double fr = c - f0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int q = q0 + i;
+                out[i] = (float)(q == (int)f0 ? 1.0 - fr : fr);
+            }
+        } else {
+            const double iw = 1.0 / (2.0 * td.w * td.w);
+            double s = 0.0;
+            for (long long q = (long long)u0 + threadIdx.x; q <= u1; q += blockDim.x) {
+                const double dq = (double)q - c;
+                s += exp(-dq * dq * iw);
+            }
+            red[threadIdx.x] = s;
+            __syncthreads();
+            for (int o = 128; o > 0; o >>= 1) {
+                if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+                __syncthreads();
+            }
+            const double inv = 1.0 / red[0];
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const double dq = (double)(q0 + i) - c;
+                out[i] = (float)(exp(-dq * dq * iw) * inv);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, cudaStream_t s) {
+    k_cycle_begin<<<1, 32, 0, s>>>(st, p, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(CycleState* st, const asp_component* comps, const Params& p, int H, int W, int g_max,
+                          cudaStream_t s) {
+    k_select<<<1, 32, 0, s>>>(st, comps, p, H, W, g_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(CycleState* st, asp_component* comps, asp_iter_record* hist, const Params& p, int H,
+                          int W, float* wbuf, cudaStream_t s) {
+    k_update<<<1, 32, 0, s>>>(st, comps, hist, p, H, W);
+    k_build_weights<<<MAX_TERMS, 256, 0, s>>>(st, &st->stopped, wbuf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_terms_from_components(CycleState* st, const asp_component* comps, int n, float gain, int H,
+                                         int W, float* wbuf, cudaStream_t s) {
+    k_terms_from_components<<<1, 32, 0, s>>>(st, comps, n, gain, H, W);
+    k_build_weights<<<MAX_TERMS, 256, 0, s>>>(st, nullptr, wbuf);
+    return cudaGetLastError();
+}
+
+}  // namespace aspd

@@ -1,0 +1,160 @@
+// Internal device-side definitions of libasp (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/asp.h"
+
+namespace aspd {
+
+// ---------------------------------------------------------------- limits
+constexpr int KMAX = ASP_KMAX;                     // members per fit
+constexpr int PMAX = 4 * KMAX;                     // parameters per fit
+constexpr int NAP_MAX = PMAX + 4;                  // [J | r] columns padded to 4
+constexpr int NB_MAX = NAP_MAX / 4;                // 4x4 tiles per side
+constexpr int NTILES_MAX = NB_MAX * (NB_MAX + 1) / 2;
+constexpr int NACC_MAX = NTILES_MAX * 16;          // accumulator entries (tile order)
+constexpr int MAX_TERMS = 2 * KMAX;                // subtraction terms per iteration
+constexpr int MAX_SCALES = 8;                      // smoothing scales
+constexpr int FIT_THREADS = 256;
+constexpr int PX_SMEM = 12288;                     // target pixels one CTA keeps in smem
+constexpr int RET_MAX = 1024;                      // retained-list capacity
+constexpr int RED_THREADS = 256;                   // threads of the image-wide kernels
+constexpr unsigned SPIN_LIMIT = 1u << 25;          // bounded grid-barrier wait (~1 s)
+
+constexpr double LOG2E = 1.4426950408889634074;
+
+// ---------------------------------------------------------------- structs
+struct LMConst {
+    double lambda0, lambda_up, lambda_down, lambda_min, lambda_max, rtol, xtol;
+    int max_iter;
+    int px_per_cta;   // launch-shape knob: target window pixels per CTA
+};
+
+// One joint fit: K members, the trailing n_old of which are added back into
+// the target.  Window in source-image coordinates.
+struct FitDesc {
+    int K, n_old;
+    int wx0, wy0, ww, wh;
+    int use_mask, grid;
+    double mcx, mcy, mr2;          // optional circular pixel mask (beam fit)
+    double omega_min;              // trial widths must exceed this
+    double bx0, bx1, by0, by1;     // trial centres must stay inside this box
+    int active, smem_ok;
+    double theta0[PMAX];
+};
+
+struct FitOut {
+    double theta[PMAX];
+    double chi2_init, chi2, lambda;
+    int iters, passes, status, error;
+    long long pixel_evals;
+};
+
+// A separable subtraction term: image value scale * wx[i] * wy[j] at
+// (qx0 + i, qy0 + j).
+struct TermDesc {
+    int qx0, nx, qy0, ny;          // clipped support
+    float scale;                   // signed flux
+    int woff_x, woff_y;            // offsets of wx, wy in the weight buffer
+    int r0;                        // first PSF row the horizontal pass needs
+    long long t1off;               // offset of this term's rows in the T1 buffer
+    double cx, cy, w;              // component centre and width
+    int bilinear;                  // 1: bilinear point deposit, 0: sampled Gaussian
+    int ux0, ux1, uy0, uy1;        // unclipped support (normalisation range)
+    int pad;
+};
+
+struct ArgRes {                    // argmax of |v| with its signed value
+    float val;
+    int j;                         // scale index (smoothing) or 0
+    long long idx;
+};
+
+// Minor-cycle control block (device memory).
+struct CycleState {
+    int t, t_stop, stopped, stop_reason;
+    int mode, error, n_comp, cap_comp;
+    int n_ret, n_terms, K, skip_smooth;
+    double last_wi, last_w0;
+    double thr;                    // stop threshold on max|R|
+    double alpha_b, omega_b;
+    double init[4];
+    int init_scale, pad1;
+    float init_value, init_s;
+    ArgRes peak;                   // argmax |R| of the current residual
+    ArgRes speak;                  // argmax |S_j| of the last smoothing
+    int members[KMAX];             // component index of each fit member (-1: new)
+    long long pixel_evals, lm_iters, lm_passes;
+    unsigned cnt_argmax, cnt_smooth, nonfinite, pad2;
+    int ret[RET_MAX];
+    TermDesc terms[MAX_TERMS];
+    FitDesc fit;
+    FitOut fout;
+};
+
+struct Params {                    // device copy of asp_params plus derived values
+    float gain, area_frac;
+    int k_max, init_mode, retained_cap, n_scales;
+    double tau;
+    LMConst lm;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ long long round_half_up(double v) { return (long long)floor(v + 0.5); }
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// |a| beats |b|, ties: lower scale index, then lower flat index.
+__device__ __forceinline__ bool arg_better(float av, int aj, long long ai, float bv, int bj, long long bi) {
+    float fa = fabsf(av), fb = fabsf(bv);
+    if (fa > fb) return true;
+    if (!(fa >= fb)) return false;   // smaller, or a NaN on either side
+
+    if (aj != bj) return aj < bj;
+    return ai < bi;
+}
+
+__device__ __forceinline__ void arg_warp_reduce(float& v, int& j, long long& i) {
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_down_sync(0xffffffffu, v, o);
+        int oj = __shfl_down_sync(0xffffffffu, j, o);
+        long long oi = __shfl_down_sync(0xffffffffu, i, o);
+        if (arg_better(ov, oj, oi, v, j, i)) { v = ov; j = oj; i = oi; }
+    }
+}
+
+// Member box of the fit window: half-width max(5, ceil(4 w)) around the
+// rounded centre (inclusive, unclipped).
+__device__ __host__ inline void member_box(double x, double y, double w, long long* b) {
+    long long h = (long long)ceil(4.0 * w);
+    if (h < 5) h = 5;
+    long long rx = (long long)floor(x + 0.5), ry = (long long)floor(y + 0.5);
+    b[0] = rx - h; b[1] = rx + h; b[2] = ry - h; b[3] = ry + h;
+}
+
+__device__ __host__ inline int fit_tiles(int K) {
+    int NA = 4 * K + 1;
+    int NAp = (NA + 3) & ~3;
+    int nb = NAp / 4;
+    return nb * (nb + 1) / 2;
+}
+
+// CTAs a fit of K members over Wn pixels uses.
+__device__ __host__ inline int fit_grid(long long Wn, int K, int px_per_cta, int g_max, int* smem_ok) {
+    int NAp = ((4 * K + 1) + 3) & ~3;
+    long long target = px_per_cta > 0 ? px_per_cta : 65536 / (NAp * NAp);
+    if (target < 256) target = 256;
+    if (target > PX_SMEM) target = PX_SMEM;
+    long long g = (Wn + target - 1) / target;
+    if (g < 1) g = 1;
+    if (g > g_max) g = g_max;
+    *smem_ok = ((Wn + g - 1) / g) <= PX_SMEM;
+    return (int)g;
+}
+
+}  // namespace aspd

@@ -1,0 +1,43 @@
+// Host-side launchers shared between the translation units of libasp.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "asp_dev.cuh"
+
+namespace aspd {
+
+struct SmoothTaps {          // unit-L2 1-D smoothing kernels, passed by value
+    const float* k;          // all taps, scale j at k + off[j], length 2 m[j] + 1
+    int off[MAX_SCALES];
+    int m[MAX_SCALES];
+    double scale[MAX_SCALES];
+    int n;
+};
+
+// asp_fit.cu
+size_t fit_smem_bytes();
+int fit_tpt_for(int k_max);
+cudaError_t fit_configure(int tpt, int* blocks_per_sm);
+cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
+                          FitOut* out, double* partials, double* sums, unsigned* bar, float* Tg, cudaStream_t s);
+
+// asp_image.cu
+cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, unsigned* ticket, ArgRes* res,
+                          unsigned* nonfinite, const int* gate, cudaStream_t s);
+cudaError_t launch_subtract(const float* B, float* R, int H, int W, CycleState* st, const int* gate,
+                            const float* wbuf, float* T1, int grid, ArgRes* part, unsigned* ticket,
+                            cudaStream_t s);
+cudaError_t launch_smooth(const float* R, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
+                          int only_scale, float* S1, float* out_S, int grid, ArgRes* part, unsigned* ticket,
+                          cudaStream_t s);
+
+// asp_cycle.cu
+cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, cudaStream_t s);
+cudaError_t launch_select(CycleState* st, const asp_component* comps, const Params& p, int H, int W, int g_max,
+                          cudaStream_t s);
+cudaError_t launch_update(CycleState* st, asp_component* comps, asp_iter_record* hist, const Params& p, int H,
+                          int W, float* wbuf, cudaStream_t s);
+cudaError_t launch_terms_from_components(CycleState* st, const asp_component* comps, int n, float gain, int H,
+                                         int W, float* wbuf, cudaStream_t s);
+
+}  // namespace aspd

@@ -13,7 +13,7 @@ value ranges of the five workload configurations:
 * ``config1``: 256x256, 5 points + 3 Gaussians, analytic PSF (Gaussian main
   lobe sigma 1.5 px plus a 2 % ring at 12 px), noise 1e-3.
 * ``config2``: 1024x1024, 50 power-law points, 20 Gaussians, one k^-3
-  Gaussian-random-field patch, PSF = |FFT| of a seeded uv mask, noise 1e-4.
+  Gaussian-random-field patch, PSF = FFT of a seeded uv mask, noise 1e-4.
 * ``config3``: 4096x4096 scaled-up config 1 (400 points, 150 Gaussians,
   4 GRF patches, PSF main lobe 2.5 px, ring at 20 px).
 * ``config4``: 64 config-1-style images of uneven sizes.

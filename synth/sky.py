@@ -75,37 +75,34 @@ def gaussian_psf(H: int, W: int, sigma: float, amp: float = 1.0) -> np.ndarray:
 
 
 def _halfmax_sigma(psf: np.ndarray) -> float:
-    """Main-lobe width of a generated PSF from its half-maximum crossings.
+    """Main-lobe width of a generated PSF from the area above half maximum.
 
-    Generator-side size control only (used to tune the uv taper): the mean of
-    the four on-axis half-maximum radii, linearly interpolated, divided by
-    sqrt(2 ln 2).
+    Generator-side size control only (used to tune the uv taper): the number
+    of pixels of the central 129x129 region at or above half the zero-lag
+    value is taken as the area of a disc of radius sigma sqrt(2 ln 2).
     """
     H2, W2 = psf.shape
     cy, cx = H2 // 2, W2 // 2
-    peak = psf[cy, cx]
-    radii = []
-    for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
-        prev = peak
-        for s in range(1, min(cy, cx)):
-            v = psf[cy + dy * s, cx + dx * s]
-            if v < 0.5 * peak:
-                radii.append(s - 1 + (prev - 0.5 * peak) / (prev - v))
-                break
-            prev = v
-    return float(np.mean(radii)) / np.sqrt(2.0 * np.log(2.0))
+    r = min(64, cy, cx)
+    core = psf[cy - r: cy + r + 1, cx - r: cx + r + 1]
+    area = float(np.count_nonzero(core >= 0.5 * psf[cy, cx]))
+    return float(np.sqrt(area / np.pi) / np.sqrt(2.0 * np.log(2.0)))
 
 
 def uv_mask_psf(H: int, W: int, rng: np.random.Generator, fill: float = 0.05,
                 k0: float = 0.08, target_sigma: float = 2.0) -> tuple[np.ndarray, float]:
-    """|FFT| of a seeded, radially denser random uv mask with a Gaussian taper.
+    """FFT of a seeded, radially denser random uv mask with a Gaussian taper.
 
     The mask is Bernoulli with ``p(k) = min(1, c exp(-|k| / k0))`` (``c`` set
     so the mean fill is ``fill``), made Hermitian-symmetric, multiplied by a
-    Gaussian taper ``exp(-|k|^2 / 2 s_t^2)``; the PSF is the modulus of its
-    inverse FFT, shifted to ``[H, W]`` and normalised to unit peak.  ``s_t`` is
-    bisected until the half-maximum width lies within 2.5 % of
-    ``target_sigma``.  Returns ``(psf, s_t)``.
+    Gaussian taper ``exp(-|k|^2 / 2 s_t^2)``; the PSF is its inverse FFT
+    (real, because the weights are Hermitian-symmetric), shifted to
+    ``[H, W]`` and normalised to unit peak, so it has negative sidelobes like
+    an interferometer's PSF.  (Taking the modulus instead rectifies the
+    sidelobes into a positive floor holding ~150x the main lobe's integral,
+    under which a main-lobe Gaussian approximation of the PSF over-subtracts
+    without bound.)  ``s_t`` is bisected until the half-maximum width lies
+    within 2.5 % of ``target_sigma``.  Returns ``(psf, s_t)``.
     """
     H2, W2 = 2 * H, 2 * W
     ky = np.fft.fftfreq(H2)[:, None]
@@ -128,9 +125,9 @@ def uv_mask_psf(H: int, W: int, rng: np.random.Generator, fill: float = 0.05,
 
     def make(s_t: float) -> np.ndarray:
         w = mask * np.exp(-(k * k) / (2.0 * s_t * s_t))
-        img = np.abs(np.fft.ifft2(w))
+        img = np.real(np.fft.ifft2(w))
         img = np.fft.fftshift(img)
-        return img / img.max()
+        return img / img[H, W]
 
     # wider taper in uv -> narrower main lobe; bisect on log s_t
     lo, hi = np.log(0.01), np.log(0.5)
@@ -261,7 +258,7 @@ def config1(seed: int = 0) -> SynthImage:
 def config2(seed: int = 0, size: int = 1024) -> SynthImage:
     """1024x1024: 50 power-law points (index -1.5 on [1e-3, 1]), 20 Gaussians
     (sigma log-uniform [2,60], peak U[0.05,0.5]), one 300x300 k^-3 GRF patch of
-    RMS 0.01; PSF = |FFT| of a seeded uv mask (main lobe ~2 px); noise 1e-4;
+    RMS 0.01; PSF = FFT of a seeded uv mask (main lobe ~2 px); noise 1e-4;
     active set <= 20, 2000 iterations."""
     rng = rng_for(2, seed)
     H = W = int(size)
