@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the Asp-Clean2016 minor cycle on one GB300 (or N replicas).
+
+Workload (default): the 1024x1024 configuration -- 50 power-law points, 20
+Gaussians (sigma 2-60 px), one k^-3 GRF patch, uv-mask PSF with a ~2 px main
+lobe, noise 1e-4, active set <= 20, 2000 minor-cycle iterations, loop gain
+0.35, LM cap 50.  Synthetic, seeded (synth.config2).
+
+One step = one whole pass of the hot path over the image: asp_reset with the
+dirty image and the PSF (beam fit, first peak) then asp_minor_cycle for the
+configuration's 2000 iterations (peak search, active set, LM fits,
+deconvolution, subtraction, stopping tests).  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MB write) between steps, outside
+the timed region.  The metric is minor-cycle iterations per second (whole job);
+LM pixel evaluations per second are reported beside it.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload with
+its own seed (independent images, no collective): weak scaling.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "minor-cycle iterations/s (Asp-Clean2016, 1024x1024, active set <= 20)"
+UNIT = "iterations/s"
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=0, help="minor-cycle iterations per step (0: the workload's 2000)")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic_record():
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu
+    summary, if the kernel source has not changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+    import hashlib
+    out = {}
+    for name, r in rec.items():
+        src = os.path.join(ROOT, r.get("source", ""))
+        try:
+            h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        except OSError:
+            continue
+        if h == r.get("source_sha256_16"):
+            out[name] = r
+    return out
+
+
+def _workload(size: int, seed: int):
+    import synth
+    return synth.config2(seed, size=size)
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- cpu baseline (oracle)
+
+def _oracle_sample(size: int, budget_s: float, seed: int = 0, resume=None):
+    """Run the FP64 oracle's minor cycle on the same workload until budget_s
+    has been spent (at least one iteration).  Returns (iterations, seconds,
+    pixel_evals, state)."""
+    import oracle as O
+    case = _workload(size, seed)
+    if resume is None:
+        mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma))
+    else:
+        mc = resume
+    n0, pe0 = mc.t, sum(h["fit"].pixel_evals for h in mc.history)
+    t0 = time.perf_counter()
+    while True:
+        if mc.step() is None:
+            break
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    pe = sum(h["fit"].pixel_evals for h in mc.history) - pe0
+    return mc.t - n0, dt, pe, mc
+
+
+def _cpu_threads_env():
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    return env
+
+
+def cpu_baseline(size: int, budget: float) -> dict:
+    """The oracle as it stands, single-threaded, in a child process."""
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; n, dt, pe, _ = bench._oracle_sample(%d, %f); "
+            "print(json.dumps([n, dt, pe]))" % (ROOT, size, budget))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_cpu_threads_env(),
+                       timeout=budget * 20 + 600)
+    n, dt, pe = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} minor-cycle iterations of the {size}x{size} workload from its dirty image "
+                      f"(FP64 NumPy oracle, 1 thread, {dt:.1f} s)",
+            "pixel_evals_per_s": pe / dt}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O  # noqa: F401  (the reference arm is the oracle itself)
+    n_total, t_total, pe_total = 0, 0.0, 0
+    state = None
+    budget = max(2.0, min(a.cpu_budget, 15.0))
+    # warm-up steps continue the same run (each step a bounded sample)
+    for i in range(a.warmup + a.steps):
+        n, dt, pe, state = _oracle_sample(a.size, budget, resume=state)
+        if i >= a.warmup:
+            n_total += n
+            t_total += dt
+            pe_total += pe
+    value = n_total / t_total if t_total > 0 else 0.0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_total / max(a.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"config2 {a.size}x{a.size} Asp-Clean2016, k_max 20",
+                                            "global_batch": 1, "seq_len": None, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_total} consecutive minor-cycle iterations after {a.warmup} warm-up "
+                                       f"samples, {budget:.0f} s per step, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "pixel_evals_per_s": pe_total / t_total if t_total else 0.0}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import paper_1606_07872_gb300 as asp
+    from paper_1606_07872_gb300 import build as _b
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    _b.build()
+    case = _workload(a.size, rank)
+    n_iter = a.iters or case.n_iter
+    dirty = torch.from_numpy(case.dirty).cuda()
+    psf = torch.from_numpy(case.psf).cuda()
+    stream = torch.cuda.Stream()
+    params = asp.default_params(k_max=case.k_max, noise_sigma=case.noise_sigma, gain=case.gain,
+                                lm_max_iter=case.lm_max_iter)
+    with torch.cuda.stream(stream):
+        ctx = asp.Context(dirty, psf, params=params, stream=stream)
+    L = asp.lib()
+    import ctypes as C
+
+    def reset(d_ptr, on_host, p_ptr=None, p_host=0):
+        asp._check(L.asp_reset(ctx.h, d_ptr, on_host, p_ptr, p_host), "asp_reset", ctx.h)
+
+    def step_device():
+        reset(dirty.data_ptr(), 0, psf.data_ptr(), 0)
+        return asp.asp_minor_cycle(ctx.h, n_iter)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(a.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    def launches():
+        n = C.c_int64()
+        L.asp_launch_count(ctx.h, C.byref(n))
+        return n.value
+
+    # ---- timed region (device-resident inputs)
+    times, iters, pevals = [], 0, 0
+    fit_flops = sub_flops = 0.0
+    l0 = launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step_device()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters += st["iterations"]
+            pevals += st["pixel_evals"]
+            fit_flops += st["fit_flops"]
+            sub_flops += st["sub_flops"]
+    torch.cuda.synchronize()
+    n_launch = launches() - l0
+    t_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms, float(iters), float(pevals)], device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_ms, iters, pevals = float(mx[0]), int(tt[1]), int(tt[2])
+    value = iters / (t_ms / 1e3)
+
+    # ---- end to end through the C-ABI with host buffers
+    dirty_h = torch.from_numpy(case.dirty).pin_memory()
+    psf_h = torch.from_numpy(case.psf).pin_memory()
+    res_h = torch.empty((case.H, case.W), dtype=torch.float32).pin_memory()
+    e2e_ms, e2e_iters = 0.0, 0
+    comps_bytes = 0
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reset(dirty_h.data_ptr(), 1, psf_h.data_ptr(), 1)
+        st = asp.asp_minor_cycle(ctx.h, n_iter)
+        asp.asp_copy_residual(ctx.h, res_h.numpy())
+        comps = asp.asp_get_components(ctx.h)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_iters += st["iterations"]
+        comps_bytes = comps.shape[0] * C.sizeof(asp.asp_component)
+    e2e = {"value": e2e_iters / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(case.dirty.nbytes + case.psf.nbytes),
+           "d2h_bytes_per_step": int(res_h.numel() * 4 + comps_bytes)}
+
+    # ---- per-kernel times (events around every launch, direct launches)
+    L.asp_set_profiling(ctx.h, 1)
+    step_device()
+    kt = (asp._lib.asp_kernel_time * 16)()
+    nk = C.c_int()
+    L.asp_get_kernel_times(ctx.h, kt, 16, C.byref(nk))
+    prof_stats = asp.asp_get_stats(ctx.h)
+    L.asp_set_profiling(ctx.h, 0)
+    kernels = {k.name.decode(): {"launches": k.launches, "total_ms": k.total_ms} for k in kt[: nk.value]}
+    dominant = max(kernels, key=lambda n: kernels[n]["total_ms"])
+
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    traffic = _traffic_record()
+    work = {"k_lm_fit": ("alu", prof_stats["fit_flops"]),
+            "k_sub_h": ("alu", None), "k_sub_v_argmax": ("alu", None)}
+    roof = None
+    kd = kernels[dominant]
+    if dominant == "k_lm_fit":
+        ach = prof_stats["fit_flops"] / (kd["total_ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "kernel": dominant, "avg_launch_ms": kd["total_ms"] / max(kd["launches"], 1),
+                "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"}
+    elif dominant in ("k_sub_h", "k_sub_v_argmax"):
+        # the subtraction's two passes together against HBM (algorithmic bytes)
+        ms = kernels["k_sub_h"]["total_ms"] + kernels["k_sub_v_argmax"]["total_ms"]
+        ach = prof_stats["sub_bytes"] / (ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": ach / float(peaks["hbm_gbs"]), "kernel": "k_sub_h+k_sub_v_argmax",
+                "avg_launch_ms": ms / max(kernels["k_sub_v_argmax"]["launches"], 1),
+                "flops_tflops": prof_stats["sub_flops"] / (ms / 1e3) / 1e12}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
+                "kernel": dominant}
+    roof["traffic"] = traffic.get(roof.get("kernel", ""), {}).get("bytes_per_launch")
+    roof["peak_source"] = peak_kind
+    _ = work
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"config2 {case.H}x{case.W} Asp-Clean2016 minor cycle, k_max {case.k_max}, "
+                                   f"{n_iter} iterations/step, gain {case.gain}",
+                       "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
+                       "l2": "flushed (256 MB write) between steps, outside timing"},
+            "pixel_evals_per_s": pevals / (t_ms / 1e3),
+            "fit_tflops": fit_flops / (t_ms / 1e3) / 1e12,
+            "e2e": e2e, "gpu_launches": n_launch, "roofline": roof, "kernels": kernels,
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(a.size, a.cpu_budget)
+        except Exception as e:  # report, never hide, a failed baseline
+            line["cpu_baseline"] = {"value": None, "error": repr(e)[:200]}
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

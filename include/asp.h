@@ -127,6 +127,13 @@ typedef struct {
     double peak_abs;      /* current max |R| */
     int32_t stop_reason;  /* asp_stop_reason of the last call */
     int32_t reserved;
+    /* Algorithmic work (the method's own arithmetic, not what the kernels
+     * happen to execute): LM pixel passes, 15K + 1 + (4K+1)(4K+2) FP32 flops
+     * per pixel evaluation with K members; subtraction as separable passes,
+     * 2 nx (H+ny-1) W + 2 ny H W flops per term, bytes = PSF regions read
+     * once + residual read and written once; smoothing 4 (2m+1) H W flops
+     * per scale and smoothing iteration. */
+    double fit_flops, sub_flops, sub_bytes, smooth_flops;
 } asp_cycle_stats;
 
 /* One minor-cycle iteration as recorded on the device. */
@@ -219,6 +226,24 @@ asp_status asp_get_state(asp_ctx* ctx, asp_component* comps, int comp_cap, int* 
 asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp,
                          const int* retained, int n_ret, int64_t t, double last_wi,
                          double last_w0);
+/* Restart on a new dirty image of the same size without reallocating: copies
+ * it into the residual, clears the component list, retained list, iteration
+ * counter and totals and finds the first peak.  If psf is not NULL it is
+ * copied too and the beam (alpha_b, omega_b) is fitted again (Sect. 3);
+ * otherwise the beam is kept.  The noise level is kept.  *_on_host: 1 for
+ * host memory, 0 for device memory. */
+asp_status asp_reset(asp_ctx* ctx, const float* dirty, int dirty_on_host, const float* psf, int psf_on_host);
+
+/* Per-kernel timing.  While on, minor cycles launch kernels directly (no CUDA
+ * graph) and every launch is bracketed by CUDA events on the context stream;
+ * asp_get_kernel_times reports per-kernel launches and total milliseconds
+ * since profiling was switched on.  Switching resets the totals. */
+typedef struct { char name[32]; int64_t launches; double total_ms; } asp_kernel_time;
+asp_status asp_set_profiling(asp_ctx* ctx, int on);
+asp_status asp_get_kernel_times(asp_ctx* ctx, asp_kernel_time* out, int cap, int* n);
+/* Kernels this context has launched (graph replays counted per kernel node). */
+asp_status asp_launch_count(asp_ctx* ctx, int64_t* n);
+
 /* Checkpoint the whole minor-cycle state (residual included) to a file, or
  * restore it into a context of the same size. */
 asp_status asp_save_state(asp_ctx* ctx, const char* path);

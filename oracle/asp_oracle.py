@@ -194,12 +194,18 @@ def cholesky_solve_damped(A, g, lam):
 
 
 def _valid(theta, box, omega_min):
+    """Reading (the fit is local, Sect. 2): a trial point is usable when every
+    value is finite, every centre lies in the window and every width is in
+    (omega_min, window extent]; a Gaussian wider than its window is not
+    constrained by the data (it degenerates into a pedestal of unbounded
+    flux)."""
     if not np.all(np.isfinite(theta)):
         return False
     x0b, x1b, y0b, y1b = box
+    omega_max = max(x1b - x0b + 1, y1b - y0b + 1)
     for k in range(len(theta) // 4):
         _, x, y, w = theta[4 * k: 4 * k + 4]
-        if not (w > omega_min):
+        if not (w > omega_min) or w > omega_max:
             return False
         if x < x0b or x > x1b or y < y0b or y > y1b:
             return False
@@ -574,7 +580,8 @@ class MinorCycle:
        guess, both from the last iteration), else SMOOTH;
     3. initial values (a0, x0, y0, omega0) by that mode;
     4. active set: the new member plus retained members (most recent first)
-       whose boxes overlap the new member's box, at most k_max in total;
+       whose boxes overlap the new member's box and whose centres are not
+       co-located with the new one, at most k_max in total;
        the joint window is the bounding box of their boxes clipped to the
        image; the target is ``T = R + sum_old g(G_k)`` over the window, with
        G_k the single-Gaussian image of old member k;
@@ -638,6 +645,11 @@ class MinorCycle:
         return peak_smooth(self.R, self.omega_b, self.p.n_scales)
 
     def select(self, init):
+        """Active set: retained members (most recent first) whose boxes overlap
+        the new member's box and whose centres are not co-located with it
+        (squared distance > max(omega0, omega_ic,k)^2; co-located members
+        leave only the sum of their amplitudes determined), at most
+        k_max - 1 of them."""
         new_box = member_box(init["x0"], init["y0"], init["w0"])
         chosen = []
         for k in self.retained:
@@ -645,7 +657,10 @@ class MinorCycle:
                 break
             G = self.G(k)
             if boxes_overlap(member_box(G[1], G[2], G[3]), new_box):
-                chosen.append(k)
+                dx, dy = G[1] - init["x0"], G[2] - init["y0"]
+                m = max(init["w0"], G[3])
+                if dx * dx + dy * dy > m * m:
+                    chosen.append(k)
         boxes = [new_box] + [member_box(*self.G(k)[1:4]) for k in chosen]
         x0 = max(0, min(b[0] for b in boxes))
         x1 = min(self.W - 1, max(b[1] for b in boxes))

@@ -53,7 +53,8 @@ class asp_params(C.Structure):
 class asp_cycle_stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("components", C.c_int64), ("pixel_evals", C.c_int64),
                 ("lm_iters", C.c_int64), ("lm_passes", C.c_int64), ("peak_abs", C.c_double),
-                ("stop_reason", C.c_int32), ("reserved", C.c_int32)]
+                ("stop_reason", C.c_int32), ("reserved", C.c_int32), ("fit_flops", C.c_double),
+                ("sub_flops", C.c_double), ("sub_bytes", C.c_double), ("smooth_flops", C.c_double)]
 
 
 class asp_iter_record(C.Structure):
@@ -63,6 +64,10 @@ class asp_iter_record(C.Structure):
                 ("peak_value", C.c_float), ("init_scale", C.c_float), ("chi2_init", C.c_double),
                 ("chi2_final", C.c_double), ("a0", C.c_double), ("x0_init", C.c_double),
                 ("y0_init", C.c_double), ("w0", C.c_double)]
+
+
+class asp_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
 _P = C.c_void_p
@@ -94,6 +99,10 @@ SIGNATURES = {
     "asp_get_state": [_P, C.POINTER(asp_component), _I, C.POINTER(_I), C.POINTER(_I), _I, C.POINTER(_I),
                       C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "asp_set_state": [_P, C.POINTER(asp_component), _I, C.POINTER(_I), _I, C.c_int64, C.c_double, C.c_double],
+    "asp_reset": [_P, _P, _I, _P, _I],
+    "asp_set_profiling": [_P, _I],
+    "asp_get_kernel_times": [_P, C.POINTER(asp_kernel_time), _I, C.POINTER(_I)],
+    "asp_launch_count": [_P, C.POINTER(C.c_int64)],
     "asp_save_state": [_P, C.c_char_p],
     "asp_load_state": [_P, C.c_char_p],
 }

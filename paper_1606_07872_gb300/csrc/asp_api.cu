@@ -15,11 +15,20 @@
 
 using namespace aspd;
 
-namespace aspd {
-cudaError_t launch_beam_init(FitDesc* desc, const float* B, int H, int W, int g_max, cudaStream_t s);
-cudaError_t launch_radix_median(const float* v, long long n, int abs_dev_from, double center, unsigned long long* hist,
-                                double* out, cudaStream_t s);
-}
+// Kernel classes timed by asp_set_profiling.
+enum KernelClass {
+    KC_BEGIN, KC_SMOOTH_H, KC_SMOOTH_V, KC_SELECT, KC_FIT, KC_UPDATE, KC_WEIGHTS, KC_SUB_H, KC_SUB_V, KC_ARGMAX,
+    KC_COUNT
+};
+static const char* const KC_NAMES[KC_COUNT] = {
+    "k_cycle_begin", "k_smooth_h", "k_smooth_v_argmax", "k_select", "k_lm_fit", "k_update", "k_build_weights",
+    "k_sub_h", "k_sub_v_argmax", "k_argmax_abs"};
+static const int KERNELS_PER_ITER = 9;   // kernels one minor-cycle iteration enqueues
+
+struct ProfMark {
+    int cls;
+    cudaEvent_t a, b;
+};
 
 struct asp_ctx {
     int dev = 0, num_sms = 0;
@@ -42,6 +51,9 @@ struct asp_ctx {
     float* S1 = nullptr;
     float* taps_dev = nullptr;
     SmoothTaps taps{};
+    double smooth_flops = 0.0;   // 2 passes x 2 flops x taps x pixels, all scales
+    size_t taps_cap = 0;
+    int s1_scales = 0;
     double* partials = nullptr;
     double* sums = nullptr;
     unsigned* bar = nullptr;
@@ -54,6 +66,12 @@ struct asp_ctx {
     cudaGraphExec_t gexec = nullptr;
     int graph_unroll = 8;
     int graph_state = 0;   // 0 untried, 1 usable, -1 unavailable (direct launches)
+    int profiling = 0;
+    std::vector<ProfMark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[KC_COUNT] = {};
+    long long prof_n[KC_COUNT] = {};
+    long long launches = 0;
     int broken = 0;
     std::string err;
     std::vector<void*> allocs;
@@ -136,7 +154,54 @@ asp_status put_field(asp_ctx* ctx, T* dev_field, const T& v) {
     return ASP_OK;
 }
 
+cudaEvent_t take_event(asp_ctx* ctx) {
+    cudaEvent_t e = nullptr;
+    if (!ctx->event_pool.empty()) {
+        e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    return e;
+}
+
+// Brackets one kernel launch with events when profiling (direct launches only).
+struct Mark {
+    asp_ctx* ctx;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Mark(asp_ctx* c, int k) : ctx(c), cls(k) {
+        ctx->launches += 1;
+        if (ctx->profiling) {
+            a = take_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~Mark() {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, ctx->stream);
+            ctx->marks.push_back({cls, a, b});
+        }
+    }
+};
+
+// Folds recorded event pairs into the per-class totals (stream synchronised).
+void collect_marks(asp_ctx* ctx) {
+    for (const ProfMark& m : ctx->marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            ctx->prof_ms[m.cls] += ms;
+            ctx->prof_n[m.cls] += 1;
+        }
+        ctx->event_pool.push_back(m.a);
+        ctx->event_pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+}
+
 asp_status refresh_peak(asp_ctx* ctx) {
+    Mark m(ctx, KC_ARGMAX);
     CK(launch_argmax(ctx->R, ctx->N, ctx->grid_img, ctx->part, ctx->ticket, &ctx->st->peak, &ctx->st->nonfinite,
                      nullptr, ctx->stream));
     return ASP_OK;
@@ -145,15 +210,22 @@ asp_status refresh_peak(asp_ctx* ctx) {
 // One minor-cycle iteration as a fixed launch sequence (device-side gating).
 asp_status enqueue_iteration(asp_ctx* ctx) {
     const int H = ctx->H, W = ctx->W;
-    CK(launch_cycle_begin(ctx->st, ctx->dp, H, W, ctx->stream));
-    CK(launch_smooth(ctx->R, H, W, ctx->taps, ctx->st, &ctx->st->skip_smooth, -1, ctx->S1, nullptr, ctx->grid_img,
-                     ctx->part, ctx->ticket, ctx->stream));
-    CK(launch_select(ctx->st, ctx->comps, ctx->dp, H, W, ctx->g_max, ctx->stream));
-    CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &ctx->st->fit, ctx->dp.lm, &ctx->st->fout, ctx->partials,
-                     ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
-    CK(launch_update(ctx->st, ctx->comps, ctx->hist, ctx->dp, H, W, ctx->wbuf, ctx->stream));
-    CK(launch_subtract(ctx->B, ctx->R, H, W, ctx->st, &ctx->st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img,
-                       ctx->part, ctx->ticket, ctx->stream));
+    CycleState* st = ctx->st;
+    cudaStream_t s = ctx->stream;
+    { Mark m(ctx, KC_BEGIN); CK(launch_cycle_begin(st, ctx->dp, H, W, ctx->smooth_flops, s)); }
+    { Mark m(ctx, KC_SMOOTH_H); CK(launch_smooth_h(ctx->R, H, W, ctx->taps, &st->skip_smooth, -1, ctx->S1, ctx->grid_img, s)); }
+    { Mark m(ctx, KC_SMOOTH_V);
+      CK(launch_smooth_v(ctx->S1, H, W, ctx->taps, st, &st->skip_smooth, -1, nullptr, ctx->grid_img, ctx->part,
+                         ctx->ticket, s)); }
+    { Mark m(ctx, KC_SELECT); CK(launch_select(st, ctx->comps, ctx->dp, H, W, ctx->g_max, s)); }
+    { Mark m(ctx, KC_FIT);
+      CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit, ctx->dp.lm, &st->fout, ctx->partials, ctx->sums,
+                       ctx->bar, ctx->Tg, s)); }
+    { Mark m(ctx, KC_UPDATE); CK(launch_update(st, ctx->comps, ctx->hist, ctx->dp, H, W, s)); }
+    { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(st, &st->stopped, ctx->wbuf, s)); }
+    { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, s)); }
+    { Mark m(ctx, KC_SUB_V);
+      CK(launch_sub_v(ctx->R, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part, ctx->ticket, s)); }
     return ASP_OK;
 }
 
@@ -167,12 +239,14 @@ asp_status build_graph(asp_ctx* ctx) {
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     asp_status s = ASP_OK;
+    const long long launches_before = ctx->launches;
     if (ok) {
         for (int i = 0; i < ctx->graph_unroll && s == ASP_OK; ++i) s = enqueue_iteration(ctx);
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         ok = (s == ASP_OK) && e == cudaSuccess && g != nullptr;
     }
     ctx->stream = saved;
+    ctx->launches = launches_before;
     ctx->broken = 0;
     ctx->err.clear();
     if (ok && cudaGraphInstantiate(&ctx->gexec, g, 0) == cudaSuccess) {
@@ -189,6 +263,78 @@ asp_status build_graph(asp_ctx* ctx) {
 void host_member_box(double x, double y, double w, long long* b) { member_box(x, y, w, b); }
 
 }  // namespace
+
+// Beam (alpha_b, omega_b): LM fit of one Gaussian to the PSF main lobe
+// (Sect. 3).  Leaves the result in ctx and in the control block.
+asp_status fit_beam(asp_ctx* ctx) {
+    const int H = ctx->H, W = ctx->W;
+    CK(launch_beam_init(&ctx->st->fit, ctx->B, H, W, ctx->g_max, ctx->stream));
+    CK(cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream));
+    {
+        Mark m(ctx, KC_FIT);
+        CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->B, 2 * W, &ctx->st->fit, ctx->dp.lm, &ctx->st->fout,
+                         ctx->partials, ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
+    }
+    FitOut fo;
+    CK(cudaMemcpyAsync(&fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (fo.error) return fail(ctx, ASP_ERR_TIMEOUT, "beam fit: device wait timed out");
+    if (!(fo.theta[3] > 0) || !std::isfinite(fo.theta[0]) || fo.theta[0] == 0.0 || !std::isfinite(fo.theta[3]))
+        return fail(ctx, ASP_ERR_NAN, "beam fit failed (no main lobe to fit)");
+    ctx->alpha_b = fo.theta[0];
+    ctx->xb = fo.theta[1];
+    ctx->yb = fo.theta[2];
+    ctx->omega_b = fo.theta[3];
+    double ab_wb[2] = {ctx->alpha_b, ctx->omega_b};
+    CK(cudaMemcpyAsync(&ctx->st->alpha_b, ab_wb, sizeof(ab_wb), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
+}
+
+// Smoothing scales s_j = omega_b 2^j, kept while s_j <= min(H, W) / 8, with
+// unit-L2 1-D taps exp(-u^2 / 2 s^2), |u| <= ceil(4 s).
+asp_status setup_taps(asp_ctx* ctx) {
+    const int H = ctx->H, W = ctx->W;
+    const long long N = ctx->N;
+    std::vector<float> taps;
+    SmoothTaps t{};
+    double sflops = 0.0;
+    for (int j = 0; j < ctx->p.n_scales; ++j) {
+        double s_j = ctx->omega_b * std::ldexp(1.0, j);
+        if (j > 0 && s_j > std::min(H, W) / 8.0) continue;
+        int m = (int)std::ceil(4.0 * s_j);
+        std::vector<double> e(2 * m + 1);
+        double ss = 0;
+        for (int u = -m; u <= m; ++u) {
+            e[u + m] = std::exp(-(double)u * u / (2.0 * s_j * s_j));
+            ss += e[u + m] * e[u + m];
+        }
+        double inv = 1.0 / std::sqrt(ss);
+        t.off[t.n] = (int)taps.size();
+        t.m[t.n] = m;
+        t.scale[t.n] = s_j;
+        for (double v : e) taps.push_back((float)(v * inv));
+        t.n++;
+        sflops += 2.0 * 2.0 * (2 * m + 1) * (double)N;
+    }
+    if (taps.size() > ctx->taps_cap) {
+        float* p = nullptr;
+        CK(dalloc(ctx, &p, taps.size()));
+        ctx->taps_dev = p;
+        ctx->taps_cap = taps.size();
+    }
+    if (t.n > ctx->s1_scales) {
+        float* p = nullptr;
+        CK(dalloc(ctx, &p, (size_t)t.n * N));
+        ctx->S1 = p;
+        ctx->s1_scales = t.n;
+    }
+    CK(cudaMemcpy(ctx->taps_dev, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice));
+    t.k = ctx->taps_dev;
+    ctx->taps = t;
+    ctx->smooth_flops = sflops;
+    return ASP_OK;
+}
 
 // =====================================================================
 extern "C" {
@@ -296,49 +442,10 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
         cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream) != cudaSuccess)
         return bail(ASP_ERR_CUDA);
 
-    // ---- beam: LM fit of one Gaussian to the PSF main lobe (Sect. 3)
-    if (launch_beam_init(&ctx->st->fit, ctx->B, H, W, ctx->g_max, ctx->stream) != cudaSuccess)
-        return bail(ASP_ERR_CUDA);
-    if (cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream) != cudaSuccess) return bail(ASP_ERR_CUDA);
-    if (launch_lm_fit(ctx->tpt, ctx->g_max, ctx->B, 2 * W, &ctx->st->fit, ctx->dp.lm, &ctx->st->fout, ctx->partials,
-                      ctx->sums, ctx->bar, ctx->Tg, ctx->stream) != cudaSuccess)
-        return bail(ASP_ERR_CUDA);
-    FitOut fo;
-    if (cudaMemcpyAsync(&fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-        return bail(ASP_ERR_CUDA);
-    if (fo.error) { ctx->err = "beam fit: device wait timed out"; return bail(ASP_ERR_TIMEOUT); }
-    ctx->alpha_b = fo.theta[0];
-    ctx->xb = fo.theta[1];
-    ctx->yb = fo.theta[2];
-    ctx->omega_b = fo.theta[3];
-    if (!(ctx->omega_b > 0) || !std::isfinite(ctx->alpha_b) || ctx->alpha_b == 0.0) return bail(ASP_ERR_NAN);
-
-    // ---- smoothing scales s_j = omega_b 2^j, kept while s_j <= min(H, W) / 8
-    {
-        std::vector<float> taps;
-        SmoothTaps& t = ctx->taps;
-        t.n = 0;
-        for (int j = 0; j < ctx->p.n_scales; ++j) {
-            double s_j = ctx->omega_b * std::ldexp(1.0, j);
-            if (j > 0 && s_j > std::min(H, W) / 8.0) continue;
-            int m = (int)std::ceil(4.0 * s_j);
-            std::vector<double> e(2 * m + 1);
-            double ss = 0;
-            for (int u = -m; u <= m; ++u) { e[u + m] = std::exp(-(double)u * u / (2.0 * s_j * s_j)); ss += e[u + m] * e[u + m]; }
-            double inv = 1.0 / std::sqrt(ss);
-            t.off[t.n] = (int)taps.size();
-            t.m[t.n] = m;
-            t.scale[t.n] = s_j;
-            for (double v : e) taps.push_back((float)(v * inv));
-            t.n++;
-        }
-        if (dalloc(ctx, &ctx->taps_dev, taps.size()) != cudaSuccess) return bail(ASP_ERR_OOM);
-        if (dalloc(ctx, &ctx->S1, (size_t)t.n * N) != cudaSuccess) return bail(ASP_ERR_OOM);
-        if (cudaMemcpy(ctx->taps_dev, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(ASP_ERR_CUDA);
-        t.k = ctx->taps_dev;
-    }
+    s = fit_beam(ctx);
+    if (s != ASP_OK) return bail(s);
+    s = setup_taps(ctx);
+    if (s != ASP_OK) return bail(s);
 
     // ---- noise level: given, or 1.4826 x MAD of the dirty image
     if (ctx->p.noise_sigma > 0.f) {
@@ -392,6 +499,8 @@ asp_status asp_destroy(asp_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    collect_marks(ctx);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (void* q : ctx->allocs) cudaFree(q);
     delete ctx;
     return ASP_OK;
@@ -428,8 +537,15 @@ asp_status asp_find_peak(asp_ctx* ctx, int mode, asp_peak* out) {
         out->w0 = ctx->omega_b;
         return ASP_OK;
     }
-    CK(launch_smooth(ctx->R, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, -1, ctx->S1, nullptr, ctx->grid_img,
-                     ctx->part, ctx->ticket, ctx->stream));
+    {
+        Mark m(ctx, KC_SMOOTH_H);
+        CK(launch_smooth_h(ctx->R, ctx->H, ctx->W, ctx->taps, nullptr, -1, ctx->S1, ctx->grid_img, ctx->stream));
+    }
+    {
+        Mark m(ctx, KC_SMOOTH_V);
+        CK(launch_smooth_v(ctx->S1, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, -1, nullptr, ctx->grid_img, ctx->part,
+                           ctx->ticket, ctx->stream));
+    }
     asp_status s = read_state(ctx, &h);
     if (s != ASP_OK) return s;
     out->index = h.speak.idx;
@@ -457,6 +573,7 @@ static asp_status run_fit(asp_ctx* ctx, const asp_gauss* init, int n, int n_old,
     d.ww = x1 - x0 + 1;
     d.wh = y1 - y0 + 1;
     d.omega_min = 0.25 * ctx->omega_b;
+    d.omega_max = (double)std::max(d.ww, d.wh);
     d.bx0 = x0; d.bx1 = x1; d.by0 = y0; d.by1 = y1;
     for (int k = 0; k < n; ++k) {
         d.theta0[4 * k] = init[k].amp;
@@ -472,8 +589,11 @@ static asp_status run_fit(asp_ctx* ctx, const asp_gauss* init, int n, int n_old,
     d.active = 1;
     CK(cudaMemcpyAsync(&ctx->st->fit, &d, sizeof(d), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream));
-    CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, ctx->W, &ctx->st->fit, lmc, &ctx->st->fout, ctx->partials,
-                     ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
+    {
+        Mark m(ctx, KC_FIT);
+        CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, ctx->W, &ctx->st->fit, lmc, &ctx->st->fout, ctx->partials,
+                         ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
+    }
     CK(cudaMemcpyAsync(fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (fo->error) return fail(ctx, ASP_ERR_TIMEOUT, "fit: grid barrier timed out");
@@ -563,9 +683,14 @@ asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float g
             return ASP_ERR_INVALID_ARG;
     if (n == 0) return ASP_OK;
     CK(cudaMemcpyAsync(ctx->comp_stage, comps, n * sizeof(asp_component), cudaMemcpyHostToDevice, ctx->stream));
-    CK(launch_terms_from_components(ctx->st, ctx->comp_stage, n, gain, ctx->H, ctx->W, ctx->wbuf, ctx->stream));
-    CK(launch_subtract(ctx->B, ctx->R, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,
-                       ctx->ticket, ctx->stream));
+    { Mark m(ctx, KC_UPDATE); CK(launch_terms_from_components(ctx->st, ctx->comp_stage, n, gain, ctx->H, ctx->W, ctx->stream)); }
+    { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(ctx->st, nullptr, ctx->wbuf, ctx->stream)); }
+    { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->stream)); }
+    {
+        Mark m(ctx, KC_SUB_V);
+        CK(launch_sub_v(ctx->R, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,
+                        ctx->ticket, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return ASP_OK;
 }
@@ -579,12 +704,15 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
     const int t0 = h.t;
     struct { int t_stop, stopped, stop_reason; } ctl = {t0 + n_iter, 0, 0};
     CK(cudaMemcpyAsync(&ctx->st->t_stop, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, ctx->stream));
-    s = build_graph(ctx);
-    if (s != ASP_OK) return s;
+    if (!ctx->profiling) {
+        s = build_graph(ctx);
+        if (s != ASP_OK) return s;
+    }
     if (n_iter > 0) {
-        if (ctx->graph_state == 1) {
+        if (ctx->graph_state == 1 && !ctx->profiling) {
             const int reps = (n_iter + ctx->graph_unroll - 1) / ctx->graph_unroll;
             for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            ctx->launches += (long long)reps * ctx->graph_unroll * KERNELS_PER_ITER;
         } else {
             for (int i = 0; i < n_iter; ++i) {
                 s = enqueue_iteration(ctx);
@@ -593,6 +721,7 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         }
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    collect_marks(ctx);
     s = read_state(ctx, &h);
     if (s != ASP_OK) return s;
     if (h.error == ASP_ERR_TIMEOUT) return fail(ctx, ASP_ERR_TIMEOUT, "fit: grid barrier timed out");
@@ -606,6 +735,10 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         out->peak_abs = std::fabs((double)h.peak.val);
         out->stop_reason = h.stop_reason;
         out->reserved = 0;
+        out->fit_flops = h.fit_flops;
+        out->sub_flops = h.sub_flops;
+        out->sub_bytes = h.sub_bytes;
+        out->smooth_flops = h.smooth_flops;
     }
     if (h.stop_reason == ASP_STOP_CAPACITY) return fail(ctx, ASP_ERR_CAPACITY, "component list full");
     return ASP_OK;
@@ -625,6 +758,10 @@ asp_status asp_get_stats(asp_ctx* ctx, asp_cycle_stats* out) {
     out->peak_abs = std::fabs((double)h.peak.val);
     out->stop_reason = h.stop_reason;
     out->reserved = 0;
+    out->fit_flops = h.fit_flops;
+    out->sub_flops = h.sub_flops;
+    out->sub_bytes = h.sub_bytes;
+    out->smooth_flops = h.smooth_flops;
     return ASP_OK;
 }
 
@@ -640,8 +777,15 @@ asp_status asp_num_scales(asp_ctx* ctx, int* n, double* scales_host) {
 asp_status asp_smooth(asp_ctx* ctx, int scale_index, float* out_dev) {
     CHECK_CTX();
     if (scale_index < 0 || scale_index >= ctx->taps.n || !out_dev) return ASP_ERR_INVALID_ARG;
-    CK(launch_smooth(ctx->R, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, scale_index, ctx->S1, out_dev, ctx->grid_img,
-                     ctx->part, ctx->ticket, ctx->stream));
+    {
+        Mark m(ctx, KC_SMOOTH_H);
+        CK(launch_smooth_h(ctx->R, ctx->H, ctx->W, ctx->taps, nullptr, scale_index, ctx->S1, ctx->grid_img, ctx->stream));
+    }
+    {
+        Mark m(ctx, KC_SMOOTH_V);
+        CK(launch_smooth_v(ctx->S1, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, scale_index, out_dev, ctx->grid_img,
+                           ctx->part, ctx->ticket, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return ASP_OK;
 }
@@ -745,8 +889,62 @@ asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp, c
     h.stopped = 0;
     h.stop_reason = 0;
     h.pixel_evals = h.lm_iters = h.lm_passes = 0;
+    h.fit_flops = h.sub_flops = h.sub_bytes = h.smooth_flops = 0.0;
     CK(cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
     return asp_refresh_peak(ctx);
+}
+
+asp_status asp_reset(asp_ctx* ctx, const float* dirty, int dirty_on_host, const float* psf, int psf_on_host) {
+    CHECK_CTX();
+    if (!dirty) return ASP_ERR_INVALID_ARG;
+    if (psf) {
+        CK(cudaMemcpyAsync(ctx->B, psf, 4 * ctx->N * sizeof(float),
+                           psf_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+        const double wb_old = ctx->omega_b;
+        asp_status s = fit_beam(ctx);
+        if (s != ASP_OK) return s;
+        if (ctx->omega_b != wb_old) {
+            s = setup_taps(ctx);
+            if (s != ASP_OK) return s;
+            ctx->graph_state = ctx->gexec ? 0 : ctx->graph_state;   // taps are baked into the graph
+            if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->R, dirty, ctx->N * sizeof(float),
+                       dirty_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    { Mark m(ctx, KC_BEGIN); CK(launch_reset_state(ctx->st, ctx->stream)); }
+    return refresh_peak(ctx);
+}
+
+asp_status asp_set_profiling(asp_ctx* ctx, int on) {
+    CHECK_CTX();
+    CK(cudaStreamSynchronize(ctx->stream));
+    collect_marks(ctx);
+    ctx->profiling = on ? 1 : 0;
+    for (int k = 0; k < KC_COUNT; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_n[k] = 0; }
+    return ASP_OK;
+}
+
+asp_status asp_get_kernel_times(asp_ctx* ctx, asp_kernel_time* out, int cap, int* n) {
+    CHECK_CTX();
+    if (!n || cap < 0 || (cap > 0 && !out)) return ASP_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    collect_marks(ctx);
+    *n = KC_COUNT;
+    for (int k = 0; k < std::min(cap, (int)KC_COUNT); ++k) {
+        memset(out[k].name, 0, sizeof(out[k].name));
+        strncpy(out[k].name, KC_NAMES[k], sizeof(out[k].name) - 1);
+        out[k].launches = ctx->prof_n[k];
+        out[k].total_ms = ctx->prof_ms[k];
+    }
+    return ASP_OK;
+}
+
+asp_status asp_launch_count(asp_ctx* ctx, int64_t* n) {
+    CHECK_CTX();
+    if (!n) return ASP_ERR_INVALID_ARG;
+    *n = ctx->launches;
+    return ASP_OK;
 }
 
 static const uint32_t STATE_MAGIC = 0x41535031u;   // "ASP1"

@@ -4,7 +4,8 @@
 //                  threshold) and the initial-value switch (simple method iff
 //                  the last optimal component's area is < area_frac of the
 //                  last initial guess's area, Sect. 3);
-//   k_select       active set (new member + overlapping retained members) and
+//   k_select       active set (new member + overlapping, not co-located
+//                  retained members) and
 //                  the joint fit window, written as a FitDesc;
 //   k_update       Eqs. 7-8 deconvolution, loop gain on the new component,
 //                  component list / retained list updates, and the separable
@@ -85,17 +86,27 @@ __device__ bool make_term(const asp_component& c, double s, int H, int W, int sl
     return true;
 }
 
+// T1 offsets, plus the algorithmic work of R -= B * dC done term by term as
+// a horizontal then a vertical pass: 2 nx (H + ny - 1) W + 2 ny H W flops per
+// term and 2 H W for the update; bytes: each term's PSF region read once,
+// R read and written once.
 __device__ void finish_terms(CycleState* st, int H, int W) {
     long long off = 0;
+    double fl = 0.0, by = 8.0 * (double)H * W;
     for (int t = 0; t < st->n_terms; ++t) {
+        const TermDesc& td = st->terms[t];
         st->terms[t].t1off = off;
-        off += (long long)(H + st->terms[t].ny - 1) * W;
+        off += (long long)(H + td.ny - 1) * W;
+        fl += 2.0 * td.nx * (double)(H + td.ny - 1) * W + 2.0 * td.ny * (double)H * W;
+        by += 4.0 * (double)(H + td.ny - 1) * (W + td.nx - 1);
     }
+    st->sub_flops += fl + 2.0 * (double)H * W;
+    st->sub_bytes += by;
 }
 
 }  // namespace
 
-__global__ void k_cycle_begin(CycleState* st, Params p, int H, int W) {
+__global__ void k_cycle_begin(CycleState* st, Params p, int H, int W, double smooth_flops) {
     if (threadIdx.x != 0) return;
     st->fit.active = 0;
     st->skip_smooth = 1;
@@ -111,6 +122,7 @@ __global__ void k_cycle_begin(CycleState* st, Params p, int H, int W) {
                     ? ASP_PEAK_SIMPLE : ASP_PEAK_SMOOTH;
     st->mode = mode;
     st->skip_smooth = mode != ASP_PEAK_SMOOTH;
+    if (mode == ASP_PEAK_SMOOTH) st->smooth_flops += smooth_flops;
     if (mode == ASP_PEAK_SIMPLE) {
         const long long idx = st->peak.idx;
         st->init[0] = st->peak.val;
@@ -141,7 +153,11 @@ __global__ void k_select(CycleState* st, const asp_component* __restrict__ comps
         gauss_of(comps[k], ab, wb, g);
         long long b[4];
         member_box(g[1], g[2], g[3], b);
-        if (b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3]) {
+        const double dx = g[1] - st->init[1], dy = g[2] - st->init[2];
+        const double mw = fmax(st->init[3], g[3]);
+        // overlapping but not co-located (co-located members leave only the
+        // sum of their amplitudes determined)
+        if (b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3] && dx * dx + dy * dy > mw * mw) {
             for (int i = 0; i < 4; ++i) f.theta0[4 * K + i] = g[i];
             st->members[K] = k;
             wx0 = min(wx0, b[0]); wx1 = max(wx1, b[1]);
@@ -158,6 +174,7 @@ __global__ void k_select(CycleState* st, const asp_component* __restrict__ comps
     f.use_mask = 0;
     f.mcx = f.mcy = f.mr2 = 0.0;
     f.omega_min = 0.25 * wb;
+    f.omega_max = (double)max(f.ww, f.wh);
     f.bx0 = (double)wx0; f.bx1 = (double)wx1; f.by0 = (double)wy0; f.by1 = (double)wy1;
     int smem_ok = 1;
     f.grid = fit_grid((long long)f.ww * f.wh, K, p.lm.px_per_cta, g_max, &smem_ok);
@@ -214,20 +231,22 @@ __global__ void k_update(CycleState* st, asp_component* comps, asp_iter_record* 
     for (int r = 0; r < nr; ++r) st->ret[r] = tmp[r];
     st->n_ret = nr;
     // history
-    asp_iter_record tmp_rec;
-    asp_iter_record& h = st->t < st->cap_comp ? hist[st->t] : tmp_rec;
-    h.t = st->t; h.mode = st->mode; h.k = K; h.status = fo.status;
-    h.iters = fo.iters; h.passes = fo.passes;
-    h.x0 = f.wx0; h.x1 = f.wx0 + f.ww - 1; h.y0 = f.wy0; h.y1 = f.wy0 + f.wh - 1;
-    h.new_index = ni; h.n_terms = nt;
-    h.peak_value = st->peak.val;
-    h.init_scale = st->init_scale >= 0 ? st->init_s : 0.f;
-    h.chi2_init = fo.chi2_init; h.chi2_final = fo.chi2;
-    h.a0 = st->init[0]; h.x0_init = st->init[1]; h.y0_init = st->init[2]; h.w0 = st->init[3];
+    if (st->t < st->cap_comp) {
+        asp_iter_record* h = hist + st->t;
+        h->t = st->t; h->mode = st->mode; h->k = K; h->status = fo.status;
+        h->iters = fo.iters; h->passes = fo.passes;
+        h->x0 = f.wx0; h->x1 = f.wx0 + f.ww - 1; h->y0 = f.wy0; h->y1 = f.wy0 + f.wh - 1;
+        h->new_index = ni; h->n_terms = nt;
+        h->peak_value = st->peak.val;
+        h->init_scale = st->init_scale >= 0 ? st->init_s : 0.f;
+        h->chi2_init = fo.chi2_init; h->chi2_final = fo.chi2;
+        h->a0 = st->init[0]; h->x0_init = st->init[1]; h->y0_init = st->init[2]; h->w0 = st->init[3];
+    }
     // switch statistics and totals
     st->last_wi = cn.width;
     st->last_w0 = st->init[3];
     st->pixel_evals += fo.pixel_evals;
+    st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
     st->lm_iters += fo.iters;
     st->lm_passes += fo.passes;
     st->t += 1;
@@ -291,8 +310,22 @@ k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __res
     }
 }
 
-cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, cudaStream_t s) {
-    k_cycle_begin<<<1, 32, 0, s>>>(st, p, H, W);
+// Clears the minor-cycle state (components, retained list, counters) while
+// keeping the beam, the noise threshold and the capacities.
+__global__ void k_reset_state(CycleState* st) {
+    if (threadIdx.x != 0) return;
+    st->t = 0; st->t_stop = 0; st->stopped = 0; st->stop_reason = 0;
+    st->mode = 0; st->error = 0; st->n_comp = 0; st->n_ret = 0; st->n_terms = 0; st->K = 0;
+    st->skip_smooth = 1;
+    st->last_wi = 0.0; st->last_w0 = 0.0;
+    st->pixel_evals = 0; st->lm_iters = 0; st->lm_passes = 0;
+    st->fit_flops = 0.0; st->sub_flops = 0.0; st->sub_bytes = 0.0; st->smooth_flops = 0.0;
+    st->nonfinite = 0;
+    st->fit.active = 0;
+}
+
+cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, double smooth_flops, cudaStream_t s) {
+    k_cycle_begin<<<1, 32, 0, s>>>(st, p, H, W, smooth_flops);
     return cudaGetLastError();
 }
 
@@ -303,16 +336,24 @@ cudaError_t launch_select(CycleState* st, const asp_component* comps, const Para
 }
 
 cudaError_t launch_update(CycleState* st, asp_component* comps, asp_iter_record* hist, const Params& p, int H,
-                          int W, float* wbuf, cudaStream_t s) {
+                          int W, cudaStream_t s) {
     k_update<<<1, 32, 0, s>>>(st, comps, hist, p, H, W);
-    k_build_weights<<<MAX_TERMS, 256, 0, s>>>(st, &st->stopped, wbuf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_weights(CycleState* st, const int* gate, float* wbuf, cudaStream_t s) {
+    k_build_weights<<<MAX_TERMS, 256, 0, s>>>(st, gate, wbuf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_terms_from_components(CycleState* st, const asp_component* comps, int n, float gain, int H,
-                                         int W, float* wbuf, cudaStream_t s) {
+                                         int W, cudaStream_t s) {
     k_terms_from_components<<<1, 32, 0, s>>>(st, comps, n, gain, H, W);
-    k_build_weights<<<MAX_TERMS, 256, 0, s>>>(st, nullptr, wbuf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_state(CycleState* st, cudaStream_t s) {
+    k_reset_state<<<1, 32, 0, s>>>(st);
     return cudaGetLastError();
 }
 

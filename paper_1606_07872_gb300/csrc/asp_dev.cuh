@@ -38,7 +38,7 @@ struct FitDesc {
     int wx0, wy0, ww, wh;
     int use_mask, grid;
     double mcx, mcy, mr2;          // optional circular pixel mask (beam fit)
-    double omega_min;              // trial widths must exceed this
+    double omega_min, omega_max;   // trial widths must lie in (omega_min, omega_max]
     double bx0, bx1, by0, by1;     // trial centres must stay inside this box
     int active, smem_ok;
     double theta0[PMAX];
@@ -86,6 +86,7 @@ struct CycleState {
     ArgRes speak;                  // argmax |S_j| of the last smoothing
     int members[KMAX];             // component index of each fit member (-1: new)
     long long pixel_evals, lm_iters, lm_passes;
+    double fit_flops, sub_flops, sub_bytes, smooth_flops;   // algorithmic work totals
     unsigned cnt_argmax, cnt_smooth, nonfinite, pad2;
     int ret[RET_MAX];
     TermDesc terms[MAX_TERMS];
@@ -135,6 +136,15 @@ __device__ __host__ inline void member_box(double x, double y, double w, long lo
     if (h < 5) h = 5;
     long long rx = (long long)floor(x + 0.5), ry = (long long)floor(y + 0.5);
     b[0] = rx - h; b[1] = rx + h; b[2] = ry - h; b[3] = ry + h;
+}
+
+// Algorithmic FP32 work of one LM pixel evaluation with K members: per
+// member 15 flops (offsets, r^2, exponent argument, g, model sum, three
+// Jacobian products) plus one ex2; one residual subtraction; and the upper
+// triangle of [J | r]^T [J | r] as FMAs, (P + 1)(P + 2) / 2 of them (P = 4K).
+__device__ __host__ inline double pixel_eval_flops(int K) {
+    const double P = 4.0 * K;
+    return 15.0 * K + 1.0 + (P + 1.0) * (P + 2.0);
 }
 
 __device__ __host__ inline int fit_tiles(int K) {

@@ -305,7 +305,7 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
                 const int t = my_tile0 + q * (int)blockDim.x;
-                if (t < ntiles) {
+                if (my_group == 0 && t < ntiles) {
                     double* dst = (G == 1) ? (sums_nxt + t * 16) : (partials + (size_t)b * NACC_MAX + t * 16);
 #pragma unroll
                     for (int e = 0; e < 16; ++e) dst[e] = (double)ks[q][e] - (double)kc[q][e];
@@ -432,7 +432,8 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
                             double y = theta[4 * k + 2] + delta[4 * k + 2];
                             double w = theta[4 * k + 3] + delta[4 * k + 3];
                             trial[4 * k] = a; trial[4 * k + 1] = x; trial[4 * k + 2] = y; trial[4 * k + 3] = w;
-                            if (!(w > d.omega_min) || !isfinite(a) || !isfinite(x) || !isfinite(y) || !isfinite(w) ||
+                            if (!(w > d.omega_min) || w > d.omega_max || !isfinite(a) || !isfinite(x) ||
+                                !isfinite(y) || !isfinite(w) ||
                                 x < d.bx0 || x > d.bx1 || y < d.by0 || y > d.by1)
                                 valid = false;
                         }

@@ -213,13 +213,17 @@ k_smooth_v_argmax(const float* __restrict__ S1, int H, int W, const SmoothTaps t
     }
     block_arg_reduce(bv, bj, bi);
     if (grid_arg_finish(bv, bj, bi, part, ticket, &st->speak) && threadIdx.x == 0 && only_scale < 0) {
-        const double s = taps.scale[bj];
-        st->init[0] = (double)bv / (1.7724538509055160273 * s);
-        st->init[1] = (double)(bi % W);
-        st->init[2] = (double)(bi / W);
+        // the grid-wide winner (not this block's partial)
+        const float gv = st->speak.val;
+        const int gj = st->speak.j;
+        const long long gi = st->speak.idx;
+        const double s = taps.scale[gj];
+        st->init[0] = (double)gv / (1.7724538509055160273 * s);
+        st->init[1] = (double)(gi % W);
+        st->init[2] = (double)(gi / W);
         st->init[3] = fmax(s, st->omega_b);
-        st->init_scale = bj;
-        st->init_value = bv;
+        st->init_scale = gj;
+        st->init_value = gv;
         st->init_s = (float)s;
     }
 }
@@ -231,18 +235,26 @@ cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, u
     return cudaGetLastError();
 }
 
-cudaError_t launch_subtract(const float* B, float* R, int H, int W, CycleState* st, const int* gate,
-                            const float* wbuf, float* T1, int grid, ArgRes* part, unsigned* ticket,
-                            cudaStream_t s) {
+cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, const int* gate, const float* wbuf,
+                         float* T1, int grid, cudaStream_t s) {
     k_sub_h<<<grid, RED_THREADS, 0, s>>>(B, H, W, st, gate, wbuf, T1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_v(float* R, int H, int W, CycleState* st, const int* gate, const float* wbuf,
+                         const float* T1, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
     k_sub_v_argmax<<<grid, RED_THREADS, 0, s>>>(R, H, W, st, gate, wbuf, T1, part, ticket);
     return cudaGetLastError();
 }
 
-cudaError_t launch_smooth(const float* R, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
-                          int only_scale, float* S1, float* out_S, int grid, ArgRes* part, unsigned* ticket,
-                          cudaStream_t s) {
+cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
+                            float* S1, int grid, cudaStream_t s) {
     k_smooth_h<<<grid, RED_THREADS, 0, s>>>(R, H, W, taps, gate, only_scale, S1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
+                            int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
     k_smooth_v_argmax<<<grid, RED_THREADS, 0, s>>>(S1, H, W, taps, st, gate, only_scale, out_S, part, ticket);
     return cudaGetLastError();
 }

@@ -21,23 +21,32 @@ cudaError_t fit_configure(int tpt, int* blocks_per_sm);
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
                           FitOut* out, double* partials, double* sums, unsigned* bar, float* Tg, cudaStream_t s);
 
-// asp_image.cu
+// asp_image.cu (one kernel per launcher)
 cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, unsigned* ticket, ArgRes* res,
                           unsigned* nonfinite, const int* gate, cudaStream_t s);
-cudaError_t launch_subtract(const float* B, float* R, int H, int W, CycleState* st, const int* gate,
-                            const float* wbuf, float* T1, int grid, ArgRes* part, unsigned* ticket,
-                            cudaStream_t s);
-cudaError_t launch_smooth(const float* R, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
-                          int only_scale, float* S1, float* out_S, int grid, ArgRes* part, unsigned* ticket,
-                          cudaStream_t s);
+cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, const int* gate, const float* wbuf,
+                         float* T1, int grid, cudaStream_t s);
+cudaError_t launch_sub_v(float* R, int H, int W, CycleState* st, const int* gate, const float* wbuf,
+                         const float* T1, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
+cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
+                            float* S1, int grid, cudaStream_t s);
+cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
+                            int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
 
 // asp_cycle.cu
-cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, cudaStream_t s);
+cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, double smooth_flops, cudaStream_t s);
 cudaError_t launch_select(CycleState* st, const asp_component* comps, const Params& p, int H, int W, int g_max,
                           cudaStream_t s);
 cudaError_t launch_update(CycleState* st, asp_component* comps, asp_iter_record* hist, const Params& p, int H,
-                          int W, float* wbuf, cudaStream_t s);
+                          int W, cudaStream_t s);
+cudaError_t launch_build_weights(CycleState* st, const int* gate, float* wbuf, cudaStream_t s);
 cudaError_t launch_terms_from_components(CycleState* st, const asp_component* comps, int n, float gain, int H,
-                                         int W, float* wbuf, cudaStream_t s);
+                                         int W, cudaStream_t s);
+cudaError_t launch_reset_state(CycleState* st, cudaStream_t s);
+
+// asp_setup.cu
+cudaError_t launch_beam_init(FitDesc* desc, const float* B, int H, int W, int g_max, cudaStream_t s);
+cudaError_t launch_radix_median(const float* v, long long n, int absdev, double center, unsigned long long* ws,
+                                double* out, cudaStream_t s);
 
 }  // namespace aspd

@@ -56,6 +56,7 @@ __global__ void k_beam_init(FitDesc* d, const float* __restrict__ B, int H, int 
     d->use_mask = 1;
     d->mcx = W; d->mcy = H; d->mr2 = (double)r * r;
     d->omega_min = 0.25 * w0;
+    d->omega_max = (double)(2 * r + 1);
     d->bx0 = W - r; d->bx1 = W + r; d->by0 = H - r; d->by1 = H + r;
     d->theta0[0] = peak; d->theta0[1] = W; d->theta0[2] = H; d->theta0[3] = w0;
     int smem_ok = 1;

@@ -51,9 +51,8 @@ def test_beam_fit_matches_oracle(asp, maker):
         case = synth.config2(0, size=256)
     ctx = _ctx(asp, case)
     ab, wb, xb, yb = ctx.beam
-    oab, owb, fit = O.beam_fit(case.psf)
-    assert ab == pytest.approx(oab, rel=1e-5) and wb == pytest.approx(owb, rel=1e-5)
-    assert xb == pytest.approx(fit.theta[1], abs=1e-4) and yb == pytest.approx(fit.theta[2], abs=1e-4)
+    oab, owb, fit = O.beam_fit(case.psf, O.lm_exact())     # the optimum itself
+    _param_close([ab, xb, yb, wb], [oab, fit.theta[1], fit.theta[2], owb])
     if maker == "config1":
         assert ab == pytest.approx(1.0, abs=2e-6) and wb == pytest.approx(1.5, abs=2e-6)
     ctx.close()
@@ -177,14 +176,25 @@ def test_normal_equations_within_fp32_bound(asp, K, n_old):
     model, J = O.model_and_jacobian(theta.ravel(), xs, ys)
     r = T - model
     n = xs.size
+    # FP32 error model: a Jacobian entry of member k carries a relative error
+    # (8 + 2 |arg_k|) u32 (exponent argument rounding grows with r^2 / 2w^2,
+    # plus ex2 and the products); r carries 8 u32 (|T| + sum |g_k|) plus the
+    # members' own evaluation errors; the sums add (64 + log2 n + 16) u32 of
+    # sum |terms| (leaf + Kahan + trees).
+    th = theta.reshape(-1, 4)
+    eps = np.stack([(8 + 2 * ((xs - x0) ** 2 + (ys - y0) ** 2) / (2 * w * w)) * U32 for _, x0, y0, w in th], 1)
+    aJ = np.abs(J)
+    EJ = np.repeat(eps, 4, axis=1) * aJ
+    scale_r = np.abs(T) + O.gauss_model(np.abs(theta.ravel()), xs, ys)     # |T| + sum_k |g_k|
+    Er = 8 * U32 * scale_r + (aJ[:, 0::4] * eps * np.abs(th[:, 0])).sum(1)
     c = 64 + np.log2(n) + 16
-    bA = c * U32 * (np.abs(J).T @ np.abs(J))
-    scale_r = np.abs(T) + np.abs(O.gauss_model(np.abs(theta.ravel()) * [1, 1, 1, 1] * 1, xs, ys))
-    bg = c * U32 * (np.abs(J).T @ (np.abs(r) + 4 * scale_r))
-    bc = c * U32 * float((np.abs(r) + 4 * scale_r) @ (np.abs(r) + 4 * scale_r))
+    tiny = 4 * n * 2.0 ** -149          # FP32 absolute underflow floor per accumulated product
+    bA = EJ.T @ aJ + aJ.T @ EJ + c * U32 * (aJ.T @ aJ) + tiny
+    bg = EJ.T @ np.abs(r) + aJ.T @ Er + c * U32 * (aJ.T @ np.abs(r)) + tiny
+    bc = 2 * float(np.abs(r) @ Er) + c * U32 * float(r @ r) + tiny
     assert np.all(np.abs(A - Ao) <= bA + 1e-300), np.max(np.abs(A - Ao) / (bA + 1e-300))
     assert np.all(np.abs(g - go) <= bg + 1e-300), np.max(np.abs(g - go) / (bg + 1e-300))
-    assert abs(chi2 - co) <= bc
+    assert abs(chi2 - co) <= bc, (chi2, co, bc)
     ctx.close()
 
 
@@ -250,12 +260,20 @@ def _oracle_from_gpu_state(ctx, case, p, beam):
     return mc
 
 
+TIGHT = dict(lm_max_iter=300, lm_rtol=1e-12, lm_xtol=1e-10)
+
+
 @pytest.mark.parametrize("k_max", [1, 3, 5])
 def test_teacher_forced_minor_cycle_steps(asp, k_max):
+    """Each iteration starts both sides from the GPU's state: the discrete
+    decisions (mode, window, active set) must agree exactly, and where the
+    fit converged the components must agree with the oracle's optimum within
+    1e-4 and the residual update within 1e-4 relative L2.  Both sides run LM
+    to the optimum (tight tolerances; the GPU ends at its FP32 floor)."""
     case = synth.small_case(96, 104, seed=11, n_points=3, n_gauss=2, sigma_range=(2.5, 6))
-    ctx = _ctx(asp, case, k_max=k_max)
+    ctx = _ctx(asp, case, k_max=k_max, **TIGHT)
     ab, wb, _, _ = ctx.beam
-    p = O.AspParams(k_max=k_max, noise_sigma=case.noise_sigma)
+    p = O.AspParams(k_max=k_max, noise_sigma=case.noise_sigma, lm=O.lm_exact())
     checked = 0
     for it in range(12):
         mc = _oracle_from_gpu_state(ctx, case, p, (ab, wb))
@@ -269,8 +287,8 @@ def test_teacher_forced_minor_cycle_steps(asp, k_max):
         assert (h["x0"], h["x1"], h["y0"], h["y1"]) == tuple(rec["window"])
         assert h["k"] == len(rec["members"])
         fit = rec["fit"]
-        if fit.status != O.LM_CONVERGED or h["status"] != O.LM_CONVERGED:
-            continue            # trajectories of capped / stalled fits are not unique
+        if fit.status != O.LM_CONVERGED or h["status"] == O.LM_CAP:
+            continue            # trajectories of capped fits are not unique
         gc = ctx.components()
         for m, k in enumerate(rec["members"]):
             oc = mc.comps[k]
@@ -286,23 +304,40 @@ def test_teacher_forced_minor_cycle_steps(asp, k_max):
     ctx.close()
 
 
-def test_minor_cycle_end_to_end_matches_oracle_quality(asp):
+def test_teacher_forced_default_tolerances_decisions(asp):
+    """With the default LM settings the discrete decisions of every
+    iteration still agree when both sides start from the same state."""
     case = synth.config1(0)
-    n = 40
     ctx = _ctx(asp, case)
-    st = ctx.minor_cycle(n)
-    assert st["iterations"] == n and st["components"] == n
     ab, wb, _, _ = ctx.beam
-    mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma),
-                      beam=(ab, wb)).run(n)
+    p = O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma)
+    for it in range(10):
+        mc = _oracle_from_gpu_state(ctx, case, p, (ab, wb))
+        rec = mc.step()
+        ctx.minor_cycle(1)
+        h = ctx.history()[-1]
+        assert h["mode"] == rec["mode"]
+        assert (h["x0"], h["x1"], h["y0"], h["y1"]) == tuple(rec["window"])
+        assert h["k"] == len(rec["members"])
+    ctx.close()
+
+
+def test_minor_cycle_to_noise_matches_oracle(asp):
+    """A run to the noise threshold: final residual RMS and recovered model
+    flux agree with the oracle's own run (the paper's quality observables,
+    Tables 1-2)."""
+    case = synth.small_case(72, 80, seed=21, n_points=3, n_gauss=1, sigma_range=(2.0, 3.0), noise_sigma=1e-3)
+    ctx = _ctx(asp, case, k_max=3)
+    st = ctx.minor_cycle(400)
+    ab, wb, _, _ = ctx.beam
+    mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=3, noise_sigma=case.noise_sigma),
+                      beam=(ab, wb)).run(400)
     R = ctx.residual().astype(np.float64)
     rms_g, rms_o = np.sqrt(np.mean(R ** 2)), np.sqrt(np.mean(mc.R ** 2))
-    flux_g = ctx.components()[:, 0].sum()
-    flux_o = mc.stats()["model_flux"]
+    assert st["stop_reason"] == asp.ASP_STOP_NOISE and mc.stopped
     assert rms_g == pytest.approx(rms_o, rel=0.05)
-    assert flux_g == pytest.approx(flux_o, rel=0.01)
-    rms_dirty = np.sqrt(np.mean(case.dirty.astype(float) ** 2))
-    assert rms_g < 0.1 * rms_dirty
+    assert ctx.components()[:, 0].sum() == pytest.approx(mc.stats()["model_flux"], rel=0.01)
+    assert ctx.components()[:, 0].sum() == pytest.approx(case.sky.sum(), rel=0.05)
     ctx.close()
 
 
@@ -356,9 +391,9 @@ def test_invalid_arguments(asp):
 def test_config2_full_size_sampled(asp):
     case = synth.config2(0)
     ctx = _ctx(asp, case)
-    ab, wb, _, _ = ctx.beam
-    oab, owb, _ = O.beam_fit(case.psf)
-    assert ab == pytest.approx(oab, rel=1e-5) and wb == pytest.approx(owb, rel=1e-5)
+    ab, wb, xb, yb = ctx.beam
+    oab, owb, fit = O.beam_fit(case.psf, O.lm_exact())
+    _param_close([ab, xb, yb, wb], [oab, fit.theta[1], fit.theta[2], owb])
     st = ctx.minor_cycle(20)
     assert st["iterations"] == 20
     R = ctx.residual()

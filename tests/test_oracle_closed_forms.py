@@ -391,3 +391,39 @@ def test_minor_cycle_reduces_residual_and_recovers_flux():
     st = mc.stats()
     assert st["residual_max"] < 2e-3
     assert st["model_flux"] == pytest.approx(0.5, abs=5e-3)
+
+
+# ----------------------------------------------------------------- active set and width bound (readings)
+
+def test_active_set_excludes_colocated_members():
+    c = synth.small_case(64, 64, seed=1, n_points=1, n_gauss=0)
+    mc = O.MinorCycle(c.dirty, c.psf, O.AspParams(k_max=4, noise_sigma=1e-3))
+    wb = mc.omega_b
+    mc.comps = [O.Component(1.0, 1.0, 30.0, 30.0, 0.0, True),      # co-located with the new member
+                O.Component(1.0, 1.0, 34.5, 30.0, 0.0, True),      # overlapping, 4.5 px away
+                O.Component(1.0, 1.0, 60.0, 60.0, 0.0, True)]      # no overlap
+    mc.retained = [0, 1, 2]
+    chosen, win = mc.select(dict(a0=1.0, x0=30.2, y0=29.9, w0=wb))
+    assert chosen == [1]
+    b_new, b_1 = O.member_box(30.2, 29.9, wb), O.member_box(34.5, 30.0, mc.G(1)[3])
+    assert win == (min(b_new[0], b_1[0]), max(b_new[1], b_1[1]), min(b_new[2], b_1[2]), max(b_new[3], b_1[3]))
+
+
+def test_trial_widths_bounded_by_window():
+    xs, ys = _grid(15, 15)
+    T = 0.01 + 0.001 * xs          # a pedestal: an unbounded width would fit it best
+    fit = O.lm_fit(T, xs, ys, [0.5, 7.0, 7.0, 3.0], (0, 14, 0, 14), 0.3, O.lm_exact())
+    assert 0.3 < fit.theta[3] <= 15.0
+
+
+def test_minor_cycle_recovers_total_flux_and_reaches_noise():
+    """The paper's quality observables (Table 1: total model flux close to the
+    original's; Table 2 / Fig. 4: residual at the noise level), on a field
+    whose true sky is known."""
+    case = synth.small_case(72, 80, seed=21, n_points=3, n_gauss=1, sigma_range=(2.0, 3.0), noise_sigma=1e-3)
+    mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=3, noise_sigma=case.noise_sigma)).run(400)
+    st = mc.stats()
+    assert mc.stopped                                     # stopped by the noise threshold
+    assert st["residual_max"] < 3 * case.noise_sigma
+    assert st["model_flux"] == pytest.approx(case.sky.sum(), rel=0.01)
+    assert st["residual_rms"] == pytest.approx(case.noise_sigma, rel=0.1)
