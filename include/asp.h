@@ -134,6 +134,13 @@ typedef struct {
      * once + residual read and written once; smoothing 4 (2m+1) H W flops
      * per scale and smoothing iteration. */
     double fit_flops, sub_flops, sub_bytes, smooth_flops;
+    /* Wall time of the LM fits split into pixel passes, reductions (CTA and
+     * cross-CTA, barriers included) and LM logic + damped solves, as seen by
+     * the fit kernel's first CTA (%globaltimer). */
+    double fit_pass_ms, fit_reduce_ms, fit_solve_ms;
+    double fit_factor_ms, fit_subst_ms;   /* parts of fit_solve_ms: damped solves, LM bookkeeping */
+    int64_t fit_refinements;  /* FP64 iterative-refinement steps of the FP32-factored solves */
+    int64_t fit_fallbacks;    /* solves that fell back to an FP64 factor */
 } asp_cycle_stats;
 
 /* One minor-cycle iteration as recorded on the device. */
@@ -226,6 +233,12 @@ asp_status asp_get_state(asp_ctx* ctx, asp_component* comps, int comp_cap, int* 
 asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp,
                          const int* retained, int n_ret, int64_t t, double last_wi,
                          double last_w0);
+/* The most recent LM fit of this context (minor-cycle iteration or
+ * asp_fit_active_set): the fitted PSF-convolved Gaussians, members in fit
+ * order (new member first in a minor cycle), and its outcome.  Copies
+ * min(cap, n) rows to host memory and sets *n to the member count. */
+asp_status asp_get_last_fit(asp_ctx* ctx, asp_gauss* out_host, int cap, int* n, asp_fit_info* info);
+
 /* Restart on a new dirty image of the same size without reallocating: copies
  * it into the residual, clears the component list, retained list, iteration
  * counter and totals and finds the first peak.  If psf is not NULL it is

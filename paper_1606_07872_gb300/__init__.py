@@ -26,6 +26,7 @@ __all__ = [
     "asp_find_peak", "asp_fit_active_set", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
+    "asp_get_last_fit",
     "Context",
 ]
 
@@ -265,6 +266,16 @@ def asp_set_state(h, comps, retained: Sequence[int], t: int, last_wi: float, las
            "asp_set_state", h)
 
 
+def asp_get_last_fit(h):
+    """The most recent fit: (rows (a, x, y, w) in member order, info dict)."""
+    n = C.c_int()
+    arr = (asp_gauss * ASP_KMAX)()
+    info = asp_fit_info()
+    _check(lib().asp_get_last_fit(h, arr, ASP_KMAX, C.byref(n), C.byref(info)), "asp_get_last_fit", h)
+    return (np.array([[g.amp, g.x, g.y, g.width] for g in arr[: n.value]]),
+            {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_})
+
+
 def asp_save_state(h, path: str):
     _check(lib().asp_save_state(h, os.fsencode(path)), "asp_save_state", h)
 
@@ -347,6 +358,9 @@ class Context:
 
     def state(self):
         return asp_get_state(self.h)
+
+    def last_fit(self):
+        return asp_get_last_fit(self.h)
 
     def set_state(self, comps, retained, t, last_wi, last_w0):
         asp_set_state(self.h, comps, retained, t, last_wi, last_w0)

@@ -54,7 +54,10 @@ class asp_cycle_stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("components", C.c_int64), ("pixel_evals", C.c_int64),
                 ("lm_iters", C.c_int64), ("lm_passes", C.c_int64), ("peak_abs", C.c_double),
                 ("stop_reason", C.c_int32), ("reserved", C.c_int32), ("fit_flops", C.c_double),
-                ("sub_flops", C.c_double), ("sub_bytes", C.c_double), ("smooth_flops", C.c_double)]
+                ("sub_flops", C.c_double), ("sub_bytes", C.c_double), ("smooth_flops", C.c_double),
+                ("fit_pass_ms", C.c_double), ("fit_reduce_ms", C.c_double), ("fit_solve_ms", C.c_double),
+                ("fit_factor_ms", C.c_double), ("fit_subst_ms", C.c_double), ("fit_refinements", C.c_int64),
+                ("fit_fallbacks", C.c_int64)]
 
 
 class asp_iter_record(C.Structure):
@@ -100,6 +103,7 @@ SIGNATURES = {
                       C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "asp_set_state": [_P, C.POINTER(asp_component), _I, C.POINTER(_I), _I, C.c_int64, C.c_double, C.c_double],
     "asp_reset": [_P, _P, _I, _P, _I],
+    "asp_get_last_fit": [_P, C.POINTER(asp_gauss), _I, C.POINTER(_I), C.POINTER(asp_fit_info)],
     "asp_set_profiling": [_P, _I],
     "asp_get_kernel_times": [_P, C.POINTER(asp_kernel_time), _I, C.POINTER(_I)],
     "asp_launch_count": [_P, C.POINTER(C.c_int64)],

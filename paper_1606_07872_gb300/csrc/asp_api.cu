@@ -225,7 +225,8 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(st, &st->stopped, ctx->wbuf, s)); }
     { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, s)); }
     { Mark m(ctx, KC_SUB_V);
-      CK(launch_sub_v(ctx->R, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part, ctx->ticket, s)); }
+      CK(launch_sub_v(ctx->R, ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part, ctx->ticket,
+                      s)); }
     return ASP_OK;
 }
 
@@ -688,7 +689,7 @@ asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float g
     { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->stream)); }
     {
         Mark m(ctx, KC_SUB_V);
-        CK(launch_sub_v(ctx->R, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,
+        CK(launch_sub_v(ctx->R, ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,
                         ctx->ticket, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -739,6 +740,13 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         out->sub_flops = h.sub_flops;
         out->sub_bytes = h.sub_bytes;
         out->smooth_flops = h.smooth_flops;
+        out->fit_pass_ms = h.fit_ns_pass * 1e-6;
+        out->fit_reduce_ms = h.fit_ns_reduce * 1e-6;
+        out->fit_solve_ms = h.fit_ns_solve * 1e-6;
+        out->fit_factor_ms = h.fit_ns_factor * 1e-6;
+        out->fit_subst_ms = h.fit_ns_subst * 1e-6;
+        out->fit_refinements = h.fit_refinements;
+        out->fit_fallbacks = h.fit_fallbacks;
     }
     if (h.stop_reason == ASP_STOP_CAPACITY) return fail(ctx, ASP_ERR_CAPACITY, "component list full");
     return ASP_OK;
@@ -762,6 +770,13 @@ asp_status asp_get_stats(asp_ctx* ctx, asp_cycle_stats* out) {
     out->sub_flops = h.sub_flops;
     out->sub_bytes = h.sub_bytes;
     out->smooth_flops = h.smooth_flops;
+    out->fit_pass_ms = h.fit_ns_pass * 1e-6;
+    out->fit_reduce_ms = h.fit_ns_reduce * 1e-6;
+    out->fit_solve_ms = h.fit_ns_solve * 1e-6;
+    out->fit_factor_ms = h.fit_ns_factor * 1e-6;
+    out->fit_subst_ms = h.fit_ns_subst * 1e-6;
+    out->fit_refinements = h.fit_refinements;
+    out->fit_fallbacks = h.fit_fallbacks;
     return ASP_OK;
 }
 
@@ -890,8 +905,39 @@ asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp, c
     h.stop_reason = 0;
     h.pixel_evals = h.lm_iters = h.lm_passes = 0;
     h.fit_flops = h.sub_flops = h.sub_bytes = h.smooth_flops = 0.0;
+    h.fit_ns_pass = h.fit_ns_reduce = h.fit_ns_solve = h.fit_ns_factor = h.fit_ns_subst = 0;
+    h.fit_refinements = h.fit_fallbacks = 0;
     CK(cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
     return asp_refresh_peak(ctx);
+}
+
+asp_status asp_get_last_fit(asp_ctx* ctx, asp_gauss* out, int cap, int* n, asp_fit_info* info) {
+    CHECK_CTX();
+    if (!n || cap < 0 || (cap > 0 && !out)) return ASP_ERR_INVALID_ARG;
+    CycleState h;
+    asp_status s = read_state(ctx, &h);
+    if (s != ASP_OK) return s;
+    const int K = h.fit.K;
+    *n = K;
+    for (int k = 0; k < std::min(cap, K); ++k) {
+        out[k].amp = h.fout.theta[4 * k];
+        out[k].x = h.fout.theta[4 * k + 1];
+        out[k].y = h.fout.theta[4 * k + 2];
+        out[k].width = h.fout.theta[4 * k + 3];
+    }
+    if (info) {
+        info->iters = h.fout.iters;
+        info->passes = h.fout.passes;
+        info->status = h.fout.status;
+        info->k = K;
+        info->x0 = h.fit.wx0; info->x1 = h.fit.wx0 + h.fit.ww - 1;
+        info->y0 = h.fit.wy0; info->y1 = h.fit.wy0 + h.fit.wh - 1;
+        info->chi2_init = h.fout.chi2_init;
+        info->chi2_final = h.fout.chi2;
+        info->lambda = h.fout.lambda;
+        info->pixel_evals = h.fout.pixel_evals;
+    }
+    return ASP_OK;
 }
 
 asp_status asp_reset(asp_ctx* ctx, const float* dirty, int dirty_on_host, const float* psf, int psf_on_host) {

@@ -86,20 +86,42 @@ __device__ bool make_term(const asp_component& c, double s, int H, int W, int sl
     return true;
 }
 
-// T1 offsets, plus the algorithmic work of R -= B * dC done term by term as
-// a horizontal then a vertical pass: 2 nx (H + ny - 1) W + 2 ny H W flops per
-// term and 2 H W for the update; bytes: each term's PSF region read once,
-// R read and written once.
+// Point-like terms become bilinear deposits (weights (1-f, f) per axis,
+// clipped to the image); extended terms get T1 offsets for the separable
+// passes.  Also the algorithmic work of R -= B * dC: per extended term
+// 2 nx (H + ny - 1) W + 2 ny H W flops, per deposit 2 H W, plus 2 H W for the
+// update; bytes: each term's PSF region read once, R read and written once.
 __device__ void finish_terms(CycleState* st, int H, int W) {
     long long off = 0;
     double fl = 0.0, by = 8.0 * (double)H * W;
+    int nd = 0;
     for (int t = 0; t < st->n_terms; ++t) {
-        const TermDesc& td = st->terms[t];
-        st->terms[t].t1off = off;
-        off += (long long)(H + td.ny - 1) * W;
-        fl += 2.0 * td.nx * (double)(H + td.ny - 1) * W + 2.0 * td.ny * (double)H * W;
-        by += 4.0 * (double)(H + td.ny - 1) * (W + td.nx - 1);
+        TermDesc& td = st->terms[t];
+        if (td.bilinear) {
+            const double fx0 = floor(td.cx), fy0 = floor(td.cy);
+            const double fx = td.cx - fx0, fy = td.cy - fy0;
+            for (int j = 0; j < 2; ++j)
+                for (int i = 0; i < 2; ++i) {
+                    const long long qx = (long long)fx0 + i, qy = (long long)fy0 + j;
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= H || nd >= MAX_DEPOSITS) continue;
+                    const double w = (double)td.scale * (i ? fx : 1.0 - fx) * (j ? fy : 1.0 - fy);
+                    st->dep[nd].qx = (int)qx;
+                    st->dep[nd].qy = (int)qy;
+                    st->dep[nd].w = (float)w;
+                    st->dep[nd].pad = 0;
+                    ++nd;
+                    fl += 2.0 * (double)H * W;
+                    by += 4.0 * (double)H * W;
+                }
+            td.t1off = -1;
+        } else {
+            td.t1off = off;
+            off += (long long)(H + td.ny - 1) * W;
+            fl += 2.0 * td.nx * (double)(H + td.ny - 1) * W + 2.0 * td.ny * (double)H * W;
+            by += 4.0 * (double)(H + td.ny - 1) * (W + td.nx - 1);
+        }
     }
+    st->n_dep = nd;
     st->sub_flops += fl + 2.0 * (double)H * W;
     st->sub_bytes += by;
 }
@@ -137,34 +159,61 @@ __global__ void k_cycle_begin(CycleState* st, Params p, int H, int W, double smo
 
 __global__ void k_select(CycleState* st, const asp_component* __restrict__ comps, Params p, int H, int W,
                          int g_max) {
-    if (threadIdx.x != 0) return;
+    // one warp: lanes test 32 retained members at a time; the first ones in
+    // list order (most recent first) are taken, as in a sequential scan
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     if (st->stopped) return;
     FitDesc& f = st->fit;
     const double ab = st->alpha_b, wb = st->omega_b;
+    const double ix = st->init[1], iy = st->init[2], iw = st->init[3];
     long long nb[4];
-    member_box(st->init[1], st->init[2], st->init[3], nb);
+    member_box(ix, iy, iw, nb);
     long long wx0 = nb[0], wx1 = nb[1], wy0 = nb[2], wy1 = nb[3];
-    for (int i = 0; i < 4; ++i) f.theta0[i] = st->init[i];
-    st->members[0] = -1;
+    if (lane == 0) {
+        for (int i = 0; i < 4; ++i) f.theta0[i] = st->init[i];
+        st->members[0] = -1;
+    }
     int K = 1;
-    for (int r = 0; r < st->n_ret && K < p.k_max; ++r) {
-        const int k = st->ret[r];
-        double g[4];
-        gauss_of(comps[k], ab, wb, g);
-        long long b[4];
-        member_box(g[1], g[2], g[3], b);
-        const double dx = g[1] - st->init[1], dy = g[2] - st->init[2];
-        const double mw = fmax(st->init[3], g[3]);
-        // overlapping but not co-located (co-located members leave only the
-        // sum of their amplitudes determined)
-        if (b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3] && dx * dx + dy * dy > mw * mw) {
-            for (int i = 0; i < 4; ++i) f.theta0[4 * K + i] = g[i];
-            st->members[K] = k;
-            wx0 = min(wx0, b[0]); wx1 = max(wx1, b[1]);
-            wy0 = min(wy0, b[2]); wy1 = max(wy1, b[3]);
+    const int n_ret = st->n_ret;
+    for (int base = 0; base < n_ret && K < p.k_max; base += 32) {
+        const int r = base + lane;
+        double g[4] = {0, 0, 0, 0};
+        long long b[4] = {0, 0, 0, 0};
+        int k = -1;
+        bool ok = false;
+        if (r < n_ret) {
+            k = st->ret[r];
+            gauss_of(comps[k], ab, wb, g);
+            member_box(g[1], g[2], g[3], b);
+            const double dx = g[1] - ix, dy = g[2] - iy;
+            const double mw = fmax(iw, g[3]);
+            // overlapping but not co-located (co-located members leave only
+            // the sum of their amplitudes determined)
+            ok = b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3] && dx * dx + dy * dy > mw * mw;
+        }
+        unsigned mask = __ballot_sync(FULL, ok);
+        while (mask != 0u && K < p.k_max) {
+            const int src = __ffs(mask) - 1;
+            double gs[4];
+            long long bs[4];
+            for (int i = 0; i < 4; ++i) {
+                gs[i] = __shfl_sync(FULL, g[i], src);
+                bs[i] = __shfl_sync(FULL, b[i], src);
+            }
+            const int ks = __shfl_sync(FULL, k, src);
+            if (lane == 0) {
+                for (int i = 0; i < 4; ++i) f.theta0[4 * K + i] = gs[i];
+                st->members[K] = ks;
+            }
+            wx0 = min(wx0, bs[0]); wx1 = max(wx1, bs[1]);
+            wy0 = min(wy0, bs[2]); wy1 = max(wy1, bs[3]);
             ++K;
+            mask &= mask - 1u;
         }
     }
+    if (lane != 0) return;
     wx0 = max(wx0, 0LL); wy0 = max(wy0, 0LL);
     wx1 = min(wx1, (long long)W - 1); wy1 = min(wy1, (long long)H - 1);
     f.K = K;
@@ -248,6 +297,13 @@ __global__ void k_update(CycleState* st, asp_component* comps, asp_iter_record* 
     st->pixel_evals += fo.pixel_evals;
     st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
     st->lm_iters += fo.iters;
+    st->fit_ns_pass += fo.ns_pass;
+    st->fit_ns_reduce += fo.ns_reduce;
+    st->fit_ns_solve += fo.ns_solve;
+    st->fit_ns_factor += fo.ns_factor;
+    st->fit_ns_subst += fo.ns_subst;
+    st->fit_refinements += fo.refinements;
+    st->fit_fallbacks += fo.fallbacks;
     st->lm_passes += fo.passes;
     st->t += 1;
 }
@@ -271,6 +327,7 @@ k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __res
     const int t = blockIdx.x;
     if (t >= st->n_terms) return;
     const TermDesc td = st->terms[t];
+    if (td.bilinear) return;          // applied as deposits, no axis weights
     __shared__ double red[256];
     for (int axis = 0; axis < 2; ++axis) {
         const double c = axis == 0 ? td.cx : td.cy;
@@ -320,6 +377,8 @@ __global__ void k_reset_state(CycleState* st) {
     st->last_wi = 0.0; st->last_w0 = 0.0;
     st->pixel_evals = 0; st->lm_iters = 0; st->lm_passes = 0;
     st->fit_flops = 0.0; st->sub_flops = 0.0; st->sub_bytes = 0.0; st->smooth_flops = 0.0;
+    st->fit_ns_pass = 0; st->fit_ns_reduce = 0; st->fit_ns_solve = 0; st->fit_ns_factor = 0; st->fit_ns_subst = 0;
+    st->fit_refinements = 0; st->fit_fallbacks = 0;
     st->nonfinite = 0;
     st->fit.active = 0;
 }

@@ -49,6 +49,9 @@ struct FitOut {
     double chi2_init, chi2, lambda;
     int iters, passes, status, error;
     long long pixel_evals;
+    long long ns_pass, ns_reduce, ns_solve;   // time split of the fit (CTA 0)
+    long long ns_factor, ns_subst;            // parts of ns_solve: damped solves, LM logic
+    int refinements, fallbacks;               // FP64 refinement steps, FP64-factor fallbacks
 };
 
 // A separable subtraction term: image value scale * wx[i] * wy[j] at
@@ -64,6 +67,14 @@ struct TermDesc {
     int ux0, ux1, uy0, uy1;        // unclipped support (normalisation range)
     int pad;
 };
+
+// One bilinear point deposit of dC: weight w at image pixel (qx, qy).
+struct Deposit {
+    int qx, qy;
+    float w;
+    int pad;
+};
+constexpr int MAX_DEPOSITS = 4 * MAX_TERMS;
 
 struct ArgRes {                    // argmax of |v| with its signed value
     float val;
@@ -87,9 +98,14 @@ struct CycleState {
     int members[KMAX];             // component index of each fit member (-1: new)
     long long pixel_evals, lm_iters, lm_passes;
     double fit_flops, sub_flops, sub_bytes, smooth_flops;   // algorithmic work totals
+    long long fit_ns_pass, fit_ns_reduce, fit_ns_solve;     // fit time split
+    long long fit_ns_factor, fit_ns_subst;
+    long long fit_refinements, fit_fallbacks;
     unsigned cnt_argmax, cnt_smooth, nonfinite, pad2;
     int ret[RET_MAX];
     TermDesc terms[MAX_TERMS];
+    int n_dep, pad3;
+    Deposit dep[MAX_DEPOSITS];     // point-like terms as bilinear deposits
     FitDesc fit;
     FitOut fout;
 };
@@ -154,10 +170,12 @@ __device__ __host__ inline int fit_tiles(int K) {
     return nb * (nb + 1) / 2;
 }
 
-// CTAs a fit of K members over Wn pixels uses.
+// CTAs a fit of K members over Wn pixels uses: enough pixels per CTA that
+// one pass is ~0.6 M accumulator FMAs (a few microseconds on one SM), so
+// small fits run on one CTA without grid barriers and large ones spread.
 __device__ __host__ inline int fit_grid(long long Wn, int K, int px_per_cta, int g_max, int* smem_ok) {
     int NAp = ((4 * K + 1) + 3) & ~3;
-    long long target = px_per_cta > 0 ? px_per_cta : 65536 / (NAp * NAp);
+    long long target = px_per_cta > 0 ? px_per_cta : 1200000 / (NAp * NAp);
     if (target < 256) target = 256;
     if (target > PX_SMEM) target = PX_SMEM;
     long long g = (Wn + target - 1) / target;

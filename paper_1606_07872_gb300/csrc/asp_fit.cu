@@ -34,6 +34,12 @@ struct MemberFrame {
     int cx, cy;
 };
 
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ int pidx(int i, int j) { return i * (i + 1) / 2 + j; }   // packed lower, j <= i
 
 __device__ __forceinline__ int tile_index(int bi, int bj, int nb) { return bi * nb - bi * (bi - 1) / 2 + (bj - bi); }
@@ -68,69 +74,260 @@ __device__ void grid_barrier(unsigned* bar, unsigned target, int* s_err, int* g_
 __device__ __forceinline__ void make_frame(const double* th, MemberFrame& f) {
     double a = th[0], x = th[1], y = th[2], w = th[3];
     double cx = floor(x + 0.5), cy = floor(y + 0.5);
+    const double iw = 1.0 / w, iw2 = iw * iw;
     f.a = (float)a;
-    f.c = (float)(LOG2E / (2.0 * w * w));
-    f.iw2 = (float)(1.0 / (w * w));
-    f.iw3 = (float)(1.0 / (w * w * w));
+    f.c = (float)(0.5 * LOG2E * iw2);
+    f.iw2 = (float)iw2;
+    f.iw3 = (float)(iw2 * iw);
     f.fx = (float)(x - cx);
     f.fy = (float)(y - cy);
     f.cx = (int)cx;
     f.cy = (int)cy;
 }
 
-// Cholesky factorisation of the packed lower matrix M (P x P) in place, all
-// threads of the block.  Returns false if a pivot is not positive.
-__device__ bool cholesky_packed(double* M, int P, double* inv_diag, int* s_flag) {
-    const int tid = threadIdx.x;
-    for (int j = 0; j < P; ++j) {
+// Pivot l = sqrt(d) and 1/l.  FP32 (the refined factor): rsqrtf, whose
+// few-ulp error the FP64 refinement removes; FP64: correctly rounded.
+__device__ __forceinline__ void pivot(float d, float& l, float& il) { il = rsqrtf(d); l = d * il; }
+__device__ __forceinline__ void pivot(double d, double& l, double& il) { l = sqrt(d); il = 1.0 / l; }
+
+// Cholesky factorisation of the packed lower matrix M in place: columns
+// 0..P-1 of rows 0..nrows-1 (nrows = P + 1 carries a right-hand side b as
+// row P, which comes out as L^-1 b: the forward substitution fused into the
+// factorisation).  Blocked right-looking with 4-column panels: thread 0
+// factors the 4x4 diagonal block, one thread per row solves the panel, and
+// the trailing rank-4 update runs one row per warp, one column per lane.
+// Three block barriers per panel.  Returns false if a pivot is not positive.
+template <class T>
+__device__ bool cholesky_packed(T* M, int P, int nrows, T* inv_diag, int* s_flag) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll 1
+    for (int j0 = 0; j0 < P; j0 += 4) {
+        const int nbk = min(4, P - j0);
         if (tid == 0) {
-            double d = M[pidx(j, j)];
-            if (!(d > 0.0) || !isfinite(d)) {
-                *s_flag = 1;
-            } else {
-                double l = sqrt(d);
-                M[pidx(j, j)] = l;
-                inv_diag[j] = 1.0 / l;
+#pragma unroll 1
+            for (int c = 0; c < nbk; ++c) {
+                const int jc = j0 + c;
+                const T d = M[pidx(jc, jc)];
+                if (!(d > T(0)) || !isfinite(d)) { *s_flag = 1; break; }
+                T l, il;
+                pivot(d, l, il);
+                M[pidx(jc, jc)] = l;
+                inv_diag[jc] = il;
+                for (int r = c + 1; r < nbk; ++r) M[pidx(j0 + r, jc)] *= il;
+                for (int r = c + 1; r < nbk; ++r)
+                    for (int s = c + 1; s <= r; ++s) M[pidx(j0 + r, j0 + s)] -= M[pidx(j0 + r, jc)] * M[pidx(j0 + s, jc)];
             }
         }
         __syncthreads();
         if (*s_flag) return false;
-        const double il = inv_diag[j];
-        for (int i = j + 1 + tid; i < P; i += blockDim.x) M[pidx(i, j)] *= il;
+        const int r0 = j0 + nbk;
+        for (int i = r0 + tid; i < nrows; i += blockDim.x) {      // panel rows below the block
+            T* row = M + pidx(i, 0);
+#pragma unroll 1
+            for (int c = 0; c < nbk; ++c) {
+                T v = row[j0 + c];
+                for (int t = 0; t < c; ++t) v -= row[j0 + t] * M[pidx(j0 + c, j0 + t)];
+                row[j0 + c] = v * inv_diag[j0 + c];
+            }
+        }
         __syncthreads();
-        const int m = P - j - 1;
-        const int total = m * (m + 1) / 2;
-        for (int q = tid; q < total; q += blockDim.x) {
-            int ii = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-            while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
-            while (ii * (ii + 1) / 2 > q) --ii;
-            int kk = q - ii * (ii + 1) / 2;
-            int i = j + 1 + ii, k = j + 1 + kk;
-            M[pidx(i, k)] -= M[pidx(i, j)] * M[pidx(k, j)];
+        for (int i = r0 + warp; i < nrows; i += nwarp) {         // trailing rank-nbk update
+            T* row = M + pidx(i, 0);
+            T li[4];
+            for (int c = 0; c < 4; ++c) li[c] = c < nbk ? row[j0 + c] : T(0);
+            const int kmax = min(i, P - 1);
+            for (int k = r0 + lane; k <= kmax; k += 32) {
+                const T* rk = M + pidx(k, 0) + j0;
+                T acc = row[k];
+                for (int c = 0; c < nbk; ++c) acc -= li[c] * rk[c];
+                row[k] = acc;
+            }
         }
         __syncthreads();
     }
     return true;
 }
 
-// Solve L L^T x = b with warp 0 (b overwritten by x).
-__device__ void chol_solve_warp(const double* M, int P, const double* inv_diag, double* b) {
+// Triangular solves with warp 0, the right-hand side held in registers
+// (lane l owns entries l, l+32, l+64, l+96), four unknowns per step: the
+// four are broadcast by shuffle, every lane solves the 4x4 diagonal block
+// redundantly, then updates its own entries.  No warp barriers (a
+// __syncwarp round costs ~200 cycles on this part, a shuffle ~30).
+// mode 1: forward (L y = b), 2: backward (L^T x = y), 3: both.
+template <class T>
+__device__ __forceinline__ T slot_get(const T (&v)[4], int s) { return s == 0 ? v[0] : s == 1 ? v[1] : s == 2 ? v[2] : v[3]; }
+
+template <class T>
+__device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ inv_diag, T* b, int mode) {
     if (threadIdx.x >= 32) return;
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x;
-    for (int j = 0; j < P; ++j) {                 // L y = b
-        double yj = b[j] * inv_diag[j];
-        __syncwarp();
-        if (lane == 0) b[j] = yj;
-        for (int i = j + 1 + lane; i < P; i += 32) b[i] -= M[pidx(i, j)] * yj;
-        __syncwarp();
+    T v[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) v[s] = lane + 32 * s < P ? b[lane + 32 * s] : T(0);
+    if (mode & 1) {
+#pragma unroll 1
+        for (int j0 = 0; j0 < P; j0 += 4) {
+            const int nb = min(4, P - j0), slot = j0 >> 5, l0 = j0 & 31;
+            const T vs = slot_get(v, slot);
+            T y[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) y[c] = __shfl_sync(FULL, vs, l0 + c);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c < nb) {
+                    T a = y[c];
+#pragma unroll
+                    for (int t = 0; t < c; ++t) a -= M[pidx(j0 + c, j0 + t)] * y[t];
+                    y[c] = a * inv_diag[j0 + c];
+                } else {
+                    y[c] = T(0);
+                }
+            }
+            // owners keep the solved values; everyone below updates
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int i = lane + 32 * s;
+                if (s == slot && i >= j0 && i < j0 + nb) v[s] = slot_get(y, i - j0);
+                if (i >= j0 + nb && i < P) {
+                    const T* ri = M + pidx(i, 0) + j0;
+                    T a = v[s];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (c < nb) a -= ri[c] * y[c];
+                    v[s] = a;
+                }
+            }
+        }
     }
-    for (int j = P - 1; j >= 0; --j) {            // L^T x = y
-        double xj = b[j] * inv_diag[j];
-        __syncwarp();
-        if (lane == 0) b[j] = xj;
-        for (int i = lane; i < j; i += 32) b[i] -= M[pidx(j, i)] * xj;
-        __syncwarp();
+    if (mode & 2) {
+        const int last = ((P - 1) / 4) * 4;
+#pragma unroll 1
+        for (int j0 = last; j0 >= 0; j0 -= 4) {
+            const int nb = min(4, P - j0), slot = j0 >> 5, l0 = j0 & 31;
+            const T vs = slot_get(v, slot);
+            T x[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[c] = __shfl_sync(FULL, vs, l0 + c);
+#pragma unroll
+            for (int c = 3; c >= 0; --c) {
+                if (c < nb) {
+                    T a = x[c];
+#pragma unroll
+                    for (int t = c + 1; t < 4; ++t)
+                        if (t < nb) a -= M[pidx(j0 + t, j0 + c)] * x[t];
+                    x[c] = a * inv_diag[j0 + c];
+                } else {
+                    x[c] = T(0);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int i = lane + 32 * s;
+                if (s == slot && i >= j0 && i < j0 + nb) v[s] = slot_get(x, i - j0);
+                if (i < j0) {
+                    T a = v[s];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (c < nb) a -= M[pidx(j0 + c, i)] * x[c];
+                    v[s] = a;
+                }
+            }
+        }
     }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (lane + 32 * s < P) b[lane + 32 * s] = v[s];
+}
+
+struct SolveWork {              // shared-memory scratch of solve_damped
+    double sv[PMAX], bt[PMAX], inv64[PMAX];
+    float yv[PMAX], cv[PMAX], inv32[PMAX];
+    int flag, refinements, fallbacks, pad;
+};
+
+// Solve (A + lam diag(dv)) delta = g, A packed lower FP64 in shared memory,
+// all threads of the block.  With S = diag(A + lam D)^-1/2 the unit-diagonal
+// matrix S (A + lam D) S, augmented by the row S g, is factored in FP32 (the
+// forward substitution comes out of the factorisation); one back
+// substitution gives x; one step of iterative refinement with the residual
+// S g - S (A + lam D) S x evaluated in FP64 corrects it; delta = S x.  If the
+// FP32 factor fails, an FP64 factor of the unscaled matrix is used.  Returns
+// false when the damped matrix is not positive definite.
+__device__ bool solve_damped(const double* __restrict__ Ac, const double* __restrict__ g,
+                             const double* __restrict__ dv, double lam, int P, void* uni, SolveWork& w,
+                             double* __restrict__ delta) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    float* L32 = reinterpret_cast<float*>(uni);
+    for (int i = tid; i < P; i += blockDim.x) {
+        const double m = Ac[pidx(i, i)] + lam * dv[i];
+        const double s = (m > 0.0) ? rsqrt(m) : 1.0;
+        w.sv[i] = s;
+        w.bt[i] = s * g[i];
+    }
+    if (tid == 0) w.flag = 0;
+    __syncthreads();
+    for (int i = warp; i <= P; i += nwarp)
+        for (int j = lane; j <= i && j < P; j += 32) {
+            float v;
+            if (i < P) {
+                double a = Ac[pidx(i, j)];
+                if (i == j) a += lam * dv[i];
+                v = (float)(w.sv[i] * a * w.sv[j]);
+            } else {
+                v = (float)w.bt[j];                          // right-hand side row
+            }
+            L32[pidx(i, j)] = v;
+        }
+    __syncthreads();
+    if (cholesky_packed<float>(L32, P, P + 1, w.inv32, &w.flag)) {
+        for (int i = tid; i < P; i += blockDim.x) w.yv[i] = L32[pidx(P, i)];
+        __syncthreads();
+        trsv_warp<float>(L32, P, w.inv32, w.yv, 2);                 // x = L^-T (L^-1 S g)
+        __syncthreads();
+        // refinement: c = (L L^T)^-1 (S g - S (A + lam D) S x), residual in
+        // FP64, one row per thread as four independent FMA chains
+        for (int i = tid; i < P; i += blockDim.x) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            for (int j0 = 0; j0 < P; j0 += 4) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = j0 + c;
+                    if (j < P) {
+                        const double a = j <= i ? Ac[pidx(i, j)] : Ac[pidx(j, i)];
+                        const double t = a * (w.sv[j] * (double)w.yv[j]);
+                        if (c == 0) a0 += t; else if (c == 1) a1 += t; else if (c == 2) a2 += t; else a3 += t;
+                    }
+                }
+            }
+            const double mx = (a0 + a1) + (a2 + a3) + lam * dv[i] * w.sv[i] * (double)w.yv[i];
+            w.cv[i] = (float)(w.bt[i] - w.sv[i] * mx);
+        }
+        if (tid == 0) w.refinements += 1;
+        __syncthreads();
+        trsv_warp<float>(L32, P, w.inv32, w.cv, 3);
+        __syncthreads();
+        for (int i = tid; i < P; i += blockDim.x) delta[i] = w.sv[i] * ((double)w.yv[i] + (double)w.cv[i]);
+        __syncthreads();
+        return true;
+    }
+    // FP64 factor of the unscaled damped matrix
+    if (tid == 0) w.fallbacks += 1;
+    double* M64 = reinterpret_cast<double*>(uni);
+    for (int i = warp; i < P; i += nwarp)
+        for (int j = lane; j <= i; j += 32) {
+            double v = Ac[pidx(i, j)];
+            if (i == j) v += lam * dv[i];
+            M64[pidx(i, j)] = v;
+        }
+    if (tid == 0) w.flag = 0;
+    __syncthreads();
+    if (!cholesky_packed<double>(M64, P, P, w.inv64, &w.flag)) return false;
+    for (int i = tid; i < P; i += blockDim.x) delta[i] = g[i];
+    __syncthreads();
+    trsv_warp<double>(M64, P, w.inv64, delta, 3);
+    __syncthreads();
+    return true;
 }
 
 }  // namespace
@@ -142,16 +339,18 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
          unsigned* __restrict__ bar, float* __restrict__ Tg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Ts = reinterpret_cast<float*>(smem_raw);                          // PX_SMEM floats
-    float* Jc = Ts + PX_SMEM;                                                // union region
-    double* Mp = reinterpret_cast<double*>(Jc);
+    double* Ac = reinterpret_cast<double*>(Ts + PX_SMEM);                    // A at the current point
+    float* Jc = reinterpret_cast<float*>(Ac + M_DOUBLES);                    // union region
     float* red = Jc;
 
     __shared__ FitDesc d;
     __shared__ MemberFrame fr[KMAX];
     __shared__ short2 ttab[NTILES_MAX];
-    __shared__ double theta[PMAX], trial[PMAX], delta[PMAX], gvec[PMAX], dvec[PMAX], inv_diag[PMAX];
+    __shared__ double theta[PMAX], trial[PMAX], delta[PMAX], gvec[PMAX], dvec[PMAX];
+    __shared__ SolveWork sw;
     __shared__ double s_lam, s_chi2, s_chi2_init;
-    __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go;
+    __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc;
+    __shared__ float s_pred[2];
 
     const int tid = threadIdx.x;
     {
@@ -209,12 +408,15 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
         for (int i = 0; i < P; ++i) theta[i] = d.theta0[i];
         s_lam = lmc.lambda0; s_cur = 0; s_iters = 0; s_passes = 0; s_status = ASP_LM_CAP;
         s_done = 0; s_err = 0; s_flag = 0;
+        sw.refinements = 0; sw.fallbacks = 0;
     }
     for (int i = tid; i < P; i += blockDim.x) trial[i] = d.theta0[i];
     __syncthreads();
 
     unsigned epoch = 0;
     bool first = true;
+    // phase clocks (CTA 0, thread 0): pass, CTA + cross-CTA reduction, LM logic + solves
+    unsigned long long t_pass = 0, t_red = 0, t_solve = 0, t_factor = 0, t_subst = 0, t0 = gtimer(), t1;
     while (true) {
         // ================= pixel pass at trial[] =================
         if (tid < K) make_frame(&trial[4 * tid], fr[tid]);
@@ -298,6 +500,7 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
             __syncthreads();
         }
 
+        t1 = gtimer(); t_pass += t1 - t0; t0 = t1;
         // ---- CTA total of each accumulator entry (FP64 across pixel groups)
         const int nxt = 1 - s_cur;
         double* sums_nxt = sums + (size_t)nxt * NACC_MAX;
@@ -345,115 +548,128 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
             __syncthreads();
         }
 
+        t1 = gtimer(); t_red += t1 - t0; t0 = t1;
         // ================= LM decision (identical in every CTA) =================
+        // every step below xtol of its scale (|a|; w for centre and width)
+        int small_i = 1;
+        if (!first && tid < P) {
+            double sc = (tid & 3) == 0 ? fabs(theta[tid]) : theta[(tid & ~3) + 3];
+            if (sc == 0.0) sc = 1.0;
+            small_i = fabs(delta[tid]) < lmc.xtol * sc;
+        }
+        const int small = __syncthreads_and(small_i);
         if (tid == 0) {
+            const double chi2_t = __ldcg(sums_nxt + chi_idx);     // FP64 acceptance test
             s_passes += 1;
-            const double chi2_t = __ldcg(sums_nxt + chi_idx);
+            s_acc = 0;
             if (first) {
                 s_cur = nxt;
                 s_chi2 = chi2_t;
                 s_chi2_init = chi2_t;
             } else if (chi2_t < s_chi2) {
-                const double rel = s_chi2 > 0.0 ? (s_chi2 - chi2_t) / s_chi2 : 0.0;
-                double mx = 0.0;
-                for (int k = 0; k < K; ++k) {
-                    double w = theta[4 * k + 3];
-                    double sa = fabs(theta[4 * k]);
-                    if (sa == 0.0) sa = 1.0;
-                    mx = fmax(mx, fabs(delta[4 * k]) / sa);
-                    mx = fmax(mx, fabs(delta[4 * k + 1]) / w);
-                    mx = fmax(mx, fabs(delta[4 * k + 2]) / w);
-                    mx = fmax(mx, fabs(delta[4 * k + 3]) / w);
-                }
-                for (int i = 0; i < P; ++i) theta[i] = trial[i];
+                // relative decrease below rtol: (chi2 - chi2_t) < rtol chi2
+                const bool flat = !(s_chi2 - chi2_t >= lmc.rtol * s_chi2) || !(s_chi2 > 0.0);
+                s_acc = 1;
                 s_cur = nxt;
                 s_chi2 = chi2_t;
                 s_lam = fmax(s_lam / lmc.lambda_down, lmc.lambda_min);
-                if (rel < lmc.rtol || mx < lmc.xtol) { s_status = ASP_LM_CONVERGED; s_done = 1; }
+                if (flat || small) { s_status = ASP_LM_CONVERGED; s_done = 1; }
             } else {
                 s_lam *= lmc.lambda_up;
                 if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
             }
         }
+        __syncthreads();
+        if (s_acc && tid < P) theta[tid] = trial[tid];
         first = false;
         __syncthreads();
+        // the current point moved (first pass or accepted step): cache its
+        // A (packed lower), g and Marquardt diagonal in shared memory
+        if (s_cur == nxt) {
+            const double* sc = sums + (size_t)s_cur * NACC_MAX;
+            const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+            for (int i = warp; i < P; i += nwarp)
+                for (int j = lane; j <= i; j += 32) Ac[pidx(i, j)] = __ldcg(sc + acc_index(i, j, nb));
+            for (int i = tid; i < P; i += blockDim.x) gvec[i] = __ldcg(sc + acc_index(i, P, nb));
+            __syncthreads();
+            for (int i = tid; i < P; i += blockDim.x) {
+                const double dd = Ac[pidx(i, i)];
+                dvec[i] = dd > 0.0 ? dd : 1.0;
+            }
+            __syncthreads();
+        }
 
         // ---- propose the next trial point (solves without a pass loop here)
-        const double* sc = sums + (size_t)s_cur * NACC_MAX;
         while (!s_done) {
             if (tid == 0 && s_iters >= lmc.max_iter) { s_status = ASP_LM_CAP; s_done = 1; }
             __syncthreads();
             if (s_done) break;
-            // damped matrix (packed lower) and right-hand side
-            for (int i = tid; i < P; i += blockDim.x) {
-                double dd = __ldcg(sc + acc_index(i, i, nb));
-                dvec[i] = dd > 0.0 ? dd : 1.0;
-                gvec[i] = __ldcg(sc + acc_index(i, P, nb));
-            }
-            __syncthreads();
             const double lam = s_lam;
-            for (int q = tid; q < P * (P + 1) / 2; q += blockDim.x) {
-                int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-                while ((i + 1) * (i + 2) / 2 <= q) ++i;
-                while (i * (i + 1) / 2 > q) --i;
-                int j = q - i * (i + 1) / 2;
-                double v = __ldcg(sc + acc_index(i, j, nb));
-                if (i == j) v += lam * dvec[i];
-                Mp[q] = v;
-            }
-            if (tid == 0) s_flag = 0;
+            const unsigned long long tf0 = gtimer();
+            const bool ok = solve_damped(Ac, gvec, dvec, lam, P, Jc, sw, delta);
+            const unsigned long long tf1 = gtimer();
+            t_factor += tf1 - tf0;
+            // predicted decrease d.g + lam d.D.d (FP32 sums), finiteness, validity
+            if (tid == 0) { s_pred[0] = 0.f; s_pred[1] = 0.f; }
             __syncthreads();
-            const bool ok = cholesky_packed(Mp, P, inv_diag, &s_flag);
-            if (ok) {
-                for (int i = tid; i < P; i += blockDim.x) delta[i] = gvec[i];
-                __syncthreads();
-                chol_solve_warp(Mp, P, inv_diag, delta);
+            int fin_i = 1, valid_i = 1;
+            float dg_i = 0.f, dd_i = 0.f;
+            if (ok && tid < P) {
+                const double di = delta[tid];
+                fin_i = isfinite(di);
+                dg_i = (float)(di * gvec[tid]);
+                dd_i = (float)(dvec[tid] * di * di);
+                trial[tid] = theta[tid] + di;
             }
-            __syncthreads();
+            if (ok && tid < K) {
+                const double a = theta[4 * tid] + delta[4 * tid];
+                const double x = theta[4 * tid + 1] + delta[4 * tid + 1];
+                const double y = theta[4 * tid + 2] + delta[4 * tid + 2];
+                const double w = theta[4 * tid + 3] + delta[4 * tid + 3];
+                valid_i = (w > d.omega_min) && !(w > d.omega_max) && isfinite(a) && isfinite(x) && isfinite(y) &&
+                          isfinite(w) && !(x < d.bx0) && !(x > d.bx1) && !(y < d.by0) && !(y > d.by1);
+            }
+            if ((tid & ~31) < P) {          // whole warps holding parameters (zeros beyond P)
+                for (int o = 16; o > 0; o >>= 1) {
+                    dg_i += __shfl_xor_sync(0xffffffffu, dg_i, o);
+                    dd_i += __shfl_xor_sync(0xffffffffu, dd_i, o);
+                }
+                if ((tid & 31) == 0) { atomicAdd(&s_pred[0], dg_i); atomicAdd(&s_pred[1], dd_i); }
+            }
+            const int fin = __syncthreads_and(fin_i) && ok;
+            const int valid = __syncthreads_and(valid_i);
             if (tid == 0) {
                 s_iters += 1;
                 s_go = 0;
-                bool fin = ok;
-                for (int i = 0; ok && i < P; ++i) fin = fin && isfinite(delta[i]);
                 if (!fin) {
                     s_lam *= lmc.lambda_up;
                     if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
+                } else if ((double)s_pred[0] + lam * (double)s_pred[1] <= lmc.rtol * s_chi2) {
+                    s_status = ASP_LM_CONVERGED; s_done = 1;
+                } else if (valid) {
+                    s_go = 1;
                 } else {
-                    double dg = 0.0, dd2 = 0.0;
-                    for (int i = 0; i < P; ++i) { dg += delta[i] * gvec[i]; dd2 += dvec[i] * delta[i] * delta[i]; }
-                    const double pred = dg + lam * dd2;
-                    if (pred <= lmc.rtol * s_chi2) {
-                        s_status = ASP_LM_CONVERGED; s_done = 1;
-                    } else {
-                        bool valid = true;
-                        for (int k = 0; k < K; ++k) {
-                            double a = theta[4 * k] + delta[4 * k];
-                            double x = theta[4 * k + 1] + delta[4 * k + 1];
-                            double y = theta[4 * k + 2] + delta[4 * k + 2];
-                            double w = theta[4 * k + 3] + delta[4 * k + 3];
-                            trial[4 * k] = a; trial[4 * k + 1] = x; trial[4 * k + 2] = y; trial[4 * k + 3] = w;
-                            if (!(w > d.omega_min) || w > d.omega_max || !isfinite(a) || !isfinite(x) ||
-                                !isfinite(y) || !isfinite(w) ||
-                                x < d.bx0 || x > d.bx1 || y < d.by0 || y > d.by1)
-                                valid = false;
-                        }
-                        if (valid) {
-                            s_go = 1;
-                        } else {
-                            s_lam *= lmc.lambda_up;
-                            if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
-                        }
-                    }
+                    s_lam *= lmc.lambda_up;
+                    if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
                 }
             }
             __syncthreads();
+            t_subst += gtimer() - tf1;
             if (s_go) break;
         }
         __syncthreads();
+        t1 = gtimer(); t_solve += t1 - t0; t0 = t1;
         if (s_done) break;
     }
 
     if (b == 0 && tid == 0) {
+        out->ns_pass = (long long)t_pass;
+        out->ns_reduce = (long long)t_red;
+        out->ns_solve = (long long)t_solve;
+        out->ns_factor = (long long)t_factor;
+        out->ns_subst = (long long)t_subst;
+        out->refinements = sw.refinements;
+        out->fallbacks = sw.fallbacks;
         for (int i = 0; i < P; ++i) out->theta[i] = theta[i];
         out->chi2_init = s_chi2_init;
         out->chi2 = s_chi2;
@@ -471,7 +687,7 @@ size_t fit_smem_bytes() {
     size_t red = (size_t)2 * FIT_THREADS * 16 * sizeof(float);
     size_t u = jc > m ? jc : m;
     if (red > u) u = red;
-    return (size_t)PX_SMEM * sizeof(float) + u;
+    return (size_t)PX_SMEM * sizeof(float) + m + u;
 }
 
 static const void* fit_kernel_ptr(int tpt) {

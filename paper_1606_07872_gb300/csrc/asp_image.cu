@@ -112,6 +112,7 @@ k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict_
     const int W2 = 2 * W;
     for (int t = 0; t < nt; ++t) {
         const TermDesc td = st->terms[t];
+        if (td.bilinear) continue;
         const long long nrows = H + td.ny - 1;
         const long long total = nrows * W;
         const float* wx = wbuf + td.woff_x;
@@ -128,33 +129,77 @@ k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict_
 }
 
 // Vertical pass + update + fused argmax:
-// R[py][px] -= sum_t scale_t sum_j wy_t[j] T1_t[py - j + ny_t - 1][px].
+// R[py][px] -= sum_t scale_t sum_j wy_t[j] T1_t[py - j + ny_t - 1][px]
+//            + sum_d w_d B[py - qy_d + H][px - qx_d + W]      (point deposits)
+// Each thread owns VROWS consecutive rows of one column: a sliding window
+// over T1 gives VROWS FMAs per T1 load; lanes hold consecutive columns.
+constexpr int VROWS = 8;
+
 __global__ void __launch_bounds__(RED_THREADS)
 k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* gate,
-               const float* __restrict__ wbuf, const float* __restrict__ T1, ArgRes* part, unsigned* ticket) {
+               const float* __restrict__ wbuf, const float* __restrict__ T1, const float* __restrict__ B,
+               ArgRes* part, unsigned* ticket) {
     if (gate && *gate) return;
+    __shared__ Deposit sdep[MAX_DEPOSITS];
     const int nt = st->n_terms;
-    const long long N = (long long)H * W;
+    const int nd = st->n_dep;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) sdep[i] = st->dep[i];
+    __syncthreads();
+    const int W2 = 2 * W;
+    const long long nblk = (H + VROWS - 1) / VROWS;
     float bv = 0.f;
     long long bi = 0x7fffffffffffffffLL;
     int bj = 0;
     unsigned bad = 0;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int py = (int)(p / W), px = (int)(p % W);
-        float acc = 0.f;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nblk * W;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int px = (int)(q % W);
+        const int py0 = (int)(q / W) * VROWS;
+        float acc[VROWS];
+#pragma unroll
+        for (int o = 0; o < VROWS; ++o) acc[o] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const TermDesc& td = st->terms[t];
+            if (td.bilinear) continue;
+            const int ny = td.ny;
+            const long long nrows_t1 = H + ny - 1;
             const float* wy = wbuf + td.woff_y;
-            const float* col = T1 + td.t1off + (long long)(py + td.ny - 1) * W + px;
-            float s = 0.f;
-            for (int j = 0; j < td.ny; ++j) s = fmaf(wy[j], __ldg(col - (long long)j * W), s);
-            acc = fmaf(td.scale, s, acc);
+            const float* col = T1 + td.t1off + px;
+            // window rows py0 + o + k for k = 0 .. ny-1 (tap j = ny - 1 - k)
+            float win[VROWS], s[VROWS];
+#pragma unroll
+            for (int o = 0; o < VROWS; ++o) {
+                const long long r = py0 + o;
+                win[o] = r < nrows_t1 ? __ldg(col + r * W) : 0.f;
+                s[o] = 0.f;
+            }
+            for (int k = 0; k < ny; ++k) {
+                const float w = __ldg(wy + (ny - 1 - k));
+#pragma unroll
+                for (int o = 0; o < VROWS; ++o) s[o] = fmaf(w, win[o], s[o]);
+#pragma unroll
+                for (int o = 0; o < VROWS - 1; ++o) win[o] = win[o + 1];
+                const long long r = (long long)py0 + VROWS + k;
+                win[VROWS - 1] = r < nrows_t1 ? __ldg(col + r * W) : 0.f;
+            }
+#pragma unroll
+            for (int o = 0; o < VROWS; ++o) acc[o] = fmaf(td.scale, s[o], acc[o]);
         }
-        const float v = R[p] - acc;
-        R[p] = v;
-        if (!isfinite(v)) bad = 1;
-        if (arg_better(v, 0, p, bv, 0, bi)) { bv = v; bi = p; }
+#pragma unroll
+        for (int o = 0; o < VROWS; ++o) {
+            const int py = py0 + o;
+            if (py < H) {
+                float dsum = 0.f;
+                for (int d = 0; d < nd; ++d)
+                    dsum = fmaf(sdep[d].w, __ldg(B + (long long)(py - sdep[d].qy + H) * W2 + (px - sdep[d].qx + W)),
+                                dsum);
+                const long long p = (long long)py * W + px;
+                const float v = R[p] - (acc[o] + dsum);
+                R[p] = v;
+                if (!isfinite(v)) bad = 1;
+                if (arg_better(v, 0, p, bv, 0, bi)) { bv = v; bi = p; }
+            }
+        }
     }
     if (bad) atomicOr(&st->nonfinite, 1u);
     block_arg_reduce(bv, bj, bi);
@@ -241,9 +286,9 @@ cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_sub_v(float* R, int H, int W, CycleState* st, const int* gate, const float* wbuf,
+cudaError_t launch_sub_v(float* R, const float* B, int H, int W, CycleState* st, const int* gate, const float* wbuf,
                          const float* T1, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
-    k_sub_v_argmax<<<grid, RED_THREADS, 0, s>>>(R, H, W, st, gate, wbuf, T1, part, ticket);
+    k_sub_v_argmax<<<grid, RED_THREADS, 0, s>>>(R, H, W, st, gate, wbuf, T1, B, part, ticket);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, u
                           unsigned* nonfinite, const int* gate, cudaStream_t s);
 cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, const int* gate, const float* wbuf,
                          float* T1, int grid, cudaStream_t s);
-cudaError_t launch_sub_v(float* R, int H, int W, CycleState* st, const int* gate, const float* wbuf,
+cudaError_t launch_sub_v(float* R, const float* B, int H, int W, CycleState* st, const int* gate, const float* wbuf,
                          const float* T1, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
 cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
                             float* S1, int grid, cudaStream_t s);
