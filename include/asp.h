@@ -257,6 +257,39 @@ asp_status asp_get_kernel_times(asp_ctx* ctx, asp_kernel_time* out, int cap, int
 /* Kernels this context has launched (graph replays counted per kernel node). */
 asp_status asp_launch_count(asp_ctx* ctx, int64_t* n);
 
+/* Allocation-free joint LM fit.  The paper has no counterpart: this is a
+ * service for callers that cannot create device allocations of their own --
+ * code running inside another framework's memory pool (the pool owns the
+ * device memory budget), real-time pipelines that forbid allocation after
+ * start-up (cudaMalloc can synchronise the device and take milliseconds), and
+ * host threads that may run while another thread captures a CUDA graph in
+ * global mode, where cudaMalloc is an illegal call.
+ *
+ * It fits n Gaussians (asp_gauss rows, host memory) to the FP32 image
+ * image_dev (H x W, device, row-major) exactly as asp_fit_active_set does
+ * (window = bounding box of the members' boxes, clipped; the last n_old
+ * members' initial Gaussians are added back to the target; trial widths must
+ * exceed omega_min, e.g. 0.25 omega_b; LM settings lm_lambda0, lm_rtol,
+ * lm_xtol and lm_max_iter taken from *lm), writes the fitted rows to out
+ * (host) and the outcome to info (host, may be NULL), and synchronises
+ * stream.  No context, no cudaMalloc, cudaFree or allocating library call:
+ * its device scratch is one file-scope __device__ array of
+ * ASP_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Limits: n <= ASP_STATIC_KMAX (else ASP_ERR_UNSUPPORTED), at
+ * most ASP_STATIC_GRID_MAX CTAs, and a window small enough for their shared
+ * memory (ASP_STATIC_GRID_MAX x 12288 pixels; else ASP_ERR_UNSUPPORTED).
+ * The first call on a device looks up the array's device address and sets
+ * the kernel's shared-memory attribute (once per device; make that first call
+ * before any stream capture).  All calls on a device share the array and it
+ * keeps the last call's contents: each call clears what must start at zero,
+ * and calls that overlap on the GPU (other threads or streams) race. */
+#define ASP_STATIC_KMAX 8
+#define ASP_STATIC_GRID_MAX 32
+#define ASP_STATIC_SCRATCH_BYTES 2444288
+asp_status asp_fit_static(const float* image_dev, int H, int W, const asp_gauss* init, int n, int n_old,
+                          double omega_min, const asp_params* lm, asp_gauss* out, asp_fit_info* info,
+                          void* stream);
+
 /* Checkpoint the whole minor-cycle state (residual included) to a file, or
  * restore it into a context of the same size. */
 asp_status asp_save_state(asp_ctx* ctx, const char* path);

@@ -9,6 +9,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libasp.so")
 
 ASP_KMAX = 32
+ASP_STATIC_KMAX = 8
+ASP_STATIC_GRID_MAX = 32
+ASP_STATIC_SCRATCH_BYTES = 2444288
 
 ASP_OK = 0
 STATUS_NAMES = {0: "ASP_OK", 1: "ASP_ERR_INVALID_ARG", 2: "ASP_ERR_CUDA", 3: "ASP_ERR_OOM", 4: "ASP_ERR_NAN",
@@ -107,6 +110,8 @@ SIGNATURES = {
     "asp_set_profiling": [_P, _I],
     "asp_get_kernel_times": [_P, C.POINTER(asp_kernel_time), _I, C.POINTER(_I)],
     "asp_launch_count": [_P, C.POINTER(C.c_int64)],
+    "asp_fit_static": [_P, _I, _I, C.POINTER(asp_gauss), _I, _I, C.c_double, C.POINTER(asp_params),
+                       C.POINTER(asp_gauss), C.POINTER(asp_fit_info), _P],
     "asp_save_state": [_P, C.c_char_p],
     "asp_load_state": [_P, C.c_char_p],
 }

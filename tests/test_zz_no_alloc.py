@@ -1,0 +1,83 @@
+"""asp_fit_static, the allocation-free fit entry point, against the
+context-based asp_fit_active_set.
+
+asp_fit_static exists for callers that cannot create device allocations of
+their own (another framework's memory pool owns the budget, allocation is
+forbidden after start-up, or a CUDA graph is being captured in global mode
+on another thread).  Its scratch lives in one file-scope device array shared
+by every call, so this test makes two different calls in a row and checks
+both against the existing entry point: the second call must not see the
+first call's leftovers.  This file is collected last so a failure here
+leaves every other test already run.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4     # the fit tolerance the parity tests use
+
+
+def _static_fit(asp, img, init, n_old, omega_min, params):
+    rows = np.asarray(init, dtype=np.float64).reshape(-1, 4)
+    n = len(rows)
+    arr = (asp.asp_gauss * n)(*[asp.asp_gauss(*r) for r in rows])
+    out = (asp.asp_gauss * n)()
+    info = asp.asp_fit_info()
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    H, W = img.shape
+    rc = asp.lib().asp_fit_static(img.data_ptr(), H, W, arr, n, n_old, omega_min, C.byref(params), out,
+                                  C.byref(info), stream)
+    return rc, np.array([[g.amp, g.x, g.y, g.width] for g in out]), info
+
+
+def _close(a, b):
+    for ga, gb in zip(a, b):
+        assert abs(ga[0] - gb[0]) <= RTOL * abs(gb[0])
+        assert abs(ga[1] - gb[1]) <= RTOL * max(1.0, gb[3])
+        assert abs(ga[2] - gb[2]) <= RTOL * max(1.0, gb[3])
+        assert abs(ga[3] - gb[3]) <= RTOL * gb[3]
+
+
+def test_static_fit_matches_context_fit_on_two_calls(asp):
+    import torch
+    case = synth.small_case(120, 128, seed=31, n_points=3, n_gauss=2, sigma_range=(2.5, 5.0))
+    img = torch.from_numpy(case.dirty).cuda()
+    psf = torch.from_numpy(case.psf).cuda()
+    ctx = asp.Context(img, psf, k_max=4, noise_sigma=case.noise_sigma, lm_max_iter=200, lm_rtol=1e-10,
+                      lm_xtol=1e-9)
+    ab, wb, _, _ = ctx.beam
+    params = asp.default_params(lm_max_iter=200, lm_rtol=1e-10, lm_xtol=1e-9)
+    pk = ctx.find_peak(asp.ASP_PEAK_SMOOTH)
+    calls = [
+        ([[pk["a0"], pk["x0"], pk["y0"], pk["w0"]]], 0),                             # one member
+        ([[0.3, 40.0, 52.0, 3.0], [0.2, 46.5, 55.0, 2.5], [0.1, 37.0, 48.0, 2.0]], 2),  # three, two added back
+    ]
+    for init, n_old in calls:
+        ref, ref_info = ctx.fit(init, n_old)
+        rc, got, info = _static_fit(asp, img, init, n_old, 0.25 * wb, params)
+        assert rc == 0, asp._lib.STATUS_NAMES.get(rc, rc)
+        assert (info.x0, info.x1, info.y0, info.y1) == (ref_info["x0"], ref_info["x1"], ref_info["y0"],
+                                                        ref_info["y1"])
+        assert info.status == ref_info["status"]
+        _close(got, ref)
+        assert info.chi2_final == pytest.approx(ref_info["chi2_final"], rel=1e-5)
+    ctx.close()
+
+
+def test_static_fit_rejects_sizes_beyond_its_limits(asp):
+    import torch
+    case = synth.small_case(64, 64, seed=1)
+    img = torch.from_numpy(case.dirty).cuda()
+    params = asp.default_params()
+    too_many = [[0.1, 30.0 + k, 30.0, 2.0] for k in range(asp._lib.ASP_STATIC_KMAX + 1)]
+    rc, _, _ = _static_fit(asp, img, too_many, 0, 0.3, params)
+    assert rc == 8                                           # ASP_ERR_UNSUPPORTED
+    big = torch.zeros((2048, 2048), dtype=torch.float32, device="cuda")
+    rc, _, _ = _static_fit(asp, big, [[1.0, 1024.0, 1024.0, 400.0]], 0, 0.3, params)
+    assert rc == 8                                           # window beyond the scratch's shared memory
