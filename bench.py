@@ -141,6 +141,19 @@ def _traffic_record():
     return out
 
 
+def _nvtx(push: bool):
+    """NVTX range 'asp_timed' around the timed steps, so that a profiler can
+    select exactly their launches (ncu --nvtx --nvtx-include asp_timed/)."""
+    try:
+        import torch
+        if push:
+            torch.cuda.nvtx.range_push("asp_timed")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def _workload(size: int, seed: int):
     import synth
     return synth.config2(seed, size=size)
@@ -151,6 +164,20 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def aggregate(t_ms: float, iters: int, pevals: int, device) -> tuple:
+    """Whole-job totals over the replicas: the slowest rank's time and the
+    sum of every rank's work (identity on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_ms, iters, pevals
+    tt = torch.tensor([t_ms, float(iters), float(pevals)], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(mx[0]), int(tt[1]), int(tt[2])
 
 
 # ---------------------------------------------------------------- cpu baseline (oracle)
@@ -279,6 +306,7 @@ def run_ours(a):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    _nvtx(True)
     with ClockSampler(local) as clk:
         for _ in range(a.steps):
             flush.zero_()
@@ -294,15 +322,10 @@ def run_ours(a):
             fit_flops += st["fit_flops"]
             sub_flops += st["sub_flops"]
     torch.cuda.synchronize()
+    _nvtx(False)
     n_launch = launches() - l0
     t_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms, float(iters), float(pevals)], device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_ms, iters, pevals = float(mx[0]), int(tt[1]), int(tt[2])
+    t_ms, iters, pevals = aggregate(t_ms, iters, pevals, "cuda")
     value = iters / (t_ms / 1e3)
 
     # ---- end to end through the C-ABI with host buffers
