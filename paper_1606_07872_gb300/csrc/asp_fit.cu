@@ -87,7 +87,6 @@ __device__ __forceinline__ void make_frame(const double* th, MemberFrame& f) {
 
 // Pivot l = sqrt(d) and 1/l.  FP32 (the refined factor): rsqrtf, whose
 // few-ulp error the FP64 refinement removes; FP64: correctly rounded.
-__device__ __forceinline__ void pivot(float d, float& l, float& il) { il = rsqrtf(d); l = d * il; }
 __device__ __forceinline__ void pivot(double d, double& l, double& il) { l = sqrt(d); il = 1.0 / l; }
 
 // Cholesky factorisation of the packed lower matrix M in place: columns
@@ -240,14 +239,187 @@ __device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ 
         if (lane + 32 * s < P) b[lane + 32 * s] = v[s];
 }
 
+// Low-latency Cholesky factorisation (FP32) of the packed lower matrix M,
+// columns 0..P-1 of rows 0..P (P a multiple of 4; row P carries a
+// right-hand side b, which comes out as L^-1 b).  Blocked right-looking,
+// 4-column panels, two block barriers per panel:
+//   A. one thread per row i >= j0: every such thread factors the 4x4
+//      diagonal block in registers (redundantly: no serial section and no
+//      barrier in front of the panel solve); rows below the block solve
+//      their four panel entries and also store them column-major in Lp
+//      (ld LP_LD) for conflict-free reads in B;
+//   B. the block's rows store its factor, then the trailing rank-4 update,
+//      one row per warp, one column per lane.
+// Every block is a full 4x4 (callers pad P with identity rows), so no load
+// sits behind a bounds test and the compiler can issue them all at once.
+// Returns false (uniformly) if a pivot is not positive; *s_flag must be 0 on
+// entry.
+constexpr int LP_LD = 132;
+constexpr int L32_LP_OFF = 8400;   // float offset of Lp behind the packed (P+1)-row matrix
+
+__device__ bool chol_lowlat(float* __restrict__ M, float* __restrict__ Lp, int P, float* __restrict__ inv_diag,
+                            int* s_flag) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int nrows = P + 1;
+#pragma unroll 1
+    for (int j0 = 0; j0 < P; j0 += 4) {
+        const int r0 = j0 + 4;
+        const int i = j0 + tid;
+        float d[4][4], inv[4];
+        if (i < nrows) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t <= c; ++t) d[c][t] = M[pidx(j0 + c, j0 + t)];
+            float a[4];
+            const int ir = i < r0 ? r0 : i;   // block rows load a valid row they do not use
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a[c] = M[pidx(ir, j0 + c)];
+            bool ok = true;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float v = d[c][c];
+#pragma unroll
+                for (int t = 0; t < c; ++t) v = fmaf(-d[c][t], d[c][t], v);
+                ok = ok && v > 0.f && isfinite(v);
+                const float il = rsqrtf(v);
+                d[c][c] = v * il;
+                inv[c] = il;
+#pragma unroll
+                for (int r = c + 1; r < 4; ++r) {
+                    float u = d[r][c];
+#pragma unroll
+                    for (int t = 0; t < c; ++t) u = fmaf(-d[r][t], d[c][t], u);
+                    d[r][c] = u * il;
+                }
+            }
+            if (i < r0) {
+                if (!ok) *s_flag = 1;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float u = a[c];
+#pragma unroll
+                    for (int t = 0; t < c; ++t) u = fmaf(-a[t], d[c][t], u);
+                    a[c] = u * inv[c];
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    M[pidx(i, j0 + c)] = a[c];
+                    Lp[c * LP_LD + i] = a[c];
+                }
+            }
+        }
+        __syncthreads();
+        if (*s_flag) return false;
+        // the block's own rows store their factor only now: every thread of
+        // A has read the unfactored block
+        if (tid < 4) {
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+                if (cc == tid) {
+#pragma unroll
+                    for (int t = 0; t <= cc; ++t) M[pidx(i, j0 + t)] = d[cc][t];
+                    inv_diag[i] = inv[cc];
+                }
+        }
+        for (int ii = r0 + warp; ii < nrows; ii += nwarp) {
+            float li[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) li[c] = Lp[c * LP_LD + ii];
+            float* row = M + pidx(ii, 0);
+            const int kmax = min(ii, P - 1);
+            for (int k = r0 + lane; k <= kmax; k += 32) {
+                float acc = row[k];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc = fmaf(-li[c], Lp[c * LP_LD + k], acc);
+                row[k] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// Back substitution L^T x = y with L from chol_lowlat (P a multiple of 4),
+// all threads, 4-row blocks from the bottom, one block barrier per block:
+// every thread solves the block's 4 unknowns redundantly from the (already
+// updated) y entries, then thread i < jb removes them from y_i.  y is
+// destroyed; x must not alias y.
+__device__ void trsv_back_block(const float* __restrict__ M, int P, const float* __restrict__ inv_diag,
+                                float* __restrict__ y, float* __restrict__ x) {
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int jb = P - 4; jb >= 0; jb -= 4) {
+        float xb[4], iv[4], l10, l20, l21, l30, l31, l32;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { xb[c] = y[jb + c]; iv[c] = inv_diag[jb + c]; }
+        l10 = M[pidx(jb + 1, jb)];
+        l20 = M[pidx(jb + 2, jb)]; l21 = M[pidx(jb + 2, jb + 1)];
+        l30 = M[pidx(jb + 3, jb)]; l31 = M[pidx(jb + 3, jb + 1)]; l32 = M[pidx(jb + 3, jb + 2)];
+        const int i = tid < jb ? tid : jb;   // others load a row nobody writes in this block
+        float lr[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) lr[c] = M[pidx(jb + c, i)];
+        float yi = y[i];
+        xb[3] = xb[3] * iv[3];
+        xb[2] = fmaf(-l32, xb[3], xb[2]) * iv[2];
+        xb[1] = fmaf(-l31, xb[3], fmaf(-l21, xb[2], xb[1])) * iv[1];
+        xb[0] = fmaf(-l30, xb[3], fmaf(-l20, xb[2], fmaf(-l10, xb[1], xb[0]))) * iv[0];
+        if (tid < 4) x[jb + tid] = slot_get(xb, tid);
+        if (tid < jb) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) yi = fmaf(-lr[c], xb[c], yi);
+            y[tid] = yi;
+        }
+        __syncthreads();
+    }
+}
+
+// Forward substitution L z = r, the mirror of trsv_back_block: blocks from
+// the top, thread i >= jb + 4 removes the block's unknowns from r_i.  r is
+// destroyed; z must not alias r.
+__device__ void trsv_fwd_block(const float* __restrict__ M, int P, const float* __restrict__ inv_diag,
+                               float* __restrict__ r, float* __restrict__ z) {
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int jb = 0; jb < P; jb += 4) {
+        float zb[4], iv[4], l10, l20, l21, l30, l31, l32;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { zb[c] = r[jb + c]; iv[c] = inv_diag[jb + c]; }
+        l10 = M[pidx(jb + 1, jb)];
+        l20 = M[pidx(jb + 2, jb)]; l21 = M[pidx(jb + 2, jb + 1)];
+        l30 = M[pidx(jb + 3, jb)]; l31 = M[pidx(jb + 3, jb + 1)]; l32 = M[pidx(jb + 3, jb + 2)];
+        const int i = jb + 4 + tid;
+        const bool upd = i < P;
+        const int ir = upd ? i : jb + 3;
+        float lr[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) lr[c] = M[pidx(ir, jb + c)];
+        float ri = r[ir];
+        zb[0] = zb[0] * iv[0];
+        zb[1] = fmaf(-l10, zb[0], zb[1]) * iv[1];
+        zb[2] = fmaf(-l21, zb[1], fmaf(-l20, zb[0], zb[2])) * iv[2];
+        zb[3] = fmaf(-l32, zb[2], fmaf(-l31, zb[1], fmaf(-l30, zb[0], zb[3]))) * iv[3];
+        if (tid < 4) z[jb + tid] = slot_get(zb, tid);
+        if (upd) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ri = fmaf(-lr[c], zb[c], ri);
+            r[i] = ri;
+        }
+        __syncthreads();
+    }
+}
+
 struct SolveWork {              // shared-memory scratch of solve_damped
-    double sv[PMAX], bt[PMAX], inv64[PMAX];
-    float yv[PMAX], cv[PMAX], inv32[PMAX];
+    double bt[PMAX], ud[PMAX], inv64[PMAX];
+    float sf[PMAX], xv[PMAX], zv[PMAX], cv[PMAX], inv32[PMAX];
     int flag, refinements, fallbacks, pad;
 };
 
 // Solve (A + lam diag(dv)) delta = g, A packed lower FP64 in shared memory,
-// all threads of the block.  With S = diag(A + lam D)^-1/2 the unit-diagonal
+// all threads of the block.  With S = diag(A + lam D)^-1/2 rounded to FP32
+// (any diagonal scaling serves; an FP32 one is exact in FP64 below), the
 // matrix S (A + lam D) S, augmented by the row S g, is factored in FP32 (the
 // forward substitution comes out of the factorisation); one back
 // substitution gives x; one step of iterative refinement with the residual
@@ -259,55 +431,67 @@ __device__ bool solve_damped(const double* __restrict__ Ac, const double* __rest
                              double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     float* L32 = reinterpret_cast<float*>(uni);
-    for (int i = tid; i < P; i += blockDim.x) {
-        const double m = Ac[pidx(i, i)] + lam * dv[i];
-        const double s = (m > 0.0) ? rsqrt(m) : 1.0;
-        w.sv[i] = s;
-        w.bt[i] = s * g[i];
+    float* Lp = L32 + L32_LP_OFF;
+    const int P4 = (P + 3) & ~3;   // padded with identity rows: every block of the factor is full
+    for (int i = tid; i < P4; i += blockDim.x) {
+        float s = 1.0f;
+        double b = 0.0;
+        if (i < P) {
+            const double m = Ac[pidx(i, i)] + lam * dv[i];
+            s = (m > 0.0) ? rsqrtf((float)m) : 1.0f;
+            b = (double)s * g[i];
+        }
+        w.sf[i] = s;
+        w.bt[i] = b;
     }
     if (tid == 0) w.flag = 0;
     __syncthreads();
-    for (int i = warp; i <= P; i += nwarp)
-        for (int j = lane; j <= i && j < P; j += 32) {
+    for (int i = warp; i <= P4; i += nwarp) {
+        const float si = i < P ? w.sf[i] : 0.f;
+        for (int j = lane; j <= i && j < P4; j += 32) {
             float v;
-            if (i < P) {
+            if (i < P && j < P) {
                 double a = Ac[pidx(i, j)];
                 if (i == j) a += lam * dv[i];
-                v = (float)(w.sv[i] * a * w.sv[j]);
+                v = (float)a * si * w.sf[j];
+            } else if (i == P4) {
+                v = (float)w.bt[j];                          // right-hand side row (0 in the padding)
             } else {
-                v = (float)w.bt[j];                          // right-hand side row
+                v = i == j ? 1.f : 0.f;                      // identity padding
             }
             L32[pidx(i, j)] = v;
         }
+    }
     __syncthreads();
-    if (cholesky_packed<float>(L32, P, P + 1, w.inv32, &w.flag)) {
-        for (int i = tid; i < P; i += blockDim.x) w.yv[i] = L32[pidx(P, i)];
-        __syncthreads();
-        trsv_warp<float>(L32, P, w.inv32, w.yv, 2);                 // x = L^-T (L^-1 S g)
+    if (chol_lowlat(L32, Lp, P4, w.inv32, &w.flag)) {
+        trsv_back_block(L32, P4, w.inv32, L32 + pidx(P4, 0), w.xv);      // x = L^-T (L^-1 S g)
+        for (int i = tid; i < P4; i += blockDim.x) w.ud[i] = (double)w.sf[i] * (double)w.xv[i];
         __syncthreads();
         // refinement: c = (L L^T)^-1 (S g - S (A + lam D) S x), residual in
         // FP64, one row per thread as four independent FMA chains
-        for (int i = tid; i < P; i += blockDim.x) {
+        for (int i = tid; i < P4; i += blockDim.x) {
+            if (i >= P) { w.cv[i] = 0.f; continue; }
             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            for (int j0 = 0; j0 < P; j0 += 4) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int j = j0 + c;
-                    if (j < P) {
-                        const double a = j <= i ? Ac[pidx(i, j)] : Ac[pidx(j, i)];
-                        const double t = a * (w.sv[j] * (double)w.yv[j]);
-                        if (c == 0) a0 += t; else if (c == 1) a1 += t; else if (c == 2) a2 += t; else a3 += t;
-                    }
-                }
+            int j = 0;
+            for (; j + 3 < P; j += 4) {          // unconditional loads, four chains
+                const int q0 = j <= i ? pidx(i, j) : pidx(j, i);
+                const int q1 = j + 1 <= i ? pidx(i, j + 1) : pidx(j + 1, i);
+                const int q2 = j + 2 <= i ? pidx(i, j + 2) : pidx(j + 2, i);
+                const int q3 = j + 3 <= i ? pidx(i, j + 3) : pidx(j + 3, i);
+                a0 = fma(Ac[q0], w.ud[j], a0);
+                a1 = fma(Ac[q1], w.ud[j + 1], a1);
+                a2 = fma(Ac[q2], w.ud[j + 2], a2);
+                a3 = fma(Ac[q3], w.ud[j + 3], a3);
             }
-            const double mx = (a0 + a1) + (a2 + a3) + lam * dv[i] * w.sv[i] * (double)w.yv[i];
-            w.cv[i] = (float)(w.bt[i] - w.sv[i] * mx);
+            for (; j < P; ++j) a0 = fma(Ac[j <= i ? pidx(i, j) : pidx(j, i)], w.ud[j], a0);
+            const double mx = (a0 + a1) + (a2 + a3) + lam * dv[i] * w.ud[i];
+            w.cv[i] = (float)(w.bt[i] - (double)w.sf[i] * mx);
         }
         if (tid == 0) w.refinements += 1;
         __syncthreads();
-        trsv_warp<float>(L32, P, w.inv32, w.cv, 3);
-        __syncthreads();
-        for (int i = tid; i < P; i += blockDim.x) delta[i] = w.sv[i] * ((double)w.yv[i] + (double)w.cv[i]);
+        trsv_fwd_block(L32, P4, w.inv32, w.cv, w.zv);
+        trsv_back_block(L32, P4, w.inv32, w.zv, w.cv);
+        for (int i = tid; i < P; i += blockDim.x) delta[i] = (double)w.sf[i] * ((double)w.xv[i] + (double)w.cv[i]);
         __syncthreads();
         return true;
     }
