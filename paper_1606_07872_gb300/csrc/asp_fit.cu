@@ -240,136 +240,176 @@ __device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ 
 }
 
 // Low-latency Cholesky factorisation (FP32) of the packed lower matrix M,
-// columns 0..P-1 of rows 0..P (P a multiple of 4; row P carries a
-// right-hand side b, which comes out as L^-1 b).  Blocked right-looking,
-// 4-column panels, two block barriers per panel:
-//   A. one thread per row i >= j0: every such thread factors the 4x4
-//      diagonal block in registers (redundantly: no serial section and no
-//      barrier in front of the panel solve); rows below the block solve
-//      their four panel entries and also store them column-major in Lp
-//      (ld LP_LD) for conflict-free reads in B;
-//   B. the block's rows store its factor, then the trailing rank-4 update,
-//      one row per warp, one column per lane.
-// Every block is a full 4x4 (callers pad P with identity rows), so no load
-// sits behind a bounds test and the compiler can issue them all at once.
-// Returns false (uniformly) if a pivot is not positive; *s_flag must be 0 on
-// entry.
+// columns 0..P-1 of rows 0..P (P a multiple of the panel width PB = 4 or 8;
+// row P carries a right-hand side b, which comes out as L^-1 b).  Blocked
+// right-looking with look-ahead, two block barriers per panel:
+//   A. one thread per row i below the panel's diagonal block: solve the
+//      row's PB panel entries against the already factored block, store
+//      them in M and column-major in Lp (ld LP_LD, conflict-free reads);
+//   B. warps 0..6: trailing rank-PB update of the rows below the next
+//      diagonal block, one row per warp, one column per lane;
+//      warp 7: the next diagonal block itself -- its rank-PB update, then
+//      its factorisation in registers (every lane redundantly), so the
+//      pivot chain of panel p+1 overlaps the update of panel p.
+// Narrow panels suit small P (fewer padded rows, shorter pivot chains on
+// the critical path), wide ones large P (half the barriers).
+// Every block is full (callers pad P with identity rows), so no load sits
+// behind a bounds test.  Returns false (uniformly) if a pivot is not
+// positive; *s_flag must be 0 on entry.
 constexpr int LP_LD = 132;
 constexpr int L32_LP_OFF = 8400;   // float offset of Lp behind the packed (P+1)-row matrix
 
+// Factor the PBxPB diagonal block at j0 (lower, packed in M) in registers,
+// every lane of the calling warp redundantly; lanes 0..PB-1 store row
+// j0+lane of the factor and its inverse pivot.  Returns false if a pivot
+// fails.
+template <int PB>
+__device__ __forceinline__ bool factor_diag(float* __restrict__ M, float* __restrict__ inv_diag, int j0, int lane) {
+    float d[PB][PB];
+#pragma unroll
+    for (int c = 0; c < PB; ++c)
+#pragma unroll
+        for (int t = 0; t <= c; ++t) d[c][t] = M[pidx(j0 + c, j0 + t)];
+    float inv[PB];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < PB; ++c) {
+        float v = d[c][c];
+#pragma unroll
+        for (int t = 0; t < c; ++t) v = fmaf(-d[c][t], d[c][t], v);
+        ok = ok && v > 0.f && isfinite(v);
+        const float il = rsqrtf(v);
+        d[c][c] = v * il;
+        inv[c] = il;
+#pragma unroll
+        for (int r = c + 1; r < PB; ++r) {
+            float u = d[r][c];
+#pragma unroll
+            for (int t = 0; t < c; ++t) u = fmaf(-d[r][t], d[c][t], u);
+            d[r][c] = u * il;
+        }
+    }
+    __syncwarp();   // every lane has read the unfactored block
+#pragma unroll
+    for (int c = 0; c < PB; ++c)
+        if (c == lane) {
+#pragma unroll
+            for (int t = 0; t <= c; ++t) M[pidx(j0 + c, j0 + t)] = d[c][t];
+            inv_diag[j0 + c] = inv[c];
+        }
+    return ok;
+}
+
+template <int PB>
 __device__ bool chol_lowlat(float* __restrict__ M, float* __restrict__ Lp, int P, float* __restrict__ inv_diag,
                             int* s_flag) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int nrows = P + 1;
+    if (warp == 0 && !factor_diag<PB>(M, inv_diag, 0, lane) && lane == 0) *s_flag = 1;
+    __syncthreads();
+    if (*s_flag) return false;
 #pragma unroll 1
-    for (int j0 = 0; j0 < P; j0 += 4) {
-        const int r0 = j0 + 4;
-        const int i = j0 + tid;
-        float d[4][4], inv[4];
+    for (int j0 = 0; j0 < P; j0 += PB) {
+        const int r0 = j0 + PB;
+        // A: panel rows below the diagonal block
+        const int i = r0 + tid;
         if (i < nrows) {
+            float a[PB], iv[PB];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < PB; ++c) { a[c] = M[pidx(i, j0 + c)]; iv[c] = inv_diag[j0 + c]; }
+            float l[PB][PB];
 #pragma unroll
-                for (int t = 0; t <= c; ++t) d[c][t] = M[pidx(j0 + c, j0 + t)];
-            float a[4];
-            const int ir = i < r0 ? r0 : i;   // block rows load a valid row they do not use
+            for (int c = 1; c < PB; ++c)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) a[c] = M[pidx(ir, j0 + c)];
-            bool ok = true;
+                for (int t = 0; t < c; ++t) l[c][t] = M[pidx(j0 + c, j0 + t)];
+            // forward solve of the row against L_d, running updates
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float v = d[c][c];
+            for (int c = 0; c < PB; ++c) {
+                a[c] *= iv[c];
 #pragma unroll
-                for (int t = 0; t < c; ++t) v = fmaf(-d[c][t], d[c][t], v);
-                ok = ok && v > 0.f && isfinite(v);
-                const float il = rsqrtf(v);
-                d[c][c] = v * il;
-                inv[c] = il;
-#pragma unroll
-                for (int r = c + 1; r < 4; ++r) {
-                    float u = d[r][c];
-#pragma unroll
-                    for (int t = 0; t < c; ++t) u = fmaf(-d[r][t], d[c][t], u);
-                    d[r][c] = u * il;
-                }
+                for (int r = c + 1; r < PB; ++r) a[r] = fmaf(-l[r][c], a[c], a[r]);
             }
-            if (i < r0) {
-                if (!ok) *s_flag = 1;
-            } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float u = a[c];
+            for (int c = 0; c < PB; ++c) {
+                M[pidx(i, j0 + c)] = a[c];
+                Lp[c * LP_LD + i] = a[c];
+            }
+        }
+        __syncthreads();
+        // B: trailing update (warps 0..nwarp-2) and look-ahead factor (last warp)
+        if (warp == nwarp - 1) {
+            if (r0 < P) {
+                // update the next diagonal block: PB(PB+1)/2 entries over the lanes
+                for (int e = lane; e < PB * (PB + 1) / 2; e += 32) {
+                    int rr = 0;
+                    while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+                    const int cc = e - rr * (rr + 1) / 2;
+                    float acc = M[pidx(r0 + rr, r0 + cc)];
 #pragma unroll
-                    for (int t = 0; t < c; ++t) u = fmaf(-a[t], d[c][t], u);
-                    a[c] = u * inv[c];
+                    for (int c = 0; c < PB; ++c) acc = fmaf(-Lp[c * LP_LD + r0 + rr], Lp[c * LP_LD + r0 + cc], acc);
+                    M[pidx(r0 + rr, r0 + cc)] = acc;
                 }
+                __syncwarp();
+                if (!factor_diag<PB>(M, inv_diag, r0, lane) && lane == 0) *s_flag = 1;
+            }
+        } else {
+            for (int ii = r0 + PB + warp; ii < nrows; ii += nwarp - 1) {
+                float li[PB];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    M[pidx(i, j0 + c)] = a[c];
-                    Lp[c * LP_LD + i] = a[c];
+                for (int c = 0; c < PB; ++c) li[c] = Lp[c * LP_LD + ii];
+                float* row = M + pidx(ii, 0);
+                const int kmax = min(ii, P - 1);
+                for (int k = r0 + lane; k <= kmax; k += 32) {
+                    float acc = row[k];
+#pragma unroll
+                    for (int c = 0; c < PB; ++c) acc = fmaf(-li[c], Lp[c * LP_LD + k], acc);
+                    row[k] = acc;
                 }
             }
         }
         __syncthreads();
         if (*s_flag) return false;
-        // the block's own rows store their factor only now: every thread of
-        // A has read the unfactored block
-        if (tid < 4) {
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc)
-                if (cc == tid) {
-#pragma unroll
-                    for (int t = 0; t <= cc; ++t) M[pidx(i, j0 + t)] = d[cc][t];
-                    inv_diag[i] = inv[cc];
-                }
-        }
-        for (int ii = r0 + warp; ii < nrows; ii += nwarp) {
-            float li[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) li[c] = Lp[c * LP_LD + ii];
-            float* row = M + pidx(ii, 0);
-            const int kmax = min(ii, P - 1);
-            for (int k = r0 + lane; k <= kmax; k += 32) {
-                float acc = row[k];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc = fmaf(-li[c], Lp[c * LP_LD + k], acc);
-                row[k] = acc;
-            }
-        }
-        __syncthreads();
     }
     return true;
 }
 
-// Back substitution L^T x = y with L from chol_lowlat (P a multiple of 4),
-// all threads, 4-row blocks from the bottom, one block barrier per block:
-// every thread solves the block's 4 unknowns redundantly from the (already
+// Back substitution L^T x = y with L from chol_lowlat (P a multiple of PB),
+// all threads, PB-row blocks from the bottom, one block barrier per block:
+// every thread solves the block's 8 unknowns redundantly from the (already
 // updated) y entries, then thread i < jb removes them from y_i.  y is
 // destroyed; x must not alias y.
+template <int PB>
 __device__ void trsv_back_block(const float* __restrict__ M, int P, const float* __restrict__ inv_diag,
                                 float* __restrict__ y, float* __restrict__ x) {
     const int tid = threadIdx.x;
 #pragma unroll 1
-    for (int jb = P - 4; jb >= 0; jb -= 4) {
-        float xb[4], iv[4], l10, l20, l21, l30, l31, l32;
+    for (int jb = P - PB; jb >= 0; jb -= PB) {
+        float xb[PB], iv[PB], l[PB][PB];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { xb[c] = y[jb + c]; iv[c] = inv_diag[jb + c]; }
-        l10 = M[pidx(jb + 1, jb)];
-        l20 = M[pidx(jb + 2, jb)]; l21 = M[pidx(jb + 2, jb + 1)];
-        l30 = M[pidx(jb + 3, jb)]; l31 = M[pidx(jb + 3, jb + 1)]; l32 = M[pidx(jb + 3, jb + 2)];
+        for (int c = 0; c < PB; ++c) { xb[c] = y[jb + c]; iv[c] = inv_diag[jb + c]; }
+#pragma unroll
+        for (int c = 1; c < PB; ++c)
+#pragma unroll
+            for (int t = 0; t < c; ++t) l[c][t] = M[pidx(jb + c, jb + t)];
         const int i = tid < jb ? tid : jb;   // others load a row nobody writes in this block
-        float lr[4];
+        float lr[PB];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) lr[c] = M[pidx(jb + c, i)];
+        for (int c = 0; c < PB; ++c) lr[c] = M[pidx(jb + c, i)];
         float yi = y[i];
-        xb[3] = xb[3] * iv[3];
-        xb[2] = fmaf(-l32, xb[3], xb[2]) * iv[2];
-        xb[1] = fmaf(-l31, xb[3], fmaf(-l21, xb[2], xb[1])) * iv[1];
-        xb[0] = fmaf(-l30, xb[3], fmaf(-l20, xb[2], fmaf(-l10, xb[1], xb[0]))) * iv[0];
-        if (tid < 4) x[jb + tid] = slot_get(xb, tid);
+#pragma unroll
+        for (int c = PB - 1; c >= 0; --c) {
+            xb[c] *= iv[c];
+#pragma unroll
+            for (int t = 0; t < c; ++t) xb[t] = fmaf(-l[c][t], xb[c], xb[t]);
+        }
+        if (tid < PB) {
+#pragma unroll
+            for (int c = 0; c < PB; ++c)
+                if (c == tid) x[jb + c] = xb[c];
+        }
         if (tid < jb) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) yi = fmaf(-lr[c], xb[c], yi);
+            for (int c = 0; c < PB; ++c) yi = fmaf(-lr[c], xb[c], yi);
             y[tid] = yi;
         }
         __syncthreads();
@@ -377,34 +417,42 @@ __device__ void trsv_back_block(const float* __restrict__ M, int P, const float*
 }
 
 // Forward substitution L z = r, the mirror of trsv_back_block: blocks from
-// the top, thread i >= jb + 4 removes the block's unknowns from r_i.  r is
+// the top, thread i >= jb + PB removes the block's unknowns from r_i.  r is
 // destroyed; z must not alias r.
+template <int PB>
 __device__ void trsv_fwd_block(const float* __restrict__ M, int P, const float* __restrict__ inv_diag,
                                float* __restrict__ r, float* __restrict__ z) {
     const int tid = threadIdx.x;
 #pragma unroll 1
-    for (int jb = 0; jb < P; jb += 4) {
-        float zb[4], iv[4], l10, l20, l21, l30, l31, l32;
+    for (int jb = 0; jb < P; jb += PB) {
+        float zb[PB], iv[PB], l[PB][PB];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { zb[c] = r[jb + c]; iv[c] = inv_diag[jb + c]; }
-        l10 = M[pidx(jb + 1, jb)];
-        l20 = M[pidx(jb + 2, jb)]; l21 = M[pidx(jb + 2, jb + 1)];
-        l30 = M[pidx(jb + 3, jb)]; l31 = M[pidx(jb + 3, jb + 1)]; l32 = M[pidx(jb + 3, jb + 2)];
-        const int i = jb + 4 + tid;
+        for (int c = 0; c < PB; ++c) { zb[c] = r[jb + c]; iv[c] = inv_diag[jb + c]; }
+#pragma unroll
+        for (int c = 1; c < PB; ++c)
+#pragma unroll
+            for (int t = 0; t < c; ++t) l[c][t] = M[pidx(jb + c, jb + t)];
+        const int i = jb + PB + tid;
         const bool upd = i < P;
-        const int ir = upd ? i : jb + 3;
-        float lr[4];
+        const int ir = upd ? i : jb + PB - 1;
+        float lr[PB];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) lr[c] = M[pidx(ir, jb + c)];
+        for (int c = 0; c < PB; ++c) lr[c] = M[pidx(ir, jb + c)];
         float ri = r[ir];
-        zb[0] = zb[0] * iv[0];
-        zb[1] = fmaf(-l10, zb[0], zb[1]) * iv[1];
-        zb[2] = fmaf(-l21, zb[1], fmaf(-l20, zb[0], zb[2])) * iv[2];
-        zb[3] = fmaf(-l32, zb[2], fmaf(-l31, zb[1], fmaf(-l30, zb[0], zb[3]))) * iv[3];
-        if (tid < 4) z[jb + tid] = slot_get(zb, tid);
+#pragma unroll
+        for (int c = 0; c < PB; ++c) {
+            zb[c] *= iv[c];
+#pragma unroll
+            for (int t = c + 1; t < PB; ++t) zb[t] = fmaf(-l[t][c], zb[c], zb[t]);
+        }
+        if (tid < PB) {
+#pragma unroll
+            for (int c = 0; c < PB; ++c)
+                if (c == tid) z[jb + c] = zb[c];
+        }
         if (upd) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) ri = fmaf(-lr[c], zb[c], ri);
+            for (int c = 0; c < PB; ++c) ri = fmaf(-lr[c], zb[c], ri);
             r[i] = ri;
         }
         __syncthreads();
@@ -417,22 +465,16 @@ struct SolveWork {              // shared-memory scratch of solve_damped
     int flag, refinements, fallbacks, pad;
 };
 
-// Solve (A + lam diag(dv)) delta = g, A packed lower FP64 in shared memory,
-// all threads of the block.  With S = diag(A + lam D)^-1/2 rounded to FP32
-// (any diagonal scaling serves; an FP32 one is exact in FP64 below), the
-// matrix S (A + lam D) S, augmented by the row S g, is factored in FP32 (the
-// forward substitution comes out of the factorisation); one back
-// substitution gives x; one step of iterative refinement with the residual
-// S g - S (A + lam D) S x evaluated in FP64 corrects it; delta = S x.  If the
-// FP32 factor fails, an FP64 factor of the unscaled matrix is used.  Returns
-// false when the damped matrix is not positive definite.
-__device__ bool solve_damped(const double* __restrict__ Ac, const double* __restrict__ g,
-                             const double* __restrict__ dv, double lam, int P, void* uni, SolveWork& w,
-                             double* __restrict__ delta) {
+// FP32 scaled factor-and-refine solve (see solve_damped) with panel width
+// PB; P4 = P rounded up to PB.  Returns false if the FP32 factor fails.
+template <int PB>
+__device__ bool solve_scaled_fp32(const double* __restrict__ Ac, const double* __restrict__ g,
+                                  const double* __restrict__ dv, double lam, int P, void* uni, SolveWork& w,
+                                  double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     float* L32 = reinterpret_cast<float*>(uni);
     float* Lp = L32 + L32_LP_OFF;
-    const int P4 = (P + 3) & ~3;   // padded with identity rows: every block of the factor is full
+    const int P4 = (P + PB - 1) & ~(PB - 1);   // padded with identity rows: every block of the factor is full
     for (int i = tid; i < P4; i += blockDim.x) {
         float s = 1.0f;
         double b = 0.0;
@@ -463,8 +505,8 @@ __device__ bool solve_damped(const double* __restrict__ Ac, const double* __rest
         }
     }
     __syncthreads();
-    if (chol_lowlat(L32, Lp, P4, w.inv32, &w.flag)) {
-        trsv_back_block(L32, P4, w.inv32, L32 + pidx(P4, 0), w.xv);      // x = L^-T (L^-1 S g)
+    if (chol_lowlat<PB>(L32, Lp, P4, w.inv32, &w.flag)) {
+        trsv_back_block<PB>(L32, P4, w.inv32, L32 + pidx(P4, 0), w.xv);      // x = L^-T (L^-1 S g)
         for (int i = tid; i < P4; i += blockDim.x) w.ud[i] = (double)w.sf[i] * (double)w.xv[i];
         __syncthreads();
         // refinement: c = (L L^T)^-1 (S g - S (A + lam D) S x), residual in
@@ -489,12 +531,31 @@ __device__ bool solve_damped(const double* __restrict__ Ac, const double* __rest
         }
         if (tid == 0) w.refinements += 1;
         __syncthreads();
-        trsv_fwd_block(L32, P4, w.inv32, w.cv, w.zv);
-        trsv_back_block(L32, P4, w.inv32, w.zv, w.cv);
+        trsv_fwd_block<PB>(L32, P4, w.inv32, w.cv, w.zv);
+        trsv_back_block<PB>(L32, P4, w.inv32, w.zv, w.cv);
         for (int i = tid; i < P; i += blockDim.x) delta[i] = (double)w.sf[i] * ((double)w.xv[i] + (double)w.cv[i]);
         __syncthreads();
         return true;
     }
+    return false;
+}
+
+// Solve (A + lam diag(dv)) delta = g, A packed lower FP64 in shared memory,
+// all threads of the block.  With S = diag(A + lam D)^-1/2 rounded to FP32
+// (any diagonal scaling serves; an FP32 one is exact in FP64 below), the
+// matrix S (A + lam D) S, augmented by the row S g, is factored in FP32 (the
+// forward substitution comes out of the factorisation); one back
+// substitution gives x; one step of iterative refinement with the residual
+// S g - S (A + lam D) S x evaluated in FP64 corrects it; delta = S x.  If the
+// FP32 factor fails, an FP64 factor of the unscaled matrix is used.  Returns
+// false when the damped matrix is not positive definite.
+__device__ bool solve_damped(const double* __restrict__ Ac, const double* __restrict__ g,
+                             const double* __restrict__ dv, double lam, int P, void* uni, SolveWork& w,
+                             double* __restrict__ delta) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    if (P <= 32 ? solve_scaled_fp32<4>(Ac, g, dv, lam, P, uni, w, delta)
+                : solve_scaled_fp32<8>(Ac, g, dv, lam, P, uni, w, delta))
+        return true;
     // FP64 factor of the unscaled damped matrix
     if (tid == 0) w.fallbacks += 1;
     double* M64 = reinterpret_cast<double*>(uni);
@@ -721,9 +782,19 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
             if (s_err) return;
             for (int e = b * (int)blockDim.x + tid; e < nacc; e += G * (int)blockDim.x) {
-                double s = 0.0;
-                for (int c = 0; c < G; ++c) s += __ldcg(partials + (size_t)c * NACC_MAX + e);
-                sums_nxt[e] = s;
+                // four independent FP64 chains (an FP64 add is ~64 cycles of
+                // latency here), combined in a fixed order
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                const double* pe = partials + e;
+                int c = 0;
+                for (; c + 3 < G; c += 4) {
+                    s0 += __ldcg(pe + (size_t)c * NACC_MAX);
+                    s1 += __ldcg(pe + (size_t)(c + 1) * NACC_MAX);
+                    s2 += __ldcg(pe + (size_t)(c + 2) * NACC_MAX);
+                    s3 += __ldcg(pe + (size_t)(c + 3) * NACC_MAX);
+                }
+                for (; c < G; ++c) s0 += __ldcg(pe + (size_t)c * NACC_MAX);
+                sums_nxt[e] = (s0 + s1) + (s2 + s3);
             }
             ++epoch;
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
