@@ -53,7 +53,7 @@ struct asp_ctx {
     SmoothTaps taps{};
     double smooth_flops = 0.0;   // 2 passes x 2 flops x taps x pixels, all scales
     size_t taps_cap = 0;
-    int s1_scales = 0;
+    size_t s1_cap = 0;              // floats of S1
     double* partials = nullptr;
     double* sums = nullptr;
     unsigned* bar = nullptr;
@@ -223,7 +223,7 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
                        ctx->bar, ctx->Tg, s)); }
     { Mark m(ctx, KC_UPDATE); CK(launch_update(st, ctx->comps, ctx->hist, ctx->dp, H, W, s)); }
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(st, &st->stopped, ctx->wbuf, s)); }
-    { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, s)); }
+    { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->taps, s)); }
     { Mark m(ctx, KC_SUB_V);
       CK(launch_sub_v(ctx->R, ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part, ctx->ticket,
                       s)); }
@@ -300,6 +300,7 @@ asp_status setup_taps(asp_ctx* ctx) {
     std::vector<float> taps;
     SmoothTaps t{};
     double sflops = 0.0;
+    int m_max = 0;
     for (int j = 0; j < ctx->p.n_scales; ++j) {
         double s_j = ctx->omega_b * std::ldexp(1.0, j);
         if (j > 0 && s_j > std::min(H, W) / 8.0) continue;
@@ -313,23 +314,42 @@ asp_status setup_taps(asp_ctx* ctx) {
         double inv = 1.0 / std::sqrt(ss);
         t.off[t.n] = (int)taps.size();
         t.m[t.n] = m;
+        t.t8[t.n] = (2 * m + 1 + 7) & ~7;
         t.scale[t.n] = s_j;
         for (double v : e) taps.push_back((float)(v * inv));
+        t.t8max = std::max(t.t8max, t.t8[t.n]);
+        m_max = std::max(m_max, m);
         t.n++;
         sflops += 2.0 * 2.0 * (2 * m + 1) * (double)N;
     }
+    // register-blocked pass geometry: 8 outputs per thread
+    const int per_row = (W + 7) / 8;
+    t.tpr = std::min(RED_THREADS, (per_row + 31) / 32 * 32);
+    t.rpb = RED_THREADS / t.tpr;
+    t.nseg = (W + 8 * t.tpr - 1) / (8 * t.tpr);
+    {
+        const int last = 8 * t.tpr + t.t8max + 7;          // largest staged index
+        t.blen = last + (last >> 3) + 1;
+    }
+    t.mpad = ((m_max + 7) & ~7) + 8;
+    t.s1rows = (long long)H + 2LL * t.mpad + 8;
     if (taps.size() > ctx->taps_cap) {
         float* p = nullptr;
         CK(dalloc(ctx, &p, taps.size()));
         ctx->taps_dev = p;
         ctx->taps_cap = taps.size();
     }
-    if (t.n > ctx->s1_scales) {
+    const size_t s1_need = (size_t)t.n * (size_t)t.s1rows * (size_t)W;
+    if (s1_need > ctx->s1_cap) {
         float* p = nullptr;
-        CK(dalloc(ctx, &p, (size_t)t.n * N));
+        CK(dalloc(ctx, &p, s1_need));
         ctx->S1 = p;
-        ctx->s1_scales = t.n;
+        ctx->s1_cap = s1_need;
     }
+    // the halo rows stay zero: only interior rows are ever written
+    CK(cudaMemset(ctx->S1, 0, s1_need * sizeof(float)));
+    const size_t smem_h = ((size_t)t.t8max + (size_t)t.rpb * t.blen) * sizeof(float);
+    if (smem_h > 48 * 1024) return ASP_ERR_UNSUPPORTED;
     CK(cudaMemcpy(ctx->taps_dev, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice));
     t.k = ctx->taps_dev;
     ctx->taps = t;
@@ -425,8 +445,10 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     AL(ctx->comps, cap);
     AL(ctx->comp_stage, MAX_TERMS);
     AL(ctx->hist, cap);
-    AL(ctx->wbuf, (size_t)MAX_TERMS * (W + H));
-    AL(ctx->T1, (size_t)ctx->terms_cap * (2 * H - 1) * W);
+    AL(ctx->wbuf, (size_t)MAX_TERMS * wslot_stride(W, H));
+    AL(ctx->T1, ((size_t)ctx->terms_cap * (2 * H - 1) + T1_SLACK_ROWS) * W);   // slack rows: see k_sub_v_argmax
+    if (cudaMemset(ctx->T1, 0, ((size_t)ctx->terms_cap * (2 * H - 1) + T1_SLACK_ROWS) * W * sizeof(float)) != cudaSuccess)
+        return bail(ASP_ERR_CUDA);
     AL(ctx->partials, (size_t)ctx->g_max * NACC_MAX);
     AL(ctx->sums, 2 * NACC_MAX);
     AL(ctx->bar, 1);
@@ -686,7 +708,7 @@ asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float g
     CK(cudaMemcpyAsync(ctx->comp_stage, comps, n * sizeof(asp_component), cudaMemcpyHostToDevice, ctx->stream));
     { Mark m(ctx, KC_UPDATE); CK(launch_terms_from_components(ctx->st, ctx->comp_stage, n, gain, ctx->H, ctx->W, ctx->stream)); }
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(ctx->st, nullptr, ctx->wbuf, ctx->stream)); }
-    { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->stream)); }
+    { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->taps, ctx->stream)); }
     {
         Mark m(ctx, KC_SUB_V);
         CK(launch_sub_v(ctx->R, ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,

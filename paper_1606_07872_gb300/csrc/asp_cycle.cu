@@ -79,8 +79,8 @@ __device__ bool make_term(const asp_component& c, double s, int H, int W, int sl
     td.uy1 = (int)(uy1 > (1LL << 30) ? (1LL << 30) : uy1);
     td.scale = (float)s;
     td.cx = c.x; td.cy = c.y; td.w = c.width;
-    td.woff_x = slot * (W + H);
-    td.woff_y = slot * (W + H) + W;
+    td.woff_x = slot * wslot_stride(W, H);
+    td.woff_y = slot * wslot_stride(W, H) + wslot_x_len(W);
     td.r0 = H - td.qy0 - td.ny + 1;
     td.pad = 0;
     return true;
@@ -336,14 +336,7 @@ k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __res
         const int u0 = axis == 0 ? td.ux0 : td.uy0;
         const int u1 = axis == 0 ? td.ux1 : td.uy1;
         float* out = wbuf + (axis == 0 ? td.woff_x : td.woff_y);
-        if (td.bilinear) {
-            const double f0 = floor(c);
-            const double fr = c - f0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int q = q0 + i;
-                out[i] = (float)(q == (int)f0 ? 1.0 - fr : fr);
-            }
-        } else {
+        {
             const double iw = 1.0 / (2.0 * td.w * td.w);
             double s = 0.0;
             for (long long q = (long long)u0 + threadIdx.x; q <= u1; q += blockDim.x) {
@@ -358,9 +351,15 @@ k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __res
             }
             const double inv = 1.0 / red[0];
             __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const double dq = (double)(q0 + i) - c;
-                out[i] = (float)(exp(-dq * dq * iw) * inv);
+            // reversed (tap i at n - 1 - i) and zero-padded to a multiple of 8
+            const int n8 = (n + 7) & ~7;
+            for (int i = threadIdx.x; i < n8; i += blockDim.x) {
+                float v = 0.f;
+                if (i < n) {
+                    const double dq = (double)(q0 + i) - c;
+                    v = (float)(exp(-dq * dq * iw) * inv);
+                }
+                out[i < n ? n - 1 - i : i] = v;
             }
         }
         __syncthreads();

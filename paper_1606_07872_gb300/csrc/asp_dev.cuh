@@ -15,6 +15,7 @@ constexpr int NB_MAX = NAP_MAX / 4;                // 4x4 tiles per side
 constexpr int NTILES_MAX = NB_MAX * (NB_MAX + 1) / 2;
 constexpr int NACC_MAX = NTILES_MAX * 16;          // accumulator entries (tile order)
 constexpr int MAX_TERMS = 2 * KMAX;                // subtraction terms per iteration
+constexpr int T1_SLACK_ROWS = 16;                  // zeroed rows behind the last subtraction term
 constexpr int MAX_SCALES = 8;                      // smoothing scales
 constexpr int FIT_THREADS = 256;
 constexpr int PX_SMEM = 12288;                     // target pixels one CTA keeps in smem
@@ -147,6 +148,12 @@ __device__ __forceinline__ void arg_warp_reduce(float& v, int& j, long long& i) 
 
 // Member box of the fit window: half-width max(5, ceil(4 w)) around the
 // rounded centre (inclusive, unclipped).
+// Axis weights of one subtraction term in the weight buffer: wx then wy,
+// each stored reversed and zero-padded to a multiple of 8 taps, each
+// region 16-byte aligned.
+__device__ __host__ inline int wslot_x_len(int W) { return (W + 8 + 3) & ~3; }
+__device__ __host__ inline int wslot_stride(int W, int H) { return wslot_x_len(W) + ((H + 8 + 3) & ~3); }
+
 __device__ __host__ inline void member_box(double x, double y, double w, long long* b) {
     long long h = (long long)ceil(4.0 * w);
     if (h < 5) h = 5;

@@ -101,92 +101,159 @@ k_argmax_abs(const float* __restrict__ R, long long N, ArgRes* part, unsigned* t
     grid_arg_finish(bv, bj, bi, part, ticket, res);
 }
 
+// Bank-padded shared-memory index of the row passes: thread t reads q = 8 (t + c) + i, padded 9 (t + c) + i,
+// so the 32 lanes of a warp hit 32 different banks.
+__device__ __forceinline__ int spad(int q) { return q + (q >> 3); }
+
 // ------------------------------------------------------------------ subtraction
-// Horizontal pass: T1_t[r][u] = sum_i wx_t[i] B[r0_t + r][u - qx0_t - i + W]
-// for r < H + ny_t - 1, u < W, every term t.
+// R -= B * dC (Sect. 2 step 3) with dC a sum of separable sampled terms:
+// for term t with axis weights wx (nx taps from column qx0) and wy (ny taps
+// from row qy0), T1_t = rows of B convolved with wx, then R -= scale_t *
+// (T1_t convolved with wy).  Both passes are register-blocked like the
+// smoothing: 8 consecutive outputs per thread, a 16-entry sliding window,
+// 8 taps per step.  The weight buffer holds each axis reversed and
+// zero-padded to a multiple of 8, so both passes are correlations
+//   T1_t[r][u] = sum_i wxr[i] B[r0 + r][c0 + u + i],  c0 = W - qx0 - nx + 1,
+//   dR[y][x]   = sum_k wyr[k] T1_t[y + k][x].
+
+// Row pass.  A block task is rpb row segments (8 tpr outputs each) of one
+// term's T1 rows; the B segment is staged in shared memory (bank-padded).
+// The geometry (tpr, rpb, nseg) depends only on W and is shared with the
+// smoothing row pass.
 __global__ void __launch_bounds__(RED_THREADS)
 k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict__ st, const int* gate,
-        const float* __restrict__ wbuf, float* __restrict__ T1) {
+        const float* __restrict__ wbuf, float* __restrict__ T1, int tpr, int rpb, int nseg, int blen) {
     if (gate && *gate) return;
+    extern __shared__ __align__(16) float sm_sub[];
+    const int tid = threadIdx.x;
+    const int sub = tid / tpr, lt = tid - sub * tpr;
+    float* buf = sm_sub + sub * blen;
     const int nt = st->n_terms;
     const int W2 = 2 * W;
-    for (int t = 0; t < nt; ++t) {
-        const TermDesc td = st->terms[t];
-        if (td.bilinear) continue;
-        const long long nrows = H + td.ny - 1;
-        const long long total = nrows * W;
-        const float* wx = wbuf + td.woff_x;
-        float* out = T1 + td.t1off;
-        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-             q += (long long)gridDim.x * blockDim.x) {
-            const int r = (int)(q / W), u = (int)(q % W);
-            const float* brow = B + (long long)(td.r0 + r) * W2 + (u - td.qx0 + W);
-            float s = 0.f;
-            for (int i = 0; i < td.nx; ++i) s = fmaf(wx[i], __ldg(brow - i), s);
-            out[q] = s;
+    long long rows_total = 0;
+    for (int t = 0; t < nt; ++t)
+        if (!st->terms[t].bilinear) rows_total += (long long)(H + st->terms[t].ny - 1) * nseg;
+    const long long btasks = (rows_total + rpb - 1) / rpb;
+    for (long long task = blockIdx.x; task < btasks; task += gridDim.x) {
+        long long rt = task * rpb + sub;
+        const bool live = sub < rpb && rt < rows_total;
+        // locate (term, row, segment) of this row task
+        int t = 0;
+        if (live) {
+            for (; t < nt; ++t) {
+                if (st->terms[t].bilinear) continue;
+                const long long n = (long long)(H + st->terms[t].ny - 1) * nseg;
+                if (rt < n) break;
+                rt -= n;
+            }
+        }
+        const TermDesc& td = st->terms[live ? t : 0];
+        const int r = live ? (int)(rt / nseg) : 0;
+        const int xs = live ? (int)(rt % nseg) * 8 * tpr : 0;
+        const int nx8 = (td.nx + 7) & ~7;
+        const int c0 = W - td.qx0 - td.nx + 1;
+        __syncthreads();                                     // previous task's reads are done
+        if (sub < rpb) {
+            const float* brow = B + (long long)(td.r0 + r) * W2;
+            const int len = 8 * tpr + nx8 + 8;
+            for (int q = lt; q < len; q += tpr) {
+                const int c = c0 + xs + q;
+                buf[spad(q)] = (live && c >= 0 && c < W2) ? __ldg(brow + c) : 0.f;
+            }
+        }
+        __syncthreads();
+        const int x0 = xs + 8 * lt;
+        if (!live || x0 >= W) continue;
+        const float* wxr = wbuf + td.woff_x;
+        float acc[8], w[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; w[i] = buf[spad(8 * lt + i)]; }
+#pragma unroll 1
+        for (int u0 = 0; u0 < nx8; u0 += 8) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[8 + i] = buf[spad(8 * lt + u0 + 8 + i)];
+            const float4 ka = __ldg(reinterpret_cast<const float4*>(wxr + u0));
+            const float4 kb = __ldg(reinterpret_cast<const float4*>(wxr + u0 + 4));
+            const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+            for (int du = 0; du < 8; ++du)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+        }
+        float* out = T1 + td.t1off + (long long)r * W + x0;
+        if (x0 + 8 <= W && (W & 3) == 0) {
+            reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (x0 + i < W) out[i] = acc[i];
         }
     }
 }
 
-// Vertical pass + update + fused argmax:
-// R[py][px] -= sum_t scale_t sum_j wy_t[j] T1_t[py - j + ny_t - 1][px]
-//            + sum_d w_d B[py - qy_d + H][px - qx_d + W]      (point deposits)
-// Each thread owns VROWS consecutive rows of one column: a sliding window
-// over T1 gives VROWS FMAs per T1 load; lanes hold consecutive columns.
-constexpr int VROWS = 8;
-
+// Column pass + update + fused argmax:
+// R[y][x] -= sum_t scale_t sum_k wyr_t[k] T1_t[y + k][x]
+//          + sum_d w_d B[y - qy_d + H][x - qx_d + W]      (point deposits)
+// Each thread owns 8 consecutive rows of one column (lanes: consecutive
+// columns), one block task is 32 columns x 64 rows.  The T1 buffer carries
+// zeroed slack rows behind its last term, so the window (which runs up to
+// 15 rows past a term's end under zero taps) needs no bounds tests.
 __global__ void __launch_bounds__(RED_THREADS)
 k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* gate,
                const float* __restrict__ wbuf, const float* __restrict__ T1, const float* __restrict__ B,
                ArgRes* part, unsigned* ticket) {
     if (gate && *gate) return;
     __shared__ Deposit sdep[MAX_DEPOSITS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = st->n_terms;
     const int nd = st->n_dep;
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) sdep[i] = st->dep[i];
+    for (int i = tid; i < nd; i += blockDim.x) sdep[i] = st->dep[i];
     __syncthreads();
     const int W2 = 2 * W;
-    const long long nblk = (H + VROWS - 1) / VROWS;
+    const int ncb = (W + 31) / 32, nrb = (H + 63) / 64;
     float bv = 0.f;
     long long bi = 0x7fffffffffffffffLL;
     int bj = 0;
     unsigned bad = 0;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nblk * W;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int px = (int)(q % W);
-        const int py0 = (int)(q / W) * VROWS;
-        float acc[VROWS];
+    for (long long task = blockIdx.x; task < (long long)ncb * nrb; task += gridDim.x) {
+        const int rb = (int)(task / ncb), cb = (int)(task % ncb);
+        const int px = cb * 32 + lane, py0 = rb * 64 + 8 * warp;
+        if (px >= W || py0 >= H) continue;
+        float acc[8];
 #pragma unroll
-        for (int o = 0; o < VROWS; ++o) acc[o] = 0.f;
+        for (int o = 0; o < 8; ++o) acc[o] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const TermDesc& td = st->terms[t];
             if (td.bilinear) continue;
-            const int ny = td.ny;
-            const long long nrows_t1 = H + ny - 1;
-            const float* wy = wbuf + td.woff_y;
-            const float* col = T1 + td.t1off + px;
-            // window rows py0 + o + k for k = 0 .. ny-1 (tap j = ny - 1 - k)
-            float win[VROWS], s[VROWS];
+            const int ny8 = (td.ny + 7) & ~7;
+            const float* wyr = wbuf + td.woff_y;
+            const float* col = T1 + td.t1off + (long long)py0 * W + px;
+            float s[8], w[16];
 #pragma unroll
-            for (int o = 0; o < VROWS; ++o) {
-                const long long r = py0 + o;
-                win[o] = r < nrows_t1 ? __ldg(col + r * W) : 0.f;
-                s[o] = 0.f;
+            for (int o = 0; o < 8; ++o) { s[o] = 0.f; w[o] = __ldg(col + (long long)o * W); }
+#pragma unroll 1
+            for (int k0 = 0; k0 < ny8; k0 += 8) {
+                const float* c8 = col + (long long)(k0 + 8) * W;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) w[8 + i] = __ldg(c8 + (long long)i * W);
+                const float4 ka = __ldg(reinterpret_cast<const float4*>(wyr + k0));
+                const float4 kb = __ldg(reinterpret_cast<const float4*>(wyr + k0 + 4));
+                const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+                for (int dk = 0; dk < 8; ++dk)
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) s[o] = fmaf(kk[dk], w[o + dk], s[o]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
             }
-            for (int k = 0; k < ny; ++k) {
-                const float w = __ldg(wy + (ny - 1 - k));
 #pragma unroll
-                for (int o = 0; o < VROWS; ++o) s[o] = fmaf(w, win[o], s[o]);
-#pragma unroll
-                for (int o = 0; o < VROWS - 1; ++o) win[o] = win[o + 1];
-                const long long r = (long long)py0 + VROWS + k;
-                win[VROWS - 1] = r < nrows_t1 ? __ldg(col + r * W) : 0.f;
-            }
-#pragma unroll
-            for (int o = 0; o < VROWS; ++o) acc[o] = fmaf(td.scale, s[o], acc[o]);
+            for (int o = 0; o < 8; ++o) acc[o] = fmaf(td.scale, s[o], acc[o]);
         }
 #pragma unroll
-        for (int o = 0; o < VROWS; ++o) {
+        for (int o = 0; o < 8; ++o) {
             const int py = py0 + o;
             if (py < H) {
                 float dsum = 0.f;
@@ -207,25 +274,75 @@ k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* g
 }
 
 // ------------------------------------------------------------------ smoothing
-// Row pass for every scale: S1_j[y][x] = sum_u k_j[u] R[y][x + u - m_j].
+// Separable Gaussian smoothing at every scale s_j (Sect. 2 step 1), zero
+// padded at the image edges, as two register-blocked passes: each thread
+// produces 8 consecutive outputs, keeping a 16-entry sliding window of the
+// input in registers, so 8 taps cost 8 loads, 2 broadcast tap loads and 64
+// FMAs.  Taps are zero-padded to a multiple of 8 (t8).
+
+// Row pass: S1_j[y + mpad][x] = sum_u k_j[u] R[y][x + u - m_j].  A block
+// task is rpb row segments of 8 tpr outputs each; the segment with its
+// halo is staged in shared memory.  Blocks loop over the tasks of every
+// scale (or only_scale).
 __global__ void __launch_bounds__(RED_THREADS)
 k_smooth_h(const float* __restrict__ R, int H, int W, const SmoothTaps taps, const int* gate,
            int only_scale, float* __restrict__ S1) {
     if (gate && *gate) return;
-    const long long N = (long long)H * W;
-    const int j0 = only_scale >= 0 ? only_scale : 0, j1 = only_scale >= 0 ? only_scale + 1 : taps.n;
-    for (int j = j0; j < j1; ++j) {
-        const float* k = taps.k + taps.off[j];
-        const int m = taps.m[j];
-        float* out = S1 + (long long)j * N;
-        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N;
-             p += (long long)gridDim.x * blockDim.x) {
-            const int y = (int)(p / W), x = (int)(p % W);
+    extern __shared__ __align__(16) float sm_h[];
+    float* ktap = sm_h;
+    const int tid = threadIdx.x;
+    const int tpr = taps.tpr, rpb = taps.rpb, nseg = taps.nseg;
+    const int sub = tid / tpr, lt = tid - sub * tpr;
+    float* buf = sm_h + taps.t8max + sub * taps.blen;
+    const int j0 = only_scale >= 0 ? only_scale : 0, nj = only_scale >= 0 ? 1 : taps.n;
+    const long long rowtasks = (long long)H * nseg;
+    const long long btasks = (rowtasks + rpb - 1) / rpb;
+    for (long long task = blockIdx.x; task < nj * btasks; task += gridDim.x) {
+        const int j = j0 + (int)(task / btasks);
+        const long long rt = (task % btasks) * rpb + sub;
+        const int m = taps.m[j], t8 = taps.t8[j];
+        const bool live = sub < rpb && rt < rowtasks;
+        const int y = live ? (int)(rt / nseg) : 0;
+        const int xs = live ? (int)(rt % nseg) * 8 * tpr : 0;
+        __syncthreads();                                     // previous task's reads are done
+        const float* kj = taps.k + taps.off[j];
+        for (int q = tid; q < t8; q += blockDim.x) ktap[q] = q < 2 * m + 1 ? kj[q] : 0.f;
+        if (sub < rpb) {
             const float* row = R + (long long)y * W;
-            const int u0 = max(0, m - x), u1 = min(2 * m, W - 1 - x + m);
-            float s = 0.f;
-            for (int u = u0; u <= u1; ++u) s = fmaf(k[u], __ldg(row + x + u - m), s);
-            out[p] = s;
+            const int len = 8 * tpr + t8 + 8;
+            for (int q = lt; q < len; q += tpr) {
+                const int x = xs - m + q;
+                buf[spad(q)] = (live && x >= 0 && x < W) ? __ldg(row + x) : 0.f;
+            }
+        }
+        __syncthreads();
+        const int x0 = xs + 8 * lt;
+        if (!live || x0 >= W) continue;
+        float acc[8], w[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; w[i] = buf[spad(8 * lt + i)]; }
+#pragma unroll 1
+        for (int u0 = 0; u0 < t8; u0 += 8) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[8 + i] = buf[spad(8 * lt + u0 + 8 + i)];
+            const float4 ka = *reinterpret_cast<const float4*>(ktap + u0);
+            const float4 kb = *reinterpret_cast<const float4*>(ktap + u0 + 4);
+            const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+            for (int du = 0; du < 8; ++du)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+        }
+        float* out = S1 + ((long long)j * taps.s1rows + y + taps.mpad) * W + x0;
+        if (x0 + 8 <= W && (W & 3) == 0) {
+            reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (x0 + i < W) out[i] = acc[i];
         }
     }
 }
@@ -233,27 +350,59 @@ k_smooth_h(const float* __restrict__ R, int H, int W, const SmoothTaps taps, con
 // Column pass for every scale with the fused argmax of |S_j| over (j, p);
 // the last block turns the winner into the initial values
 // (S/(sqrt(pi) s), x*, y*, max(s, omega_b)).  out_S (optional) receives S_j.
+// A block task is 32 columns x 64 rows of one scale: lane = column, warp w
+// = rows 8w..8w+7.  The row-pass image has mpad zero rows above and below,
+// so the sliding window needs no bounds tests.
 __global__ void __launch_bounds__(RED_THREADS)
 k_smooth_v_argmax(const float* __restrict__ S1, int H, int W, const SmoothTaps taps, CycleState* st,
                   const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket) {
     if (gate && *gate) return;
-    const long long N = (long long)H * W;
-    const int j0 = only_scale >= 0 ? only_scale : 0, j1 = only_scale >= 0 ? only_scale + 1 : taps.n;
+    extern __shared__ __align__(16) float ktap[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = only_scale >= 0 ? only_scale : 0, nj = only_scale >= 0 ? 1 : taps.n;
+    const int ncb = (W + 31) / 32, nrb = (H + 63) / 64;
+    const long long per = (long long)ncb * nrb;
     float bv = 0.f;
     long long bi = 0x7fffffffffffffffLL;
     int bj = 0x7fffffff;
-    for (int j = j0; j < j1; ++j) {
-        const float* k = taps.k + taps.off[j];
-        const int m = taps.m[j];
-        const float* in = S1 + (long long)j * N;
-        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N;
-             p += (long long)gridDim.x * blockDim.x) {
-            const int y = (int)(p / W), x = (int)(p % W);
-            const int u0 = max(0, m - y), u1 = min(2 * m, H - 1 - y + m);
-            float s = 0.f;
-            for (int u = u0; u <= u1; ++u) s = fmaf(k[u], __ldg(in + (long long)(y + u - m) * W + x), s);
-            if (out_S) out_S[p] = s;
-            if (arg_better(s, j, p, bv, bj, bi)) { bv = s; bj = j; bi = p; }
+    for (long long task = blockIdx.x; task < nj * per; task += gridDim.x) {
+        const int j = j0 + (int)(task / per);
+        const int rem = (int)(task % per);
+        const int rb = rem / ncb, cb = rem - rb * ncb;
+        const int m = taps.m[j], t8 = taps.t8[j];
+        __syncthreads();
+        const float* kj = taps.k + taps.off[j];
+        for (int q = tid; q < t8; q += blockDim.x) ktap[q] = q < 2 * m + 1 ? kj[q] : 0.f;
+        __syncthreads();
+        const int x = cb * 32 + lane, y0 = rb * 64 + 8 * warp;
+        if (x >= W || y0 >= H) continue;
+        const float* col = S1 + ((long long)j * taps.s1rows + (y0 - m + taps.mpad)) * W + x;
+        float acc[8], w[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; w[i] = __ldg(col + (long long)i * W); }
+#pragma unroll 1
+        for (int u0 = 0; u0 < t8; u0 += 8) {
+            const float* c8 = col + (long long)(u0 + 8) * W;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[8 + i] = __ldg(c8 + (long long)i * W);
+            const float4 ka = *reinterpret_cast<const float4*>(ktap + u0);
+            const float4 kb = *reinterpret_cast<const float4*>(ktap + u0 + 4);
+            const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+            for (int du = 0; du < 8; ++du)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int y = y0 + i;
+            if (y < H) {
+                const long long p = (long long)y * W + x;
+                if (out_S) out_S[p] = acc[i];
+                if (arg_better(acc[i], j, p, bv, bj, bi)) { bv = acc[i]; bj = j; bi = p; }
+            }
         }
     }
     block_arg_reduce(bv, bj, bi);
@@ -281,8 +430,12 @@ cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, u
 }
 
 cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, const int* gate, const float* wbuf,
-                         float* T1, int grid, cudaStream_t s) {
-    k_sub_h<<<grid, RED_THREADS, 0, s>>>(B, H, W, st, gate, wbuf, T1);
+                          float* T1, int grid, const SmoothTaps& geo, cudaStream_t s) {
+    // segment buffer: 8 tpr outputs + up to roundup8(W) taps + 8 window slack, bank-padded
+    const int last = 8 * geo.tpr + ((W + 7) & ~7) + 7;
+    const int blen = last + (last >> 3) + 1;
+    const size_t smem = (size_t)geo.rpb * blen * sizeof(float);
+    k_sub_h<<<grid, RED_THREADS, smem, s>>>(B, H, W, st, gate, wbuf, T1, geo.tpr, geo.rpb, geo.nseg, blen);
     return cudaGetLastError();
 }
 
@@ -294,13 +447,15 @@ cudaError_t launch_sub_v(float* R, const float* B, int H, int W, CycleState* st,
 
 cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
                             float* S1, int grid, cudaStream_t s) {
-    k_smooth_h<<<grid, RED_THREADS, 0, s>>>(R, H, W, taps, gate, only_scale, S1);
+    const size_t smem = ((size_t)taps.t8max + (size_t)taps.rpb * taps.blen) * sizeof(float);
+    k_smooth_h<<<grid, RED_THREADS, smem, s>>>(R, H, W, taps, gate, only_scale, S1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
                             int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
-    k_smooth_v_argmax<<<grid, RED_THREADS, 0, s>>>(S1, H, W, taps, st, gate, only_scale, out_S, part, ticket);
+    k_smooth_v_argmax<<<grid, RED_THREADS, (size_t)taps.t8max * sizeof(float), s>>>(S1, H, W, taps, st, gate,
+                                                                                   only_scale, out_S, part, ticket);
     return cudaGetLastError();
 }
 

@@ -10,8 +10,17 @@ struct SmoothTaps {          // unit-L2 1-D smoothing kernels, passed by value
     const float* k;          // all taps, scale j at k + off[j], length 2 m[j] + 1
     int off[MAX_SCALES];
     int m[MAX_SCALES];
+    int t8[MAX_SCALES];      // 2 m[j] + 1 rounded up to 8 (zero taps beyond 2 m[j])
     double scale[MAX_SCALES];
     int n;
+    int t8max;               // max over scales of t8
+    // launch geometry of the register-blocked passes (8 outputs per thread)
+    int tpr;                 // row pass: threads per row segment (multiple of 32, <= 256)
+    int rpb;                 // row pass: row segments per block (256 / tpr)
+    int nseg;                // row pass: segments per image row
+    int blen;                // row pass: shared floats per segment buffer (bank-padded)
+    int mpad;                // zero halo rows above and below each scale's row-pass image
+    long long s1rows;        // rows of each scale's row-pass image (H + 2 mpad + 8)
 };
 
 // asp_fit.cu
@@ -25,7 +34,7 @@ cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const 
 cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, unsigned* ticket, ArgRes* res,
                           unsigned* nonfinite, const int* gate, cudaStream_t s);
 cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, const int* gate, const float* wbuf,
-                         float* T1, int grid, cudaStream_t s);
+                          float* T1, int grid, const SmoothTaps& geo, cudaStream_t s);
 cudaError_t launch_sub_v(float* R, const float* B, int H, int W, CycleState* st, const int* gate, const float* wbuf,
                          const float* T1, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
 cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
