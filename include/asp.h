@@ -295,6 +295,60 @@ asp_status asp_fit_static(const float* image_dev, int H, int W, const asp_gauss*
 asp_status asp_save_state(asp_ctx* ctx, const char* path);
 asp_status asp_load_state(asp_ctx* ctx, const char* path);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent images -- each with its own size, PSF, dirty image and
+ * minor-cycle state -- advanced together.  The paper runs one image at a
+ * time and has no batch of its own; its test data are 32-channel wide-band
+ * observations (Sect. 4), and channels or fields imaged separately are
+ * independent minor cycles, which this serves.  One minor-cycle iteration of
+ * the whole batch is one
+ * launch per kernel of the iteration with the images on grid.y, and the LM
+ * fits (Eq. 6) of all images run in ONE cooperative launch in which image i
+ * owns a fixed group of CTAs with its own grid barrier.  asp_batch_minor_cycle
+ * captures eight batch iterations into a CUDA graph and replays it.
+ *
+ * Every image's result is exactly what a context of its own would compute
+ * (same kernels, same per-image buffers), given the same fit-group size. */
+typedef struct asp_batch asp_batch;
+
+typedef struct {
+    int px_per_cta;        /* chosen LM window tile: target pixels per CTA (0: automatic rule) */
+    int share_policy;      /* 0: equal CTA groups, 1: groups proportional to image area */
+    int n_candidates;      /* candidates timed */
+    double best_ms;        /* time of the chosen candidate over the trial iterations */
+    double default_ms;     /* time of the untuned setting (px_per_cta 0, equal groups) */
+} asp_batch_tuning;
+
+/* Create a batch of n images (1 <= n <= 152): image i is H[i] x W[i], its
+ * dirty image dirty[i] (H x W) and PSF psf[i] (2H x 2W, zero lag at
+ * [H, W]), FP32 row-major, all in host memory if on_host else device memory
+ * (copied; the caller keeps ownership).  Every image gets its own context
+ * (asp_init: beam fit, noise level) with the shared params and the batch's
+ * stream (NULL: the legacy default stream).  Errors: ASP_ERR_INVALID_ARG
+ * (bad n, size or pointer), ASP_ERR_UNSUPPORTED (more images than fit CTAs),
+ * ASP_ERR_OOM, ASP_ERR_CUDA, or an image's asp_init error.  On error nothing
+ * is left allocated. */
+asp_status asp_batch_create(const asp_params* params, int n, const int* H, const int* W,
+                            const float* const* dirty, const float* const* psf, int on_host, void* stream,
+                            asp_batch** out);
+asp_status asp_batch_destroy(asp_batch* b);
+/* Restart every image from its dirty image (state, components and history
+ * cleared; beam and noise level kept). */
+asp_status asp_batch_reset(asp_batch* b);
+/* Run up to n_iter more minor-cycle iterations on every image (an image
+ * stops early on its own noise test).  stats: NULL or n entries (host),
+ * filled per image as asp_minor_cycle fills its one.  Synchronises. */
+asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stats);
+/* Autotuner of the batched fit: times n_trial_iter batch iterations from a
+ * reset for each candidate window tile (pixels per CTA) and CTA-group
+ * policy, keeps the fastest, and resets the batch.  out (host) may be NULL. */
+asp_status asp_batch_autotune(asp_batch* b, int n_trial_iter, asp_batch_tuning* out);
+/* Borrow image i's context for queries (residual, components, history,
+ * stats, state); owned by the batch -- do not destroy it. */
+asp_status asp_batch_image(asp_batch* b, int i, asp_ctx** ctx);
+/* Kernels the batch has launched (graph nodes counted per replay). */
+asp_status asp_batch_launch_count(asp_batch* b, int64_t* n);
+
 #ifdef __cplusplus
 }
 #endif

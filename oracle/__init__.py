@@ -19,3 +19,4 @@ details) are pinned only to the paper's degenerate cases and to invariants;
 they carry a "reading" note in their docstrings.
 """
 from .asp_oracle import *  # noqa: F401,F403
+from . import mlp_oracle  # noqa: F401,E402  (learned initial values: MLP, loss, optimiser)

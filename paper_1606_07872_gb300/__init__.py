@@ -26,8 +26,9 @@ __all__ = [
     "asp_find_peak", "asp_fit_active_set", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
-    "asp_get_last_fit",
-    "Context",
+    "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
+    "asp_batch_autotune", "asp_batch_image", "asp_batch_launch_count",
+    "Context", "Batch",
 ]
 
 _LIB: Optional[C.CDLL] = None
@@ -284,6 +285,69 @@ def asp_load_state(h, path: str):
     _check(lib().asp_load_state(h, os.fsencode(path)), "asp_load_state", h)
 
 
+# ----------------------------------------------------------------- batches
+
+def asp_batch_create(params: asp_params, dirty: Sequence, psf: Sequence, stream=None):
+    """asp_batch_create: lists of per-image dirty (H x W) and psf (2H x 2W)
+    arrays, all numpy (host) or all float32 CUDA tensors (device)."""
+    n = len(dirty)
+    if n != len(psf) or n == 0:
+        raise ValueError("dirty and psf must be non-empty lists of equal length")
+    on_host = isinstance(dirty[0], np.ndarray)
+    H = (C.c_int * n)()
+    W = (C.c_int * n)()
+    dp = (C.c_void_p * n)()
+    pp = (C.c_void_p * n)()
+    keep = []
+    for i in range(n):
+        h_, w_ = (int(dirty[i].shape[0]), int(dirty[i].shape[1]))
+        H[i], W[i] = h_, w_
+        if on_host:
+            d = _host_f32(dirty[i], (h_, w_), "dirty")
+            q = _host_f32(psf[i], (2 * h_, 2 * w_), "psf")
+            keep += [d, q]
+            dp[i], pp[i] = d.ctypes.data, q.ctypes.data
+        else:
+            dp[i] = _cuda_f32(dirty[i], (h_, w_), "dirty")
+            pp[i] = _cuda_f32(psf[i], (2 * h_, 2 * w_), "psf")
+    h = C.c_void_p()
+    _check(lib().asp_batch_create(C.byref(params), n, H, W, dp, pp, 1 if on_host else 0, _stream_handle(stream),
+                                  C.byref(h)), "asp_batch_create")
+    return h.value
+
+
+def asp_batch_destroy(b):
+    _check(lib().asp_batch_destroy(b), "asp_batch_destroy")
+
+
+def asp_batch_reset(b):
+    _check(lib().asp_batch_reset(b), "asp_batch_reset")
+
+
+def asp_batch_minor_cycle(b, n_iter: int, n_images: int) -> list:
+    stats = (asp_cycle_stats * n_images)()
+    _check(lib().asp_batch_minor_cycle(b, n_iter, stats), "asp_batch_minor_cycle")
+    return [_stats_dict(stats[i]) for i in range(n_images)]
+
+
+def asp_batch_autotune(b, n_trial_iter: int) -> dict:
+    t = _lib.asp_batch_tuning()
+    _check(lib().asp_batch_autotune(b, n_trial_iter, C.byref(t)), "asp_batch_autotune")
+    return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def asp_batch_image(b, i: int):
+    h = C.c_void_p()
+    _check(lib().asp_batch_image(b, i, C.byref(h)), "asp_batch_image")
+    return h.value
+
+
+def asp_batch_launch_count(b) -> int:
+    n = C.c_int64()
+    _check(lib().asp_batch_launch_count(b, C.byref(n)), "asp_batch_launch_count")
+    return n.value
+
+
 # ----------------------------------------------------------------- convenience
 
 class Context:
@@ -299,10 +363,18 @@ class Context:
             self.h = asp_init(self.params, dirty, psf, stream)
             self.H, self.W = int(dirty.shape[0]), int(dirty.shape[1])
 
+    @classmethod
+    def borrow(cls, h, H: int, W: int, params: asp_params) -> "Context":
+        """A view of a context owned elsewhere (a batch image): same queries,
+        close() leaves it alone."""
+        c = cls.__new__(cls)
+        c.h, c.H, c.W, c.params, c._borrowed = h, H, W, params, True
+        return c
+
     def close(self):
-        if self.h:
+        if self.h and not getattr(self, "_borrowed", False):
             asp_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __enter__(self):
         return self
@@ -372,3 +444,51 @@ class Context:
 
     def scales(self):
         return asp_num_scales(self.h)
+
+
+class Batch:
+    """Owns one libasp batch: independent images advanced together, the LM
+    fits of all images in one cooperative launch per iteration."""
+
+    def __init__(self, dirty: Sequence, psf: Sequence, params: Optional[asp_params] = None, stream=None,
+                 **overrides):
+        self.params = params if params is not None else default_params(**overrides)
+        self.shapes = [(int(d.shape[0]), int(d.shape[1])) for d in dirty]
+        self.h = asp_batch_create(self.params, dirty, psf, stream)
+
+    @property
+    def n(self) -> int:
+        return len(self.shapes)
+
+    def close(self):
+        if self.h:
+            asp_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        asp_batch_reset(self.h)
+
+    def minor_cycle(self, n_iter: int) -> list:
+        return asp_batch_minor_cycle(self.h, n_iter, self.n)
+
+    def autotune(self, n_trial_iter: int = 16) -> dict:
+        return asp_batch_autotune(self.h, n_trial_iter)
+
+    def image(self, i: int) -> Context:
+        H, W = self.shapes[i]
+        return Context.borrow(asp_batch_image(self.h, i), H, W, self.params)
+
+    def launches(self) -> int:
+        return asp_batch_launch_count(self.h)

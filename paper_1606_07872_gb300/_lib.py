@@ -72,6 +72,11 @@ class asp_iter_record(C.Structure):
                 ("y0_init", C.c_double), ("w0", C.c_double)]
 
 
+class asp_batch_tuning(C.Structure):
+    _fields_ = [("px_per_cta", C.c_int32), ("share_policy", C.c_int32), ("n_candidates", C.c_int32),
+                ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+
 class asp_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -114,6 +119,14 @@ SIGNATURES = {
                        C.POINTER(asp_gauss), C.POINTER(asp_fit_info), _P],
     "asp_save_state": [_P, C.c_char_p],
     "asp_load_state": [_P, C.c_char_p],
+    "asp_batch_create": [C.POINTER(asp_params), _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_P), C.POINTER(_P), _I,
+                         _P, C.POINTER(_P)],
+    "asp_batch_destroy": [_P],
+    "asp_batch_reset": [_P],
+    "asp_batch_minor_cycle": [_P, _I, C.POINTER(asp_cycle_stats)],
+    "asp_batch_autotune": [_P, _I, C.POINTER(asp_batch_tuning)],
+    "asp_batch_image": [_P, _I, C.POINTER(_P)],
+    "asp_batch_launch_count": [_P, C.POINTER(C.c_int64)],
 }
 _RESTYPES = {"asp_status_string": C.c_char_p, "asp_default_params": None, "asp_last_error": C.c_char_p}
 

@@ -1067,3 +1067,354 @@ asp_status asp_load_state(asp_ctx* ctx, const char* path) {
 }
 
 }  // extern "C"
+
+// =====================================================================
+// Batches: independent images advanced together, one launch per kernel of
+// the iteration (images on grid.y) and one cooperative launch for all the
+// images' LM fits (image i owns a fixed CTA group).
+struct asp_batch {
+    int dev = 0, num_sms = 0, g_total = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<asp_ctx*> imgs;
+    std::vector<float*> dirty;           // device copies of the dirty images (resets)
+    std::vector<ImgDesc> h_desc;
+    ImgDesc* d_desc = nullptr;
+    unsigned* bars = nullptr;
+    BatchFitMap map{};
+    int tpt = 1, grid_x = 1;
+    int px_per_cta = 0, share_policy = 0;
+    size_t smem_smooth_h = 0, smem_smooth_v = 0, smem_sub_h = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_unroll = 8, graph_state = 0;
+    long long launches = 0;
+    int broken = 0;
+};
+
+namespace {
+
+const int BATCH_KERNELS_PER_ITER = 9;
+
+asp_status batch_fail(asp_batch* b, asp_status s) {
+    if (b && (s == ASP_ERR_CUDA || s == ASP_ERR_TIMEOUT)) b->broken = 1;
+    return s;
+}
+
+#define BK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return batch_fail(b, e_ == cudaErrorMemoryAllocation ? ASP_ERR_OOM : ASP_ERR_CUDA);    \
+    } while (0)
+
+// CTA groups of the batched fit: equal shares, or shares proportional to the
+// image areas; every image gets at least one CTA and the total is g_total.
+void batch_shares(asp_batch* b) {
+    const int n = (int)b->imgs.size();
+    std::vector<int> share(n, 1);
+    int left = b->g_total - n;
+    if (b->share_policy == 0) {
+        for (int i = 0; i < n && left > 0; ++i) {
+            const int extra = (b->g_total - n) / n;
+            share[i] += extra;
+        }
+    } else {
+        double tot = 0;
+        for (asp_ctx* c : b->imgs) tot += (double)c->N;
+        int used = 0;
+        for (int i = 0; i < n; ++i) {
+            const int extra = (int)std::floor((double)(b->g_total - n) * b->imgs[i]->N / tot);
+            share[i] += extra;
+            used += extra;
+        }
+        (void)used;
+    }
+    b->map.n = n;
+    b->map.start[0] = 0;
+    for (int i = 0; i < n; ++i) b->map.start[i + 1] = b->map.start[i] + share[i];
+    for (int i = 0; i < n; ++i) b->h_desc[i].g_share = share[i];
+}
+
+asp_status batch_upload(asp_batch* b) {
+    for (size_t i = 0; i < b->h_desc.size(); ++i) b->h_desc[i].dp.lm.px_per_cta = b->px_per_cta;
+    BK(cudaMemcpyAsync(b->d_desc, b->h_desc.data(), b->h_desc.size() * sizeof(ImgDesc), cudaMemcpyHostToDevice,
+                       b->stream));
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    b->graph_state = 0;
+    return ASP_OK;
+}
+
+asp_status batch_enqueue_iteration(asp_batch* b, cudaStream_t s) {
+    const int n = (int)b->imgs.size();
+    BK(launch_cycle_begin_b(b->d_desc, n, s));
+    BK(launch_smooth_h_b(b->d_desc, n, b->grid_x, b->smem_smooth_h, s));
+    BK(launch_smooth_v_b(b->d_desc, n, b->grid_x, b->smem_smooth_v, s));
+    BK(launch_select_b(b->d_desc, n, s));
+    BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s));
+    BK(launch_update_b(b->d_desc, n, s));
+    BK(launch_build_weights_b(b->d_desc, n, s));
+    BK(launch_sub_h_b(b->d_desc, n, b->grid_x, b->smem_sub_h, s));
+    BK(launch_sub_v_b(b->d_desc, n, b->grid_x, s));
+    return ASP_OK;
+}
+
+asp_status batch_build_graph(asp_batch* b) {
+    if (b->graph_state != 0) return ASP_OK;
+    if (getenv("ASP_NO_GRAPH")) { b->graph_state = -1; return ASP_OK; }
+    cudaStream_t cs = nullptr;
+    BK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    asp_status s = ASP_OK;
+    if (ok) {
+        for (int i = 0; i < b->graph_unroll && s == ASP_OK; ++i) s = batch_enqueue_iteration(b, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        ok = (s == ASP_OK) && e == cudaSuccess && g != nullptr;
+    }
+    b->broken = 0;
+    if (ok && cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess) {
+        b->graph_state = 1;
+    } else {
+        b->graph_state = -1;
+        cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return ASP_OK;
+}
+
+asp_status batch_run(asp_batch* b, int n_iter) {
+    const int n = (int)b->imgs.size();
+    BK(launch_arm_b(b->d_desc, n, n_iter, b->stream));
+    asp_status s = batch_build_graph(b);
+    if (s != ASP_OK) return s;
+    if (n_iter > 0) {
+        if (b->graph_state == 1) {
+            const int reps = (n_iter + b->graph_unroll - 1) / b->graph_unroll;
+            for (int r = 0; r < reps; ++r) BK(cudaGraphLaunch(b->gexec, b->stream));
+            b->launches += (long long)reps * b->graph_unroll * BATCH_KERNELS_PER_ITER;
+        } else {
+            for (int i = 0; i < n_iter; ++i) {
+                s = batch_enqueue_iteration(b, b->stream);
+                if (s != ASP_OK) return s;
+            }
+            b->launches += (long long)n_iter * BATCH_KERNELS_PER_ITER;
+        }
+    }
+    BK(cudaStreamSynchronize(b->stream));
+    return ASP_OK;
+}
+
+#undef BK
+
+}  // namespace
+
+#define BK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return batch_fail(b, e_ == cudaErrorMemoryAllocation ? ASP_ERR_OOM : ASP_ERR_CUDA);    \
+    } while (0)
+
+extern "C" {
+
+asp_status asp_batch_destroy(asp_batch* b) {
+    if (!b) return ASP_ERR_INVALID_ARG;
+    cudaSetDevice(b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (asp_ctx* c : b->imgs) asp_destroy(c);
+    for (float* d : b->dirty) cudaFree(d);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->bars) cudaFree(b->bars);
+    delete b;
+    return ASP_OK;
+}
+
+asp_status asp_batch_create(const asp_params* params, int n, const int* H, const int* W,
+                            const float* const* dirty, const float* const* psf, int on_host, void* stream,
+                            asp_batch** out) {
+    if (!out) return ASP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || n < 1 || n > MAX_BATCH || !H || !W || !dirty || !psf) return ASP_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (H[i] < 1 || W[i] < 1 || !dirty[i] || !psf[i]) return ASP_ERR_INVALID_ARG;
+    asp_batch* b = new asp_batch();
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    auto bail = [&](asp_status st) { asp_batch_destroy(b); return st; };
+    if (cudaGetDevice(&b->dev) != cudaSuccess) return bail(ASP_ERR_CUDA);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, b->dev) != cudaSuccess) return bail(ASP_ERR_CUDA);
+    b->num_sms = prop.multiProcessorCount;
+    for (int i = 0; i < n; ++i) {
+        asp_ctx* c = nullptr;
+        asp_status s = on_host ? asp_init_host(params, H[i], W[i], dirty[i], psf[i], stream, &c)
+                               : asp_init(params, H[i], W[i], dirty[i], psf[i], stream, &c);
+        if (s != ASP_OK) return bail(s);
+        b->imgs.push_back(c);
+        float* d = nullptr;
+        if (cudaMalloc(&d, (size_t)c->N * sizeof(float)) != cudaSuccess) return bail(ASP_ERR_OOM);
+        b->dirty.push_back(d);
+        if (cudaMemcpyAsync(d, dirty[i], (size_t)c->N * sizeof(float),
+                            on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+            return bail(ASP_ERR_CUDA);
+    }
+    b->tpt = b->imgs[0]->tpt;
+    int bps = 0;
+    if (fit_configure(b->tpt, &bps) != cudaSuccess || bps < 1) return bail(ASP_ERR_CUDA);
+    b->g_total = b->num_sms * bps;
+    if (n > b->g_total) return bail(ASP_ERR_UNSUPPORTED);
+    if (cudaMalloc(&b->bars, sizeof(unsigned) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_desc, sizeof(ImgDesc) * n) != cudaSuccess)
+        return bail(ASP_ERR_OOM);
+    long long n_max = 0;
+    b->h_desc.resize(n);
+    for (int i = 0; i < n; ++i) {
+        asp_ctx* c = b->imgs[i];
+        ImgDesc& g = b->h_desc[i];
+        memset(&g, 0, sizeof(g));
+        g.R = c->R; g.B = c->B; g.H = c->H; g.W = c->W;
+        g.st = c->st; g.comps = c->comps; g.hist = c->hist;
+        g.wbuf = c->wbuf; g.T1 = c->T1; g.S1 = c->S1;
+        g.taps = c->taps; g.smooth_flops = c->smooth_flops;
+        g.partials = c->partials; g.sums = c->sums; g.bar = b->bars + i; g.Tg = c->Tg;
+        g.part = c->part; g.ticket = c->ticket;
+        g.dp = c->dp;
+        g.sub_blen = sub_h_blen(c->W, c->taps);
+        b->smem_smooth_h = std::max(b->smem_smooth_h,
+                                    ((size_t)c->taps.t8max + (size_t)c->taps.rpb * c->taps.blen) * sizeof(float));
+        b->smem_smooth_v = std::max(b->smem_smooth_v, (size_t)c->taps.t8max * sizeof(float));
+        b->smem_sub_h = std::max(b->smem_sub_h, (size_t)c->taps.rpb * g.sub_blen * sizeof(float));
+        n_max = std::max(n_max, c->N);
+    }
+    if (b->smem_smooth_h > 48 * 1024 || b->smem_sub_h > 48 * 1024) return bail(ASP_ERR_UNSUPPORTED);
+    // image-wide kernels: enough blocks per image for the largest one (64k
+    // pixels a block); smaller images leave most of theirs idle
+    b->grid_x = (int)std::min<long long>(std::max<long long>((n_max + 65535) / 65536, 4), b->imgs[0]->grid_img);
+    batch_shares(b);
+    asp_status s = batch_upload(b);
+    if (s != ASP_OK) return bail(s);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bail(ASP_ERR_CUDA);
+    *out = b;
+    return ASP_OK;
+}
+
+asp_status asp_batch_reset(asp_batch* b) {
+    if (!b) return ASP_ERR_INVALID_ARG;
+    if (b->broken) return ASP_ERR_STATE;
+    cudaSetDevice(b->dev);
+    for (size_t i = 0; i < b->imgs.size(); ++i) {
+        asp_ctx* c = b->imgs[i];
+        // the image's statistics restart with it
+        asp_status s = asp_reset(c, b->dirty[i], 0, nullptr, 0);
+        if (s != ASP_OK) return batch_fail(b, s);
+    }
+    BK(cudaStreamSynchronize(b->stream));
+    return ASP_OK;
+}
+
+asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stats) {
+    if (!b || n_iter < 0) return ASP_ERR_INVALID_ARG;
+    if (b->broken) return ASP_ERR_STATE;
+    cudaSetDevice(b->dev);
+    asp_status s = batch_run(b, n_iter);
+    if (s != ASP_OK) return s;
+    asp_status first_err = ASP_OK;
+    for (size_t i = 0; i < b->imgs.size(); ++i) {
+        asp_ctx* c = b->imgs[i];
+        CycleState h;
+        BK(cudaMemcpyAsync(&h, c->st, sizeof(CycleState), cudaMemcpyDeviceToHost, b->stream));
+        BK(cudaStreamSynchronize(b->stream));
+        if (h.error == ASP_ERR_TIMEOUT) { b->broken = 1; return ASP_ERR_TIMEOUT; }
+        if ((h.error == ASP_ERR_NAN || h.nonfinite) && first_err == ASP_OK) first_err = ASP_ERR_NAN;
+        if (h.stop_reason == ASP_STOP_CAPACITY && first_err == ASP_OK) first_err = ASP_ERR_CAPACITY;
+        if (stats) {
+            asp_cycle_stats& o = stats[i];
+            memset(&o, 0, sizeof(o));
+            o.iterations = h.t;
+            o.components = h.n_comp;
+            o.pixel_evals = h.pixel_evals;
+            o.lm_iters = h.lm_iters;
+            o.lm_passes = h.lm_passes;
+            o.peak_abs = std::fabs((double)h.peak.val);
+            o.stop_reason = h.stop_reason;
+            o.fit_flops = h.fit_flops;
+            o.sub_flops = h.sub_flops;
+            o.sub_bytes = h.sub_bytes;
+            o.smooth_flops = h.smooth_flops;
+            o.fit_pass_ms = h.fit_ns_pass * 1e-6;
+            o.fit_reduce_ms = h.fit_ns_reduce * 1e-6;
+            o.fit_solve_ms = h.fit_ns_solve * 1e-6;
+            o.fit_factor_ms = h.fit_ns_factor * 1e-6;
+            o.fit_subst_ms = h.fit_ns_subst * 1e-6;
+            o.fit_refinements = h.fit_refinements;
+            o.fit_fallbacks = h.fit_fallbacks;
+        }
+    }
+    return first_err;
+}
+
+asp_status asp_batch_autotune(asp_batch* b, int n_trial_iter, asp_batch_tuning* out) {
+    if (!b || n_trial_iter < 1) return ASP_ERR_INVALID_ARG;
+    if (b->broken) return ASP_ERR_STATE;
+    cudaSetDevice(b->dev);
+    const int cand_px[] = {0, 256, 512, 1024, 2048, 4096};   // pixels per CTA (0: the automatic rule)
+    const int n_px = (int)(sizeof(cand_px) / sizeof(cand_px[0]));
+    cudaEvent_t e0, e1;
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    double best = 1e300, dflt = 0.0;
+    int best_px = 0, best_pol = 0, tried = 0;
+    asp_status s = ASP_OK;
+    for (int pol = 0; pol < 2 && s == ASP_OK; ++pol)
+        for (int k = 0; k < n_px && s == ASP_OK; ++k) {
+            b->share_policy = pol;
+            b->px_per_cta = cand_px[k];
+            batch_shares(b);
+            s = batch_upload(b);
+            if (s == ASP_OK) s = asp_batch_reset(b);
+            if (s == ASP_OK) s = batch_build_graph(b);
+            if (s != ASP_OK) break;
+            BK(cudaEventRecord(e0, b->stream));
+            s = batch_run(b, n_trial_iter);
+            BK(cudaEventRecord(e1, b->stream));
+            BK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BK(cudaEventElapsedTime(&ms, e0, e1));
+            ++tried;
+            if (pol == 0 && k == 0) dflt = ms;
+            if (ms < best) { best = ms; best_px = cand_px[k]; best_pol = pol; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != ASP_OK) return s;
+    b->share_policy = best_pol;
+    b->px_per_cta = best_px;
+    batch_shares(b);
+    s = batch_upload(b);
+    if (s == ASP_OK) s = asp_batch_reset(b);
+    if (s != ASP_OK) return s;
+    if (out) {
+        out->px_per_cta = best_px;
+        out->share_policy = best_pol;
+        out->n_candidates = tried;
+        out->best_ms = best;
+        out->default_ms = dflt;
+    }
+    return ASP_OK;
+}
+
+asp_status asp_batch_image(asp_batch* b, int i, asp_ctx** ctx) {
+    if (!b || !ctx || i < 0 || i >= (int)b->imgs.size()) return ASP_ERR_INVALID_ARG;
+    *ctx = b->imgs[i];
+    return ASP_OK;
+}
+
+asp_status asp_batch_launch_count(asp_batch* b, int64_t* n) {
+    if (!b || !n) return ASP_ERR_INVALID_ARG;
+    *n = b->launches;
+    return ASP_OK;
+}
+
+}  // extern "C"
+#undef BK

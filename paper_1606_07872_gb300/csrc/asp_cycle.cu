@@ -128,7 +128,7 @@ __device__ void finish_terms(CycleState* st, int H, int W) {
 
 }  // namespace
 
-__global__ void k_cycle_begin(CycleState* st, Params p, int H, int W, double smooth_flops) {
+__device__ __forceinline__ void cycle_begin_body(CycleState* st, Params p, int H, int W, double smooth_flops) {
     if (threadIdx.x != 0) return;
     st->fit.active = 0;
     st->skip_smooth = 1;
@@ -157,7 +157,9 @@ __global__ void k_cycle_begin(CycleState* st, Params p, int H, int W, double smo
     }
 }
 
-__global__ void k_select(CycleState* st, const asp_component* __restrict__ comps, Params p, int H, int W,
+__global__ void k_cycle_begin(CycleState* st, Params p, int H, int W, double smooth_flops) { cycle_begin_body(st, p, H, W, smooth_flops); }
+
+__device__ __forceinline__ void select_body(CycleState* st, const asp_component* __restrict__ comps, Params p, int H, int W,
                          int g_max) {
     // one warp: lanes test 32 retained members at a time; the first ones in
     // list order (most recent first) are taken, as in a sequential scan
@@ -233,80 +235,114 @@ __global__ void k_select(CycleState* st, const asp_component* __restrict__ comps
     st->fout.error = 0;
 }
 
-__global__ void k_update(CycleState* st, asp_component* comps, asp_iter_record* hist, Params p, int H, int W) {
-    if (threadIdx.x != 0) return;
+__global__ void k_select(CycleState* st, const asp_component* __restrict__ comps, Params p, int H, int W,
+                         int g_max) { select_body(st, comps, p, H, W, g_max); }
+
+// One warp.  Lane m (1 <= m < K) deconvolves refit member m and tests its
+// retention; lane 0 lays out the subtraction terms in the fixed order (new,
+// then (refit, -old) per member), writes the history and the totals; the
+// retained list is compacted by ballot.
+__device__ __forceinline__ void update_body(CycleState* st, asp_component* comps, asp_iter_record* hist, Params p, int H, int W) {
+    const int lane = threadIdx.x;
+    if (lane >= 32) return;
     if (st->stopped) return;
     const FitOut& fo = st->fout;
     const FitDesc& f = st->fit;
-    if (fo.error) { st->stopped = 1; st->error = fo.error; st->n_terms = 0; return; }
+    if (fo.error) {
+        if (lane == 0) { st->stopped = 1; st->error = fo.error; st->n_terms = 0; }
+        return;
+    }
+    __shared__ asp_component s_old[KMAX], s_new[KMAX];
+    __shared__ int s_drop[KMAX];
     const double ab = st->alpha_b, wb = st->omega_b;
     const int K = f.K;
-    int nt = 0;
-    // new component with the loop gain (Sect. 3, after Eq. 8)
     const int ni = st->n_comp;
-    asp_component cn = deconvolve(fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], ab, wb, (double)p.gain);
-    comps[ni] = cn;
-    st->n_comp = ni + 1;
-    if (make_term(cn, cn.flux, H, W, nt, st->terms[nt])) ++nt;
-    // old members are replaced by their refit values
-    int keep[KMAX];
-    for (int m = 1; m < K; ++m) {
+    // refit members in parallel: retention test (tau) and the deconvolved new value
+    for (int m = 1 + lane; m < K; m += 32) {
         const int k = st->members[m];
-        const asp_component old = comps[k];
         const double* g0 = &f.theta0[4 * m];
         const double* g1 = &fo.theta[4 * m];
         const double tau = p.tau;
-        keep[m] = fabs(g1[0] - g0[0]) > tau * fabs(g0[0]) || fabs(g1[1] - g0[1]) > tau * g0[3] ||
-                  fabs(g1[2] - g0[2]) > tau * g0[3] || fabs(g1[3] - g0[3]) > tau * g0[3];
-        asp_component nc = deconvolve(g1[0], g1[1], g1[2], g1[3], ab, wb, 1.0);
-        comps[k] = nc;
-        if (make_term(nc, nc.flux, H, W, nt, st->terms[nt])) ++nt;
-        if (make_term(old, -old.flux, H, W, nt, st->terms[nt])) ++nt;
+        const bool keep = fabs(g1[0] - g0[0]) > tau * fabs(g0[0]) || fabs(g1[1] - g0[1]) > tau * g0[3] ||
+                          fabs(g1[2] - g0[2]) > tau * g0[3] || fabs(g1[3] - g0[3]) > tau * g0[3];
+        s_drop[m] = keep ? -1 : k;
+        s_old[m] = comps[k];
+        s_new[m] = deconvolve(g1[0], g1[1], g1[2], g1[3], ab, wb, 1.0);
     }
-    st->n_terms = nt;
-    finish_terms(st, H, W);
+    __syncwarp();
+    if (lane == 0) {
+        int nt = 0;
+        // new component with the loop gain (Sect. 3, after Eq. 8)
+        const asp_component cn = deconvolve(fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], ab, wb, (double)p.gain);
+        comps[ni] = cn;
+        st->n_comp = ni + 1;
+        if (make_term(cn, cn.flux, H, W, nt, st->terms[nt])) ++nt;
+        // old members are replaced by their refit values
+        for (int m = 1; m < K; ++m) {
+            comps[st->members[m]] = s_new[m];
+            if (make_term(s_new[m], s_new[m].flux, H, W, nt, st->terms[nt])) ++nt;
+            if (make_term(s_old[m], -s_old[m].flux, H, W, nt, st->terms[nt])) ++nt;
+        }
+        st->n_terms = nt;
+        finish_terms(st, H, W);
+        st->last_wi = cn.width;
+    }
     // retained list: new first, then the previous list minus members whose
-    // fit moved no parameter by more than tau
-    int nr = 0;
-    int tmp[RET_MAX];
-    tmp[nr++] = ni;
-    for (int r = 0; r < st->n_ret && nr < p.retained_cap; ++r) {
-        const int k = st->ret[r];
-        bool drop = false;
-        for (int m = 1; m < K; ++m)
-            if (st->members[m] == k && !keep[m]) drop = true;
-        if (!drop) tmp[nr++] = k;
+    // fit moved no parameter by more than tau (order kept)
+    const int n_old = st->n_ret;
+    const int cap = p.retained_cap;
+    __shared__ int s_ret[RET_MAX];
+    for (int r = lane; r < n_old; r += 32) s_ret[r] = st->ret[r];   // staged: the list is rewritten in place
+    __syncwarp();
+    int out = 1;   // slot 0 is the new component
+    for (int r0 = 0; r0 < n_old; r0 += 32) {
+        const int r = r0 + lane;
+        int k = -1;
+        bool keep_r = false;
+        if (r < n_old) {
+            k = s_ret[r];
+            keep_r = true;
+            for (int m = 1; m < K; ++m)
+                if (s_drop[m] == k) keep_r = false;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep_r);
+        const int pos = out + __popc(bal & ((1u << lane) - 1u));
+        if (keep_r && pos < cap) st->ret[pos] = k;
+        out += __popc(bal);
     }
-    for (int r = 0; r < nr; ++r) st->ret[r] = tmp[r];
-    st->n_ret = nr;
-    // history
-    if (st->t < st->cap_comp) {
-        asp_iter_record* h = hist + st->t;
-        h->t = st->t; h->mode = st->mode; h->k = K; h->status = fo.status;
-        h->iters = fo.iters; h->passes = fo.passes;
-        h->x0 = f.wx0; h->x1 = f.wx0 + f.ww - 1; h->y0 = f.wy0; h->y1 = f.wy0 + f.wh - 1;
-        h->new_index = ni; h->n_terms = nt;
-        h->peak_value = st->peak.val;
-        h->init_scale = st->init_scale >= 0 ? st->init_s : 0.f;
-        h->chi2_init = fo.chi2_init; h->chi2_final = fo.chi2;
-        h->a0 = st->init[0]; h->x0_init = st->init[1]; h->y0_init = st->init[2]; h->w0 = st->init[3];
+    if (lane == 0) {
+        st->ret[0] = ni;
+        st->n_ret = out < cap ? out : cap;
+        // history
+        if (st->t < st->cap_comp) {
+            asp_iter_record* h = hist + st->t;
+            h->t = st->t; h->mode = st->mode; h->k = K; h->status = fo.status;
+            h->iters = fo.iters; h->passes = fo.passes;
+            h->x0 = f.wx0; h->x1 = f.wx0 + f.ww - 1; h->y0 = f.wy0; h->y1 = f.wy0 + f.wh - 1;
+            h->new_index = ni; h->n_terms = st->n_terms;
+            h->peak_value = st->peak.val;
+            h->init_scale = st->init_scale >= 0 ? st->init_s : 0.f;
+            h->chi2_init = fo.chi2_init; h->chi2_final = fo.chi2;
+            h->a0 = st->init[0]; h->x0_init = st->init[1]; h->y0_init = st->init[2]; h->w0 = st->init[3];
+        }
+        // switch statistics and totals
+        st->last_w0 = st->init[3];
+        st->pixel_evals += fo.pixel_evals;
+        st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
+        st->lm_iters += fo.iters;
+        st->fit_ns_pass += fo.ns_pass;
+        st->fit_ns_reduce += fo.ns_reduce;
+        st->fit_ns_solve += fo.ns_solve;
+        st->fit_ns_factor += fo.ns_factor;
+        st->fit_ns_subst += fo.ns_subst;
+        st->fit_refinements += fo.refinements;
+        st->fit_fallbacks += fo.fallbacks;
+        st->lm_passes += fo.passes;
+        st->t += 1;
     }
-    // switch statistics and totals
-    st->last_wi = cn.width;
-    st->last_w0 = st->init[3];
-    st->pixel_evals += fo.pixel_evals;
-    st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
-    st->lm_iters += fo.iters;
-    st->fit_ns_pass += fo.ns_pass;
-    st->fit_ns_reduce += fo.ns_reduce;
-    st->fit_ns_solve += fo.ns_solve;
-    st->fit_ns_factor += fo.ns_factor;
-    st->fit_ns_subst += fo.ns_subst;
-    st->fit_refinements += fo.refinements;
-    st->fit_fallbacks += fo.fallbacks;
-    st->lm_passes += fo.passes;
-    st->t += 1;
 }
+
+__global__ void k_update(CycleState* st, asp_component* comps, asp_iter_record* hist, Params p, int H, int W) { update_body(st, comps, hist, p, H, W); }
 
 __global__ void k_terms_from_components(CycleState* st, const asp_component* __restrict__ comps, int n, float gain,
                                         int H, int W) {
@@ -321,8 +357,7 @@ __global__ void k_terms_from_components(CycleState* st, const asp_component* __r
 // Axis weights of every term: sampled Gaussian normalised to unit sum over the
 // unclipped support (so the component's discrete flux is its F), or the
 // bilinear pair (1 - f, f).  One block per term.
-__global__ void __launch_bounds__(256)
-k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __restrict__ wbuf) {
+__device__ __forceinline__ void build_weights_body(const CycleState* __restrict__ st, const int* gate, float* __restrict__ wbuf) {
     if (gate && *gate) return;
     const int t = blockIdx.x;
     if (t >= st->n_terms) return;
@@ -366,6 +401,9 @@ k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __res
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __restrict__ wbuf) { build_weights_body(st, gate, wbuf); }
+
 // Clears the minor-cycle state (components, retained list, counters) while
 // keeping the beam, the noise threshold and the capacities.
 __global__ void k_reset_state(CycleState* st) {
@@ -380,6 +418,56 @@ __global__ void k_reset_state(CycleState* st) {
     st->fit_refinements = 0; st->fit_fallbacks = 0;
     st->nonfinite = 0;
     st->fit.active = 0;
+}
+
+
+// ------------------------------------------------------------------ batched wrappers (grid.y = image)
+__global__ void k_cycle_begin_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    cycle_begin_body(g.st, g.dp, g.H, g.W, g.smooth_flops);
+}
+__global__ void k_select_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    select_body(g.st, g.comps, g.dp, g.H, g.W, g.g_share);
+}
+__global__ void k_update_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    update_body(g.st, g.comps, g.hist, g.dp, g.H, g.W);
+}
+__global__ void __launch_bounds__(256) k_build_weights_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    build_weights_body(g.st, &g.st->stopped, g.wbuf);
+}
+// Every image may run n_iter more iterations (the batch counterpart of the
+// host-side stop reset of asp_minor_cycle).
+__global__ void k_arm_b(const ImgDesc* __restrict__ imgs, int n, int n_iter) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    CycleState* st = imgs[i].st;
+    st->t_stop = st->t + n_iter;
+    st->stopped = 0;
+    st->stop_reason = 0;
+}
+
+cudaError_t launch_cycle_begin_b(const ImgDesc* imgs, int n, cudaStream_t s) {
+    k_cycle_begin_b<<<dim3(1, n), 32, 0, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_select_b(const ImgDesc* imgs, int n, cudaStream_t s) {
+    k_select_b<<<dim3(1, n), 32, 0, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_b(const ImgDesc* imgs, int n, cudaStream_t s) {
+    k_update_b<<<dim3(1, n), 32, 0, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_build_weights_b(const ImgDesc* imgs, int n, cudaStream_t s) {
+    k_build_weights_b<<<dim3(MAX_TERMS, n), 256, 0, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_arm_b(const ImgDesc* imgs, int n, int n_iter, cudaStream_t s) {
+    k_arm_b<<<(n + 127) / 128, 128, 0, s>>>(imgs, n, n_iter);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, double smooth_flops, cudaStream_t s) {

@@ -577,11 +577,13 @@ __device__ bool solve_damped(const double* __restrict__ Ac, const double* __rest
 
 }  // namespace
 
+// The whole fit of one window, run by the CTAs of one fit group; b is this
+// CTA's rank in the group (the group has d.grid CTAs).
 template <int TPT>
-__global__ void __launch_bounds__(FIT_THREADS, 1)
-k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ descp, LMConst lmc,
-         FitOut* __restrict__ out, double* __restrict__ partials, double* __restrict__ sums,
-         unsigned* __restrict__ bar, float* __restrict__ Tg) {
+__device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ descp,
+                                            const LMConst& lmc, FitOut* __restrict__ out, double* __restrict__ partials,
+                                            double* __restrict__ sums, unsigned* __restrict__ bar,
+                                            float* __restrict__ Tg, const int b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Ts = reinterpret_cast<float*>(smem_raw);                          // PX_SMEM floats
     double* Ac = reinterpret_cast<double*>(Ts + PX_SMEM);                    // A at the current point
@@ -606,7 +608,6 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
     __syncthreads();
     if (!d.active) return;
     const int G = d.grid;
-    const int b = blockIdx.x;
     if (b >= G) return;
 
     const int K = d.K, P = 4 * K, NA = P + 1, NAp = (NA + 3) & ~3, nb = NAp / 4;
@@ -936,6 +937,28 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
     }
 }
 
+template <int TPT>
+__global__ void __launch_bounds__(FIT_THREADS, 1)
+k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ descp, const __grid_constant__ LMConst lmc,
+         FitOut* __restrict__ out, double* __restrict__ partials, double* __restrict__ sums,
+         unsigned* __restrict__ bar, float* __restrict__ Tg) {
+    lm_fit_body<TPT>(src, src_w, descp, lmc, out, partials, sums, bar, Tg, blockIdx.x);
+}
+
+// Batched: the fits of many images in one cooperative launch.  Image i owns
+// CTAs [map.start[i], map.start[i+1]); each group runs its own fit with its
+// own barrier counter, partials and sums.
+template <int TPT>
+__global__ void __launch_bounds__(FIT_THREADS, 1)
+k_lm_fit_b(const ImgDesc* __restrict__ imgs, const __grid_constant__ BatchFitMap map) {
+    int i = 0;
+    while (i + 1 < map.n && (int)blockIdx.x >= map.start[i + 1]) ++i;
+    if ((int)blockIdx.x >= map.start[map.n]) return;
+    const ImgDesc& g = imgs[i];
+    lm_fit_body<TPT>(g.R, g.W, &g.st->fit, g.dp.lm, &g.st->fout, g.partials, g.sums, g.bar, g.Tg,
+                     (int)blockIdx.x - map.start[i]);
+}
+
 size_t fit_smem_bytes() {
     size_t jc = (size_t)JC_FLOATS * sizeof(float);
     size_t m = (size_t)M_DOUBLES * sizeof(double);
@@ -955,7 +978,29 @@ cudaError_t fit_configure(int tpt, int* blocks_per_sm) {
     const void* fn = fit_kernel_ptr(tpt);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem_bytes());
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tpt == 1 ? (const void*)k_lm_fit_b<1> : (const void*)k_lm_fit_b<3>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem_bytes());
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, FIT_THREADS, fit_smem_bytes());
+}
+
+cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMap& map, unsigned* bars, int n_bars,
+                                  cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bars, 0, sizeof(unsigned) * (size_t)n_bars, s);
+    if (e != cudaSuccess) return e;
+    if (map.start[map.n] < 1) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(map.start[map.n]);
+    cfg.blockDim = dim3(FIT_THREADS);
+    cfg.dynamicSmemBytes = fit_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1>, imgs, map);
+    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3>, imgs, map);
 }
 
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,

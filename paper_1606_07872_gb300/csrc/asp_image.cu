@@ -120,8 +120,7 @@ __device__ __forceinline__ int spad(int q) { return q + (q >> 3); }
 // term's T1 rows; the B segment is staged in shared memory (bank-padded).
 // The geometry (tpr, rpb, nseg) depends only on W and is shared with the
 // smoothing row pass.
-__global__ void __launch_bounds__(RED_THREADS)
-k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict__ st, const int* gate,
+__device__ __forceinline__ void sub_h_body(const float* __restrict__ B, int H, int W, const CycleState* __restrict__ st, const int* gate,
         const float* __restrict__ wbuf, float* __restrict__ T1, int tpr, int rpb, int nseg, int blen) {
     if (gate && *gate) return;
     extern __shared__ __align__(16) float sm_sub[];
@@ -194,6 +193,10 @@ k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict_
     }
 }
 
+__global__ void __launch_bounds__(RED_THREADS)
+k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict__ st, const int* gate,
+        const float* __restrict__ wbuf, float* __restrict__ T1, int tpr, int rpb, int nseg, int blen) { sub_h_body(B, H, W, st, gate, wbuf, T1, tpr, rpb, nseg, blen); }
+
 // Column pass + update + fused argmax:
 // R[y][x] -= sum_t scale_t sum_k wyr_t[k] T1_t[y + k][x]
 //          + sum_d w_d B[y - qy_d + H][x - qx_d + W]      (point deposits)
@@ -201,8 +204,7 @@ k_sub_h(const float* __restrict__ B, int H, int W, const CycleState* __restrict_
 // columns), one block task is 32 columns x 64 rows.  The T1 buffer carries
 // zeroed slack rows behind its last term, so the window (which runs up to
 // 15 rows past a term's end under zero taps) needs no bounds tests.
-__global__ void __launch_bounds__(RED_THREADS)
-k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* gate,
+__device__ __forceinline__ void sub_v_body(float* __restrict__ R, int H, int W, CycleState* st, const int* gate,
                const float* __restrict__ wbuf, const float* __restrict__ T1, const float* __restrict__ B,
                ArgRes* part, unsigned* ticket) {
     if (gate && *gate) return;
@@ -273,6 +275,11 @@ k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* g
     grid_arg_finish(bv, bj, bi, part, ticket, &st->peak);
 }
 
+__global__ void __launch_bounds__(RED_THREADS)
+k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* gate,
+               const float* __restrict__ wbuf, const float* __restrict__ T1, const float* __restrict__ B,
+               ArgRes* part, unsigned* ticket) { sub_v_body(R, H, W, st, gate, wbuf, T1, B, part, ticket); }
+
 // ------------------------------------------------------------------ smoothing
 // Separable Gaussian smoothing at every scale s_j (Sect. 2 step 1), zero
 // padded at the image edges, as two register-blocked passes: each thread
@@ -284,8 +291,7 @@ k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* g
 // task is rpb row segments of 8 tpr outputs each; the segment with its
 // halo is staged in shared memory.  Blocks loop over the tasks of every
 // scale (or only_scale).
-__global__ void __launch_bounds__(RED_THREADS)
-k_smooth_h(const float* __restrict__ R, int H, int W, const SmoothTaps taps, const int* gate,
+__device__ __forceinline__ void smooth_h_body(const float* __restrict__ R, int H, int W, const SmoothTaps& taps, const int* gate,
            int only_scale, float* __restrict__ S1) {
     if (gate && *gate) return;
     extern __shared__ __align__(16) float sm_h[];
@@ -347,14 +353,17 @@ k_smooth_h(const float* __restrict__ R, int H, int W, const SmoothTaps taps, con
     }
 }
 
+__global__ void __launch_bounds__(RED_THREADS)
+k_smooth_h(const float* __restrict__ R, int H, int W, const __grid_constant__ SmoothTaps taps, const int* gate,
+           int only_scale, float* __restrict__ S1) { smooth_h_body(R, H, W, taps, gate, only_scale, S1); }
+
 // Column pass for every scale with the fused argmax of |S_j| over (j, p);
 // the last block turns the winner into the initial values
 // (S/(sqrt(pi) s), x*, y*, max(s, omega_b)).  out_S (optional) receives S_j.
 // A block task is 32 columns x 64 rows of one scale: lane = column, warp w
 // = rows 8w..8w+7.  The row-pass image has mpad zero rows above and below,
 // so the sliding window needs no bounds tests.
-__global__ void __launch_bounds__(RED_THREADS)
-k_smooth_v_argmax(const float* __restrict__ S1, int H, int W, const SmoothTaps taps, CycleState* st,
+__device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int H, int W, const SmoothTaps& taps, CycleState* st,
                   const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket) {
     if (gate && *gate) return;
     extern __shared__ __align__(16) float ktap[];
@@ -422,18 +431,64 @@ k_smooth_v_argmax(const float* __restrict__ S1, int H, int W, const SmoothTaps t
     }
 }
 
+__global__ void __launch_bounds__(RED_THREADS)
+k_smooth_v_argmax(const float* __restrict__ S1, int H, int W, const __grid_constant__ SmoothTaps taps, CycleState* st,
+                  const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket) { smooth_v_body(S1, H, W, taps, st, gate, only_scale, out_S, part, ticket); }
+
+
+// ------------------------------------------------------------------ batched wrappers
+// grid.y = image; every image runs the same body with its own buffers.
+__global__ void __launch_bounds__(RED_THREADS) k_smooth_h_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    smooth_h_body(g.R, g.H, g.W, g.taps, &g.st->skip_smooth, -1, g.S1);
+}
+__global__ void __launch_bounds__(RED_THREADS) k_smooth_v_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    smooth_v_body(g.S1, g.H, g.W, g.taps, g.st, &g.st->skip_smooth, -1, nullptr, g.part, g.ticket);
+}
+__global__ void __launch_bounds__(RED_THREADS) k_sub_h_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    sub_h_body(g.B, g.H, g.W, g.st, &g.st->stopped, g.wbuf, g.T1, g.taps.tpr, g.taps.rpb, g.taps.nseg, g.sub_blen);
+}
+__global__ void __launch_bounds__(RED_THREADS) k_sub_v_b(const ImgDesc* __restrict__ imgs) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    sub_v_body(g.R, g.H, g.W, g.st, &g.st->stopped, g.wbuf, g.T1, g.B, g.part, g.ticket);
+}
+
 // ------------------------------------------------------------------ launchers
+cudaError_t launch_smooth_h_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s) {
+    k_smooth_h_b<<<dim3(grid_x, n), RED_THREADS, smem, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_smooth_v_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s) {
+    k_smooth_v_b<<<dim3(grid_x, n), RED_THREADS, smem, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_sub_h_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s) {
+    k_sub_h_b<<<dim3(grid_x, n), RED_THREADS, smem, s>>>(imgs);
+    return cudaGetLastError();
+}
+cudaError_t launch_sub_v_b(const ImgDesc* imgs, int n, int grid_x, cudaStream_t s) {
+    k_sub_v_b<<<dim3(grid_x, n), RED_THREADS, 0, s>>>(imgs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_argmax(const float* R, long long N, int grid, ArgRes* part, unsigned* ticket, ArgRes* res,
                           unsigned* nonfinite, const int* gate, cudaStream_t s) {
     k_argmax_abs<<<grid, RED_THREADS, 0, s>>>(R, N, part, ticket, res, nonfinite, gate);
     return cudaGetLastError();
 }
 
+// Row-pass buffer of the subtraction: 8 tpr outputs + up to roundup8(W)
+// taps + 8 window slack, bank-padded.
+int sub_h_blen(int W, const SmoothTaps& geo) {
+    const int last = 8 * geo.tpr + ((W + 7) & ~7) + 7;
+    return last + (last >> 3) + 1;
+}
+
 cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, const int* gate, const float* wbuf,
                           float* T1, int grid, const SmoothTaps& geo, cudaStream_t s) {
-    // segment buffer: 8 tpr outputs + up to roundup8(W) taps + 8 window slack, bank-padded
-    const int last = 8 * geo.tpr + ((W + 7) & ~7) + 7;
-    const int blen = last + (last >> 3) + 1;
+    const int blen = sub_h_blen(W, geo);
     const size_t smem = (size_t)geo.rpb * blen * sizeof(float);
     k_sub_h<<<grid, RED_THREADS, smem, s>>>(B, H, W, st, gate, wbuf, T1, geo.tpr, geo.rpb, geo.nseg, blen);
     return cudaGetLastError();

@@ -23,10 +23,44 @@ struct SmoothTaps {          // unit-L2 1-D smoothing kernels, passed by value
     long long s1rows;        // rows of each scale's row-pass image (H + 2 mpad + 8)
 };
 
+// One image of a batch as the batched kernels see it (device memory).
+struct ImgDesc {
+    float* R;
+    const float* B;
+    int H, W;
+    CycleState* st;
+    asp_component* comps;
+    asp_iter_record* hist;
+    float* wbuf;
+    float* T1;
+    float* S1;
+    SmoothTaps taps;
+    double smooth_flops;
+    double* partials;
+    double* sums;
+    unsigned* bar;
+    float* Tg;
+    ArgRes* part;
+    unsigned* ticket;
+    Params dp;
+    int g_share;        // CTAs of the batched fit given to this image
+    int sub_blen;       // floats of one row-pass buffer of the subtraction
+};
+
+constexpr int MAX_BATCH = 256;
+struct BatchFitMap {    // CTA ranges of the batched fit: image i owns [start[i], start[i+1])
+    int n;
+    int start[MAX_BATCH + 1];
+};
+
+int sub_h_blen(int W, const SmoothTaps& geo);
+
 // asp_fit.cu
 size_t fit_smem_bytes();
 int fit_tpt_for(int k_max);
 cudaError_t fit_configure(int tpt, int* blocks_per_sm);
+cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMap& map, unsigned* bars, int n_bars,
+                                  cudaStream_t s);
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
                           FitOut* out, double* partials, double* sums, unsigned* bar, float* Tg, cudaStream_t s);
 
@@ -54,6 +88,16 @@ cudaError_t launch_terms_from_components(CycleState* st, const asp_component* co
 cudaError_t launch_reset_state(CycleState* st, cudaStream_t s);
 
 // asp_setup.cu
+// batched iteration kernels (grid.y = image; grid_x blocks per image)
+cudaError_t launch_cycle_begin_b(const ImgDesc* imgs, int n, cudaStream_t s);
+cudaError_t launch_smooth_h_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s);
+cudaError_t launch_smooth_v_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s);
+cudaError_t launch_select_b(const ImgDesc* imgs, int n, cudaStream_t s);
+cudaError_t launch_update_b(const ImgDesc* imgs, int n, cudaStream_t s);
+cudaError_t launch_build_weights_b(const ImgDesc* imgs, int n, cudaStream_t s);
+cudaError_t launch_sub_h_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s);
+cudaError_t launch_sub_v_b(const ImgDesc* imgs, int n, int grid_x, cudaStream_t s);
+cudaError_t launch_arm_b(const ImgDesc* imgs, int n, int n_iter, cudaStream_t s);
 cudaError_t launch_beam_init(FitDesc* desc, const float* B, int H, int W, int g_max, cudaStream_t s);
 cudaError_t launch_radix_median(const float* v, long long n, int absdev, double center, unsigned long long* ws,
                                 double* out, cudaStream_t s);

@@ -52,8 +52,9 @@ def test_struct_sizes_match_header(libpath):
 #include <stdio.h>
 #include "asp.h"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(asp_gauss), sizeof(asp_component), sizeof(asp_peak),
-         sizeof(asp_fit_info), sizeof(asp_params), sizeof(asp_cycle_stats), sizeof(asp_iter_record));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(asp_gauss), sizeof(asp_component), sizeof(asp_peak),
+         sizeof(asp_fit_info), sizeof(asp_params), sizeof(asp_cycle_stats), sizeof(asp_iter_record),
+         sizeof(asp_batch_tuning), sizeof(asp_kernel_time));
   return 0;
 }}
 """
@@ -65,7 +66,8 @@ int main(void) {{
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (_lib.asp_gauss, _lib.asp_component, _lib.asp_peak, _lib.asp_fit_info,
-                                       _lib.asp_params, _lib.asp_cycle_stats, _lib.asp_iter_record)]
+                                       _lib.asp_params, _lib.asp_cycle_stats, _lib.asp_iter_record,
+                                       _lib.asp_batch_tuning, _lib.asp_kernel_time)]
     assert sizes == mine
 
 
