@@ -349,6 +349,50 @@ asp_status asp_batch_image(asp_batch* b, int i, asp_ctx** ctx);
 /* Kernels the batch has launched (graph nodes counted per replay). */
 asp_status asp_batch_launch_count(asp_batch* b, int64_t* n);
 
+/* ---------------------------------------------------------------- learned initial values
+ * A 1024-256-256-4 GELU network proposes a new component's starting point
+ * (amplitude / R(p*), log(omega / omega_b), x - x*, y - y*) from the 32 x 32
+ * residual patch at the plain method's peak p*.  The paper has no learned
+ * part: its initial values are the peak (simple method) or the peak of
+ * smoothed residuals (Sect. 2 step 1, Sect. 3); the network only changes
+ * where LM starts -- the active set and fit window still come from the
+ * plain method, and a worse learned fit falls back to the plain start.
+ *
+ * The tensor-core product used for the network's wide layers, exposed for
+ * tests: C[M x N] (FP32, row-major, ldc) = A[M x K] x B[N x K]^T with A and
+ * B BF16 row-major (lda, ldb elements), all device pointers.  M % 128 == 0,
+ * N % 256 == 0, K % 64 == 0, lda, ldb multiples of 8 and >= K, ldc a
+ * multiple of 4 and >= N, 16-byte aligned bases; else ASP_ERR_INVALID_ARG.
+ * Synchronises stream; ASP_ERR_TIMEOUT if a tensor-core wait ran out. */
+asp_status asp_mlp_gemm(const void* A_dev, int lda, const void* B_dev, int ldb, float* C_dev, int ldc, int M, int N,
+                        int K, void* stream);
+
+/* Trainer of the network.  Parameters are one FP32 vector (host order
+ * W1 [256 x 1024 row-major], b1 [256], W2 [256 x 256], b2 [256], W3 [4 x 256],
+ * b3 [4]; asp_mlp_num_params gives its length).  The trainer keeps FP32
+ * master weights and Adam moments on the device, BF16 copies of W1 and W2
+ * for the tensor-core products, a data set and the scratch of a batch of up
+ * to max_batch rows (rounded up to 128).  All host arrays are copied; the
+ * trainer owns its device memory.  Errors: ASP_ERR_INVALID_ARG, ASP_ERR_OOM,
+ * ASP_ERR_CUDA, ASP_ERR_TIMEOUT (a tensor-core wait ran out). */
+typedef struct asp_mlp asp_mlp;
+asp_status asp_mlp_num_params(long long* n);
+asp_status asp_mlp_create(const float* params_host, int max_batch, void* stream, asp_mlp** out);
+asp_status asp_mlp_destroy(asp_mlp* m);
+/* Training set: n patches (n x 1024, host FP32, stored as BF16) and targets
+ * (n x 4, host FP32). */
+asp_status asp_mlp_set_data(asp_mlp* m, const float* X_host, const float* T_host, long long n);
+/* Forward and backward pass (mean squared error) on data rows idx_host[0 ..
+ * bn) (bn <= max_batch); with update != 0 one Adam step (learning rate lr,
+ * beta1 0.9, beta2 0.999, eps 1e-8).  loss_out (1 float) and grads_out
+ * (num_params floats, parameter order) are host pointers and may be NULL.
+ * Synchronises. */
+asp_status asp_mlp_step(asp_mlp* m, const int* idx_host, int bn, float lr, int update, float* loss_out,
+                        float* grads_out);
+/* Outputs (n x 4, host) for patches X_host (n x 1024, host), n <= max_batch. */
+asp_status asp_mlp_predict(asp_mlp* m, const float* X_host, int n, float* Y_host);
+asp_status asp_mlp_get_params(asp_mlp* m, float* params_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ __all__ = [
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
     "asp_batch_autotune", "asp_batch_image", "asp_batch_launch_count",
-    "Context", "Batch",
+    "Context", "Batch", "MLP", "mlp_pack", "mlp_unpack",
 ]
 
 _LIB: Optional[C.CDLL] = None
@@ -492,3 +492,75 @@ class Batch:
 
     def launches(self) -> int:
         return asp_batch_launch_count(self.h)
+
+
+# ----------------------------------------------------------------- learned initial values
+
+MLP_SHAPES = (("W1", (256, 1024)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (4, 256)), ("b3", (4,)))
+
+
+def mlp_pack(weights: dict) -> np.ndarray:
+    """Parameter dict (W1, b1, W2, b2, W3, b3) -> the library's FP32 vector."""
+    return np.concatenate([np.asarray(weights[n], dtype=np.float32).reshape(-1) for n, _ in MLP_SHAPES])
+
+
+def mlp_unpack(vec) -> dict:
+    out, o = {}, 0
+    for n, shp in MLP_SHAPES:
+        k = int(np.prod(shp))
+        out[n] = np.asarray(vec[o:o + k]).reshape(shp)
+        o += k
+    return out
+
+
+class MLP:
+    """Owns one trainer of the learned-initial-value network (asp_mlp_*)."""
+
+    def __init__(self, weights: dict, max_batch: int = 1024, stream=None):
+        n = C.c_longlong()
+        _check(lib().asp_mlp_num_params(C.byref(n)), "asp_mlp_num_params")
+        self.n_params = n.value
+        v = np.ascontiguousarray(mlp_pack(weights), dtype=np.float32)
+        if v.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {v.size}")
+        h = C.c_void_p()
+        _check(lib().asp_mlp_create(v.ctypes.data, int(max_batch), _stream_handle(stream), C.byref(h)), "asp_mlp_create")
+        self.h = h.value
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if self.h:
+            lib().asp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        if X.ndim != 2 or X.shape[1] != 1024 or T.shape != (X.shape[0], 4):
+            raise ValueError("X must be n x 1024 and T n x 4")
+        _check(lib().asp_mlp_set_data(self.h, X.ctypes.data, T.ctypes.data, X.shape[0]), "asp_mlp_set_data")
+
+    def step(self, idx, lr: float = 1e-3, update: bool = True, grads: bool = False):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        loss = C.c_float()
+        g = np.empty(self.n_params, dtype=np.float32) if grads else None
+        _check(lib().asp_mlp_step(self.h, idx.ctypes.data_as(C.POINTER(C.c_int)), idx.size, float(lr), int(update),
+                                  C.byref(loss), g.ctypes.data if grads else None), "asp_mlp_step")
+        return (loss.value, mlp_unpack(g)) if grads else loss.value
+
+    def predict(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.empty((X.shape[0], 4), dtype=np.float32)
+        _check(lib().asp_mlp_predict(self.h, X.ctypes.data, X.shape[0], Y.ctypes.data), "asp_mlp_predict")
+        return Y
+
+    def params(self) -> dict:
+        v = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().asp_mlp_get_params(self.h, v.ctypes.data), "asp_mlp_get_params")
+        return mlp_unpack(v)

@@ -127,6 +127,14 @@ SIGNATURES = {
     "asp_batch_autotune": [_P, _I, C.POINTER(asp_batch_tuning)],
     "asp_batch_image": [_P, _I, C.POINTER(_P)],
     "asp_batch_launch_count": [_P, C.POINTER(C.c_int64)],
+    "asp_mlp_gemm": [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P],
+    "asp_mlp_num_params": [C.POINTER(C.c_longlong)],
+    "asp_mlp_create": [_P, _I, _P, C.POINTER(_P)],
+    "asp_mlp_destroy": [_P],
+    "asp_mlp_set_data": [_P, _P, _P, C.c_longlong],
+    "asp_mlp_step": [_P, C.POINTER(_I), _I, C.c_float, _I, C.POINTER(C.c_float), _P],
+    "asp_mlp_predict": [_P, _P, _I, _P],
+    "asp_mlp_get_params": [_P, _P],
 }
 _RESTYPES = {"asp_status_string": C.c_char_p, "asp_default_params": None, "asp_last_error": C.c_char_p}
 

@@ -29,3 +29,4 @@ from .sky import (  # noqa: F401
     gaussian_psf,
     rng_for,
 )
+from .mlp_init import mlp_init  # noqa: F401,E402  (initial weights of the learned-init network)

@@ -1,0 +1,134 @@
+"""The learned-initial-value network on the GPU: the tcgen05 BF16 product,
+gradients against the FP64 oracle, training, inference and the fallback."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_bits(a):
+    """float -> BF16 bit patterns (round to nearest even), as uint16."""
+    from oracle import mlp_oracle as M
+    r = M.bf16(a).astype(np.float32)
+    return (r.view(np.uint32) >> 16).astype(np.uint16)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 1024), (384, 256, 192)])
+def test_tensor_core_gemm_exact_products(asp, M, N, K):
+    """C = A B^T on BF16 operands: every entry within the FP32 accumulation
+    bound K u32 sum_k |a_ik b_jk| of the exact (FP64) product of the same
+    BF16 values."""
+    import torch
+    from oracle import mlp_oracle as Mo
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(0, 1, (M, K))
+    B = rng.normal(0, 1, (N, K))
+    Ab, Bb = _bf16_bits(A), _bf16_bits(B)
+    Ad = torch.from_numpy(Ab.view(np.int16).copy()).cuda()
+    Bd = torch.from_numpy(Bb.view(np.int16).copy()).cuda()
+    Cd = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    st = asp.lib().asp_mlp_gemm(Ad.data_ptr(), K, Bd.data_ptr(), K, Cd.data_ptr(), N, M, N, K, None)
+    assert st == 0, asp.lib().asp_status_string(st)
+    A64, B64 = Mo.bf16(A), Mo.bf16(B)
+    exact = A64 @ B64.T
+    bound = K * 2.0 ** -24 * (np.abs(A64) @ np.abs(B64).T) + 1e-30
+    err = np.abs(Cd.cpu().numpy().astype(np.float64) - exact)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_tensor_core_gemm_rejects_bad_shapes(asp):
+    st = asp.lib().asp_mlp_gemm(1, 64, 1, 64, 1, 256, 100, 256, 64, None)
+    assert st == 1          # ASP_ERR_INVALID_ARG
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (n, 1024)) * np.exp(-np.linspace(-2, 2, 32)[None, :].repeat(32, 0).reshape(1, -1) ** 2)
+    T = rng.normal(0, 1, (n, 4))
+    return X, T
+
+
+def _oracle_weights(w):
+    from oracle import mlp_oracle as Mo
+    return Mo.MLPWeights(*(np.asarray(w[n], dtype=np.float64) for n in ("W1", "b1", "W2", "b2", "W3", "b3")))
+
+
+def _f32(w):
+    return {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in w.items()}
+
+
+def test_forward_matches_oracle(asp):
+    """Outputs of the tensor-core forward pass against the FP64 oracle fed
+    the same BF16-rounded operands: within 2e-3 relative L2 (FP32 sums and
+    erff against FP64, and BF16 rounding of h1 that may flip by one unit)."""
+    import synth
+    from oracle import mlp_oracle as Mo
+    w = _f32(synth.mlp_init(1))
+    X, _ = _data(300, 2)
+    net = asp.MLP(w, max_batch=300)
+    Y = net.predict(X.astype(np.float32))
+    Yo, _ = Mo.forward(_oracle_weights(w), X.astype(np.float32), round_bf16=True)
+    assert np.linalg.norm(Y - Yo) / np.linalg.norm(Yo) < 2e-3
+    net.close()
+
+
+def test_gradients_match_oracle(asp):
+    """Every parameter block's gradient (forward + backward on the GPU: three
+    tcgen05 products per pass direction, FP32 elsewhere) against the FP64
+    oracle with the same BF16 operand rounding: relative L2 error per block
+    within 1e-2.  The bound allows for FP32 accumulation and erff against
+    FP64 (~1e-6) and for the rare hidden activation whose BF16 rounding
+    flips by one unit (2^-8) between the FP32 and FP64 pre-activations."""
+    import synth
+    from oracle import mlp_oracle as Mo
+    w = _f32(synth.mlp_init(3))
+    X, T = _data(200, 4)
+    X = X.astype(np.float32).astype(np.float64)
+    T = T.astype(np.float32).astype(np.float64)
+    net = asp.MLP(w, max_batch=256)
+    net.set_data(X, T)
+    loss, g = net.step(np.arange(200), update=False, grads=True)
+    Yo, c = Mo.forward(_oracle_weights(w), X, round_bf16=True)
+    Lo, dY = Mo.mse(Yo, T)
+    go = Mo.backward(_oracle_weights(w), c, dY)
+    assert loss == pytest.approx(Lo, rel=1e-3)
+    for n in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        ref = getattr(go, n)
+        err = np.linalg.norm(g[n] - ref) / np.linalg.norm(ref)
+        assert err < 1e-2, (n, err)
+    net.close()
+
+
+def test_adam_first_step_closed_form(asp):
+    """From zero moments the first update is -lr g / (|g| + eps) with the
+    GPU's own gradient g (FP32)."""
+    import synth
+    w = _f32(synth.mlp_init(5))
+    X, T = _data(128, 6)
+    net = asp.MLP(w, max_batch=128)
+    net.set_data(X, T)
+    _, g = net.step(np.arange(128), update=False, grads=True)
+    p0 = net.params()
+    net.step(np.arange(128), lr=1e-3, update=True)
+    p1 = net.params()
+    for n in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        expect = -1e-3 * g[n] / (np.abs(g[n]) + 1e-8)
+        np.testing.assert_allclose(p1[n] - p0[n], expect, rtol=1e-3, atol=1e-9)
+    net.close()
+
+
+def test_training_reduces_loss(asp):
+    """A learnable target (linear functionals of the patch) is fitted: the
+    loss falls by 10x within 300 Adam steps of batch 256."""
+    import synth
+    rng = np.random.default_rng(7)
+    X, _ = _data(4096, 8)
+    P = rng.normal(0, 1, (1024, 4)) / 32.0
+    T = np.tanh(X @ P)
+    net = asp.MLP(_f32(synth.mlp_init(9)), max_batch=256)
+    net.set_data(X, T)
+    first = net.step(rng.integers(0, 4096, 256), lr=1e-3, update=True)
+    for _ in range(300):
+        last = net.step(rng.integers(0, 4096, 256), lr=1e-3, update=True)
+    assert last < first / 10, (first, last)
+    net.close()
