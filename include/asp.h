@@ -141,6 +141,9 @@ typedef struct {
     double fit_factor_ms, fit_subst_ms;   /* parts of fit_solve_ms: damped solves, LM bookkeeping */
     int64_t fit_refinements;  /* FP64 iterative-refinement steps of the FP32-factored solves */
     int64_t fit_fallbacks;    /* solves that fell back to an FP64 factor */
+    int64_t learned_fits;     /* fits started from the network's proposal */
+    int64_t learned_refits;   /* of those, refitted from the plain start by the fallback rule */
+    int64_t learned_kept;     /* of those, whose learned-start result was kept */
 } asp_cycle_stats;
 
 /* One minor-cycle iteration as recorded on the device. */
@@ -392,6 +395,29 @@ asp_status asp_mlp_step(asp_mlp* m, const int* idx_host, int bn, float lr, int u
 /* Outputs (n x 4, host) for patches X_host (n x 1024, host), n <= max_batch. */
 asp_status asp_mlp_predict(asp_mlp* m, const float* X_host, int n, float* Y_host);
 asp_status asp_mlp_get_params(asp_mlp* m, float* params_host);
+
+/* Learned initial values in a context's minor cycle.  params_host: the
+ * network's FP32 parameter vector (order as above), copied; enable = 0
+ * switches the proposals off again.  With it on, each iteration:
+ *   1. the plain method (peak or smoothed peak, Sect. 2 step 1, Sect. 3)
+ *      picks p*, the active set and the fit window as without it;
+ *   2. the network maps the 32 x 32 patch of R at p* (divided by |R(p*)|)
+ *      to (a0 / R(p*), log(omega0 / omega_b), x0 - x*, y0 - y*) -- BF16
+ *      tensor-core products -- and LM starts the new member there (kept
+ *      plain if the proposal is outside the window, not finite or below the
+ *      width bound);
+ *   3. fallback: if that fit hits the LM cap, ends non-finite or at the width
+ *      bound, or ends with a chi^2 above chi^2 at the plain start point, LM
+ *      is run again from the plain start and the better chi^2 is kept.
+ * Both fits use the same window and members, so their chi^2 compare. */
+asp_status asp_set_mlp(asp_ctx* ctx, const float* params_host, int enable);
+/* Training-data harvest: while set, iteration t of the minor cycle writes
+ * the 32 x 32 patch at the plain peak (1024 floats, divided by |R(p*)|) to
+ * patches_dev + 1024 t and (a / R(p*), log(omega / omega_b), x - x*,
+ * y - y*, R(p*), x*, y*, LM status) of the converged new member to
+ * targets_dev + 8 t, for t < capacity (device pointers owned by the caller;
+ * NULL patches_dev switches the harvest off). */
+asp_status asp_set_harvest(asp_ctx* ctx, float* patches_dev, float* targets_dev, int capacity);
 
 #ifdef __cplusplus
 }

@@ -595,7 +595,8 @@ class MinorCycle:
        list is capped at retained_cap_factor * k_max (oldest dropped).
     """
 
-    def __init__(self, dirty, psf, params: AspParams, beam=None):
+    def __init__(self, dirty, psf, params: AspParams, beam=None, mlp=None):
+        self.mlp = mlp   # learned initial values (mlp_oracle.MLPWeights) or None
         self.R = np.array(dirty, dtype=np.float64)
         self.B = np.asarray(psf, dtype=np.float64)
         self.H, self.W = self.R.shape
@@ -690,7 +691,11 @@ class MinorCycle:
             T += gauss_model(G, xs, ys)
             theta0 += list(G)
         theta0 = np.array(theta0)
-        fit = lm_fit(T, xs, ys, theta0, win, 0.25 * self.omega_b, self.p.lm)
+        learned = None
+        if self.mlp is not None:
+            fit, learned = self._learned_fit(T, xs, ys, theta0, win, init)
+        else:
+            fit = lm_fit(T, xs, ys, theta0, win, 0.25 * self.omega_b, self.p.lm)
         th = fit.theta
         terms = []
         new = self._component_from_fit(*th[0:4], gain=self.p.gain)
@@ -725,10 +730,49 @@ class MinorCycle:
         self.last_wi = new.width
         self.last_w0 = init["w0"]
         rec = dict(t=self.t, mode=mode, peak_index=pidx, peak_value=pval, init=init,
-                   members=[new_index] + chosen, window=win, fit=fit, n_terms=len(terms))
+                   members=[new_index] + chosen, window=win, fit=fit, n_terms=len(terms), learned=learned)
         self.history.append(rec)
         self.t += 1
         return rec
+
+    def _learned_fit(self, T, xs, ys, theta0, win, init):
+        """Learned initial values (reading of the fallback rule): the plain
+        method fixed p*, the members and the window; the network proposes the
+        new member's start from the 32 x 32 patch at p* (BF16 operands as on
+        the GPU).  A proposal that is not finite, has a zero amplitude, or
+        lies outside the window or the width bounds is not used.  Otherwise
+        LM runs from it; if that fit hits the cap, ends non-finite or at the
+        width bound, or ends above chi^2 at the plain start, LM runs again
+        from the plain start and the lower chi^2 is kept."""
+        from . import mlp_oracle as Mo
+        omega_min = 0.25 * self.omega_b
+        px, py = int(init["x0"]), int(init["y0"])
+        rp = float(self.R[py, px])
+        patch = Mo.extract_patch(self.R, px, py)
+        out, _ = Mo.forward(self.mlp, patch[None, :], round_bf16=True)
+        prop = Mo.init_from_output(out[0], rp, px, py, self.omega_b) if rp != 0 else np.full(4, np.nan)
+        x0b, x1b, y0b, y1b = win
+        omega_max = max(x1b - x0b + 1, y1b - y0b + 1)
+        ok = (np.all(np.isfinite(prop)) and prop[0] != 0 and prop[3] > omega_min and not prop[3] > omega_max
+              and x0b <= prop[1] <= x1b and y0b <= prop[2] <= y1b)
+        info = dict(used=bool(ok), refit=False, kept=False, proposal=prop)
+        if not ok:
+            return lm_fit(T, xs, ys, theta0, win, omega_min, self.p.lm), info
+        chi2_plain = float(np.sum((T - gauss_model(theta0, xs, ys)) ** 2))
+        th_l = theta0.copy()
+        th_l[0:4] = prop
+        fit_l = lm_fit(T, xs, ys, th_l, win, omega_min, self.p.lm)
+        bad = (fit_l.status == LM_CAP or not np.isfinite(fit_l.chi2) or not fit_l.theta[3] > omega_min
+               or fit_l.chi2 > chi2_plain)
+        if not bad:
+            info["kept"] = True
+            return fit_l, info
+        info["refit"] = True
+        fit_p = lm_fit(T, xs, ys, theta0, win, omega_min, self.p.lm)
+        if fit_p.chi2 < fit_l.chi2 or not np.isfinite(fit_l.chi2):
+            return fit_p, info
+        info["kept"] = True
+        return fit_l, info
 
     def run(self, n_iter):
         for _ in range(n_iter):

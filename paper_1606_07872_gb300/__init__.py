@@ -445,6 +445,27 @@ class Context:
     def scales(self):
         return asp_num_scales(self.h)
 
+    def set_mlp(self, weights: Optional[dict], enable: bool = True):
+        """Learned initial values from the network ``weights`` (dict of
+        W1 b1 W2 b2 W3 b3); ``enable=False`` (or None) switches them off."""
+        if weights is None or not enable:
+            _check(lib().asp_set_mlp(self.h, None, 0), "asp_set_mlp")
+            return
+        v = np.ascontiguousarray(mlp_pack(weights), dtype=np.float32)
+        _check(lib().asp_set_mlp(self.h, v.ctypes.data, 1), "asp_set_mlp")
+
+    def set_harvest(self, patches=None, targets=None):
+        """Record (patch, converged-fit target) pairs into CUDA tensors
+        patches (cap x 1024) and targets (cap x 8); None switches it off."""
+        if patches is None:
+            _check(lib().asp_set_harvest(self.h, None, None, 0), "asp_set_harvest")
+            return
+        cap = int(patches.shape[0])
+        if tuple(patches.shape) != (cap, 1024) or tuple(targets.shape) != (cap, 8):
+            raise ValueError("patches must be cap x 1024 and targets cap x 8")
+        _check(lib().asp_set_harvest(self.h, _cuda_f32(patches, (cap, 1024), "patches"),
+                                     _cuda_f32(targets, (cap, 8), "targets"), cap), "asp_set_harvest")
+
 
 class Batch:
     """Owns one libasp batch: independent images advanced together, the LM

@@ -60,7 +60,8 @@ class asp_cycle_stats(C.Structure):
                 ("sub_flops", C.c_double), ("sub_bytes", C.c_double), ("smooth_flops", C.c_double),
                 ("fit_pass_ms", C.c_double), ("fit_reduce_ms", C.c_double), ("fit_solve_ms", C.c_double),
                 ("fit_factor_ms", C.c_double), ("fit_subst_ms", C.c_double), ("fit_refinements", C.c_int64),
-                ("fit_fallbacks", C.c_int64)]
+                ("fit_fallbacks", C.c_int64), ("learned_fits", C.c_int64), ("learned_refits", C.c_int64),
+                ("learned_kept", C.c_int64)]
 
 
 class asp_iter_record(C.Structure):
@@ -135,6 +136,8 @@ SIGNATURES = {
     "asp_mlp_step": [_P, C.POINTER(_I), _I, C.c_float, _I, C.POINTER(C.c_float), _P],
     "asp_mlp_predict": [_P, _P, _I, _P],
     "asp_mlp_get_params": [_P, _P],
+    "asp_set_mlp": [_P, _P, _I],
+    "asp_set_harvest": [_P, _P, _P, _I],
 }
 _RESTYPES = {"asp_status_string": C.c_char_p, "asp_default_params": None, "asp_last_error": C.c_char_p}
 

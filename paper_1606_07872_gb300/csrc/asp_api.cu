@@ -18,11 +18,11 @@ using namespace aspd;
 // Kernel classes timed by asp_set_profiling.
 enum KernelClass {
     KC_BEGIN, KC_SMOOTH_H, KC_SMOOTH_V, KC_SELECT, KC_FIT, KC_UPDATE, KC_WEIGHTS, KC_SUB_H, KC_SUB_V, KC_ARGMAX,
-    KC_COUNT
+    KC_MLP, KC_LEARNED, KC_HARVEST, KC_COUNT
 };
 static const char* const KC_NAMES[KC_COUNT] = {
     "k_cycle_begin", "k_smooth_h", "k_smooth_v_argmax", "k_select", "k_lm_fit", "k_update", "k_build_weights",
-    "k_sub_h", "k_sub_v_argmax", "k_argmax_abs"};
+    "k_sub_h", "k_sub_v_argmax", "k_argmax_abs", "mlp_infer (tcgen05)", "k_learned_*", "k_harvest"};
 static const int KERNELS_PER_ITER = 9;   // kernels one minor-cycle iteration enqueues
 
 struct ProfMark {
@@ -72,6 +72,20 @@ struct asp_ctx {
     double prof_ms[KC_COUNT] = {};
     long long prof_n[KC_COUNT] = {};
     long long launches = 0;
+    int iter_kernels = KERNELS_PER_ITER;   // kernels one captured iteration holds
+    // learned initial values
+    int learned = 0;
+    float* mlpP = nullptr;                 // FP32 parameter vector
+    void* W1b = nullptr;                   // BF16 copies of W1, W2
+    void* W2b = nullptr;
+    void* Xinf = nullptr;                  // 128 x 1024 BF16 network input (row 0 used)
+    void* H1b = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *Yinf = nullptr;
+    unsigned* mlp_err = nullptr;
+    // training-data harvest
+    float* harvest_p = nullptr;
+    float* harvest_t = nullptr;
+    int harvest_cap = 0;
     int broken = 0;
     std::string err;
     std::vector<void*> allocs;
@@ -218,10 +232,38 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
       CK(launch_smooth_v(ctx->S1, H, W, ctx->taps, st, &st->skip_smooth, -1, nullptr, ctx->grid_img, ctx->part,
                          ctx->ticket, s)); }
     { Mark m(ctx, KC_SELECT); CK(launch_select(st, ctx->comps, ctx->dp, H, W, ctx->g_max, s)); }
+    if (ctx->learned) {
+        // chi^2 at the plain start (one pass), then the network's proposal
+        LMConst lm0 = ctx->dp.lm;
+        lm0.max_iter = 0;
+        { Mark m(ctx, KC_LEARNED); CK(launch_learned_prep(st, ctx->R, H, W, ctx->Xinf, s)); }
+        { Mark m(ctx, KC_FIT);
+          CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit2, lm0, &st->fout2, ctx->partials, ctx->sums,
+                           ctx->bar, ctx->Tg, s)); }
+        {
+            Mark m(ctx, KC_MLP);
+            ctx->launches += mlp_infer_kernels() - 1;
+            CK(launch_mlp_infer(ctx->Xinf, ctx->W1b, ctx->W2b, ctx->mlpP, ctx->Z1, ctx->H1b, ctx->Z2, ctx->H2, ctx->Yinf,
+                                ctx->mlp_err, s));
+        }
+        { Mark m(ctx, KC_LEARNED); CK(launch_learned_apply(st, ctx->Yinf, s)); }
+    }
     { Mark m(ctx, KC_FIT);
       CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit, ctx->dp.lm, &st->fout, ctx->partials, ctx->sums,
                        ctx->bar, ctx->Tg, s)); }
+    if (ctx->learned) {
+        // fallback: refit from the plain start when the learned fit is worse
+        { Mark m(ctx, KC_LEARNED); CK(launch_learned_check(st, s)); }
+        { Mark m(ctx, KC_FIT);
+          CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit2, ctx->dp.lm, &st->fout2, ctx->partials, ctx->sums,
+                           ctx->bar, ctx->Tg, s)); }
+        { Mark m(ctx, KC_LEARNED); CK(launch_learned_pick(st, s)); }
+    }
     { Mark m(ctx, KC_UPDATE); CK(launch_update(st, ctx->comps, ctx->hist, ctx->dp, H, W, s)); }
+    if (ctx->harvest_p) {
+        Mark m(ctx, KC_HARVEST);
+        CK(launch_harvest(st, ctx->R, H, W, ctx->harvest_p, ctx->harvest_t, ctx->harvest_cap, s));
+    }
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(st, &st->stopped, ctx->wbuf, s)); }
     { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->taps, s)); }
     { Mark m(ctx, KC_SUB_V);
@@ -246,6 +288,7 @@ asp_status build_graph(asp_ctx* ctx) {
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         ok = (s == ASP_OK) && e == cudaSuccess && g != nullptr;
     }
+    ctx->iter_kernels = (int)((ctx->launches - launches_before) / std::max(ctx->graph_unroll, 1));
     ctx->stream = saved;
     ctx->launches = launches_before;
     ctx->broken = 0;
@@ -735,7 +778,7 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         if (ctx->graph_state == 1 && !ctx->profiling) {
             const int reps = (n_iter + ctx->graph_unroll - 1) / ctx->graph_unroll;
             for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-            ctx->launches += (long long)reps * ctx->graph_unroll * KERNELS_PER_ITER;
+            ctx->launches += (long long)reps * ctx->graph_unroll * ctx->iter_kernels;
         } else {
             for (int i = 0; i < n_iter; ++i) {
                 s = enqueue_iteration(ctx);
@@ -748,6 +791,11 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
     s = read_state(ctx, &h);
     if (s != ASP_OK) return s;
     if (h.error == ASP_ERR_TIMEOUT) return fail(ctx, ASP_ERR_TIMEOUT, "fit: grid barrier timed out");
+    if (ctx->learned && ctx->mlp_err) {
+        unsigned me = 0;
+        CK(cudaMemcpy(&me, ctx->mlp_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (me) return fail(ctx, ASP_ERR_TIMEOUT, "network inference: tensor-core wait timed out");
+    }
     if (h.error == ASP_ERR_NAN || h.nonfinite) return fail(ctx, ASP_ERR_NAN, "non-finite value in the residual");
     if (out) {
         out->iterations = h.t;
@@ -769,6 +817,9 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         out->fit_subst_ms = h.fit_ns_subst * 1e-6;
         out->fit_refinements = h.fit_refinements;
         out->fit_fallbacks = h.fit_fallbacks;
+        out->learned_fits = h.learned_fits;
+        out->learned_refits = h.learned_refits;
+        out->learned_kept = h.learned_kept;
     }
     if (h.stop_reason == ASP_STOP_CAPACITY) return fail(ctx, ASP_ERR_CAPACITY, "component list full");
     return ASP_OK;
@@ -799,6 +850,9 @@ asp_status asp_get_stats(asp_ctx* ctx, asp_cycle_stats* out) {
     out->fit_subst_ms = h.fit_ns_subst * 1e-6;
     out->fit_refinements = h.fit_refinements;
     out->fit_fallbacks = h.fit_fallbacks;
+    out->learned_fits = h.learned_fits;
+    out->learned_refits = h.learned_refits;
+    out->learned_kept = h.learned_kept;
     return ASP_OK;
 }
 
@@ -1016,6 +1070,63 @@ asp_status asp_launch_count(asp_ctx* ctx, int64_t* n) {
 }
 
 static const uint32_t STATE_MAGIC = 0x41535031u;   // "ASP1"
+
+asp_status asp_set_mlp(asp_ctx* ctx, const float* params_host, int enable) {
+    CHECK_CTX();
+    if (enable && !params_host) return ASP_ERR_INVALID_ARG;
+    if (enable) {
+        if (!ctx->mlpP) {
+            const long long np = mlp_num_params();
+#define AL(ptr, n) if (dalloc(ctx, &(ptr), (size_t)(n)) != cudaSuccess) return fail(ctx, ASP_ERR_OOM, "asp_set_mlp")
+            float* P = nullptr;
+            uint16_t *w1 = nullptr, *w2 = nullptr, *x = nullptr, *h1 = nullptr;
+            AL(P, np);
+            AL(w1, 256 * 1024);
+            AL(w2, 256 * 256);
+            AL(x, 128 * 1024);
+            AL(h1, 128 * 256);
+            AL(ctx->Z1, 128 * 256);
+            AL(ctx->Z2, 128 * 256);
+            AL(ctx->H2, 128 * 256);
+            AL(ctx->Yinf, 128 * 4);
+            AL(ctx->mlp_err, 1);
+#undef AL
+            ctx->mlpP = P;
+            ctx->W1b = w1;
+            ctx->W2b = w2;
+            ctx->Xinf = x;
+            ctx->H1b = h1;
+            CK(cudaMemsetAsync(ctx->Xinf, 0, 128 * 1024 * sizeof(uint16_t), ctx->stream));
+            CK(cudaMemsetAsync(ctx->mlp_err, 0, sizeof(unsigned), ctx->stream));
+            // the fallback's fit descriptor starts inactive
+            CK(cudaMemsetAsync(&ctx->st->fit2, 0, sizeof(FitDesc), ctx->stream));
+        }
+        CK(cudaMemcpyAsync(ctx->mlpP, params_host, mlp_num_params() * sizeof(float), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(mlp_prepare(ctx->mlpP, ctx->W1b, ctx->W2b, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (ctx->learned != (enable ? 1 : 0)) {
+        ctx->learned = enable ? 1 : 0;
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        ctx->graph_state = 0;
+    }
+    return ASP_OK;
+}
+
+asp_status asp_set_harvest(asp_ctx* ctx, float* patches_dev, float* targets_dev, int capacity) {
+    CHECK_CTX();
+    if (patches_dev && (!targets_dev || capacity < 1)) return ASP_ERR_INVALID_ARG;
+    const bool was = ctx->harvest_p != nullptr, now = patches_dev != nullptr;
+    ctx->harvest_p = patches_dev;
+    ctx->harvest_t = now ? targets_dev : nullptr;
+    ctx->harvest_cap = now ? capacity : 0;
+    if (was || now) {   // the pointers are baked into the captured graph
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        ctx->graph_state = 0;
+    }
+    return ASP_OK;
+}
 
 asp_status asp_save_state(asp_ctx* ctx, const char* path) {
     CHECK_CTX();
@@ -1349,6 +1460,9 @@ asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stat
             o.fit_subst_ms = h.fit_ns_subst * 1e-6;
             o.fit_refinements = h.fit_refinements;
             o.fit_fallbacks = h.fit_fallbacks;
+            o.learned_fits = h.learned_fits;
+            o.learned_refits = h.learned_refits;
+            o.learned_kept = h.learned_kept;
         }
     }
     return first_err;

@@ -12,6 +12,8 @@
 //                  subtraction terms dC = gain c_new + sum_old (c'_k - c_k);
 //   k_build_weights the sampled, flux-normalised axis weights of each term.
 // These are scalar control kernels: one thread (or one block per term).
+#include <cuda_bf16.h>
+
 #include "asp_dev.cuh"
 #include "asp_internal.h"
 
@@ -418,6 +420,9 @@ __global__ void k_reset_state(CycleState* st) {
     st->fit_refinements = 0; st->fit_fallbacks = 0;
     st->nonfinite = 0;
     st->fit.active = 0;
+    st->fit2.active = 0;
+    st->learned_used = 0; st->need_plain = 0;
+    st->learned_fits = 0; st->learned_refits = 0; st->learned_kept = 0;
 }
 
 
@@ -467,6 +472,195 @@ cudaError_t launch_build_weights_b(const ImgDesc* imgs, int n, cudaStream_t s) {
 }
 cudaError_t launch_arm_b(const ImgDesc* imgs, int n, int n_iter, cudaStream_t s) {
     k_arm_b<<<(n + 127) / 128, 128, 0, s>>>(imgs, n, n_iter);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ learned initial values
+// (see asp_set_mlp).  The plain method has already chosen p*, the members
+// and the window (k_select); these kernels only move the new member's LM
+// start and apply the fallback rule.
+
+namespace {
+__device__ void copy_words(void* dst, const void* src, int bytes) {
+    int* d = reinterpret_cast<int*>(dst);
+    const int* q = reinterpret_cast<const int*>(src);
+    for (int i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = q[i];
+}
+__device__ void account_fit(CycleState* st, const FitOut& fo, int K) {
+    st->pixel_evals += fo.pixel_evals;
+    st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
+    st->lm_iters += fo.iters;
+    st->lm_passes += fo.passes;
+    st->fit_ns_pass += fo.ns_pass;
+    st->fit_ns_reduce += fo.ns_reduce;
+    st->fit_ns_solve += fo.ns_solve;
+    st->fit_ns_factor += fo.ns_factor;
+    st->fit_ns_subst += fo.ns_subst;
+    st->fit_refinements += fo.refinements;
+    st->fit_fallbacks += fo.fallbacks;
+}
+}  // namespace
+
+// After k_select: keep the plain start, arm fit2 as the chi^2-only
+// evaluation at it, and write the input patch (divided by |R(p*)|, BF16) to
+// Xrow.  One block.
+__device__ __forceinline__ void learned_prep_body(CycleState* st, const float* __restrict__ R, int H, int W,
+                                                  __nv_bfloat16* __restrict__ Xrow) {
+    const bool live = !st->stopped && st->fit.active;
+    __syncthreads();
+    if (!live) {
+        if (threadIdx.x == 0) { st->fit2.active = 0; st->learned_used = 0; st->need_plain = 0; }
+        for (int q = threadIdx.x; q < 1024; q += blockDim.x) Xrow[q] = __float2bfloat16(0.f);
+        return;
+    }
+    copy_words(&st->fit2, &st->fit, (int)sizeof(FitDesc));
+    const int px = (int)st->init[1], py = (int)st->init[2];
+    const float rp = R[(long long)py * W + px];
+    const float inv = rp != 0.f ? 1.0f / fabsf(rp) : 0.f;
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
+        const int y = py - 16 + (q >> 5), x = px - 16 + (q & 31);
+        const float v = (y >= 0 && y < H && x >= 0 && x < W) ? R[(long long)y * W + x] * inv : 0.f;
+        Xrow[q] = __float2bfloat16(v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) st->plain_theta[i] = st->fit.theta0[i];
+        st->learned_rp = rp;
+        st->learned_px = px;
+        st->learned_py = py;
+        st->fit2.active = 1;
+        st->learned_used = 0;
+        st->need_plain = 0;
+    }
+}
+__global__ void k_learned_prep(CycleState* st, const float* __restrict__ R, int H, int W, __nv_bfloat16* Xrow) {
+    learned_prep_body(st, R, H, W, Xrow);
+}
+
+// After the chi^2-only fit and the network: the learned start of the new
+// member (y = the network's 4 outputs), kept plain when it is not finite,
+// outside the window or not above the width bound.
+__device__ __forceinline__ void learned_apply_body(CycleState* st, const float* __restrict__ y) {
+    if (threadIdx.x != 0) return;
+    if (!st->fit2.active) return;
+    st->fit2.active = 0;
+    account_fit(st, st->fout2, st->fit.K);          // the chi^2 evaluation pass
+    FitDesc& f = st->fit;
+    const double a0 = (double)y[0] * st->learned_rp;
+    const double w0 = st->omega_b * exp((double)y[1]);
+    const double x0 = st->learned_px + (double)y[2];
+    const double y0 = st->learned_py + (double)y[3];
+    const bool ok = isfinite(a0) && isfinite(w0) && isfinite(x0) && isfinite(y0) && a0 != 0.0 && w0 > f.omega_min &&
+                    !(w0 > f.omega_max) && !(x0 < f.bx0) && !(x0 > f.bx1) && !(y0 < f.by0) && !(y0 > f.by1);
+    if (ok) {
+        f.theta0[0] = a0; f.theta0[1] = x0; f.theta0[2] = y0; f.theta0[3] = w0;
+        st->learned_used = 1;
+        st->learned_fits += 1;
+    }
+}
+__global__ void k_learned_apply(CycleState* st, const float* __restrict__ y) { learned_apply_body(st, y); }
+
+// After the fit from the learned start: the fallback rule.
+__device__ __forceinline__ void learned_check_body(CycleState* st) {
+    const bool go = st->fit.active && st->learned_used;
+    __syncthreads();
+    if (!go) {
+        if (threadIdx.x == 0) { st->fit2.active = 0; st->need_plain = 0; }
+        return;
+    }
+    const FitOut& fo = st->fout;
+    const bool bad = fo.status == ASP_LM_CAP || !isfinite(fo.chi2) || !(fo.theta[3] > st->fit.omega_min) ||
+                     fo.chi2 > st->fout2.chi2_init;
+    if (!bad) {
+        if (threadIdx.x == 0) { st->learned_kept += 1; st->fit2.active = 0; st->need_plain = 0; }
+        return;
+    }
+    copy_words(&st->fit2, &st->fit, (int)sizeof(FitDesc));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) st->fit2.theta0[i] = st->plain_theta[i];
+        st->fit2.active = 1;
+        st->need_plain = 1;
+        st->learned_refits += 1;
+    }
+}
+__global__ void k_learned_check(CycleState* st) { learned_check_body(st); }
+
+// After the refit: keep the better chi^2; the other fit's work is counted
+// here (the kept one is counted by k_update).
+__device__ __forceinline__ void learned_pick_body(CycleState* st) {
+    const bool go = st->need_plain != 0;
+    __syncthreads();
+    if (!go) return;
+    const bool plain_better = st->fout2.chi2 < st->fout.chi2 || !isfinite(st->fout.chi2);
+    __syncthreads();
+    if (threadIdx.x == 0) account_fit(st, plain_better ? st->fout : st->fout2, st->fit.K);
+    __syncthreads();
+    if (plain_better) copy_words(&st->fout, &st->fout2, (int)sizeof(FitOut));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (plain_better) {
+            for (int i = 0; i < 4; ++i) st->fit.theta0[i] = st->plain_theta[i];
+        } else {
+            st->learned_kept += 1;
+        }
+        st->fit2.active = 0;
+        st->need_plain = 0;
+    }
+}
+__global__ void k_learned_pick(CycleState* st) { learned_pick_body(st); }
+
+// Training-data harvest, after k_update (R not yet updated): record t-1.
+__device__ __forceinline__ void harvest_body(const CycleState* __restrict__ st, const float* __restrict__ R, int H, int W,
+                                             float* __restrict__ patches, float* __restrict__ targets, int capacity,
+                                             int last_t) {
+    const int t = st->t - 1;
+    if (st->t == last_t || t < 0 || t >= capacity || !st->fit.active) return;   // no new iteration ran
+    const int px = (int)st->init[1], py = (int)st->init[2];
+    const double rp = R[(long long)py * W + px];
+    const float inv = rp != 0.0 ? (float)(1.0 / fabs(rp)) : 0.f;
+    float* pt = patches + (long long)t * 1024;
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
+        const int y = py - 16 + (q >> 5), x = px - 16 + (q & 31);
+        pt[q] = (y >= 0 && y < H && x >= 0 && x < W) ? R[(long long)y * W + x] * inv : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        const double* th = st->fout.theta;
+        float* tg = targets + (long long)t * 8;
+        tg[0] = (float)(th[0] / rp);
+        tg[1] = (float)log(th[3] / st->omega_b);
+        tg[2] = (float)(th[1] - px);
+        tg[3] = (float)(th[2] - py);
+        tg[4] = (float)rp;
+        tg[5] = (float)px;
+        tg[6] = (float)py;
+        tg[7] = (float)st->fout.status;
+    }
+}
+__global__ void k_harvest(const CycleState* __restrict__ st, const float* __restrict__ R, int H, int W, float* patches,
+                          float* targets, int capacity) {
+    harvest_body(st, R, H, W, patches, targets, capacity, -1);
+}
+
+cudaError_t launch_learned_prep(CycleState* st, const float* R, int H, int W, void* Xrow, cudaStream_t s) {
+    k_learned_prep<<<1, 256, 0, s>>>(st, R, H, W, reinterpret_cast<__nv_bfloat16*>(Xrow));
+    return cudaGetLastError();
+}
+cudaError_t launch_learned_apply(CycleState* st, const float* y, cudaStream_t s) {
+    k_learned_apply<<<1, 32, 0, s>>>(st, y);
+    return cudaGetLastError();
+}
+cudaError_t launch_learned_check(CycleState* st, cudaStream_t s) {
+    k_learned_check<<<1, 256, 0, s>>>(st);
+    return cudaGetLastError();
+}
+cudaError_t launch_learned_pick(CycleState* st, cudaStream_t s) {
+    k_learned_pick<<<1, 256, 0, s>>>(st);
+    return cudaGetLastError();
+}
+cudaError_t launch_harvest(const CycleState* st, const float* R, int H, int W, float* patches, float* targets,
+                           int capacity, cudaStream_t s) {
+    k_harvest<<<1, 256, 0, s>>>(st, R, H, W, patches, targets, capacity);
     return cudaGetLastError();
 }
 

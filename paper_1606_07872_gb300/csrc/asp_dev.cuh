@@ -109,6 +109,15 @@ struct CycleState {
     Deposit dep[MAX_DEPOSITS];     // point-like terms as bilinear deposits
     FitDesc fit;
     FitOut fout;
+    // learned initial values: the plain start, a second fit (chi^2 at the
+    // plain start, then the fallback refit) and the counters
+    FitDesc fit2;
+    FitOut fout2;
+    double plain_theta[4];
+    double learned_rp;             // R(p*) at the plain peak
+    int learned_px, learned_py;    // the plain peak pixel
+    int learned_used, need_plain;
+    long long learned_fits, learned_refits, learned_kept;
 };
 
 struct Params {                    // device copy of asp_params plus derived values

@@ -98,6 +98,18 @@ cudaError_t launch_build_weights_b(const ImgDesc* imgs, int n, cudaStream_t s);
 cudaError_t launch_sub_h_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s);
 cudaError_t launch_sub_v_b(const ImgDesc* imgs, int n, int grid_x, cudaStream_t s);
 cudaError_t launch_arm_b(const ImgDesc* imgs, int n, int n_iter, cudaStream_t s);
+// learned initial values (asp_mlp.cu, asp_cycle.cu)
+cudaError_t launch_mlp_infer(const void* X, const void* W1b, const void* W2b, const float* P, float* Z1, void* H1b,
+                             float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s);
+int mlp_infer_kernels();
+cudaError_t mlp_prepare(const float* P, void* W1b, void* W2b, cudaStream_t s);
+long long mlp_num_params();
+cudaError_t launch_learned_prep(CycleState* st, const float* R, int H, int W, void* Xrow, cudaStream_t s);
+cudaError_t launch_learned_apply(CycleState* st, const float* y, cudaStream_t s);
+cudaError_t launch_learned_check(CycleState* st, cudaStream_t s);
+cudaError_t launch_learned_pick(CycleState* st, cudaStream_t s);
+cudaError_t launch_harvest(const CycleState* st, const float* R, int H, int W, float* patches, float* targets,
+                           int capacity, cudaStream_t s);
 cudaError_t launch_beam_init(FitDesc* desc, const float* B, int H, int W, int g_max, cudaStream_t s);
 cudaError_t launch_radix_median(const float* v, long long n, int absdev, double center, unsigned long long* ws,
                                 double* out, cudaStream_t s);

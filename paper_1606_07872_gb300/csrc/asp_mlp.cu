@@ -252,6 +252,8 @@ namespace aspd {
 namespace {
 
 constexpr int NI = 1024, NH = 256, NO = 4;
+
+int ew_grid(long long n) { return (int)(n + 255) / 256 < 4096 ? (int)((n + 255) / 256) : 4096; }
 constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (size_t)NH * NI, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + (size_t)NH * NH,
                  OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + (size_t)NO * NH, N_PARAMS = OFF_B3 + NO;
 
@@ -421,6 +423,38 @@ __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restri
 }  // namespace
 }  // namespace aspd
 
+namespace aspd {
+
+// In-cycle inference for up to 128 patches (rows of X, BF16; unused rows
+// zero): two tensor-core products and the FP32 output layer, Y (128 x 4).
+cudaError_t launch_mlp_infer(const void* X, const void* W1b, const void* W2b, const float* P, float* Z1, void* H1b,
+                             float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s) {
+    cudaError_t e = launch_gemm_bf16(X, NI, W1b, NI, Z1, NH, 128, NH, NI, err, s);
+    if (e != cudaSuccess) return e;
+    k_bias_gelu<<<ew_grid(128LL * NH), 256, 0, s>>>(Z1, P + OFF_B1, 128, reinterpret_cast<__nv_bfloat16*>(H1b), nullptr,
+                                                     nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_gemm_bf16(H1b, NH, W2b, NH, Z2, NH, 128, NH, NH, err, s)) != cudaSuccess) return e;
+    k_bias_gelu<<<ew_grid(128LL * NH), 256, 0, s>>>(Z2, P + OFF_B2, 128, nullptr, nullptr, H2);
+    k_out_fwd<<<(128 * 32 + 255) / 256, 256, 0, s>>>(H2, P + OFF_W3, P + OFF_B3, 128, Y);
+    return cudaGetLastError();
+}
+int mlp_infer_kernels() { return 5; }
+
+// BF16 copies of W1 and W2 from the FP32 parameter vector P (device).
+cudaError_t mlp_prepare(const float* P, void* W1b, void* W2b, cudaStream_t s) {
+    cudaError_t e = gemm_bf16_configure();
+    if (e != cudaSuccess) return e;
+    k_to_bf16<<<ew_grid((long long)NH * NI), 256, 0, s>>>(P + OFF_W1, reinterpret_cast<__nv_bfloat16*>(W1b),
+                                                            (long long)NH * NI);
+    k_to_bf16<<<ew_grid((long long)NH * NH), 256, 0, s>>>(P + OFF_W2, reinterpret_cast<__nv_bfloat16*>(W2b),
+                                                            (long long)NH * NH);
+    return cudaGetLastError();
+}
+long long mlp_num_params() { return (long long)N_PARAMS; }
+
+}  // namespace aspd
+
 struct asp_mlp {
     int B = 0;                    // batch capacity (multiple of 128)
     cudaStream_t stream = nullptr;
@@ -451,7 +485,6 @@ cudaError_t malloc_m(asp_mlp* m, T** p, size_t count) {
     return cudaSuccess;
 }
 
-int ew_grid(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
 
 // forward (and backward) of the batch already gathered into m->Xb/XbT/Tb
 asp_status mlp_pass(asp_mlp* m, int bn, bool backward) {

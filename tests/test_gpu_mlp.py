@@ -132,3 +132,114 @@ def test_training_reduces_loss(asp):
         last = net.step(rng.integers(0, 4096, 256), lr=1e-3, update=True)
     assert last < first / 10, (first, last)
     net.close()
+
+
+# ----------------------------------------------------------------- learned initial values in the minor cycle
+
+def _const_net(b3):
+    return {"W1": np.zeros((256, 1024)), "b1": np.zeros(256), "W2": np.zeros((256, 256)), "b2": np.zeros(256),
+            "W3": np.zeros((4, 256)), "b3": np.asarray(b3, dtype=np.float64)}
+
+
+def _ctx(asp, case, **kw):
+    kw.setdefault("noise_sigma", case.noise_sigma)
+    kw.setdefault("k_max", 3)
+    return asp.Context(case.dirty, case.psf, **kw)
+
+
+@pytest.mark.parametrize("b3,used", [([1.0, 0.0, 0.0, 0.0], True), ([1.0, 0.0, 1e6, 0.0], False)])
+def test_learned_degenerate_networks_equal_plain(asp, b3, used):
+    """A network proposing exactly the simple method's start, or a start
+    outside the window (not used), leaves every fit -- and so the residual
+    -- bit for bit as without it."""
+    import synth
+    case = synth.small_case(64, 72, seed=4)
+    plain = _ctx(asp, case, init_mode=1)
+    learn = _ctx(asp, case, init_mode=1)
+    learn.set_mlp(_const_net(b3))
+    a = plain.minor_cycle(6)
+    b = learn.minor_cycle(6)
+    np.testing.assert_array_equal(plain.residual(), learn.residual())
+    np.testing.assert_array_equal(plain.components(), learn.components())
+    assert b["learned_fits"] == (6 if used else 0)
+    assert b["learned_refits"] == 0
+    assert a["iterations"] == b["iterations"] == 6
+    plain.close()
+    learn.close()
+
+
+def test_learned_steps_match_oracle(asp):
+    """Teacher-forced learned steps with a seeded random network and one that
+    proposes bad starts: the GPU uses the proposal exactly when the oracle
+    does, takes the fallback refit when the oracle does (margins above the
+    FP32 floor), and where the kept fit converged its chi^2 is the oracle's
+    within 1e-5."""
+    import synth
+    import oracle as O
+    from oracle import mlp_oracle as Mo
+    case = synth.small_case(80, 88, seed=6, n_points=3, n_gauss=1)
+    # a seeded random network with LM run to the optimum, and a network
+    # proposing bad starts with the default LM settings and the simple
+    # initial values, where the fallback must act
+    runs = [(synth.mlp_init(11), True), (_const_net([-3.0, np.log(5.0), 6.0, -6.0]), False)]
+    checked = refits = 0
+    for net, tight in runs:
+        w32 = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in net.items()}
+        W = Mo.MLPWeights(*(w32[n] for n in ("W1", "b1", "W2", "b2", "W3", "b3")))
+        kw = dict(lm_max_iter=300, lm_rtol=1e-12, lm_xtol=1e-10) if tight else dict(init_mode=1)
+        ctx = _ctx(asp, case, **kw)
+        ctx.set_mlp(w32)
+        ab, wb, _, _ = ctx.beam
+        p = O.AspParams(k_max=3, noise_sigma=case.noise_sigma, lm=O.lm_exact() if tight else O.LMParams(),
+                        init_mode="auto" if tight else "simple")
+        prev = ctx.stats()
+        for it in range(6):
+            st = ctx.state()
+            mc = O.MinorCycle(case.dirty, case.psf, p, beam=(ab, wb), mlp=W)
+            comps = [O.Component(q[0], q[1], q[2], q[3], q[4], bool(q[5])) for q in st["comps"]]
+            mc.set_state(ctx.residual().astype(np.float64), comps, st["retained"], st["t"], st["last_wi"],
+                         st["last_w0"])
+            rec = mc.step()
+            if rec is None:
+                break
+            now = ctx.minor_cycle(1)
+            used = now["learned_fits"] - prev["learned_fits"]
+            refit = now["learned_refits"] - prev["learned_refits"]
+            prev = now
+            assert used == int(rec["learned"]["used"])
+            if rec["learned"]["used"]:
+                assert refit == int(rec["learned"]["refit"]), it
+                refits += refit
+                fit = rec["fit"]
+                if tight and fit.status == O.LM_CONVERGED:
+                    h = ctx.history()[-1]
+                    if h["status"] != O.LM_CAP:
+                        assert h["chi2_final"] <= fit.chi2 * (1 + 1e-5) + 1e-12
+                        checked += 1
+        ctx.close()
+    assert checked >= 4 and refits >= 1
+
+
+def test_harvest_records(asp):
+    """Each harvested record is the 32 x 32 patch at the plain peak of the
+    residual before that iteration (divided by |R(p*)|) and the target made
+    from the converged new member of its fit."""
+    import torch
+    import synth
+    from oracle import mlp_oracle as Mo
+    case = synth.small_case(72, 64, seed=8, n_points=3, n_gauss=1)
+    ctx = _ctx(asp, case)
+    P = torch.zeros((5, 1024), dtype=torch.float32, device="cuda")
+    T = torch.zeros((5, 8), dtype=torch.float32, device="cuda")
+    ctx.set_harvest(P, T)
+    _, wb, _, _ = ctx.beam
+    for t in range(5):
+        R0 = ctx.residual().astype(np.float64)
+        ctx.minor_cycle(1)
+        th, _ = ctx.last_fit()
+        rec = T[t].cpu().numpy().astype(np.float64)
+        px, py = int(rec[5]), int(rec[6])
+        assert rec[4] == np.float32(R0[py, px])
+        np.testing.assert_allclose(P[t].cpu().numpy(), Mo.extract_patch(R0, px, py), rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(rec[:4], Mo.fit_target(th[0], R0[py, px], px, py, wb), rtol=1e-5, atol=1e-6)
+    ctx.close()

@@ -122,3 +122,55 @@ def test_target_and_init_are_inverse():
     t = M.fit_target(theta, 0.5, 100, 56, 2.0)
     np.testing.assert_allclose(t, [0.74, math.log(1.6), 1.25, -0.5])
     np.testing.assert_allclose(M.init_from_output(t, 0.5, 100, 56, 2.0), theta)
+
+
+# ---------------------------------------------------------------- the learned step of the minor cycle
+
+def _const_net(b3):
+    """A network whose output is the constant b3 (zero weights)."""
+    return M.MLPWeights(np.zeros((256, 1024)), np.zeros(256), np.zeros((256, 256)), np.zeros(256),
+                        np.zeros((4, 256)), np.asarray(b3, dtype=np.float64))
+
+
+def _run(case, mlp, n=5, mode="simple"):
+    import oracle as O
+    mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=3, noise_sigma=case.noise_sigma, init_mode=mode),
+                      mlp=mlp)
+    recs = [mc.step() for _ in range(n)]
+    return mc, recs
+
+
+def test_learned_step_reproducing_the_plain_start_changes_nothing():
+    """A network that proposes exactly the simple method's start (a0 = R(p*),
+    omega0 = omega_b, the peak pixel) gives the plain run, fit for fit."""
+    import synth
+    case = synth.small_case(64, 72, seed=4)
+    plain, rp = _run(case, None)
+    learn, rl = _run(case, _const_net([1.0, 0.0, 0.0, 0.0]))
+    for a, b in zip(rp, rl):
+        assert b["learned"]["used"] and b["learned"]["kept"]
+        np.testing.assert_allclose(a["fit"].theta, b["fit"].theta, rtol=0, atol=0)
+    np.testing.assert_array_equal(plain.R, learn.R)
+
+
+def test_learned_proposal_outside_the_window_is_not_used():
+    import synth
+    case = synth.small_case(64, 72, seed=4)
+    _, rp = _run(case, None)
+    _, rl = _run(case, _const_net([1.0, 0.0, 1e6, 0.0]))
+    for a, b in zip(rp, rl):
+        assert not b["learned"]["used"]
+        np.testing.assert_array_equal(a["fit"].theta, b["fit"].theta)
+
+
+def test_learned_fallback_keeps_the_better_fit():
+    """A start far from the source (wrong sign, 6 px off, 5x too wide) ends in
+    a worse minimum or at the cap: the plain start is refitted and the lower
+    chi^2 kept, so the result is never worse than the plain fit."""
+    import synth
+    case = synth.small_case(64, 72, seed=4)
+    _, rp = _run(case, None, n=3)
+    _, rl = _run(case, _const_net([-3.0, np.log(5.0), 6.0, -6.0]), n=3)
+    assert any(b["learned"]["refit"] for b in rl)
+    for a, b in zip(rp, rl):
+        assert b["fit"].chi2 <= a["fit"].chi2 * (1 + 1e-9)
