@@ -406,9 +406,9 @@ asp_status asp_mlp_get_params(asp_mlp* m, float* params_host);
  *      tensor-core products -- and LM starts the new member there (kept
  *      plain if the proposal is outside the window, not finite or below the
  *      width bound);
- *   3. fallback: if that fit hits the LM cap, ends non-finite or at the width
- *      bound, or ends with a chi^2 above chi^2 at the plain start point, LM
- *      is run again from the plain start and the better chi^2 is kept.
+ *   3. fallback: if that fit ends non-finite or at the width bound, or ends
+ *      with a chi^2 above chi^2 at the plain start point, LM is run again
+ *      from the plain start and the better chi^2 is kept.
  * Both fits use the same window and members, so their chi^2 compare. */
 asp_status asp_set_mlp(asp_ctx* ctx, const float* params_host, int enable);
 /* Training-data harvest: while set, iteration t of the minor cycle writes

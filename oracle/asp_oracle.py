@@ -741,9 +741,11 @@ class MinorCycle:
         new member's start from the 32 x 32 patch at p* (BF16 operands as on
         the GPU).  A proposal that is not finite, has a zero amplitude, or
         lies outside the window or the width bounds is not used.  Otherwise
-        LM runs from it; if that fit hits the cap, ends non-finite or at the
-        width bound, or ends above chi^2 at the plain start, LM runs again
-        from the plain start and the lower chi^2 is kept."""
+        LM runs from it; if that fit ends non-finite or at the width bound,
+        or ends above chi^2 at the plain start (a fit from the plain start
+        could only end lower), LM runs again from the plain start and the
+        lower chi^2 is kept.  Hitting the LM cap alone is no reason: plain
+        fits of joint active sets hit it as often."""
         from . import mlp_oracle as Mo
         omega_min = 0.25 * self.omega_b
         px, py = int(init["x0"]), int(init["y0"])
@@ -762,8 +764,7 @@ class MinorCycle:
         th_l = theta0.copy()
         th_l[0:4] = prop
         fit_l = lm_fit(T, xs, ys, th_l, win, omega_min, self.p.lm)
-        bad = (fit_l.status == LM_CAP or not np.isfinite(fit_l.chi2) or not fit_l.theta[3] > omega_min
-               or fit_l.chi2 > chi2_plain)
+        bad = not np.isfinite(fit_l.chi2) or not fit_l.theta[3] > omega_min or fit_l.chi2 > chi2_plain
         if not bad:
             info["kept"] = True
             return fit_l, info

@@ -569,8 +569,10 @@ __device__ __forceinline__ void learned_check_body(CycleState* st) {
         return;
     }
     const FitOut& fo = st->fout;
-    const bool bad = fo.status == ASP_LM_CAP || !isfinite(fo.chi2) || !(fo.theta[3] > st->fit.omega_min) ||
-                     fo.chi2 > st->fout2.chi2_init;
+    // a learned fit is redone from the plain start when it ended non-finite,
+    // at the width bound, or above chi^2 at the plain start (hitting the LM
+    // cap alone is no reason: plain joint fits hit it as often)
+    const bool bad = !isfinite(fo.chi2) || !(fo.theta[3] > st->fit.omega_min) || fo.chi2 > st->fout2.chi2_init;
     if (!bad) {
         if (threadIdx.x == 0) { st->learned_kept += 1; st->fit2.active = 0; st->need_plain = 0; }
         return;
