@@ -346,6 +346,10 @@ asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stat
  * reset for each candidate window tile (pixels per CTA) and CTA-group
  * policy, keeps the fastest, and resets the batch.  out (host) may be NULL. */
 asp_status asp_batch_autotune(asp_batch* b, int n_trial_iter, asp_batch_tuning* out);
+/* Learned initial values for every image of the batch (as asp_set_mlp
+ * for a context; one tensor-core inference per iteration covers all
+ * images). */
+asp_status asp_batch_set_mlp(asp_batch* b, const float* params_host, int enable);
 /* Borrow image i's context for queries (residual, components, history,
  * stats, state); owned by the batch -- do not destroy it. */
 asp_status asp_batch_image(asp_batch* b, int i, asp_ctx** ctx);

@@ -514,6 +514,14 @@ class Batch:
     def launches(self) -> int:
         return asp_batch_launch_count(self.h)
 
+    def set_mlp(self, weights: Optional[dict], enable: bool = True):
+        """Learned initial values for every image (see Context.set_mlp)."""
+        if weights is None or not enable:
+            _check(lib().asp_batch_set_mlp(self.h, None, 0), "asp_batch_set_mlp")
+            return
+        v = np.ascontiguousarray(mlp_pack(weights), dtype=np.float32)
+        _check(lib().asp_batch_set_mlp(self.h, v.ctypes.data, 1), "asp_batch_set_mlp")
+
 
 # ----------------------------------------------------------------- learned initial values
 

@@ -128,6 +128,7 @@ SIGNATURES = {
     "asp_batch_autotune": [_P, _I, C.POINTER(asp_batch_tuning)],
     "asp_batch_image": [_P, _I, C.POINTER(_P)],
     "asp_batch_launch_count": [_P, C.POINTER(C.c_int64)],
+    "asp_batch_set_mlp": [_P, _P, _I],
     "asp_mlp_gemm": [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P],
     "asp_mlp_num_params": [C.POINTER(C.c_longlong)],
     "asp_mlp_create": [_P, _I, _P, C.POINTER(_P)],

@@ -1199,11 +1199,19 @@ struct asp_batch {
     int graph_unroll = 8, graph_state = 0;
     long long launches = 0;
     int broken = 0;
+    // learned initial values for the whole batch: one network input row per image
+    int learned = 0, mlp_rows = 0;
+    float* mlpP = nullptr;
+    void *W1b = nullptr, *W2b = nullptr, *Xinf = nullptr, *H1b = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *Yinf = nullptr;
+    unsigned* mlp_err = nullptr;
+    std::vector<void*> mlp_allocs;
 };
 
 namespace {
 
 const int BATCH_KERNELS_PER_ITER = 9;
+const int BATCH_LEARNED_KERNELS = 11;   // prep, chi^2 fit, 5 inference kernels, apply, check, refit, pick
 
 asp_status batch_fail(asp_batch* b, asp_status s) {
     if (b && (s == ASP_ERR_CUDA || s == ASP_ERR_TIMEOUT)) b->broken = 1;
@@ -1260,7 +1268,19 @@ asp_status batch_enqueue_iteration(asp_batch* b, cudaStream_t s) {
     BK(launch_smooth_h_b(b->d_desc, n, b->grid_x, b->smem_smooth_h, s));
     BK(launch_smooth_v_b(b->d_desc, n, b->grid_x, b->smem_smooth_v, s));
     BK(launch_select_b(b->d_desc, n, s));
+    if (b->learned) {
+        BK(launch_learned_b(b->d_desc, n, 0, s));
+        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s, 1, 0));   // chi^2 at the plain start
+        BK(launch_mlp_infer(b->Xinf, b->W1b, b->W2b, b->mlpP, b->Z1, b->H1b, b->Z2, b->H2, b->Yinf, b->mlp_err, s,
+                            b->mlp_rows));
+        BK(launch_learned_b(b->d_desc, n, 1, s));
+    }
     BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s));
+    if (b->learned) {
+        BK(launch_learned_b(b->d_desc, n, 2, s));
+        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s, 1, -1));  // fallback refit
+        BK(launch_learned_b(b->d_desc, n, 3, s));
+    }
     BK(launch_update_b(b->d_desc, n, s));
     BK(launch_build_weights_b(b->d_desc, n, s));
     BK(launch_sub_h_b(b->d_desc, n, b->grid_x, b->smem_sub_h, s));
@@ -1302,13 +1322,14 @@ asp_status batch_run(asp_batch* b, int n_iter) {
         if (b->graph_state == 1) {
             const int reps = (n_iter + b->graph_unroll - 1) / b->graph_unroll;
             for (int r = 0; r < reps; ++r) BK(cudaGraphLaunch(b->gexec, b->stream));
-            b->launches += (long long)reps * b->graph_unroll * BATCH_KERNELS_PER_ITER;
+            b->launches += (long long)reps * b->graph_unroll *
+                           (BATCH_KERNELS_PER_ITER + (b->learned ? BATCH_LEARNED_KERNELS : 0));
         } else {
             for (int i = 0; i < n_iter; ++i) {
                 s = batch_enqueue_iteration(b, b->stream);
                 if (s != ASP_OK) return s;
             }
-            b->launches += (long long)n_iter * BATCH_KERNELS_PER_ITER;
+            b->launches += (long long)n_iter * (BATCH_KERNELS_PER_ITER + (b->learned ? BATCH_LEARNED_KERNELS : 0));
         }
     }
     BK(cudaStreamSynchronize(b->stream));
@@ -1338,6 +1359,7 @@ asp_status asp_batch_destroy(asp_batch* b) {
     for (float* d : b->dirty) cudaFree(d);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->bars) cudaFree(b->bars);
+    for (void* q : b->mlp_allocs) cudaFree(q);
     delete b;
     return ASP_OK;
 }
@@ -1430,6 +1452,11 @@ asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stat
     cudaSetDevice(b->dev);
     asp_status s = batch_run(b, n_iter);
     if (s != ASP_OK) return s;
+    if (b->learned) {
+        unsigned me = 0;
+        BK(cudaMemcpy(&me, b->mlp_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (me) { b->broken = 1; return ASP_ERR_TIMEOUT; }
+    }
     asp_status first_err = ASP_OK;
     for (size_t i = 0; i < b->imgs.size(); ++i) {
         asp_ctx* c = b->imgs[i];
@@ -1515,6 +1542,45 @@ asp_status asp_batch_autotune(asp_batch* b, int n_trial_iter, asp_batch_tuning* 
         out->best_ms = best;
         out->default_ms = dflt;
     }
+    return ASP_OK;
+}
+
+asp_status asp_batch_set_mlp(asp_batch* b, const float* params_host, int enable) {
+    if (!b || (enable && !params_host)) return ASP_ERR_INVALID_ARG;
+    if (b->broken) return ASP_ERR_STATE;
+    cudaSetDevice(b->dev);
+    const int n = (int)b->imgs.size();
+    if (enable) {
+        if (!b->mlpP) {
+            b->mlp_rows = ((n + 127) / 128) * 128;
+            const size_t R = b->mlp_rows;
+            auto al = [&](void** p, size_t bytes) -> bool {
+                if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+                b->mlp_allocs.push_back(*p);
+                return true;
+            };
+            void *P = nullptr, *z1 = nullptr, *z2 = nullptr, *h2 = nullptr, *y = nullptr, *er = nullptr;
+            if (!al(&P, mlp_num_params() * sizeof(float)) || !al(&b->W1b, 256 * 1024 * 2) || !al(&b->W2b, 256 * 256 * 2) ||
+                !al(&b->Xinf, R * 1024 * 2) || !al(&b->H1b, R * 256 * 2) || !al(&z1, R * 256 * 4) ||
+                !al(&z2, R * 256 * 4) || !al(&h2, R * 256 * 4) || !al(&y, R * 4 * 4) || !al(&er, sizeof(unsigned)))
+                return ASP_ERR_OOM;
+            b->mlpP = (float*)P; b->Z1 = (float*)z1; b->Z2 = (float*)z2; b->H2 = (float*)h2; b->Yinf = (float*)y;
+            b->mlp_err = (unsigned*)er;
+            BK(cudaMemsetAsync(b->Xinf, 0, R * 1024 * 2, b->stream));
+            BK(cudaMemsetAsync(b->mlp_err, 0, sizeof(unsigned), b->stream));
+            for (int i = 0; i < n; ++i) {
+                BK(cudaMemsetAsync(&b->imgs[i]->st->fit2, 0, sizeof(FitDesc), b->stream));
+                b->h_desc[i].Xrow = static_cast<uint16_t*>(b->Xinf) + (size_t)i * 1024;
+                b->h_desc[i].Yrow = b->Yinf + (size_t)i * 4;
+            }
+        }
+        BK(cudaMemcpyAsync(b->mlpP, params_host, mlp_num_params() * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+        BK(mlp_prepare(b->mlpP, b->W1b, b->W2b, b->stream));
+    }
+    b->learned = enable ? 1 : 0;
+    asp_status s = batch_upload(b);
+    if (s != ASP_OK) return s;
+    BK(cudaStreamSynchronize(b->stream));
     return ASP_OK;
 }
 

@@ -644,6 +644,21 @@ __global__ void k_harvest(const CycleState* __restrict__ st, const float* __rest
     harvest_body(st, R, H, W, patches, targets, capacity, -1);
 }
 
+
+// Batched learned-initial-value steps (grid.y = image): 0 prep, 1 apply,
+// 2 check, 3 pick.
+__global__ void k_learned_b(const ImgDesc* __restrict__ imgs, int step) {
+    const ImgDesc& g = imgs[blockIdx.y];
+    if (step == 0) learned_prep_body(g.st, g.R, g.H, g.W, reinterpret_cast<__nv_bfloat16*>(g.Xrow));
+    else if (step == 1) learned_apply_body(g.st, g.Yrow);
+    else if (step == 2) learned_check_body(g.st);
+    else learned_pick_body(g.st);
+}
+cudaError_t launch_learned_b(const ImgDesc* imgs, int n, int step, cudaStream_t s) {
+    k_learned_b<<<dim3(1, n), 256, 0, s>>>(imgs, step);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_learned_prep(CycleState* st, const float* R, int H, int W, void* Xrow, cudaStream_t s) {
     k_learned_prep<<<1, 256, 0, s>>>(st, R, H, W, reinterpret_cast<__nv_bfloat16*>(Xrow));
     return cudaGetLastError();

@@ -950,13 +950,17 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
 // own barrier counter, partials and sums.
 template <int TPT>
 __global__ void __launch_bounds__(FIT_THREADS, 1)
-k_lm_fit_b(const ImgDesc* __restrict__ imgs, const __grid_constant__ BatchFitMap map) {
+k_lm_fit_b(const ImgDesc* __restrict__ imgs, const __grid_constant__ BatchFitMap map, int which, int max_iter_override) {
     int i = 0;
     while (i + 1 < map.n && (int)blockIdx.x >= map.start[i + 1]) ++i;
     if ((int)blockIdx.x >= map.start[map.n]) return;
     const ImgDesc& g = imgs[i];
-    lm_fit_body<TPT>(g.R, g.W, &g.st->fit, g.dp.lm, &g.st->fout, g.partials, g.sums, g.bar, g.Tg,
-                     (int)blockIdx.x - map.start[i]);
+    // which = 1: the second fit (learned initial values: chi^2 at the plain
+    // start, the fallback refit)
+    LMConst lmc = g.dp.lm;
+    if (max_iter_override >= 0) lmc.max_iter = max_iter_override;
+    lm_fit_body<TPT>(g.R, g.W, which ? &g.st->fit2 : &g.st->fit, lmc, which ? &g.st->fout2 : &g.st->fout, g.partials,
+                     g.sums, g.bar, g.Tg, (int)blockIdx.x - map.start[i]);
 }
 
 size_t fit_smem_bytes() {
@@ -985,7 +989,7 @@ cudaError_t fit_configure(int tpt, int* blocks_per_sm) {
 }
 
 cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMap& map, unsigned* bars, int n_bars,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int which, int max_iter_override) {
     cudaError_t e = cudaMemsetAsync(bars, 0, sizeof(unsigned) * (size_t)n_bars, s);
     if (e != cudaSuccess) return e;
     if (map.start[map.n] < 1) return cudaSuccess;
@@ -999,8 +1003,8 @@ cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMa
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1>, imgs, map);
-    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3>, imgs, map);
+    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1>, imgs, map, which, max_iter_override);
+    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3>, imgs, map, which, max_iter_override);
 }
 
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,

@@ -45,6 +45,8 @@ struct ImgDesc {
     Params dp;
     int g_share;        // CTAs of the batched fit given to this image
     int sub_blen;       // floats of one row-pass buffer of the subtraction
+    void* Xrow;         // learned initial values: this image's row of the shared network input (BF16)
+    const float* Yrow;  // and of the network output (4 floats)
 };
 
 constexpr int MAX_BATCH = 256;
@@ -60,7 +62,7 @@ size_t fit_smem_bytes();
 int fit_tpt_for(int k_max);
 cudaError_t fit_configure(int tpt, int* blocks_per_sm);
 cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMap& map, unsigned* bars, int n_bars,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int which = 0, int max_iter_override = -1);
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
                           FitOut* out, double* partials, double* sums, unsigned* bar, float* Tg, cudaStream_t s);
 
@@ -100,7 +102,8 @@ cudaError_t launch_sub_v_b(const ImgDesc* imgs, int n, int grid_x, cudaStream_t 
 cudaError_t launch_arm_b(const ImgDesc* imgs, int n, int n_iter, cudaStream_t s);
 // learned initial values (asp_mlp.cu, asp_cycle.cu)
 cudaError_t launch_mlp_infer(const void* X, const void* W1b, const void* W2b, const float* P, float* Z1, void* H1b,
-                             float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s);
+                             float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s, int rows = 128);
+cudaError_t launch_learned_b(const ImgDesc* imgs, int n, int step, cudaStream_t s);
 int mlp_infer_kernels();
 cudaError_t mlp_prepare(const float* P, void* W1b, void* W2b, cudaStream_t s);
 long long mlp_num_params();

@@ -428,15 +428,16 @@ namespace aspd {
 // In-cycle inference for up to 128 patches (rows of X, BF16; unused rows
 // zero): two tensor-core products and the FP32 output layer, Y (128 x 4).
 cudaError_t launch_mlp_infer(const void* X, const void* W1b, const void* W2b, const float* P, float* Z1, void* H1b,
-                             float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s) {
-    cudaError_t e = launch_gemm_bf16(X, NI, W1b, NI, Z1, NH, 128, NH, NI, err, s);
+                             float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s, int rows) {
+    if (rows < 128 || rows % 128) return cudaErrorInvalidValue;
+    cudaError_t e = launch_gemm_bf16(X, NI, W1b, NI, Z1, NH, rows, NH, NI, err, s);
     if (e != cudaSuccess) return e;
-    k_bias_gelu<<<ew_grid(128LL * NH), 256, 0, s>>>(Z1, P + OFF_B1, 128, reinterpret_cast<__nv_bfloat16*>(H1b), nullptr,
-                                                     nullptr);
+    k_bias_gelu<<<ew_grid((long long)rows * NH), 256, 0, s>>>(Z1, P + OFF_B1, rows,
+                                                              reinterpret_cast<__nv_bfloat16*>(H1b), nullptr, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_gemm_bf16(H1b, NH, W2b, NH, Z2, NH, 128, NH, NH, err, s)) != cudaSuccess) return e;
-    k_bias_gelu<<<ew_grid(128LL * NH), 256, 0, s>>>(Z2, P + OFF_B2, 128, nullptr, nullptr, H2);
-    k_out_fwd<<<(128 * 32 + 255) / 256, 256, 0, s>>>(H2, P + OFF_W3, P + OFF_B3, 128, Y);
+    if ((e = launch_gemm_bf16(H1b, NH, W2b, NH, Z2, NH, rows, NH, NH, err, s)) != cudaSuccess) return e;
+    k_bias_gelu<<<ew_grid((long long)rows * NH), 256, 0, s>>>(Z2, P + OFF_B2, rows, nullptr, nullptr, H2);
+    k_out_fwd<<<(rows * 32 + 255) / 256, 256, 0, s>>>(H2, P + OFF_W3, P + OFF_B3, rows, Y);
     return cudaGetLastError();
 }
 int mlp_infer_kernels() { return 5; }

@@ -152,3 +152,24 @@ def test_batch_invalid_arguments(asp):
         asp.Batch([c.dirty], [])
     with pytest.raises(ValueError):
         asp.Batch([c.dirty], [c.psf[:10, :10]])          # PSF must be 2H x 2W
+
+
+def test_batch_learned_equals_single_contexts(asp):
+    """Learned initial values in a batch (one network pass for all images
+    per iteration) give every image exactly what its own context with the
+    same network computes."""
+    cases = _cases([41, 42, 43], sizes=(64, 96, 128))
+    w = {k: np.asarray(v, dtype=np.float32) for k, v in synth.mlp_init(2).items()}
+    b = _batch(asp, cases)
+    b.set_mlp(w)
+    stats = b.minor_cycle(12)
+    assert all(s["learned_fits"] > 0 for s in stats)
+    for i, c in enumerate(cases):
+        ctx = asp.Context(c.dirty, c.psf, noise_sigma=c.noise_sigma, k_max=c.k_max)
+        ctx.set_mlp(w)
+        st = ctx.minor_cycle(12)
+        for k in ("iterations", "learned_fits", "learned_refits", "learned_kept", "pixel_evals"):
+            assert stats[i][k] == st[k], k
+        np.testing.assert_array_equal(b.image(i).residual(), ctx.residual())
+        ctx.close()
+    b.close()
