@@ -48,6 +48,10 @@ def _args():
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batch comparison")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-value comparison")
+    ap.add_argument("--batch-images", type=int, default=64)
+    ap.add_argument("--learned-train-images", type=int, default=120, help="config-1 images harvested for training")
     return ap.parse_args()
 
 
@@ -256,6 +260,95 @@ def run_reference(a):
     return 0
 
 
+# ---------------------------------------------------------------- batched and learned comparisons
+
+def batched_comparison(asp, n_images: int, seed0: int = 0, weights=None) -> dict:
+    """The 64-image workload: config-1-style images of sizes drawn from
+    {256, 512, 1024, 2048}^2, each with its own PSF and seed, 200 iterations.
+    The batch (autotuned window tile, one launch per kernel, all fits in one
+    cooperative launch) against the same images' own contexts run one after
+    another; both from the dirty images, device-synchronised wall time.
+    With trained weights the batch also runs with learned initial values
+    (batched + learned against the same sequential plain runs)."""
+    import numpy as np
+    import synth
+    cases = [synth.config4(seed0 + i) for i in range(n_images)]
+    n_iter = cases[0].n_iter
+    b = asp.Batch([c.dirty for c in cases], [c.psf for c in cases], noise_sigma=cases[0].noise_sigma,
+                  k_max=cases[0].k_max)
+    tune = b.autotune(8)
+    # sequential: each image's own context (graph captured before the clock)
+    b.reset()
+    views = [b.image(i) for i in range(n_images)]
+    for v in views:
+        v.minor_cycle(0)
+    t0 = time.perf_counter()
+    seq = [v.minor_cycle(n_iter) for v in views]
+    t_seq = time.perf_counter() - t0
+    seq_rms = [float(np.sqrt(np.mean(v.residual().astype(np.float64) ** 2))) for v in views]
+    b.reset()
+    b.minor_cycle(0)
+    l0 = b.launches()
+    t0 = time.perf_counter()
+    bat = b.minor_cycle(n_iter)
+    t_bat = time.perf_counter() - t0
+    launches = b.launches() - l0
+    bat_rms = [float(np.sqrt(np.mean(b.image(i).residual().astype(np.float64) ** 2))) for i in range(n_images)]
+    it_seq = sum(s["iterations"] for s in seq)
+    it_bat = sum(s["iterations"] for s in bat)
+    out = {"workload": f"config4: {n_images} images, sizes {{256,512,1024,2048}}^2, PSF sigma U[1.2,3], "
+                       f"k_max {cases[0].k_max}, {n_iter} iterations each",
+           "sizes": [int(c.H) for c in cases],
+           "iterations_per_s": it_bat / t_bat, "sequential_iterations_per_s": it_seq / t_seq,
+           "speedup": (it_bat / t_bat) / (it_seq / t_seq),
+           "pixel_evals_per_s": sum(s["pixel_evals"] for s in bat) / t_bat,
+           "sequential_pixel_evals_per_s": sum(s["pixel_evals"] for s in seq) / t_seq,
+           "max_rms_ratio_batch_vs_sequential": max(x / y for x, y in zip(bat_rms, seq_rms)),
+           "gpu_launches": launches, "autotune": tune}
+    if weights is not None:
+        b.set_mlp(weights)
+        b.reset()
+        b.minor_cycle(0)
+        t0 = time.perf_counter()
+        lrn = b.minor_cycle(n_iter)
+        t_l = time.perf_counter() - t0
+        l_rms = [float(np.sqrt(np.mean(b.image(i).residual().astype(np.float64) ** 2))) for i in range(n_images)]
+        it_l = sum(x["iterations"] for x in lrn)
+        out["learned"] = {"iterations_per_s": it_l / t_l, "speedup_vs_sequential_plain": (it_l / t_l) / (it_seq / t_seq),
+                          "pixel_evals_per_s": sum(x["pixel_evals"] for x in lrn) / t_l,
+                          "mean_rms_ratio_vs_plain": float(np.mean([x / y for x, y in zip(l_rms, seq_rms)])),
+                          "lm_iters_per_fit": sum(x["lm_iters"] for x in lrn) / max(it_l, 1),
+                          "plain_lm_iters_per_fit": sum(x["lm_iters"] for x in seq) / max(it_seq, 1),
+                          "learned_fits": sum(x["learned_fits"] for x in lrn),
+                          "learned_refits": sum(x["learned_refits"] for x in lrn)}
+    b.close()
+    return out
+
+
+def learned_comparison(asp, n_train_images: int, seed: int = 0):
+    """Learned initial values: harvest (patch, converged fit) pairs from
+    GPU runs of config-1 and config-2-style images (seeds >= 10000), train
+    the network on the GPU, then the equal-RMS protocol on the 1024x1024
+    workload (plain for 2000 iterations gives RMS_p; learned until RMS <=
+    1.01 RMS_p or 2000 iterations)."""
+    from paper_1606_07872_gb300 import learned as L
+    import synth
+    t0 = time.perf_counter()
+    X, T = L.harvest(L.default_training_cases(n_train_images, 2))
+    t_h = time.perf_counter() - t0
+    w = L.train(X, T, L.weight_init(seed), epochs=200, batch=1024, lr=1e-3)
+    t_t = time.perf_counter() - t0 - t_h
+    res = L.compare_equal_rms(synth.config2(0), w)
+    p, q = res["plain"], res["learned"]
+    return {"training_pairs": int(X.shape[0]), "harvest_s": t_h, "train_s": t_t,
+            "plain": {k: p[k] for k in ("iterations", "seconds", "rms", "lm_iters_per_fit", "pixel_evals")},
+            "learned": {k: q[k] for k in ("iterations", "seconds", "rms", "lm_iters_per_fit", "pixel_evals",
+                                          "learned_fits", "learned_refits", "learned_kept")},
+            "reached_equal_rms": bool(res["reached"]),
+            "time_to_rms_ratio_plain_over_learned": res["time_ratio"],
+            "lm_iters_per_fit_ratio_plain_over_learned": res["lm_iters_ratio"]}, w
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(a):
@@ -403,6 +496,17 @@ def run_ours(a):
             "fit_tflops": fit_flops / (t_ms / 1e3) / 1e12,
             "e2e": e2e, "gpu_launches": n_launch, "roofline": roof, "kernels": kernels,
             "clocks": clk.summary()}
+    weights = None
+    if rank == 0 and not a.no_learned:
+        try:
+            line["learned"], weights = learned_comparison(asp, a.learned_train_images)
+        except Exception as e:   # report, never hide, a failed comparison
+            line["learned"] = {"error": repr(e)[:300]}
+    if rank == 0 and not a.no_batched:
+        try:
+            line["batched"] = batched_comparison(asp, a.batch_images, seed0=1000 * rank, weights=weights)
+        except Exception as e:
+            line["batched"] = {"error": repr(e)[:300]}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(a.size, a.cpu_budget)

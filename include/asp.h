@@ -307,7 +307,9 @@ asp_status asp_load_state(asp_ctx* ctx, const char* path);
  * the whole batch is one
  * launch per kernel of the iteration with the images on grid.y, and the LM
  * fits (Eq. 6) of all images run in ONE cooperative launch in which image i
- * owns a fixed group of CTAs with its own grid barrier.  asp_batch_minor_cycle
+ * owns a group of CTAs (sized on the device each iteration from its fit
+ * window and the policy the autotuner chose) with its own grid barrier.
+ * asp_batch_minor_cycle
  * captures eight batch iterations into a CUDA graph and replays it.
  *
  * Every image's result is exactly what a context of its own would compute
@@ -316,7 +318,7 @@ typedef struct asp_batch asp_batch;
 
 typedef struct {
     int px_per_cta;        /* chosen LM window tile: target pixels per CTA (0: automatic rule) */
-    int share_policy;      /* 0: equal CTA groups, 1: groups proportional to image area */
+    int share_policy;      /* 0: equal CTA groups, 1: proportional to image area, 2: on demand each iteration */
     int n_candidates;      /* candidates timed */
     double best_ms;        /* time of the chosen candidate over the trial iterations */
     double default_ms;     /* time of the untuned setting (px_per_cta 0, equal groups) */

@@ -83,7 +83,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if err.strip():
                 print(f"--- {os.path.basename(obj)}\n{err}", file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static",
+           "-Xlinker", "--no-undefined"]   # a missing definition fails here, not at load time
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

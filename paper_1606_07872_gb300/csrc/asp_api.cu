@@ -1191,7 +1191,7 @@ struct asp_batch {
     std::vector<ImgDesc> h_desc;
     ImgDesc* d_desc = nullptr;
     unsigned* bars = nullptr;
-    BatchFitMap map{};
+    int* dmap = nullptr;                 // CTA ranges of the batched fit (device, n + 1)
     int tpt = 1, grid_x = 1;
     int px_per_cta = 0, share_policy = 0;
     size_t smem_smooth_h = 0, smem_smooth_v = 0, smem_sub_h = 0;
@@ -1210,7 +1210,7 @@ struct asp_batch {
 
 namespace {
 
-const int BATCH_KERNELS_PER_ITER = 9;
+const int BATCH_KERNELS_PER_ITER = 10;   // the 9 of an iteration plus the CTA map of the fit
 const int BATCH_LEARNED_KERNELS = 11;   // prep, chi^2 fit, 5 inference kernels, apply, check, refit, pick
 
 asp_status batch_fail(asp_batch* b, asp_status s) {
@@ -1225,31 +1225,23 @@ asp_status batch_fail(asp_batch* b, asp_status s) {
             return batch_fail(b, e_ == cudaErrorMemoryAllocation ? ASP_ERR_OOM : ASP_ERR_CUDA);    \
     } while (0)
 
-// CTA groups of the batched fit: equal shares, or shares proportional to the
-// image areas; every image gets at least one CTA and the total is g_total.
+// Caps on each image's CTA group for the batched fit: 0 equal shares, 1
+// shares proportional to the image areas (each at least one CTA, summing to
+// at most g_total), 2 on demand (every image may ask for all g_total CTAs;
+// k_fit_map_b scales the requests of each iteration down to g_total).
 void batch_shares(asp_batch* b) {
     const int n = (int)b->imgs.size();
     std::vector<int> share(n, 1);
-    int left = b->g_total - n;
     if (b->share_policy == 0) {
-        for (int i = 0; i < n && left > 0; ++i) {
-            const int extra = (b->g_total - n) / n;
-            share[i] += extra;
-        }
-    } else {
+        for (int i = 0; i < n; ++i) share[i] += (b->g_total - n) / n;
+    } else if (b->share_policy == 1) {
         double tot = 0;
         for (asp_ctx* c : b->imgs) tot += (double)c->N;
-        int used = 0;
-        for (int i = 0; i < n; ++i) {
-            const int extra = (int)std::floor((double)(b->g_total - n) * b->imgs[i]->N / tot);
-            share[i] += extra;
-            used += extra;
-        }
-        (void)used;
+        for (int i = 0; i < n; ++i)
+            share[i] += (int)std::floor((double)(b->g_total - n) * b->imgs[i]->N / tot);
+    } else {
+        for (int i = 0; i < n; ++i) share[i] = b->g_total;
     }
-    b->map.n = n;
-    b->map.start[0] = 0;
-    for (int i = 0; i < n; ++i) b->map.start[i + 1] = b->map.start[i] + share[i];
     for (int i = 0; i < n; ++i) b->h_desc[i].g_share = share[i];
 }
 
@@ -1268,17 +1260,18 @@ asp_status batch_enqueue_iteration(asp_batch* b, cudaStream_t s) {
     BK(launch_smooth_h_b(b->d_desc, n, b->grid_x, b->smem_smooth_h, s));
     BK(launch_smooth_v_b(b->d_desc, n, b->grid_x, b->smem_smooth_v, s));
     BK(launch_select_b(b->d_desc, n, s));
+    BK(launch_fit_map_b(b->d_desc, n, b->g_total, b->dmap, s));
     if (b->learned) {
         BK(launch_learned_b(b->d_desc, n, 0, s));
-        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s, 1, 0));   // chi^2 at the plain start
+        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s, 1, 0));   // chi^2 at the plain start
         BK(launch_mlp_infer(b->Xinf, b->W1b, b->W2b, b->mlpP, b->Z1, b->H1b, b->Z2, b->H2, b->Yinf, b->mlp_err, s,
                             b->mlp_rows));
         BK(launch_learned_b(b->d_desc, n, 1, s));
     }
-    BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s));
+    BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s));
     if (b->learned) {
         BK(launch_learned_b(b->d_desc, n, 2, s));
-        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->map, b->bars, n, s, 1, -1));  // fallback refit
+        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s, 1, -1));  // fallback refit
         BK(launch_learned_b(b->d_desc, n, 3, s));
     }
     BK(launch_update_b(b->d_desc, n, s));
@@ -1359,6 +1352,7 @@ asp_status asp_batch_destroy(asp_batch* b) {
     for (float* d : b->dirty) cudaFree(d);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->bars) cudaFree(b->bars);
+    if (b->dmap) cudaFree(b->dmap);
     for (void* q : b->mlp_allocs) cudaFree(q);
     delete b;
     return ASP_OK;
@@ -1398,6 +1392,7 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
     b->g_total = b->num_sms * bps;
     if (n > b->g_total) return bail(ASP_ERR_UNSUPPORTED);
     if (cudaMalloc(&b->bars, sizeof(unsigned) * n) != cudaSuccess ||
+        cudaMalloc(&b->dmap, sizeof(int) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_desc, sizeof(ImgDesc) * n) != cudaSuccess)
         return bail(ASP_ERR_OOM);
     long long n_max = 0;
@@ -1507,7 +1502,7 @@ asp_status asp_batch_autotune(asp_batch* b, int n_trial_iter, asp_batch_tuning* 
     double best = 1e300, dflt = 0.0;
     int best_px = 0, best_pol = 0, tried = 0;
     asp_status s = ASP_OK;
-    for (int pol = 0; pol < 2 && s == ASP_OK; ++pol)
+    for (int pol = 0; pol < 3 && s == ASP_OK; ++pol)
         for (int k = 0; k < n_px && s == ASP_OK; ++k) {
             b->share_policy = pol;
             b->px_per_cta = cand_px[k];

@@ -454,6 +454,55 @@ __global__ void k_arm_b(const ImgDesc* __restrict__ imgs, int n, int n_iter) {
     st->stop_reason = 0;
 }
 
+// CTA groups of the batched fit for this iteration: image i asks for its
+// fit's grid (capped by its g_share when select ran); if the requests exceed
+// g_total they are scaled down proportionally (at least one CTA each).  The
+// granted grid is written back into the image's fit descriptor (and whether
+// the window still fits the group's shared memory), the CTA ranges to dmap.
+__global__ void k_fit_map_b(const ImgDesc* __restrict__ imgs, int n, int g_total, int* __restrict__ dmap) {
+    __shared__ int req[MAX_BATCH];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const FitDesc& f = imgs[i].st->fit;
+        req[i] = f.active ? max(f.grid, 1) : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += req[i];
+    if (total > g_total) {
+        long long sum = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!req[i]) continue;
+            const int sh = (int)((long long)req[i] * g_total / total);
+            req[i] = sh > 1 ? sh : 1;
+            sum += req[i];
+        }
+        while (sum > g_total) {                 // trim the largest groups (n <= g_total: this ends)
+            int j = 0;
+            for (int i = 1; i < n; ++i) if (req[i] > req[j]) j = i;
+            if (req[j] <= 1) break;
+            req[j] -= 1;
+            sum -= 1;
+        }
+    }
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        dmap[i] = acc;
+        if (req[i]) {
+            FitDesc& f = imgs[i].st->fit;
+            const long long Wn = (long long)f.ww * f.wh;
+            f.grid = req[i];
+            f.smem_ok = ((Wn + req[i] - 1) / req[i]) <= PX_SMEM;
+        }
+        acc += req[i];
+    }
+    dmap[n] = acc;
+}
+cudaError_t launch_fit_map_b(const ImgDesc* imgs, int n, int g_total, int* dmap, cudaStream_t s) {
+    k_fit_map_b<<<1, 256, 0, s>>>(imgs, n, g_total, dmap);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cycle_begin_b(const ImgDesc* imgs, int n, cudaStream_t s) {
     k_cycle_begin_b<<<dim3(1, n), 32, 0, s>>>(imgs);
     return cudaGetLastError();

@@ -945,24 +945,28 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
     lm_fit_body<TPT>(src, src_w, descp, lmc, out, partials, sums, bar, Tg, blockIdx.x);
 }
 
-// Batched: the fits of many images in one cooperative launch.  Image i owns
-// CTAs [map.start[i], map.start[i+1]); each group runs its own fit with its
-// own barrier counter, partials and sums.
+// Batched: the fits of many images in one cooperative launch of g_total
+// CTAs.  Image i owns CTAs [dmap[i], dmap[i+1]) (written on the device each
+// iteration by k_fit_map_b); each group runs its own fit with its own
+// barrier counter, partials and sums; CTAs beyond dmap[n] return.
 template <int TPT>
 __global__ void __launch_bounds__(FIT_THREADS, 1)
-k_lm_fit_b(const ImgDesc* __restrict__ imgs, const __grid_constant__ BatchFitMap map, int which, int max_iter_override) {
-    int i = 0;
-    while (i + 1 < map.n && (int)blockIdx.x >= map.start[i + 1]) ++i;
-    if ((int)blockIdx.x >= map.start[map.n]) return;
-    const ImgDesc& g = imgs[i];
+k_lm_fit_b(const ImgDesc* __restrict__ imgs, const int* __restrict__ dmap, int n, int which, int max_iter_override) {
+    const int c = (int)blockIdx.x;
+    if (c >= dmap[n]) return;
+    int lo = 0, hi = n - 1;                 // image i with dmap[i] <= c < dmap[i+1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (dmap[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    const ImgDesc& g = imgs[lo];
     // which = 1: the second fit (learned initial values: chi^2 at the plain
     // start, the fallback refit)
     LMConst lmc = g.dp.lm;
     if (max_iter_override >= 0) lmc.max_iter = max_iter_override;
     lm_fit_body<TPT>(g.R, g.W, which ? &g.st->fit2 : &g.st->fit, lmc, which ? &g.st->fout2 : &g.st->fout, g.partials,
-                     g.sums, g.bar, g.Tg, (int)blockIdx.x - map.start[i]);
+                     g.sums, g.bar, g.Tg, c - dmap[lo]);
 }
-
 size_t fit_smem_bytes() {
     size_t jc = (size_t)JC_FLOATS * sizeof(float);
     size_t m = (size_t)M_DOUBLES * sizeof(double);
@@ -988,13 +992,12 @@ cudaError_t fit_configure(int tpt, int* blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, FIT_THREADS, fit_smem_bytes());
 }
 
-cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMap& map, unsigned* bars, int n_bars,
+cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap, int n, int g_total, unsigned* bars,
                                   cudaStream_t s, int which, int max_iter_override) {
-    cudaError_t e = cudaMemsetAsync(bars, 0, sizeof(unsigned) * (size_t)n_bars, s);
+    cudaError_t e = cudaMemsetAsync(bars, 0, sizeof(unsigned) * (size_t)n, s);
     if (e != cudaSuccess) return e;
-    if (map.start[map.n] < 1) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(map.start[map.n]);
+    cfg.gridDim = dim3(g_total);
     cfg.blockDim = dim3(FIT_THREADS);
     cfg.dynamicSmemBytes = fit_smem_bytes();
     cfg.stream = s;
@@ -1003,8 +1006,8 @@ cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMa
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1>, imgs, map, which, max_iter_override);
-    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3>, imgs, map, which, max_iter_override);
+    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1>, imgs, dmap, n, which, max_iter_override);
+    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3>, imgs, dmap, n, which, max_iter_override);
 }
 
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,

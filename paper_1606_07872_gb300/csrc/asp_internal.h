@@ -50,10 +50,6 @@ struct ImgDesc {
 };
 
 constexpr int MAX_BATCH = 256;
-struct BatchFitMap {    // CTA ranges of the batched fit: image i owns [start[i], start[i+1])
-    int n;
-    int start[MAX_BATCH + 1];
-};
 
 int sub_h_blen(int W, const SmoothTaps& geo);
 
@@ -61,7 +57,7 @@ int sub_h_blen(int W, const SmoothTaps& geo);
 size_t fit_smem_bytes();
 int fit_tpt_for(int k_max);
 cudaError_t fit_configure(int tpt, int* blocks_per_sm);
-cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const BatchFitMap& map, unsigned* bars, int n_bars,
+cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap, int n, int g_total, unsigned* bars,
                                   cudaStream_t s, int which = 0, int max_iter_override = -1);
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
                           FitOut* out, double* partials, double* sums, unsigned* bar, float* Tg, cudaStream_t s);
@@ -100,6 +96,7 @@ cudaError_t launch_build_weights_b(const ImgDesc* imgs, int n, cudaStream_t s);
 cudaError_t launch_sub_h_b(const ImgDesc* imgs, int n, int grid_x, size_t smem, cudaStream_t s);
 cudaError_t launch_sub_v_b(const ImgDesc* imgs, int n, int grid_x, cudaStream_t s);
 cudaError_t launch_arm_b(const ImgDesc* imgs, int n, int n_iter, cudaStream_t s);
+cudaError_t launch_fit_map_b(const ImgDesc* imgs, int n, int g_total, int* dmap, cudaStream_t s);
 // learned initial values (asp_mlp.cu, asp_cycle.cu)
 cudaError_t launch_mlp_infer(const void* X, const void* W1b, const void* W2b, const float* P, float* Z1, void* H1b,
                              float* Z2, float* H2, float* Y, unsigned* err, cudaStream_t s, int rows = 128);
