@@ -60,7 +60,7 @@ typedef enum {
 } asp_stop_reason;
 
 /* Largest active set one fit accepts (members fitted jointly). */
-#define ASP_KMAX 32
+#define ASP_KMAX 50
 
 /* A PSF-convolved Gaussian a exp(-((x-x0)^2+(y-y0)^2)/(2 w^2)): the fitted
  * function of Eq. 6, (alpha_ic, x_ic, y_ic, omega_ic). */
@@ -288,7 +288,7 @@ asp_status asp_launch_count(asp_ctx* ctx, int64_t* n);
  * and calls that overlap on the GPU (other threads or streams) race. */
 #define ASP_STATIC_KMAX 8
 #define ASP_STATIC_GRID_MAX 32
-#define ASP_STATIC_SCRATCH_BYTES 2444288
+#define ASP_STATIC_SCRATCH_BYTES 5774592
 asp_status asp_fit_static(const float* image_dev, int H, int W, const asp_gauss* init, int n, int n_old,
                           double omega_min, const asp_params* lm, asp_gauss* out, asp_fit_info* info,
                           void* stream);

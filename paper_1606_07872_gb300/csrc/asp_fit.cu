@@ -25,9 +25,18 @@ namespace aspd {
 namespace {
 
 constexpr int CH_SMALL = 256;   // chunk pixels when NAp <= 64
-constexpr int CH_LARGE = 128;   // chunk pixels otherwise
-constexpr int JC_FLOATS = 128 * NAP_MAX;   // >= 256 * 64
-constexpr int M_DOUBLES = PMAX * (PMAX + 1) / 2;
+constexpr int CH_LARGE = 128;   // chunk pixels when NAp <= PMAX_S + 4
+constexpr int CH_XL = 64;       // chunk pixels of the large-active-set variant
+// Two shared-memory layouts.  Variant S (K <= KMAX_S) caches A of the
+// current point in shared memory; variant L (K <= KMAX) reads A from the
+// L2-resident sums buffer and gives the union region to the J chunk or the
+// FP32 factor with its panel.
+constexpr int KMAX_S = 32;
+constexpr int PMAX_S = 4 * KMAX_S;
+constexpr int JC_FLOATS = 128 * (PMAX_S + 4);                 // union region of S (>= 256 * 64)
+constexpr int M_DOUBLES = PMAX_S * (PMAX_S + 1) / 2;          // cached A of S
+constexpr int UNI_L_FLOATS = ((PMAX + 1) * (PMAX + 2) / 2 + 3) / 4 * 4 + 8 * (PMAX + 4);
+static_assert(UNI_L_FLOATS >= CH_XL * NAP_MAX, "J chunk of the large variant must fit its union region");
 
 struct MemberFrame {
     float a, c, iw2, iw3, fx, fy;   // c = log2(e) / (2 w^2)
@@ -256,8 +265,9 @@ __device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ 
 // Every block is full (callers pad P with identity rows), so no load sits
 // behind a bounds test.  Returns false (uniformly) if a pivot is not
 // positive; *s_flag must be 0 on entry.
-constexpr int LP_LD = 132;
-constexpr int L32_LP_OFF = 8400;   // float offset of Lp behind the packed (P+1)-row matrix
+// Lp (PB columns of ld lp_ld >= P + 1) sits behind the packed (P+1)-row
+// factor, at a 4-float-aligned offset.
+__host__ __device__ constexpr int lp_offset(int P4) { return ((P4 + 1) * (P4 + 2) / 2 + 3) & ~3; }
 
 // Factor the PBxPB diagonal block at j0 (lower, packed in M) in registers,
 // every lane of the calling warp redundantly; lanes 0..PB-1 store row
@@ -302,7 +312,7 @@ __device__ __forceinline__ bool factor_diag(float* __restrict__ M, float* __rest
 
 template <int PB>
 __device__ bool chol_lowlat(float* __restrict__ M, float* __restrict__ Lp, int P, float* __restrict__ inv_diag,
-                            int* s_flag) {
+                            int* s_flag, const int LP_LD) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int nrows = P + 1;
     if (warp == 0 && !factor_diag<PB>(M, inv_diag, 0, lane) && lane == 0) *s_flag = 1;
@@ -459,6 +469,19 @@ __device__ void trsv_fwd_block(const float* __restrict__ M, int P, const float* 
     }
 }
 
+// A (the normal-equation matrix of the current point, FP64, symmetric)
+// as the solve reads it: packed lower in shared memory (variant S), or the
+// tile-ordered accumulator buffer in global memory / L2 (variant L).
+struct PackedA {
+    const double* p;
+    __device__ __forceinline__ double operator()(int i, int j) const { return i >= j ? p[pidx(i, j)] : p[pidx(j, i)]; }
+};
+struct TileA {
+    const double* p;
+    int nb;
+    __device__ __forceinline__ double operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
+};
+
 struct SolveWork {              // shared-memory scratch of solve_damped
     double bt[PMAX], ud[PMAX], inv64[PMAX];
     float sf[PMAX], xv[PMAX], zv[PMAX], cv[PMAX], inv32[PMAX];
@@ -467,19 +490,19 @@ struct SolveWork {              // shared-memory scratch of solve_damped
 
 // FP32 scaled factor-and-refine solve (see solve_damped) with panel width
 // PB; P4 = P rounded up to PB.  Returns false if the FP32 factor fails.
-template <int PB>
-__device__ bool solve_scaled_fp32(const double* __restrict__ Ac, const double* __restrict__ g,
-                                  const double* __restrict__ dv, double lam, int P, void* uni, SolveWork& w,
-                                  double* __restrict__ delta) {
+template <int PB, class AT>
+__device__ bool solve_scaled_fp32(const AT& A, const double* __restrict__ g, const double* __restrict__ dv, double lam,
+                                  int P, void* uni, SolveWork& w, double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    float* L32 = reinterpret_cast<float*>(uni);
-    float* Lp = L32 + L32_LP_OFF;
     const int P4 = (P + PB - 1) & ~(PB - 1);   // padded with identity rows: every block of the factor is full
+    float* L32 = reinterpret_cast<float*>(uni);
+    float* Lp = L32 + lp_offset(P4);
+    const int lp_ld = P4 + 4;
     for (int i = tid; i < P4; i += blockDim.x) {
         float s = 1.0f;
         double b = 0.0;
         if (i < P) {
-            const double m = Ac[pidx(i, i)] + lam * dv[i];
+            const double m = A(i, i) + lam * dv[i];
             s = (m > 0.0) ? rsqrtf((float)m) : 1.0f;
             b = (double)s * g[i];
         }
@@ -493,7 +516,7 @@ __device__ bool solve_scaled_fp32(const double* __restrict__ Ac, const double* _
         for (int j = lane; j <= i && j < P4; j += 32) {
             float v;
             if (i < P && j < P) {
-                double a = Ac[pidx(i, j)];
+                double a = A(i, j);
                 if (i == j) a += lam * dv[i];
                 v = (float)a * si * w.sf[j];
             } else if (i == P4) {
@@ -505,7 +528,7 @@ __device__ bool solve_scaled_fp32(const double* __restrict__ Ac, const double* _
         }
     }
     __syncthreads();
-    if (chol_lowlat<PB>(L32, Lp, P4, w.inv32, &w.flag)) {
+    if (chol_lowlat<PB>(L32, Lp, P4, w.inv32, &w.flag, lp_ld)) {
         trsv_back_block<PB>(L32, P4, w.inv32, L32 + pidx(P4, 0), w.xv);      // x = L^-T (L^-1 S g)
         for (int i = tid; i < P4; i += blockDim.x) w.ud[i] = (double)w.sf[i] * (double)w.xv[i];
         __syncthreads();
@@ -516,16 +539,13 @@ __device__ bool solve_scaled_fp32(const double* __restrict__ Ac, const double* _
             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
             int j = 0;
             for (; j + 3 < P; j += 4) {          // unconditional loads, four chains
-                const int q0 = j <= i ? pidx(i, j) : pidx(j, i);
-                const int q1 = j + 1 <= i ? pidx(i, j + 1) : pidx(j + 1, i);
-                const int q2 = j + 2 <= i ? pidx(i, j + 2) : pidx(j + 2, i);
-                const int q3 = j + 3 <= i ? pidx(i, j + 3) : pidx(j + 3, i);
-                a0 = fma(Ac[q0], w.ud[j], a0);
-                a1 = fma(Ac[q1], w.ud[j + 1], a1);
-                a2 = fma(Ac[q2], w.ud[j + 2], a2);
-                a3 = fma(Ac[q3], w.ud[j + 3], a3);
+                const double v0 = A(i, j), v1 = A(i, j + 1), v2 = A(i, j + 2), v3 = A(i, j + 3);
+                a0 = fma(v0, w.ud[j], a0);
+                a1 = fma(v1, w.ud[j + 1], a1);
+                a2 = fma(v2, w.ud[j + 2], a2);
+                a3 = fma(v3, w.ud[j + 3], a3);
             }
-            for (; j < P; ++j) a0 = fma(Ac[j <= i ? pidx(i, j) : pidx(j, i)], w.ud[j], a0);
+            for (; j < P; ++j) a0 = fma(A(i, j), w.ud[j], a0);
             const double mx = (a0 + a1) + (a2 + a3) + lam * dv[i] * w.ud[i];
             w.cv[i] = (float)(w.bt[i] - (double)w.sf[i] * mx);
         }
@@ -547,21 +567,23 @@ __device__ bool solve_scaled_fp32(const double* __restrict__ Ac, const double* _
 // forward substitution comes out of the factorisation); one back
 // substitution gives x; one step of iterative refinement with the residual
 // S g - S (A + lam D) S x evaluated in FP64 corrects it; delta = S x.  If the
-// FP32 factor fails, an FP64 factor of the unscaled matrix is used.  Returns
-// false when the damped matrix is not positive definite.
-__device__ bool solve_damped(const double* __restrict__ Ac, const double* __restrict__ g,
-                             const double* __restrict__ dv, double lam, int P, void* uni, SolveWork& w,
-                             double* __restrict__ delta) {
+// FP32 factor fails, an FP64 factor of the unscaled matrix is used, in m64
+// (P (P+1) / 2 doubles: shared memory for variant S, the CTA's partial row
+// in global memory for variant L).  Returns false when the damped matrix is
+// not positive definite.
+template <class AT>
+__device__ bool solve_damped(const AT& A, const double* __restrict__ g, const double* __restrict__ dv, double lam, int P,
+                             void* uni, double* m64, SolveWork& w, double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    if (P <= 32 ? solve_scaled_fp32<4>(Ac, g, dv, lam, P, uni, w, delta)
-                : solve_scaled_fp32<8>(Ac, g, dv, lam, P, uni, w, delta))
+    if (P <= 32 ? solve_scaled_fp32<4>(A, g, dv, lam, P, uni, w, delta)
+                : solve_scaled_fp32<8>(A, g, dv, lam, P, uni, w, delta))
         return true;
     // FP64 factor of the unscaled damped matrix
     if (tid == 0) w.fallbacks += 1;
-    double* M64 = reinterpret_cast<double*>(uni);
+    double* M64 = m64;
     for (int i = warp; i < P; i += nwarp)
         for (int j = lane; j <= i; j += 32) {
-            double v = Ac[pidx(i, j)];
+            double v = A(i, j);
             if (i == j) v += lam * dv[i];
             M64[pidx(i, j)] = v;
         }
@@ -579,15 +601,17 @@ __device__ bool solve_damped(const double* __restrict__ Ac, const double* __rest
 
 // The whole fit of one window, run by the CTAs of one fit group; b is this
 // CTA's rank in the group (the group has d.grid CTAs).
-template <int TPT>
+template <int TPT, bool LARGE>
 __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ descp,
                                             const LMConst& lmc, FitOut* __restrict__ out, double* __restrict__ partials,
                                             double* __restrict__ sums, unsigned* __restrict__ bar,
                                             float* __restrict__ Tg, const int b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Ts = reinterpret_cast<float*>(smem_raw);                          // PX_SMEM floats
-    double* Ac = reinterpret_cast<double*>(Ts + PX_SMEM);                    // A at the current point
-    float* Jc = reinterpret_cast<float*>(Ac + M_DOUBLES);                    // union region
+    // variant S: A at the current point cached in shared memory; variant L:
+    // A read from the sums buffer (L2), the union region follows Ts
+    double* Ac = LARGE ? nullptr : reinterpret_cast<double*>(Ts + PX_SMEM);
+    float* Jc = LARGE ? Ts + PX_SMEM : reinterpret_cast<float*>(Ac + M_DOUBLES);   // union region
     float* red = Jc;
 
     __shared__ FitDesc d;
@@ -617,7 +641,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     const long long s0 = Wn * b / G, s1 = Wn * (b + 1) / G;
     const int slen = (int)(s1 - s0);
     const bool in_smem = d.smem_ok != 0;
-    const int CH = (NAp <= 64) ? CH_SMALL : CH_LARGE;
+    const int CH = (NAp <= 64) ? CH_SMALL : (NAp <= PMAX_S + 4 ? CH_LARGE : CH_XL);
     const int chi_idx = acc_index(P, P, nb);
 
     // ---- tile table and thread -> (tile, group) assignment
@@ -667,6 +691,14 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         // ================= pixel pass at trial[] =================
         if (tid < K) make_frame(&trial[4 * tid], fr[tid]);
         __syncthreads();
+        const int nxt = 1 - s_cur;
+        double* sums_nxt = sums + (size_t)nxt * NACC_MAX;
+        // the tiles in rounds of TPT per thread (one round unless the active
+        // set is large), re-evaluating the J rows each round
+        const int tiles_per_round = TPT * (int)blockDim.x;
+        const int n_rounds = n_groups == 1 ? (ntiles + tiles_per_round - 1) / tiles_per_round : 1;
+        for (int round = 0; round < n_rounds; ++round) {
+        const int tbase = my_tile0 + round * tiles_per_round;
         float acc[TPT][16], ks[TPT][16], kc[TPT][16];
 #pragma unroll
         for (int q = 0; q < TPT; ++q)
@@ -717,7 +749,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     const int l1 = min(pb, l0 + 64);
 #pragma unroll
                     for (int q = 0; q < TPT; ++q) {
-                        const int t = my_tile0 + q * (int)blockDim.x;
+                        const int t = tbase + q * (int)blockDim.x;
                         if (t < ntiles) {
                             const short2 bij = ttab[t];
                             for (int l = l0; l < l1; ++l) {
@@ -746,28 +778,28 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             __syncthreads();
         }
 
-        t1 = gtimer(); t_pass += t1 - t0; t0 = t1;
-        // ---- CTA total of each accumulator entry (FP64 across pixel groups)
-        const int nxt = 1 - s_cur;
-        double* sums_nxt = sums + (size_t)nxt * NACC_MAX;
+        // ---- CTA total of each accumulator entry of this round
         if (n_groups == 1) {
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
-                const int t = my_tile0 + q * (int)blockDim.x;
+                const int t = tbase + q * (int)blockDim.x;
                 if (my_group == 0 && t < ntiles) {
                     double* dst = (G == 1) ? (sums_nxt + t * 16) : (partials + (size_t)b * NACC_MAX + t * 16);
 #pragma unroll
                     for (int e = 0; e < 16; ++e) dst[e] = (double)ks[q][e] - (double)kc[q][e];
                 }
             }
-        } else {
-            if (my_group >= 0) {
+        } else if (my_group >= 0) {
+            // several pixel groups per tile: park each group's leaf sums
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    red[(my_group * ntiles + my_tile0) * 16 + e] = ks[0][e];
-                    red[(n_groups * ntiles + my_group * ntiles + my_tile0) * 16 + e] = kc[0][e];
-                }
+            for (int e = 0; e < 16; ++e) {
+                red[(my_group * ntiles + my_tile0) * 16 + e] = ks[0][e];
+                red[(n_groups * ntiles + my_group * ntiles + my_tile0) * 16 + e] = kc[0][e];
             }
+        }
+        }   // rounds
+        t1 = gtimer(); t_pass += t1 - t0; t0 = t1;
+        if (n_groups > 1) {
             __syncthreads();
             for (int e = tid; e < nacc; e += blockDim.x) {
                 double s = 0.0;
@@ -840,16 +872,18 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         first = false;
         __syncthreads();
         // the current point moved (first pass or accepted step): cache its
-        // A (packed lower), g and Marquardt diagonal in shared memory
+        // g and Marquardt diagonal (and, variant S, A packed lower) in shared
+        // memory; variant L keeps reading A from sums[s_cur]
         if (s_cur == nxt) {
             const double* sc = sums + (size_t)s_cur * NACC_MAX;
             const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-            for (int i = warp; i < P; i += nwarp)
-                for (int j = lane; j <= i; j += 32) Ac[pidx(i, j)] = __ldcg(sc + acc_index(i, j, nb));
+            if (!LARGE)
+                for (int i = warp; i < P; i += nwarp)
+                    for (int j = lane; j <= i; j += 32) Ac[pidx(i, j)] = __ldcg(sc + acc_index(i, j, nb));
             for (int i = tid; i < P; i += blockDim.x) gvec[i] = __ldcg(sc + acc_index(i, P, nb));
             __syncthreads();
             for (int i = tid; i < P; i += blockDim.x) {
-                const double dd = Ac[pidx(i, i)];
+                const double dd = LARGE ? __ldcg(sc + acc_index(i, i, nb)) : Ac[pidx(i, i)];
                 dvec[i] = dd > 0.0 ? dd : 1.0;
             }
             __syncthreads();
@@ -862,7 +896,12 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             if (s_done) break;
             const double lam = s_lam;
             const unsigned long long tf0 = gtimer();
-            const bool ok = solve_damped(Ac, gvec, dvec, lam, P, Jc, sw, delta);
+            bool ok;
+            if (LARGE)
+                ok = solve_damped(TileA{sums + (size_t)s_cur * NACC_MAX, nb}, gvec, dvec, lam, P, Jc,
+                                  partials + (size_t)b * NACC_MAX, sw, delta);
+            else
+                ok = solve_damped(PackedA{Ac}, gvec, dvec, lam, P, Jc, reinterpret_cast<double*>(Jc), sw, delta);
             const unsigned long long tf1 = gtimer();
             t_factor += tf1 - tf0;
             // predicted decrease d.g + lam d.D.d (FP32 sums), finiteness, validity
@@ -937,19 +976,19 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     }
 }
 
-template <int TPT>
+template <int TPT, bool LARGE>
 __global__ void __launch_bounds__(FIT_THREADS, 1)
 k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ descp, const __grid_constant__ LMConst lmc,
          FitOut* __restrict__ out, double* __restrict__ partials, double* __restrict__ sums,
          unsigned* __restrict__ bar, float* __restrict__ Tg) {
-    lm_fit_body<TPT>(src, src_w, descp, lmc, out, partials, sums, bar, Tg, blockIdx.x);
+    lm_fit_body<TPT, LARGE>(src, src_w, descp, lmc, out, partials, sums, bar, Tg, blockIdx.x);
 }
 
 // Batched: the fits of many images in one cooperative launch of g_total
 // CTAs.  Image i owns CTAs [dmap[i], dmap[i+1]) (written on the device each
 // iteration by k_fit_map_b); each group runs its own fit with its own
 // barrier counter, partials and sums; CTAs beyond dmap[n] return.
-template <int TPT>
+template <int TPT, bool LARGE>
 __global__ void __launch_bounds__(FIT_THREADS, 1)
 k_lm_fit_b(const ImgDesc* __restrict__ imgs, const int* __restrict__ dmap, int n, int which, int max_iter_override) {
     const int c = (int)blockIdx.x;
@@ -964,10 +1003,14 @@ k_lm_fit_b(const ImgDesc* __restrict__ imgs, const int* __restrict__ dmap, int n
     // start, the fallback refit)
     LMConst lmc = g.dp.lm;
     if (max_iter_override >= 0) lmc.max_iter = max_iter_override;
-    lm_fit_body<TPT>(g.R, g.W, which ? &g.st->fit2 : &g.st->fit, lmc, which ? &g.st->fout2 : &g.st->fout, g.partials,
-                     g.sums, g.bar, g.Tg, c - dmap[lo]);
+    lm_fit_body<TPT, LARGE>(g.R, g.W, which ? &g.st->fit2 : &g.st->fit, lmc, which ? &g.st->fout2 : &g.st->fout,
+                            g.partials, g.sums, g.bar, g.Tg, c - dmap[lo]);
 }
-size_t fit_smem_bytes() {
+// Fit variants: 1 = one tile per thread (K <= 7), 3 = three tiles per
+// thread (K <= 32), 4 = the large variant (three tiles per thread in rounds,
+// A read from L2; K <= KMAX).
+size_t fit_smem_bytes(int variant) {
+    if (variant == 4) return (size_t)PX_SMEM * sizeof(float) + (size_t)UNI_L_FLOATS * sizeof(float);
     size_t jc = (size_t)JC_FLOATS * sizeof(float);
     size_t m = (size_t)M_DOUBLES * sizeof(double);
     size_t red = (size_t)2 * FIT_THREADS * 16 * sizeof(float);
@@ -975,21 +1018,29 @@ size_t fit_smem_bytes() {
     if (red > u) u = red;
     return (size_t)PX_SMEM * sizeof(float) + m + u;
 }
+size_t fit_smem_bytes() { return fit_smem_bytes(1); }
 
-static const void* fit_kernel_ptr(int tpt) {
-    return tpt == 1 ? (const void*)k_lm_fit<1> : (const void*)k_lm_fit<3>;
+static const void* fit_kernel_ptr(int variant) {
+    return variant == 1 ? (const void*)k_lm_fit<1, false>
+                        : variant == 3 ? (const void*)k_lm_fit<3, false> : (const void*)k_lm_fit<3, true>;
+}
+static const void* fit_kernel_b_ptr(int variant) {
+    return variant == 1 ? (const void*)k_lm_fit_b<1, false>
+                        : variant == 3 ? (const void*)k_lm_fit_b<3, false> : (const void*)k_lm_fit_b<3, true>;
 }
 
-int fit_tpt_for(int k_max) { return fit_tiles(k_max) <= FIT_THREADS ? 1 : 3; }
+int fit_tpt_for(int k_max) {
+    if (fit_tiles(k_max) <= FIT_THREADS) return 1;
+    return k_max <= KMAX_S ? 3 : 4;
+}
 
-cudaError_t fit_configure(int tpt, int* blocks_per_sm) {
-    const void* fn = fit_kernel_ptr(tpt);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem_bytes());
+cudaError_t fit_configure(int variant, int* blocks_per_sm) {
+    const int smem = (int)fit_smem_bytes(variant);
+    cudaError_t e = cudaFuncSetAttribute(fit_kernel_ptr(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(tpt == 1 ? (const void*)k_lm_fit_b<1> : (const void*)k_lm_fit_b<3>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem_bytes());
+    e = cudaFuncSetAttribute(fit_kernel_b_ptr(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, FIT_THREADS, fit_smem_bytes());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fit_kernel_ptr(variant), FIT_THREADS, smem);
 }
 
 cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap, int n, int g_total, unsigned* bars,
@@ -999,15 +1050,16 @@ cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap,
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g_total);
     cfg.blockDim = dim3(FIT_THREADS);
-    cfg.dynamicSmemBytes = fit_smem_bytes();
+    cfg.dynamicSmemBytes = fit_smem_bytes(tpt);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1>, imgs, dmap, n, which, max_iter_override);
-    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3>, imgs, dmap, n, which, max_iter_override);
+    if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1, false>, imgs, dmap, n, which, max_iter_override);
+    if (tpt == 3) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3, false>, imgs, dmap, n, which, max_iter_override);
+    return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3, true>, imgs, dmap, n, which, max_iter_override);
 }
 
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
@@ -1018,7 +1070,7 @@ cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(FIT_THREADS);
-    cfg.dynamicSmemBytes = fit_smem_bytes();
+    cfg.dynamicSmemBytes = fit_smem_bytes(tpt);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1026,8 +1078,10 @@ cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (tpt == 1)
-        return cudaLaunchKernelEx(&cfg, k_lm_fit<1>, src, src_w, desc, lmc, out, partials, sums, bar, Tg);
-    return cudaLaunchKernelEx(&cfg, k_lm_fit<3>, src, src_w, desc, lmc, out, partials, sums, bar, Tg);
+        return cudaLaunchKernelEx(&cfg, k_lm_fit<1, false>, src, src_w, desc, lmc, out, partials, sums, bar, Tg);
+    if (tpt == 3)
+        return cudaLaunchKernelEx(&cfg, k_lm_fit<3, false>, src, src_w, desc, lmc, out, partials, sums, bar, Tg);
+    return cudaLaunchKernelEx(&cfg, k_lm_fit<3, true>, src, src_w, desc, lmc, out, partials, sums, bar, Tg);
 }
 
 }  // namespace aspd
