@@ -482,6 +482,8 @@ struct TileA {
     __device__ __forceinline__ double operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
 };
 
+constexpr float REFINE_INV_MAX = 10.0f;   // refine when some 1/L_jj of the scaled factor exceeds this
+
 struct SolveWork {              // shared-memory scratch of solve_damped
     double bt[PMAX], ud[PMAX], inv64[PMAX];
     float sf[PMAX], xv[PMAX], zv[PMAX], cv[PMAX], inv32[PMAX];
@@ -530,6 +532,17 @@ __device__ bool solve_scaled_fp32(const AT& A, const double* __restrict__ g, con
     __syncthreads();
     if (chol_lowlat<PB>(L32, Lp, P4, w.inv32, &w.flag, lp_ld)) {
         trsv_back_block<PB>(L32, P4, w.inv32, L32 + pidx(P4, 0), w.xv);      // x = L^-T (L^-1 S g)
+        // The scaled matrix has a unit diagonal, so its Cholesky pivots
+        // L_jj^2 lie in (0, 1] and a small one marks a near-dependency.  With
+        // every pivot >= 1e-2 (1/L_jj <= 10) the FP32 solution is accurate to
+        // a few 1e-5 relative -- the FP32 normal equations' own level -- and
+        // the FP64 refinement is skipped.
+        const int refine = __syncthreads_or(tid < P4 && !(w.inv32[tid] <= REFINE_INV_MAX));
+        if (!refine) {
+            for (int i = tid; i < P; i += blockDim.x) delta[i] = (double)w.sf[i] * (double)w.xv[i];
+            __syncthreads();
+            return true;
+        }
         for (int i = tid; i < P4; i += blockDim.x) w.ud[i] = (double)w.sf[i] * (double)w.xv[i];
         __syncthreads();
         // refinement: c = (L L^T)^-1 (S g - S (A + lam D) S x), residual in
