@@ -51,6 +51,19 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 __device__ __forceinline__ int pidx(int i, int j) { return i * (i + 1) / 2 + j; }   // packed lower, j <= i
 
+// Error-free FP32 sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// Add the FP32 pair (hi, lo) into the running pair (s, c), in FP32.
+__device__ __forceinline__ void pair_add(float& s, float& c, float hi, float lo) {
+    float e;
+    two_sum(s, hi, s, e);
+    c += e + lo;
+}
+
 __device__ __forceinline__ int tile_index(int bi, int bj, int nb) { return bi * nb - bi * (bi - 1) / 2 + (bj - bi); }
 
 // Accumulator entry of (i, j) of [J | r]^T [J | r].
@@ -792,14 +805,23 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         }
 
         // ---- CTA total of each accumulator entry of this round
+        // CTA partials stay FP32 pairs (hi, lo) = (Kahan sum, -compensation):
+        // every FP64 operation or conversion costs the narrow FP64 pipe;
+        // only a single-CTA fit writes its FP64 sums here
         if (n_groups == 1) {
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
                 const int t = tbase + q * (int)blockDim.x;
                 if (my_group == 0 && t < ntiles) {
-                    double* dst = (G == 1) ? (sums_nxt + t * 16) : (partials + (size_t)b * NACC_MAX + t * 16);
+                    if (G == 1) {
+                        double* dst = sums_nxt + t * 16;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) dst[e] = (double)ks[q][e] - (double)kc[q][e];
+                        for (int e = 0; e < 16; ++e) dst[e] = (double)ks[q][e] - (double)kc[q][e];
+                    } else {
+                        float2* dst = reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX) + t * 16;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) dst[e] = make_float2(ks[q][e], -kc[q][e]);
+                    }
                 }
             }
         } else if (my_group >= 0) {
@@ -813,12 +835,13 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         }   // rounds
         t1 = gtimer(); t_pass += t1 - t0; t0 = t1;
         if (n_groups > 1) {
+            // the pixel groups' pairs combined error-free in FP32, in group order
             __syncthreads();
             for (int e = tid; e < nacc; e += blockDim.x) {
-                double s = 0.0;
-                for (int g = 0; g < n_groups; ++g)
-                    s += (double)red[g * nacc + e] - (double)red[(n_groups + g) * nacc + e];
-                if (G == 1) sums_nxt[e] = s; else partials[(size_t)b * NACC_MAX + e] = s;
+                float sh = 0.f, sl = 0.f;
+                for (int g = 0; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                if (G == 1) sums_nxt[e] = (double)sh + (double)sl;
+                else reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX)[e] = make_float2(sh, sl);
             }
         }
 
@@ -828,19 +851,28 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
             if (s_err) return;
             for (int e = b * (int)blockDim.x + tid; e < nacc; e += G * (int)blockDim.x) {
-                // four independent FP64 chains (an FP64 add is ~64 cycles of
-                // latency here), combined in a fixed order
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                const double* pe = partials + e;
+                // the CTAs' FP32 pairs combined error-free in FP32 as four
+                // independent chains (fixed order), one conversion to FP64
+                float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+                const float2* pe = reinterpret_cast<const float2*>(partials) + e;
+                const size_t stride = NACC_MAX;   // a partial row: NACC_MAX doubles = NACC_MAX float2
                 int c = 0;
                 for (; c + 3 < G; c += 4) {
-                    s0 += __ldcg(pe + (size_t)c * NACC_MAX);
-                    s1 += __ldcg(pe + (size_t)(c + 1) * NACC_MAX);
-                    s2 += __ldcg(pe + (size_t)(c + 2) * NACC_MAX);
-                    s3 += __ldcg(pe + (size_t)(c + 3) * NACC_MAX);
+                    const float2 v0 = __ldcg(pe + (size_t)c * stride), v1 = __ldcg(pe + (size_t)(c + 1) * stride);
+                    const float2 v2 = __ldcg(pe + (size_t)(c + 2) * stride), v3 = __ldcg(pe + (size_t)(c + 3) * stride);
+                    pair_add(h0, l0, v0.x, v0.y);
+                    pair_add(h1, l1, v1.x, v1.y);
+                    pair_add(h2, l2, v2.x, v2.y);
+                    pair_add(h3, l3, v3.x, v3.y);
                 }
-                for (; c < G; ++c) s0 += __ldcg(pe + (size_t)c * NACC_MAX);
-                sums_nxt[e] = (s0 + s1) + (s2 + s3);
+                for (; c < G; ++c) {
+                    const float2 v = __ldcg(pe + (size_t)c * stride);
+                    pair_add(h0, l0, v.x, v.y);
+                }
+                pair_add(h0, l0, h1, l1);
+                pair_add(h2, l2, h3, l3);
+                pair_add(h0, l0, h2, l2);
+                sums_nxt[e] = (double)h0 + (double)l0;
             }
             ++epoch;
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
