@@ -115,6 +115,10 @@ typedef struct {
     double tau;           /* active-set retention threshold (1e-3) */
     int32_t retained_cap; /* retained-list cap (0: 8 x k_max) */
     int32_t max_components; /* component-list capacity (0: 65536) */
+    int32_t fit_px_per_cta; /* launch shape of the LM fit: window pixels per CTA
+                               (0: 96; clamped to [32, 12288]); changes the
+                               grid and so the FP32 summation order, not the
+                               method */
 } asp_params;
 
 /* Totals of asp_minor_cycle since asp_init (or the last asp_set_state). */

@@ -50,7 +50,8 @@ class asp_params(C.Structure):
                 ("lm_lambda0", C.c_double), ("lm_rtol", C.c_double), ("lm_xtol", C.c_double),
                 ("noise_sigma", C.c_float), ("stop_ksigma", C.c_float), ("n_scales", C.c_int32),
                 ("area_frac", C.c_float), ("init_mode", C.c_int32), ("tau", C.c_double),
-                ("retained_cap", C.c_int32), ("max_components", C.c_int32)]
+                ("retained_cap", C.c_int32), ("max_components", C.c_int32),
+                ("fit_px_per_cta", C.c_int32)]
 
 
 class asp_cycle_stats(C.Structure):

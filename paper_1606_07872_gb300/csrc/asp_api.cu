@@ -136,8 +136,7 @@ LMConst lmconst_from(const asp_params& p, int max_iter_override = -1) {
     l.rtol = p.lm_rtol;
     l.xtol = p.lm_xtol;
     l.max_iter = max_iter_override >= 0 ? max_iter_override : p.lm_max_iter;
-    const char* env = getenv("ASP_FIT_PX_PER_CTA");
-    l.px_per_cta = env ? atoi(env) : 0;
+    l.px_per_cta = p.fit_px_per_cta;
     return l;
 }
 
@@ -148,6 +147,7 @@ asp_status validate_params(const asp_params* p) {
     if (p->k_max > ASP_KMAX) return ASP_ERR_UNSUPPORTED;
     if (p->lm_max_iter < 0 || p->n_scales < 1 || p->n_scales > MAX_SCALES) return ASP_ERR_INVALID_ARG;
     if (!(p->lm_lambda0 > 0) || !(p->lm_rtol >= 0) || !(p->lm_xtol >= 0)) return ASP_ERR_INVALID_ARG;
+    if (p->fit_px_per_cta < 0) return ASP_ERR_INVALID_ARG;
     if (p->init_mode < 0 || p->init_mode > 2) return ASP_ERR_INVALID_ARG;
     if (p->retained_cap < 0 || p->retained_cap > RET_MAX) return ASP_ERR_UNSUPPORTED;
     if (p->max_components < 0) return ASP_ERR_INVALID_ARG;
@@ -1387,6 +1387,7 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
             return bail(ASP_ERR_CUDA);
     }
     b->tpt = b->imgs[0]->tpt;
+    b->px_per_cta = params->fit_px_per_cta;
     int bps = 0;
     if (fit_configure(b->tpt, &bps) != cudaSuccess || bps < 1) return bail(ASP_ERR_CUDA);
     b->g_total = b->num_sms * bps;
@@ -1494,7 +1495,7 @@ asp_status asp_batch_autotune(asp_batch* b, int n_trial_iter, asp_batch_tuning* 
     if (!b || n_trial_iter < 1) return ASP_ERR_INVALID_ARG;
     if (b->broken) return ASP_ERR_STATE;
     cudaSetDevice(b->dev);
-    const int cand_px[] = {0, 256, 512, 1024, 2048, 4096};   // pixels per CTA (0: the automatic rule)
+    const int cand_px[] = {0, 48, 192, 384, 768, 1536};   // pixels per CTA (0: the default, 96)
     const int n_px = (int)(sizeof(cand_px) / sizeof(cand_px[0]));
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));

@@ -19,6 +19,7 @@ constexpr int T1_SLACK_ROWS = 16;                  // zeroed rows behind the las
 constexpr int MAX_SCALES = 8;                      // smoothing scales
 constexpr int FIT_THREADS = 256;
 constexpr int PX_SMEM = 12288;                     // target pixels one CTA keeps in smem
+constexpr int FIT_PX_PER_CTA = 96;                 // default fit tile: window pixels per CTA (measured best on the 1024^2 workload)
 constexpr int RET_MAX = 1024;                      // retained-list capacity
 constexpr int RED_THREADS = 256;                   // threads of the image-wide kernels
 constexpr unsigned SPIN_LIMIT = 1u << 25;          // bounded grid-barrier wait (~1 s)
@@ -186,13 +187,15 @@ __device__ __host__ inline int fit_tiles(int K) {
     return nb * (nb + 1) / 2;
 }
 
-// CTAs a fit of K members over Wn pixels uses: enough pixels per CTA that
-// one pass is ~0.6 M accumulator FMAs (a few microseconds on one SM), so
-// small fits run on one CTA without grid barriers and large ones spread.
+// CTAs a fit of K members over Wn pixels uses: one CTA per px_per_cta
+// window pixels (default FIT_PX_PER_CTA), capped at g_max.  An LM iteration
+// is latency-bound (grid barriers and the serial solve dominate), so the
+// accumulation phase is spread as thin as the barriers allow; windows below
+// one tile run on a single CTA without grid barriers.
 __device__ __host__ inline int fit_grid(long long Wn, int K, int px_per_cta, int g_max, int* smem_ok) {
-    int NAp = ((4 * K + 1) + 3) & ~3;
-    long long target = px_per_cta > 0 ? px_per_cta : 1200000 / (NAp * NAp);
-    if (target < 256) target = 256;
+    (void)K;   // one tile size serves every active-set size (measured)
+    long long target = px_per_cta > 0 ? px_per_cta : FIT_PX_PER_CTA;
+    if (target < 32) target = 32;
     if (target > PX_SMEM) target = PX_SMEM;
     long long g = (Wn + target - 1) / target;
     if (g < 1) g = 1;

@@ -407,6 +407,35 @@ def test_invalid_arguments(asp):
     with pytest.raises(asp.AspError):
         ctx.subtract([[1, 0, 5, 5, np.nan, 0]])
     ctx.close()
+    with pytest.raises(asp.AspError) as e:
+        _ctx(asp, case, fit_px_per_cta=-1)        # negative fit tile
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("px", [32, 200, 5000])
+def test_fit_tile_changes_only_rounding(asp, px):
+    """The fit's launch shape (window pixels per CTA) decides how many CTAs
+    share the accumulation, hence only the FP32 summation order: a joint fit
+    of three overlapping Gaussians from a fixed start converges to the
+    default shape's optimum within the parity bound (1e-4 per parameter)."""
+    rng = np.random.default_rng(40 + px)
+    H = W = 96
+    truth = np.array([[0.8, 40.3, 47.1, 2.6], [-0.4, 52.2, 50.6, 3.1], [0.3, 47.0, 38.5, 2.2]])
+    ys, xs = np.mgrid[0:H, 0:W]
+    img = O.gauss_model(truth.ravel(), xs.astype(float), ys.astype(float)) + rng.normal(0, 1e-3, (H, W))
+    psf = synth.gaussian_psf(H, W, 1.5)
+    start = truth * [1.1, 1, 1, 0.9] + [0, 0.3, -0.2, 0]
+    fits = []
+    for kw in ({}, dict(fit_px_per_cta=px)):
+        ctx = asp.Context(_t(img), _t(psf), k_max=5, noise_sigma=1e-3, lm_max_iter=300, lm_rtol=1e-12,
+                          lm_xtol=1e-10, **kw)
+        out, info = ctx.fit(start, 0)
+        fits.append((np.asarray(out, float), info))
+        ctx.close()
+    (a, ia), (b, ib) = fits
+    assert ia["status"] == ib["status"] == O.LM_CONVERGED
+    assert np.all(np.abs(a - b) <= 1e-4 * np.maximum(np.abs(a), 1.0)), (a, b)
+    assert ia["chi2_final"] == pytest.approx(ib["chi2_final"], rel=1e-5)
 
 
 def test_config2_full_size_sampled(asp):
