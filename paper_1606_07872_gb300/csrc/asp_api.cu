@@ -493,7 +493,7 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     if (cudaMemset(ctx->T1, 0, ((size_t)ctx->terms_cap * (2 * H - 1) + T1_SLACK_ROWS) * W * sizeof(float)) != cudaSuccess)
         return bail(ASP_ERR_CUDA);
     AL(ctx->partials, (size_t)ctx->g_max * NACC_MAX);
-    AL(ctx->sums, 2 * NACC_MAX);
+    AL(ctx->sums, SUMS_DOUBLES);
     AL(ctx->bar, 1);
     AL(ctx->Tg, 4 * N);   // window targets beyond shared memory (image or PSF windows)
     AL(ctx->part, std::max(ctx->grid_img, ctx->g_max));

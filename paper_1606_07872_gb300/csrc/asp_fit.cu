@@ -10,8 +10,9 @@
 //      4K Jacobian entries, accumulated as the upper triangle of
 //      [J | r]^T [J | r] (J^T J, J^T r and r^T r) in 4x4 register tiles,
 //      leaf sums of <= 64 pixels, Kahan-compensated across leaves;
-//   2. CTA partials (FP64) -> grid barrier -> column-split FP64 reduction ->
-//      grid barrier;
+//   2. CTA partials (FP32 hi/lo pairs) -> grid barrier -> error-free FP32
+//      pair reduction, each entry split over up to 32 lanes, one FP64 sum
+//      per entry -> grid barrier;
 //   3. every CTA redundantly runs the LM decision logic and the FP64
 //      Cholesky solve of (A + lambda diag A) delta = g, so no third barrier
 //      is needed to broadcast the next trial point.
@@ -33,8 +34,8 @@ constexpr int CH_XL = 64;       // chunk pixels of the large-active-set variant
 // FP32 factor with its panel.
 constexpr int KMAX_S = 32;
 constexpr int PMAX_S = 4 * KMAX_S;
-constexpr int JC_FLOATS = 128 * (PMAX_S + 4);                 // union region of S (>= 256 * 64)
-constexpr int M_DOUBLES = PMAX_S * (PMAX_S + 1) / 2;          // cached A of S
+constexpr int M_DOUBLES = PMAX_S * (PMAX_S + 1) / 2;          // cached A of S (FP64 and an FP32 copy)
+constexpr int M32_FLOATS = (M_DOUBLES + 3) / 4 * 4;
 constexpr int UNI_L_FLOATS = ((PMAX + 1) * (PMAX + 2) / 2 + 3) / 4 * 4 + 8 * (PMAX + 4);
 static_assert(UNI_L_FLOATS >= CH_XL * NAP_MAX, "J chunk of the large variant must fit its union region");
 
@@ -281,6 +282,12 @@ __device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ 
 // Lp (PB columns of ld lp_ld >= P + 1) sits behind the packed (P+1)-row
 // factor, at a 4-float-aligned offset.
 __host__ __device__ constexpr int lp_offset(int P4) { return ((P4 + 1) * (P4 + 2) / 2 + 3) & ~3; }
+// Union region of S: the J chunk (rows x NAp floats, rows chosen to fit),
+// the FP32 factor of P4 <= PMAX_S with its 8-column panel, or the CTA's leaf
+// sums of several pixel groups (2 x FIT_THREADS x 16 floats).
+constexpr int JC_FLOATS = lp_offset(PMAX_S) + 8 * (PMAX_S + 4);
+static_assert(JC_FLOATS >= 2 * FIT_THREADS * 16, "leaf sums must fit the union region");
+static_assert(JC_FLOATS / (PMAX_S + 4) >= 64, "the J chunk of S must hold 64 rows");
 
 // Factor the PBxPB diagonal block at j0 (lower, packed in M) in registers,
 // every lane of the calling warp redundantly; lanes 0..PB-1 store row
@@ -320,6 +327,75 @@ __device__ __forceinline__ bool factor_diag(float* __restrict__ M, float* __rest
             for (int t = 0; t <= c; ++t) M[pidx(j0 + c, j0 + t)] = d[c][t];
             inv_diag[j0 + c] = inv[c];
         }
+    return ok;
+}
+
+// factor_diag with the panel's update folded in, right-looking: every lane
+// of the calling warp loads the PBxPB block at r0 and, if Lp is given, the
+// panel rows r0..r0+PB-1 (PB columns of ld LP_LD), subtracts their products
+// (panel columns in ascending order), then eliminates column by column with
+// the trailing entries updated at once, so the chain from one pivot to the
+// next is one multiply, one FMA and the reciprocal square root.  Same
+// operations in the same order as the separate update plus factor_diag, so
+// bitwise the same factor.
+template <int PB>
+__device__ __forceinline__ bool factor_diag_rl(float* __restrict__ M, const float* __restrict__ Lp, int LP_LD,
+                                               float* __restrict__ inv_diag, int r0, int lane) {
+    float d[PB][PB];
+#pragma unroll
+    for (int r = 0; r < PB; ++r)
+#pragma unroll
+        for (int t = 0; t <= r; ++t) d[r][t] = M[pidx(r0 + r, r0 + t)];
+    if (Lp) {
+#pragma unroll
+        for (int c = 0; c < PB; ++c) {
+            float l[PB];
+#pragma unroll
+            for (int q = 0; q < PB; q += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(Lp + c * LP_LD + r0 + q);
+                l[q] = v.x; l[q + 1] = v.y; l[q + 2] = v.z; l[q + 3] = v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < PB; ++r)
+#pragma unroll
+                for (int t = 0; t <= r; ++t) d[r][t] = fmaf(-l[r], l[t], d[r][t]);
+        }
+    }
+    // The next pivot's update and reciprocal square root are issued first in
+    // each column (warps issue in program order), the rest of the column's
+    // update while it is in flight.  v > 0 && v < inf also rejects NaN.
+    float inv[PB];
+    bool ok = (d[0][0] > 0.f) & (d[0][0] < INFINITY);
+    float il = rsqrtf(d[0][0]);
+#pragma unroll
+    for (int c = 0; c < PB; ++c) {
+        inv[c] = il;
+        d[c][c] = d[c][c] * il;
+        float il_next = 0.f;
+        if (c + 1 < PB) {
+            d[c + 1][c] *= il;
+            d[c + 1][c + 1] = fmaf(-d[c + 1][c], d[c + 1][c], d[c + 1][c + 1]);
+            const float vn = d[c + 1][c + 1];
+            ok = ok & (vn > 0.f) & (vn < INFINITY);
+            il_next = rsqrtf(vn);
+        }
+#pragma unroll
+        for (int r = c + 2; r < PB; ++r) d[r][c] *= il;
+#pragma unroll
+        for (int r = c + 2; r < PB; ++r)
+#pragma unroll
+            for (int t = c + 1; t <= r; ++t) d[r][t] = fmaf(-d[r][c], d[t][c], d[r][t]);
+        il = il_next;
+    }
+    __syncwarp();   // every lane has read the block
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < PB; ++c) {
+#pragma unroll
+            for (int t = 0; t <= c; ++t) M[pidx(r0 + c, r0 + t)] = d[c][t];
+            inv_diag[r0 + c] = inv[c];
+        }
+    }
     return ok;
 }
 
@@ -396,6 +472,96 @@ __device__ bool chol_lowlat(float* __restrict__ M, float* __restrict__ Lp, int P
     return true;
 }
 
+// The same factorisation as chol_lowlat (same operations in the same order,
+// so bitwise the same factor) with the trailing update register-tiled: each
+// thread of warps 0..nwarp-2 updates 4x4 tiles of the trailing matrix, two
+// 16-byte panel loads per panel column for 16 FMAs, where the row-per-warp
+// update needed one shared-memory load per FMA and was bound by the
+// shared-memory pipe.  Tiles cover rows r0 + 4 bi (bi >= PB / 4: the next
+// diagonal block is the last warp's) and columns r0 + 4 bj, bj <= bi.
+template <int PB>
+__device__ bool chol_tiled(float* __restrict__ M, float* __restrict__ Lp, int P, float* __restrict__ inv_diag,
+                           int* s_flag, const int LP_LD) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int nrows = P + 1;
+    const int nupd = (nwarp - 1) * 32;
+    if (warp == nwarp - 1 && !factor_diag_rl<PB>(M, nullptr, LP_LD, inv_diag, 0, lane) && lane == 0) *s_flag = 1;
+    __syncthreads();
+    if (*s_flag) return false;
+#pragma unroll 1
+    for (int j0 = 0; j0 < P; j0 += PB) {
+        const int r0 = j0 + PB;
+        // A: panel rows below the diagonal block
+        const int i = r0 + tid;
+        if (i < nrows) {
+            float a[PB], iv[PB];
+#pragma unroll
+            for (int c = 0; c < PB; ++c) { a[c] = M[pidx(i, j0 + c)]; iv[c] = inv_diag[j0 + c]; }
+            float l[PB][PB];
+#pragma unroll
+            for (int c = 1; c < PB; ++c)
+#pragma unroll
+                for (int t = 0; t < c; ++t) l[c][t] = M[pidx(j0 + c, j0 + t)];
+#pragma unroll
+            for (int c = 0; c < PB; ++c) {
+                a[c] *= iv[c];
+#pragma unroll
+                for (int r = c + 1; r < PB; ++r) a[r] = fmaf(-l[r][c], a[c], a[r]);
+            }
+#pragma unroll
+            for (int c = 0; c < PB; ++c) {
+                M[pidx(i, j0 + c)] = a[c];
+                Lp[c * LP_LD + i] = a[c];
+            }
+        }
+        __syncthreads();
+        if (warp == nwarp - 1) {
+            if (r0 < P && !factor_diag_rl<PB>(M, Lp, LP_LD, inv_diag, r0, lane) && lane == 0) *s_flag = 1;
+        } else {
+            const int nbr = (nrows - r0 + 3) >> 2;
+            const int T0 = (PB / 4) * (PB / 4 + 1) / 2;
+            const int ntile = nbr * (nbr + 1) / 2 - T0;
+            for (int u = tid; u < ntile; u += nupd) {
+                const int uu = u + T0;
+                int bi = (int)((sqrtf(8.f * (float)uu + 1.f) - 1.f) * 0.5f);
+                while (bi * (bi + 1) / 2 > uu) --bi;
+                while ((bi + 1) * (bi + 2) / 2 <= uu) ++bi;
+                const int bj = uu - bi * (bi + 1) / 2;
+                const int i0 = r0 + 4 * bi, k0 = r0 + 4 * bj;
+                float acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ii = i0 + r, kk = k0 + q;
+                        acc[r][q] = (ii < nrows && kk <= ii && kk < P) ? M[pidx(ii, kk)] : 0.f;
+                    }
+#pragma unroll
+                for (int c = 0; c < PB; ++c) {
+                    const float4 li = *reinterpret_cast<const float4*>(Lp + c * LP_LD + i0);
+                    const float4 lk = *reinterpret_cast<const float4*>(Lp + c * LP_LD + k0);
+                    const float lr[4] = {li.x, li.y, li.z, li.w};
+                    const float lq[4] = {lk.x, lk.y, lk.z, lk.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(-lr[r], lq[q], acc[r][q]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ii = i0 + r, kk = k0 + q;
+                        if (ii < nrows && kk <= ii && kk < P) M[pidx(ii, kk)] = acc[r][q];
+                    }
+            }
+        }
+        __syncthreads();
+        if (*s_flag) return false;
+    }
+    return true;
+}
+
 // Back substitution L^T x = y with L from chol_lowlat (P a multiple of PB),
 // all threads, PB-row blocks from the bottom, one block barrier per block:
 // every thread solves the block's 8 unknowns redundantly from the (already
@@ -407,6 +573,7 @@ __device__ void trsv_back_block(const float* __restrict__ M, int P, const float*
     const int tid = threadIdx.x;
 #pragma unroll 1
     for (int jb = P - PB; jb >= 0; jb -= PB) {
+        if (tid < max(jb, PB)) {     // warps without rows to update skip the loads
         float xb[PB], iv[PB], l[PB][PB];
 #pragma unroll
         for (int c = 0; c < PB; ++c) { xb[c] = y[jb + c]; iv[c] = inv_diag[jb + c]; }
@@ -426,14 +593,16 @@ __device__ void trsv_back_block(const float* __restrict__ M, int P, const float*
             for (int t = 0; t < c; ++t) xb[t] = fmaf(-l[c][t], xb[c], xb[t]);
         }
         if (tid < PB) {
+            float xv = xb[0];
 #pragma unroll
-            for (int c = 0; c < PB; ++c)
-                if (c == tid) x[jb + c] = xb[c];
+            for (int c = 1; c < PB; ++c) xv = tid == c ? xb[c] : xv;
+            x[jb + tid] = xv;
         }
         if (tid < jb) {
 #pragma unroll
             for (int c = 0; c < PB; ++c) yi = fmaf(-lr[c], xb[c], yi);
             y[tid] = yi;
+        }
         }
         __syncthreads();
     }
@@ -448,6 +617,7 @@ __device__ void trsv_fwd_block(const float* __restrict__ M, int P, const float* 
     const int tid = threadIdx.x;
 #pragma unroll 1
     for (int jb = 0; jb < P; jb += PB) {
+        if (tid < max(P - jb - PB, PB)) {     // warps without rows to update skip the loads
         float zb[PB], iv[PB], l[PB][PB];
 #pragma unroll
         for (int c = 0; c < PB; ++c) { zb[c] = r[jb + c]; iv[c] = inv_diag[jb + c]; }
@@ -469,14 +639,16 @@ __device__ void trsv_fwd_block(const float* __restrict__ M, int P, const float* 
             for (int t = c + 1; t < PB; ++t) zb[t] = fmaf(-l[t][c], zb[c], zb[t]);
         }
         if (tid < PB) {
+            float zv = zb[0];
 #pragma unroll
-            for (int c = 0; c < PB; ++c)
-                if (c == tid) z[jb + c] = zb[c];
+            for (int c = 1; c < PB; ++c) zv = tid == c ? zb[c] : zv;
+            z[jb + tid] = zv;
         }
         if (upd) {
 #pragma unroll
             for (int c = 0; c < PB; ++c) ri = fmaf(-lr[c], zb[c], ri);
             r[i] = ri;
+        }
         }
         __syncthreads();
     }
@@ -494,35 +666,48 @@ struct TileA {
     int nb;
     __device__ __forceinline__ double operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
 };
+// The same matrix rounded to FP32 (the reduction writes both copies).
+struct PackedA32 {
+    const float* p;
+    __device__ __forceinline__ float operator()(int i, int j) const { return i >= j ? p[pidx(i, j)] : p[pidx(j, i)]; }
+};
+struct TileA32 {
+    const float* p;
+    int nb;
+    __device__ __forceinline__ float operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
+};
 
 constexpr float REFINE_INV_MAX = 10.0f;   // refine when some 1/L_jj of the scaled factor exceeds this
 
 struct SolveWork {              // shared-memory scratch of solve_damped
     double bt[PMAX], ud[PMAX], inv64[PMAX];
-    float sf[PMAX], xv[PMAX], zv[PMAX], cv[PMAX], inv32[PMAX];
+    float sf[PMAX], mf[PMAX], xv[PMAX], zv[PMAX], cv[PMAX], inv32[PMAX];
     int flag, refinements, fallbacks, pad;
 };
 
 // FP32 scaled factor-and-refine solve (see solve_damped) with panel width
-// PB; P4 = P rounded up to PB.  Returns false if the FP32 factor fails.
-template <int PB, class AT>
-__device__ bool solve_scaled_fp32(const AT& A, const double* __restrict__ g, const double* __restrict__ dv, double lam,
-                                  int P, void* uni, SolveWork& w, double* __restrict__ delta) {
+// PB; P4 = P rounded up to PB.  The scaled matrix is built from the FP32
+// copy A32 of A (g32, dv32 likewise): no FP64 instruction outside the
+// refinement.  Returns false if the FP32 factor fails.
+template <int PB, class AT, class AT32>
+__device__ bool solve_scaled_fp32(const AT& A, const AT32& A32, const double* __restrict__ g,
+                                  const float* __restrict__ g32, const double* __restrict__ dv,
+                                  const float* __restrict__ dv32, double lam, int P, void* uni, SolveWork& w,
+                                  double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int P4 = (P + PB - 1) & ~(PB - 1);   // padded with identity rows: every block of the factor is full
     float* L32 = reinterpret_cast<float*>(uni);
     float* Lp = L32 + lp_offset(P4);
     const int lp_ld = P4 + 4;
+    const float lam32 = (float)lam;
     for (int i = tid; i < P4; i += blockDim.x) {
-        float s = 1.0f;
-        double b = 0.0;
+        float sc = 1.0f, m = 1.0f;
         if (i < P) {
-            const double m = A(i, i) + lam * dv[i];
-            s = (m > 0.0) ? rsqrtf((float)m) : 1.0f;
-            b = (double)s * g[i];
+            m = fmaf(lam32, dv32[i], A32(i, i));
+            sc = m > 0.f ? rsqrtf(m) : 1.0f;
         }
-        w.sf[i] = s;
-        w.bt[i] = b;
+        w.sf[i] = sc;
+        w.mf[i] = m;
     }
     if (tid == 0) w.flag = 0;
     __syncthreads();
@@ -530,20 +715,14 @@ __device__ bool solve_scaled_fp32(const AT& A, const double* __restrict__ g, con
         const float si = i < P ? w.sf[i] : 0.f;
         for (int j = lane; j <= i && j < P4; j += 32) {
             float v;
-            if (i < P && j < P) {
-                double a = A(i, j);
-                if (i == j) a += lam * dv[i];
-                v = (float)a * si * w.sf[j];
-            } else if (i == P4) {
-                v = (float)w.bt[j];                          // right-hand side row (0 in the padding)
-            } else {
-                v = i == j ? 1.f : 0.f;                      // identity padding
-            }
+            if (i < P && j < P) v = (i == j ? w.mf[i] : A32(i, j)) * si * w.sf[j];
+            else if (i == P4) v = j < P ? w.sf[j] * g32[j] : 0.f;    // right-hand side row S g
+            else v = i == j ? 1.f : 0.f;                            // identity padding
             L32[pidx(i, j)] = v;
         }
     }
     __syncthreads();
-    if (chol_lowlat<PB>(L32, Lp, P4, w.inv32, &w.flag, lp_ld)) {
+    if (chol_tiled<PB>(L32, Lp, P4, w.inv32, &w.flag, lp_ld)) {
         trsv_back_block<PB>(L32, P4, w.inv32, L32 + pidx(P4, 0), w.xv);      // x = L^-T (L^-1 S g)
         // The scaled matrix has a unit diagonal, so its Cholesky pivots
         // L_jj^2 lie in (0, 1] and a small one marks a near-dependency.  With
@@ -556,7 +735,10 @@ __device__ bool solve_scaled_fp32(const AT& A, const double* __restrict__ g, con
             __syncthreads();
             return true;
         }
-        for (int i = tid; i < P4; i += blockDim.x) w.ud[i] = (double)w.sf[i] * (double)w.xv[i];
+        for (int i = tid; i < P4; i += blockDim.x) {
+            w.ud[i] = (double)w.sf[i] * (double)w.xv[i];
+            w.bt[i] = i < P ? (double)w.sf[i] * g[i] : 0.0;
+        }
         __syncthreads();
         // refinement: c = (L L^T)^-1 (S g - S (A + lam D) S x), residual in
         // FP64, one row per thread as four independent FMA chains
@@ -597,12 +779,13 @@ __device__ bool solve_scaled_fp32(const AT& A, const double* __restrict__ g, con
 // (P (P+1) / 2 doubles: shared memory for variant S, the CTA's partial row
 // in global memory for variant L).  Returns false when the damped matrix is
 // not positive definite.
-template <class AT>
-__device__ bool solve_damped(const AT& A, const double* __restrict__ g, const double* __restrict__ dv, double lam, int P,
+template <class AT, class AT32>
+__device__ bool solve_damped(const AT& A, const AT32& A32, const double* __restrict__ g, const float* __restrict__ g32,
+                             const double* __restrict__ dv, const float* __restrict__ dv32, double lam, int P,
                              void* uni, double* m64, SolveWork& w, double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    if (P <= 32 ? solve_scaled_fp32<4>(A, g, dv, lam, P, uni, w, delta)
-                : solve_scaled_fp32<8>(A, g, dv, lam, P, uni, w, delta))
+    if (P <= 32 ? solve_scaled_fp32<4>(A, A32, g, g32, dv, dv32, lam, P, uni, w, delta)
+                : solve_scaled_fp32<8>(A, A32, g, g32, dv, dv32, lam, P, uni, w, delta))
         return true;
     // FP64 factor of the unscaled damped matrix
     if (tid == 0) w.fallbacks += 1;
@@ -637,13 +820,16 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     // variant S: A at the current point cached in shared memory; variant L:
     // A read from the sums buffer (L2), the union region follows Ts
     double* Ac = LARGE ? nullptr : reinterpret_cast<double*>(Ts + PX_SMEM);
-    float* Jc = LARGE ? Ts + PX_SMEM : reinterpret_cast<float*>(Ac + M_DOUBLES);   // union region
+    float* Ac32 = LARGE ? nullptr : reinterpret_cast<float*>(Ac + M_DOUBLES);
+    float* Jc = LARGE ? Ts + PX_SMEM : Ac32 + M32_FLOATS;                      // union region
     float* red = Jc;
+    float* sums32 = reinterpret_cast<float*>(sums + 2 * NACC_MAX);            // FP32 copies of both buffers
 
     __shared__ FitDesc d;
     __shared__ MemberFrame fr[KMAX];
     __shared__ short2 ttab[NTILES_MAX];
     __shared__ double theta[PMAX], trial[PMAX], delta[PMAX], gvec[PMAX], dvec[PMAX];
+    __shared__ float g32[PMAX], dv32[PMAX];
     __shared__ SolveWork sw;
     __shared__ double s_lam, s_chi2, s_chi2_init;
     __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc;
@@ -667,7 +853,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     const long long s0 = Wn * b / G, s1 = Wn * (b + 1) / G;
     const int slen = (int)(s1 - s0);
     const bool in_smem = d.smem_ok != 0;
-    const int CH = (NAp <= 64) ? CH_SMALL : (NAp <= PMAX_S + 4 ? CH_LARGE : CH_XL);
+    const int CH = LARGE ? CH_XL : min(NAp <= 64 ? CH_SMALL : CH_LARGE, JC_FLOATS / NAp);
     const int chi_idx = acc_index(P, P, nb);
 
     // ---- tile table and thread -> (tile, group) assignment
@@ -719,6 +905,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         __syncthreads();
         const int nxt = 1 - s_cur;
         double* sums_nxt = sums + (size_t)nxt * NACC_MAX;
+        float* sums32_nxt = sums32 + (size_t)nxt * NACC_MAX;
         // the tiles in rounds of TPT per thread (one round unless the active
         // set is large), re-evaluating the J rows each round
         const int tiles_per_round = TPT * (int)blockDim.x;
@@ -815,8 +1002,12 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 if (my_group == 0 && t < ntiles) {
                     if (G == 1) {
                         double* dst = sums_nxt + t * 16;
+                        float* dst32 = sums32_nxt + t * 16;
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) dst[e] = (double)ks[q][e] - (double)kc[q][e];
+                        for (int e = 0; e < 16; ++e) {
+                            dst[e] = (double)ks[q][e] - (double)kc[q][e];
+                            dst32[e] = ks[q][e] - kc[q][e];
+                        }
                     } else {
                         float2* dst = reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX) + t * 16;
 #pragma unroll
@@ -840,39 +1031,61 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             for (int e = tid; e < nacc; e += blockDim.x) {
                 float sh = 0.f, sl = 0.f;
                 for (int g = 0; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
-                if (G == 1) sums_nxt[e] = (double)sh + (double)sl;
+                if (G == 1) { sums_nxt[e] = (double)sh + (double)sl; sums32_nxt[e] = sh + sl; }
                 else reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX)[e] = make_float2(sh, sl);
             }
         }
 
-        // ---- cross-CTA reduction (FP64, fixed order -> identical in every CTA)
+        // ---- cross-CTA reduction (fixed order -> identical in every CTA)
         if (G > 1) {
             ++epoch;
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
             if (s_err) return;
-            for (int e = b * (int)blockDim.x + tid; e < nacc; e += G * (int)blockDim.x) {
-                // the CTAs' FP32 pairs combined error-free in FP32 as four
-                // independent chains (fixed order), one conversion to FP64
+            // T lanes per entry (a power of two <= 32 and <= G, as many as the
+            // grid's threads allow): lane (e_local, s) of a warp holds entry
+            // e0 + e_local and combines the CTAs s, s + T, ... as four FP32
+            // pair chains; the T lanes' pairs then meet in a fixed shuffle
+            // tree.  Same order in every CTA and every launch.
+            const int nwarp = (int)blockDim.x >> 5, lane = tid & 31;
+            int T = 1;
+            while (T < 32 && 2 * T <= G && (long long)G * (int)blockDim.x >= (long long)nacc * 2 * T) T *= 2;
+            const int E = 32 / T;
+            const int el = lane & (E - 1), s0 = lane / E;
+            const float2* pbase = reinterpret_cast<const float2*>(partials);
+            const size_t stride = NACC_MAX;   // a partial row: NACC_MAX doubles = NACC_MAX float2
+            for (int e0 = (b * nwarp + (tid >> 5)) * E; e0 < nacc; e0 += G * nwarp * E) {
+                const int e = e0 + el;
                 float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
-                const float2* pe = reinterpret_cast<const float2*>(partials) + e;
-                const size_t stride = NACC_MAX;   // a partial row: NACC_MAX doubles = NACC_MAX float2
-                int c = 0;
-                for (; c + 3 < G; c += 4) {
-                    const float2 v0 = __ldcg(pe + (size_t)c * stride), v1 = __ldcg(pe + (size_t)(c + 1) * stride);
-                    const float2 v2 = __ldcg(pe + (size_t)(c + 2) * stride), v3 = __ldcg(pe + (size_t)(c + 3) * stride);
-                    pair_add(h0, l0, v0.x, v0.y);
-                    pair_add(h1, l1, v1.x, v1.y);
-                    pair_add(h2, l2, v2.x, v2.y);
-                    pair_add(h3, l3, v3.x, v3.y);
+                if (e < nacc) {
+                    const float2* pe = pbase + e;
+                    int c = s0;
+                    for (; c + 3 * T < G; c += 4 * T) {
+                        const float2 v0 = __ldcg(pe + (size_t)c * stride);
+                        const float2 v1 = __ldcg(pe + (size_t)(c + T) * stride);
+                        const float2 v2 = __ldcg(pe + (size_t)(c + 2 * T) * stride);
+                        const float2 v3 = __ldcg(pe + (size_t)(c + 3 * T) * stride);
+                        pair_add(h0, l0, v0.x, v0.y);
+                        pair_add(h1, l1, v1.x, v1.y);
+                        pair_add(h2, l2, v2.x, v2.y);
+                        pair_add(h3, l3, v3.x, v3.y);
+                    }
+                    for (; c < G; c += T) {
+                        const float2 v = __ldcg(pe + (size_t)c * stride);
+                        pair_add(h0, l0, v.x, v.y);
+                    }
+                    pair_add(h0, l0, h1, l1);
+                    pair_add(h2, l2, h3, l3);
+                    pair_add(h0, l0, h2, l2);
                 }
-                for (; c < G; ++c) {
-                    const float2 v = __ldcg(pe + (size_t)c * stride);
-                    pair_add(h0, l0, v.x, v.y);
+                for (int o = 16; o >= E; o >>= 1) {
+                    const float hh = __shfl_down_sync(0xffffffffu, h0, o);
+                    const float ll = __shfl_down_sync(0xffffffffu, l0, o);
+                    pair_add(h0, l0, hh, ll);
                 }
-                pair_add(h0, l0, h1, l1);
-                pair_add(h2, l2, h3, l3);
-                pair_add(h0, l0, h2, l2);
-                sums_nxt[e] = (double)h0 + (double)l0;
+                if (s0 == 0 && e < nacc) {
+                    sums_nxt[e] = (double)h0 + (double)l0;
+                    sums32_nxt[e] = h0 + l0;      // the FP64 sum rounded to FP32
+                }
             }
             ++epoch;
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
@@ -917,19 +1130,28 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         first = false;
         __syncthreads();
         // the current point moved (first pass or accepted step): cache its
-        // g and Marquardt diagonal (and, variant S, A packed lower) in shared
-        // memory; variant L keeps reading A from sums[s_cur]
+        // g and Marquardt diagonal in FP64 and FP32 (and, variant S, A packed
+        // lower in FP64 and FP32) in shared memory; variant L keeps reading A
+        // from sums[s_cur]
         if (s_cur == nxt) {
             const double* sc = sums + (size_t)s_cur * NACC_MAX;
+            const float* sc32 = sums32 + (size_t)s_cur * NACC_MAX;
             const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
             if (!LARGE)
                 for (int i = warp; i < P; i += nwarp)
-                    for (int j = lane; j <= i; j += 32) Ac[pidx(i, j)] = __ldcg(sc + acc_index(i, j, nb));
-            for (int i = tid; i < P; i += blockDim.x) gvec[i] = __ldcg(sc + acc_index(i, P, nb));
-            __syncthreads();
+                    for (int j = lane; j <= i; j += 32) {
+                        const int q = acc_index(i, j, nb);
+                        Ac[pidx(i, j)] = __ldcg(sc + q);
+                        Ac32[pidx(i, j)] = __ldcg(sc32 + q);
+                    }
             for (int i = tid; i < P; i += blockDim.x) {
-                const double dd = LARGE ? __ldcg(sc + acc_index(i, i, nb)) : Ac[pidx(i, i)];
+                const int qg = acc_index(i, P, nb), qd = acc_index(i, i, nb);
+                gvec[i] = __ldcg(sc + qg);
+                g32[i] = __ldcg(sc32 + qg);
+                const double dd = __ldcg(sc + qd);
+                const float dd32 = __ldcg(sc32 + qd);
                 dvec[i] = dd > 0.0 ? dd : 1.0;
+                dv32[i] = dd32 > 0.f ? dd32 : 1.f;
             }
             __syncthreads();
         }
@@ -942,11 +1164,15 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             const double lam = s_lam;
             const unsigned long long tf0 = gtimer();
             bool ok;
+            // the FP64 fallback factor goes to this CTA's partial row (consumed
+            // by the reduction, rewritten by the next pass)
             if (LARGE)
-                ok = solve_damped(TileA{sums + (size_t)s_cur * NACC_MAX, nb}, gvec, dvec, lam, P, Jc,
+                ok = solve_damped(TileA{sums + (size_t)s_cur * NACC_MAX, nb},
+                                  TileA32{sums32 + (size_t)s_cur * NACC_MAX, nb}, gvec, g32, dvec, dv32, lam, P, Jc,
                                   partials + (size_t)b * NACC_MAX, sw, delta);
             else
-                ok = solve_damped(PackedA{Ac}, gvec, dvec, lam, P, Jc, reinterpret_cast<double*>(Jc), sw, delta);
+                ok = solve_damped(PackedA{Ac}, PackedA32{Ac32}, gvec, g32, dvec, dv32, lam, P, Jc,
+                                  partials + (size_t)b * NACC_MAX, sw, delta);
             const unsigned long long tf1 = gtimer();
             t_factor += tf1 - tf0;
             // predicted decrease d.g + lam d.D.d (FP32 sums), finiteness, validity
@@ -957,8 +1183,9 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             if (ok && tid < P) {
                 const double di = delta[tid];
                 fin_i = isfinite(di);
-                dg_i = (float)(di * gvec[tid]);
-                dd_i = (float)(dvec[tid] * di * di);
+                const float df = (float)di;
+                dg_i = df * g32[tid];
+                dd_i = dv32[tid] * df * df;
                 trial[tid] = theta[tid] + di;
             }
             if (ok && tid < K) {
@@ -1056,12 +1283,8 @@ k_lm_fit_b(const ImgDesc* __restrict__ imgs, const int* __restrict__ dmap, int n
 // A read from L2; K <= KMAX).
 size_t fit_smem_bytes(int variant) {
     if (variant == 4) return (size_t)PX_SMEM * sizeof(float) + (size_t)UNI_L_FLOATS * sizeof(float);
-    size_t jc = (size_t)JC_FLOATS * sizeof(float);
-    size_t m = (size_t)M_DOUBLES * sizeof(double);
-    size_t red = (size_t)2 * FIT_THREADS * 16 * sizeof(float);
-    size_t u = jc > m ? jc : m;
-    if (red > u) u = red;
-    return (size_t)PX_SMEM * sizeof(float) + m + u;
+    return (size_t)PX_SMEM * sizeof(float) + (size_t)M_DOUBLES * sizeof(double) + (size_t)M32_FLOATS * sizeof(float) +
+           (size_t)JC_FLOATS * sizeof(float);
 }
 size_t fit_smem_bytes() { return fit_smem_bytes(1); }
 

@@ -31,7 +31,7 @@ constexpr size_t OFF_DESC = 0;
 constexpr size_t OFF_OUT = align256(OFF_DESC + sizeof(FitDesc));
 constexpr size_t OFF_BAR = align256(OFF_OUT + sizeof(FitOut));
 constexpr size_t OFF_SUMS = align256(OFF_BAR + sizeof(unsigned));
-constexpr size_t OFF_PART = align256(OFF_SUMS + 2 * NACC_MAX * sizeof(double));
+constexpr size_t OFF_PART = align256(OFF_SUMS + (size_t)SUMS_DOUBLES * sizeof(double));
 constexpr size_t STATIC_BYTES = align256(OFF_PART + (size_t)ASP_STATIC_GRID_MAX * NACC_MAX * sizeof(double));
 constexpr int STATIC_NB = ((4 * ASP_STATIC_KMAX + 1) + 3) / 4;
 static_assert(STATIC_NB * (STATIC_NB + 1) / 2 <= FIT_THREADS, "the one-tile-per-thread fit variant must cover K");
