@@ -23,7 +23,7 @@ constexpr int PX_SMEM = 12288;                     // target pixels one CTA keep
 constexpr int FIT_PX_PER_CTA = 96;                 // default fit tile: window pixels per CTA (measured best on the 1024^2 workload)
 constexpr int RET_MAX = 1024;                      // retained-list capacity
 constexpr int RED_THREADS = 256;                   // threads of the image-wide kernels
-constexpr unsigned SPIN_LIMIT = 1u << 25;          // bounded grid-barrier wait (~1 s)
+constexpr unsigned SPIN_LIMIT = 1u << 22;          // bounded grid-barrier wait (polls of ~0.3 us: ~1-2 s)
 
 constexpr double LOG2E = 1.4426950408889634074;
 
@@ -136,6 +136,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+// Arrival with release semantics (orders this thread's earlier writes, and
+// those it observed through a block barrier, before the increment).
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
 // |a| beats |b|, ties: lower scale index, then lower flat index.

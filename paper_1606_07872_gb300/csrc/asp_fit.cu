@@ -34,8 +34,8 @@ constexpr int CH_XL = 64;       // chunk pixels of the large-active-set variant
 // FP32 factor with its panel.
 constexpr int KMAX_S = 32;
 constexpr int PMAX_S = 4 * KMAX_S;
-constexpr int M_DOUBLES = PMAX_S * (PMAX_S + 1) / 2;          // cached A of S (FP64 and an FP32 copy)
-constexpr int M32_FLOATS = (M_DOUBLES + 3) / 4 * 4;
+constexpr int NB_S = (PMAX_S + 4) / 4;
+constexpr int NACC_S = NB_S * (NB_S + 1) / 2 * 16;            // cached sums of S, tile order (FP64 and FP32)
 constexpr int UNI_L_FLOATS = ((PMAX + 1) * (PMAX + 2) / 2 + 3) / 4 * 4 + 8 * (PMAX + 4);
 static_assert(UNI_L_FLOATS >= CH_XL * NAP_MAX, "J chunk of the large variant must fit its union region");
 
@@ -73,11 +73,14 @@ __device__ __forceinline__ int acc_index(int i, int j, int nb) {
     return tile_index(i >> 2, j >> 2, nb) * 16 + (i & 3) * 4 + (j & 3);
 }
 
+// Grid barrier of the fit group: a release increment and acquire polls by
+// thread 0, block barriers around them (the block barrier makes the CTA's
+// writes visible to thread 0; release and acquire are cumulative).  Bounded:
+// after SPIN_LIMIT polls the CTA records a timeout and returns.
 __device__ void grid_barrier(unsigned* bar, unsigned target, int* s_err, int* g_err) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
+        red_release_add_u32(bar, 1u);
         unsigned spins = 0;
         while (ld_acquire_u32(bar) < target) {
             if (++spins > SPIN_LIMIT) {
@@ -85,9 +88,7 @@ __device__ void grid_barrier(unsigned* bar, unsigned target, int* s_err, int* g_
                 atomicExch(g_err, ASP_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
         }
-        __threadfence();
     }
     __syncthreads();
 }
@@ -655,11 +656,12 @@ __device__ void trsv_fwd_block(const float* __restrict__ M, int P, const float* 
 }
 
 // A (the normal-equation matrix of the current point, FP64, symmetric)
-// as the solve reads it: packed lower in shared memory (variant S), or the
-// tile-ordered accumulator buffer in global memory / L2 (variant L).
-struct PackedA {
+// as the solve reads it: the tile-ordered accumulator sums, copied to shared
+// memory (variant S) or read from global memory / L2 (variant L).
+struct SmemTileA {
     const double* p;
-    __device__ __forceinline__ double operator()(int i, int j) const { return i >= j ? p[pidx(i, j)] : p[pidx(j, i)]; }
+    int nb;
+    __device__ __forceinline__ double operator()(int i, int j) const { return p[acc_index(i, j, nb)]; }
 };
 struct TileA {
     const double* p;
@@ -667,9 +669,10 @@ struct TileA {
     __device__ __forceinline__ double operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
 };
 // The same matrix rounded to FP32 (the reduction writes both copies).
-struct PackedA32 {
+struct SmemTileA32 {
     const float* p;
-    __device__ __forceinline__ float operator()(int i, int j) const { return i >= j ? p[pidx(i, j)] : p[pidx(j, i)]; }
+    int nb;
+    __device__ __forceinline__ float operator()(int i, int j) const { return p[acc_index(i, j, nb)]; }
 };
 struct TileA32 {
     const float* p;
@@ -820,8 +823,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     // variant S: A at the current point cached in shared memory; variant L:
     // A read from the sums buffer (L2), the union region follows Ts
     double* Ac = LARGE ? nullptr : reinterpret_cast<double*>(Ts + PX_SMEM);
-    float* Ac32 = LARGE ? nullptr : reinterpret_cast<float*>(Ac + M_DOUBLES);
-    float* Jc = LARGE ? Ts + PX_SMEM : Ac32 + M32_FLOATS;                      // union region
+    float* Ac32 = LARGE ? nullptr : reinterpret_cast<float*>(Ac + NACC_S);
+    float* Jc = LARGE ? Ts + PX_SMEM : Ac32 + NACC_S;                          // union region
     float* red = Jc;
     float* sums32 = reinterpret_cast<float*>(sums + 2 * NACC_MAX);            // FP32 copies of both buffers
 
@@ -1057,21 +1060,24 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 const int e = e0 + el;
                 float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
                 if (e < nacc) {
+                    // batches of RB loads in flight, then four pair chains
+                    // (chain k % 4); absent CTAs load nothing and add zero
+                    constexpr int RB = 16;
                     const float2* pe = pbase + e;
-                    int c = s0;
-                    for (; c + 3 * T < G; c += 4 * T) {
-                        const float2 v0 = __ldcg(pe + (size_t)c * stride);
-                        const float2 v1 = __ldcg(pe + (size_t)(c + T) * stride);
-                        const float2 v2 = __ldcg(pe + (size_t)(c + 2 * T) * stride);
-                        const float2 v3 = __ldcg(pe + (size_t)(c + 3 * T) * stride);
-                        pair_add(h0, l0, v0.x, v0.y);
-                        pair_add(h1, l1, v1.x, v1.y);
-                        pair_add(h2, l2, v2.x, v2.y);
-                        pair_add(h3, l3, v3.x, v3.y);
-                    }
-                    for (; c < G; c += T) {
-                        const float2 v = __ldcg(pe + (size_t)c * stride);
-                        pair_add(h0, l0, v.x, v.y);
+                    for (int cb = s0; cb < G; cb += RB * T) {
+                        float2 v[RB];
+#pragma unroll
+                        for (int k = 0; k < RB; ++k) {
+                            const int c = cb + k * T;
+                            v[k] = c < G ? __ldcg(pe + (size_t)c * stride) : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int k = 0; k < RB; k += 4) {
+                            pair_add(h0, l0, v[k].x, v[k].y);
+                            pair_add(h1, l1, v[k + 1].x, v[k + 1].y);
+                            pair_add(h2, l2, v[k + 2].x, v[k + 2].y);
+                            pair_add(h3, l3, v[k + 3].x, v[k + 3].y);
+                        }
                     }
                     pair_add(h0, l0, h1, l1);
                     pair_add(h2, l2, h3, l3);
@@ -1129,27 +1135,28 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         if (s_acc && tid < P) theta[tid] = trial[tid];
         first = false;
         __syncthreads();
-        // the current point moved (first pass or accepted step): cache its
-        // g and Marquardt diagonal in FP64 and FP32 (and, variant S, A packed
-        // lower in FP64 and FP32) in shared memory; variant L keeps reading A
-        // from sums[s_cur]
+        // the current point moved (first pass or accepted step): variant S
+        // copies its sums (FP64 and FP32, tile order) to shared memory, a
+        // flat batched copy; both cache g and the Marquardt diagonal
         if (s_cur == nxt) {
             const double* sc = sums + (size_t)s_cur * NACC_MAX;
             const float* sc32 = sums32 + (size_t)s_cur * NACC_MAX;
-            const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-            if (!LARGE)
-                for (int i = warp; i < P; i += nwarp)
-                    for (int j = lane; j <= i; j += 32) {
-                        const int q = acc_index(i, j, nb);
-                        Ac[pidx(i, j)] = __ldcg(sc + q);
-                        Ac32[pidx(i, j)] = __ldcg(sc32 + q);
-                    }
+            if (!LARGE) {
+#pragma unroll 4
+                for (int e = tid; e < nacc; e += blockDim.x) {
+                    Ac[e] = __ldcg(sc + e);
+                    Ac32[e] = __ldcg(sc32 + e);
+                }
+                __syncthreads();
+            }
+            const double* ad = LARGE ? sc : Ac;
+            const float* af = LARGE ? sc32 : Ac32;
             for (int i = tid; i < P; i += blockDim.x) {
                 const int qg = acc_index(i, P, nb), qd = acc_index(i, i, nb);
-                gvec[i] = __ldcg(sc + qg);
-                g32[i] = __ldcg(sc32 + qg);
-                const double dd = __ldcg(sc + qd);
-                const float dd32 = __ldcg(sc32 + qd);
+                gvec[i] = LARGE ? __ldcg(ad + qg) : ad[qg];
+                g32[i] = LARGE ? __ldcg(af + qg) : af[qg];
+                const double dd = LARGE ? __ldcg(ad + qd) : ad[qd];
+                const float dd32 = LARGE ? __ldcg(af + qd) : af[qd];
                 dvec[i] = dd > 0.0 ? dd : 1.0;
                 dv32[i] = dd32 > 0.f ? dd32 : 1.f;
             }
@@ -1171,7 +1178,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                                   TileA32{sums32 + (size_t)s_cur * NACC_MAX, nb}, gvec, g32, dvec, dv32, lam, P, Jc,
                                   partials + (size_t)b * NACC_MAX, sw, delta);
             else
-                ok = solve_damped(PackedA{Ac}, PackedA32{Ac32}, gvec, g32, dvec, dv32, lam, P, Jc,
+                ok = solve_damped(SmemTileA{Ac, nb}, SmemTileA32{Ac32, nb}, gvec, g32, dvec, dv32, lam, P, Jc,
                                   partials + (size_t)b * NACC_MAX, sw, delta);
             const unsigned long long tf1 = gtimer();
             t_factor += tf1 - tf0;
@@ -1283,7 +1290,7 @@ k_lm_fit_b(const ImgDesc* __restrict__ imgs, const int* __restrict__ dmap, int n
 // A read from L2; K <= KMAX).
 size_t fit_smem_bytes(int variant) {
     if (variant == 4) return (size_t)PX_SMEM * sizeof(float) + (size_t)UNI_L_FLOATS * sizeof(float);
-    return (size_t)PX_SMEM * sizeof(float) + (size_t)M_DOUBLES * sizeof(double) + (size_t)M32_FLOATS * sizeof(float) +
+    return (size_t)PX_SMEM * sizeof(float) + (size_t)NACC_S * (sizeof(double) + sizeof(float)) +
            (size_t)JC_FLOATS * sizeof(float);
 }
 size_t fit_smem_bytes() { return fit_smem_bytes(1); }
