@@ -37,7 +37,7 @@ constexpr int PMAX_S = 4 * KMAX_S;
 constexpr int NB_S = (PMAX_S + 4) / 4;
 constexpr int NACC_S = NB_S * (NB_S + 1) / 2 * 16;            // cached sums of S, tile order (FP64 and FP32)
 constexpr int UNI_L_FLOATS = ((PMAX + 1) * (PMAX + 2) / 2 + 3) / 4 * 4 + 8 * (PMAX + 4);
-static_assert(UNI_L_FLOATS >= CH_XL * NAP_MAX, "J chunk of the large variant must fit its union region");
+static_assert(UNI_L_FLOATS >= CH_XL * (NAP_MAX + 4), "J chunk of the large variant must fit its union region");
 
 struct MemberFrame {
     float a, c, iw2, iw3, fx, fy;   // c = log2(e) / (2 w^2)
@@ -288,7 +288,7 @@ __host__ __device__ constexpr int lp_offset(int P4) { return ((P4 + 1) * (P4 + 2
 // sums of several pixel groups (2 x FIT_THREADS x 16 floats).
 constexpr int JC_FLOATS = lp_offset(PMAX_S) + 8 * (PMAX_S + 4);
 static_assert(JC_FLOATS >= 2 * FIT_THREADS * 16, "leaf sums must fit the union region");
-static_assert(JC_FLOATS / (PMAX_S + 4) >= 64, "the J chunk of S must hold 64 rows");
+static_assert(JC_FLOATS / (PMAX_S + 8) >= 64, "the J chunk of S must hold 64 rows");
 
 // Factor the PBxPB diagonal block at j0 (lower, packed in M) in registers,
 // every lane of the calling warp redundantly; lanes 0..PB-1 store row
@@ -668,16 +668,15 @@ struct TileA {
     int nb;
     __device__ __forceinline__ double operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
 };
-// The same matrix rounded to FP32 (the reduction writes both copies).
-struct SmemTileA32 {
-    const float* p;
-    int nb;
-    __device__ __forceinline__ float operator()(int i, int j) const { return p[acc_index(i, j, nb)]; }
-};
-struct TileA32 {
-    const float* p;
-    int nb;
-    __device__ __forceinline__ float operator()(int i, int j) const { return __ldcg(p + acc_index(i, j, nb)); }
+// The FP32 copy of A (the reduction writes both) for the solve's setup: its
+// tile-ordered entries (shared memory for variant S, global memory / L2 for
+// variant L), the tile table (tile -> (bi, bj)) and the diagonal.
+struct TiledA32 {
+    const float* p;          // nacc entries, tile order
+    const short2* ttab;
+    const float* diag;       // A_ii, i < P
+    int nacc;
+    bool global;
 };
 
 constexpr float REFINE_INV_MAX = 10.0f;   // refine when some 1/L_jj of the scaled factor exceeds this
@@ -692,12 +691,12 @@ struct SolveWork {              // shared-memory scratch of solve_damped
 // PB; P4 = P rounded up to PB.  The scaled matrix is built from the FP32
 // copy A32 of A (g32, dv32 likewise): no FP64 instruction outside the
 // refinement.  Returns false if the FP32 factor fails.
-template <int PB, class AT, class AT32>
-__device__ bool solve_scaled_fp32(const AT& A, const AT32& A32, const double* __restrict__ g,
+template <int PB, class AT>
+__device__ bool solve_scaled_fp32(const AT& A, const TiledA32& A32, const double* __restrict__ g,
                                   const float* __restrict__ g32, const double* __restrict__ dv,
                                   const float* __restrict__ dv32, double lam, int P, void* uni, SolveWork& w,
                                   double* __restrict__ delta) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     const int P4 = (P + PB - 1) & ~(PB - 1);   // padded with identity rows: every block of the factor is full
     float* L32 = reinterpret_cast<float*>(uni);
     float* Lp = L32 + lp_offset(P4);
@@ -706,7 +705,7 @@ __device__ bool solve_scaled_fp32(const AT& A, const AT32& A32, const double* __
     for (int i = tid; i < P4; i += blockDim.x) {
         float sc = 1.0f, m = 1.0f;
         if (i < P) {
-            m = fmaf(lam32, dv32[i], A32(i, i));
+            m = fmaf(lam32, dv32[i], A32.diag[i]);
             sc = m > 0.f ? rsqrtf(m) : 1.0f;
         }
         w.sf[i] = sc;
@@ -714,15 +713,21 @@ __device__ bool solve_scaled_fp32(const AT& A, const AT32& A32, const double* __
     }
     if (tid == 0) w.flag = 0;
     __syncthreads();
-    for (int i = warp; i <= P4; i += nwarp) {
-        const float si = i < P ? w.sf[i] : 0.f;
-        for (int j = lane; j <= i && j < P4; j += 32) {
-            float v;
-            if (i < P && j < P) v = (i == j ? w.mf[i] : A32(i, j)) * si * w.sf[j];
-            else if (i == P4) v = j < P ? w.sf[j] * g32[j] : 0.f;    // right-hand side row S g
-            else v = i == j ? 1.f : 0.f;                            // identity padding
-            L32[pidx(i, j)] = v;
-        }
+    // S (A + lam D) S into the packed lower factor, straight from the tile
+    // order (entry e of tile (bi, bj), bi <= bj, is (i, j) = (4 bi + e/4 % 4,
+    // 4 bj + e % 4); diagonal tiles also hold i > j, skipped)
+#pragma unroll 4
+    for (int e = tid; e < A32.nacc; e += blockDim.x) {
+        const float a = A32.global ? __ldcg(A32.p + e) : A32.p[e];
+        const short2 bij = A32.ttab[e >> 4];
+        const int i = 4 * bij.x + ((e >> 2) & 3), j = 4 * bij.y + (e & 3);
+        if (i <= j && j < P) L32[pidx(j, i)] = (i == j ? w.mf[j] : a) * w.sf[j] * w.sf[i];
+    }
+    // right-hand side row S g; identity padding rows P..P4-1
+    for (int j = tid; j < P4; j += blockDim.x) L32[pidx(P4, j)] = j < P ? w.sf[j] * g32[j] : 0.f;
+    for (int q = tid; q < (P4 - P) * P4; q += blockDim.x) {
+        const int i = P + q / P4, j = q % P4;
+        if (j <= i) L32[pidx(i, j)] = i == j ? 1.f : 0.f;
     }
     __syncthreads();
     if (chol_tiled<PB>(L32, Lp, P4, w.inv32, &w.flag, lp_ld)) {
@@ -782,8 +787,8 @@ __device__ bool solve_scaled_fp32(const AT& A, const AT32& A32, const double* __
 // (P (P+1) / 2 doubles: shared memory for variant S, the CTA's partial row
 // in global memory for variant L).  Returns false when the damped matrix is
 // not positive definite.
-template <class AT, class AT32>
-__device__ bool solve_damped(const AT& A, const AT32& A32, const double* __restrict__ g, const float* __restrict__ g32,
+template <class AT>
+__device__ bool solve_damped(const AT& A, const TiledA32& A32, const double* __restrict__ g, const float* __restrict__ g32,
                              const double* __restrict__ dv, const float* __restrict__ dv32, double lam, int P,
                              void* uni, double* m64, SolveWork& w, double* __restrict__ delta) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
@@ -822,8 +827,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     float* Ts = reinterpret_cast<float*>(smem_raw);                          // PX_SMEM floats
     // variant S: A at the current point cached in shared memory; variant L:
     // A read from the sums buffer (L2), the union region follows Ts
-    double* Ac = LARGE ? nullptr : reinterpret_cast<double*>(Ts + PX_SMEM);
-    float* Ac32 = LARGE ? nullptr : reinterpret_cast<float*>(Ac + NACC_S);
+    double* Ac = LARGE ? nullptr : reinterpret_cast<double*>(Ts + PX_SMEM);   // FP64 sums, tile order
+    float* Ac32 = LARGE ? nullptr : reinterpret_cast<float*>(Ac + NACC_S);    // FP32 sums, tile order
     float* Jc = LARGE ? Ts + PX_SMEM : Ac32 + NACC_S;                          // union region
     float* red = Jc;
     float* sums32 = reinterpret_cast<float*>(sums + 2 * NACC_MAX);            // FP32 copies of both buffers
@@ -832,10 +837,11 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     __shared__ MemberFrame fr[KMAX];
     __shared__ short2 ttab[NTILES_MAX];
     __shared__ double theta[PMAX], trial[PMAX], delta[PMAX], gvec[PMAX], dvec[PMAX];
-    __shared__ float g32[PMAX], dv32[PMAX];
+    __shared__ float g32[PMAX], dv32[PMAX], a32d[PMAX];
     __shared__ SolveWork sw;
     __shared__ double s_lam, s_chi2, s_chi2_init;
-    __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc;
+    __shared__ double s_lam_acc, s_lam_rej, s_thr;   // the decision's FP64 terms, computed during the pass
+    __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc, s_small, s_rej_stall;
     __shared__ float s_pred[2];
 
     const int tid = threadIdx.x;
@@ -856,7 +862,10 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     const long long s0 = Wn * b / G, s1 = Wn * (b + 1) / G;
     const int slen = (int)(s1 - s0);
     const bool in_smem = d.smem_ok != 0;
-    const int CH = LARGE ? CH_XL : min(NAp <= 64 ? CH_SMALL : CH_LARGE, JC_FLOATS / NAp);
+    // J rows: stride of an odd number of float4s, so the row-per-thread
+    // stores of phase A hit distinct bank groups
+    const int JS = (nb & 1) ? NAp : NAp + 4;
+    const int CH = LARGE ? CH_XL : min(NAp <= 64 ? CH_SMALL : CH_LARGE, JC_FLOATS / JS);
     const int chi_idx = acc_index(P, P, nb);
 
     // ---- tile table and thread -> (tile, group) assignment
@@ -898,6 +907,15 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     for (int i = tid; i < P; i += blockDim.x) trial[i] = d.theta0[i];
     __syncthreads();
 
+    // pixel coordinates of this thread's J row in the first chunk (the only
+    // chunk when the slice fits one), computed once for all passes
+    int x_first = 0, y_first = 0;
+    if (tid < CH && tid < slen) {
+        const long long gi = s0 + tid;
+        y_first = d.wy0 + (int)(gi / d.ww);
+        x_first = d.wx0 + (int)(gi % d.ww);
+    }
+
     unsigned epoch = 0;
     bool first = true;
     // phase clocks (CTA 0, thread 0): pass, CTA + cross-CTA reduction, LM logic + solves
@@ -905,6 +923,16 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     while (true) {
         // ================= pixel pass at trial[] =================
         if (tid < K) make_frame(&trial[4 * tid], fr[tid]);
+        if (tid == (int)blockDim.x - 1 && !first) {
+            // the LM decision's FP64 arithmetic (a division among it), done
+            // here by a thread without a J row so that it stays off the
+            // critical path: lambda after an accepted or rejected step and
+            // the flatness threshold rtol chi^2
+            s_lam_acc = fmax(s_lam / lmc.lambda_down, lmc.lambda_min);
+            s_lam_rej = s_lam * lmc.lambda_up;
+            s_rej_stall = s_lam_rej > lmc.lambda_max;
+            s_thr = lmc.rtol * s_chi2;
+        }
         __syncthreads();
         const int nxt = 1 - s_cur;
         double* sums_nxt = sums + (size_t)nxt * NACC_MAX;
@@ -925,13 +953,18 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             const int cn = min(CH, slen - c0);
             // phase A: one pixel row of [J | r] per thread
             if (tid < CH) {
-                float* row = Jc + tid * NAp;
+                float* row = Jc + tid * JS;
                 bool live = tid < cn;
                 int x = 0, y = 0;
                 if (live) {
-                    long long gi = s0 + c0 + tid;
-                    y = d.wy0 + (int)(gi / d.ww);
-                    x = d.wx0 + (int)(gi % d.ww);
+                    if (c0 == 0) {
+                        x = x_first;
+                        y = y_first;
+                    } else {
+                        const long long gi = s0 + c0 + tid;
+                        y = d.wy0 + (int)(gi / d.ww);
+                        x = d.wx0 + (int)(gi % d.ww);
+                    }
                     if (d.use_mask) {
                         double ddx = x - d.mcx, ddy = y - d.mcy;
                         live = ddx * ddx + ddy * ddy <= d.mr2;
@@ -969,8 +1002,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         if (t < ntiles) {
                             const short2 bij = ttab[t];
                             for (int l = l0; l < l1; ++l) {
-                                const float4 av = *reinterpret_cast<const float4*>(Jc + l * NAp + 4 * bij.x);
-                                const float4 bv = *reinterpret_cast<const float4*>(Jc + l * NAp + 4 * bij.y);
+                                const float4 av = *reinterpret_cast<const float4*>(Jc + l * JS + 4 * bij.x);
+                                const float4 bv = *reinterpret_cast<const float4*>(Jc + l * JS + 4 * bij.y);
                                 const float aa[4] = {av.x, av.y, av.z, av.w};
                                 const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
@@ -1032,8 +1065,25 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             // the pixel groups' pairs combined error-free in FP32, in group order
             __syncthreads();
             for (int e = tid; e < nacc; e += blockDim.x) {
+                // up to 4 groups in order; more as four chains (group g in
+                // chain g % 4) joined pairwise
                 float sh = 0.f, sl = 0.f;
-                for (int g = 0; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                if (n_groups <= 4) {
+                    for (int g = 0; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                } else {
+                    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
+                    int g = 0;
+                    for (; g + 3 < n_groups; g += 4) {
+                        pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                        pair_add(h1, l1, red[(g + 1) * nacc + e], -red[(n_groups + g + 1) * nacc + e]);
+                        pair_add(h2, l2, red[(g + 2) * nacc + e], -red[(n_groups + g + 2) * nacc + e]);
+                        pair_add(h3, l3, red[(g + 3) * nacc + e], -red[(n_groups + g + 3) * nacc + e]);
+                    }
+                    for (; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                    pair_add(sh, sl, h1, l1);
+                    pair_add(h2, l2, h3, l3);
+                    pair_add(sh, sl, h2, l2);
+                }
                 if (G == 1) { sums_nxt[e] = (double)sh + (double)sl; sums32_nxt[e] = sh + sl; }
                 else reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX)[e] = make_float2(sh, sl);
             }
@@ -1102,14 +1152,6 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
 
         t1 = gtimer(); t_red += t1 - t0; t0 = t1;
         // ================= LM decision (identical in every CTA) =================
-        // every step below xtol of its scale (|a|; w for centre and width)
-        int small_i = 1;
-        if (!first && tid < P) {
-            double sc = (tid & 3) == 0 ? fabs(theta[tid]) : theta[(tid & ~3) + 3];
-            if (sc == 0.0) sc = 1.0;
-            small_i = fabs(delta[tid]) < lmc.xtol * sc;
-        }
-        const int small = __syncthreads_and(small_i);
         if (tid == 0) {
             const double chi2_t = __ldcg(sums_nxt + chi_idx);     // FP64 acceptance test
             s_passes += 1;
@@ -1120,15 +1162,15 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 s_chi2_init = chi2_t;
             } else if (chi2_t < s_chi2) {
                 // relative decrease below rtol: (chi2 - chi2_t) < rtol chi2
-                const bool flat = !(s_chi2 - chi2_t >= lmc.rtol * s_chi2) || !(s_chi2 > 0.0);
+                const bool flat = !(s_chi2 - chi2_t >= s_thr) || !(s_chi2 > 0.0);
                 s_acc = 1;
                 s_cur = nxt;
                 s_chi2 = chi2_t;
-                s_lam = fmax(s_lam / lmc.lambda_down, lmc.lambda_min);
-                if (flat || small) { s_status = ASP_LM_CONVERGED; s_done = 1; }
+                s_lam = s_lam_acc;
+                if (flat || s_small) { s_status = ASP_LM_CONVERGED; s_done = 1; }
             } else {
-                s_lam *= lmc.lambda_up;
-                if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
+                s_lam = s_lam_rej;
+                if (s_rej_stall) { s_status = ASP_LM_STALLED; s_done = 1; }
             }
         }
         __syncthreads();
@@ -1137,7 +1179,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         __syncthreads();
         // the current point moved (first pass or accepted step): variant S
         // copies its sums (FP64 and FP32, tile order) to shared memory, a
-        // flat batched copy; both cache g and the Marquardt diagonal
+        // flat batched copy; both cache g, diag A and the Marquardt diagonal
         if (s_cur == nxt) {
             const double* sc = sums + (size_t)s_cur * NACC_MAX;
             const float* sc32 = sums32 + (size_t)s_cur * NACC_MAX;
@@ -1158,6 +1200,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 const double dd = LARGE ? __ldcg(ad + qd) : ad[qd];
                 const float dd32 = LARGE ? __ldcg(af + qd) : af[qd];
                 dvec[i] = dd > 0.0 ? dd : 1.0;
+                a32d[i] = dd32;
                 dv32[i] = dd32 > 0.f ? dd32 : 1.f;
             }
             __syncthreads();
@@ -1175,21 +1218,26 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             // by the reduction, rewritten by the next pass)
             if (LARGE)
                 ok = solve_damped(TileA{sums + (size_t)s_cur * NACC_MAX, nb},
-                                  TileA32{sums32 + (size_t)s_cur * NACC_MAX, nb}, gvec, g32, dvec, dv32, lam, P, Jc,
+                                  TiledA32{sums32 + (size_t)s_cur * NACC_MAX, ttab, a32d, nacc, true}, gvec, g32,
+                                  dvec, dv32, lam, P, Jc,
                                   partials + (size_t)b * NACC_MAX, sw, delta);
             else
-                ok = solve_damped(SmemTileA{Ac, nb}, SmemTileA32{Ac32, nb}, gvec, g32, dvec, dv32, lam, P, Jc,
+                ok = solve_damped(SmemTileA{Ac, nb}, TiledA32{Ac32, ttab, a32d, nacc, false}, gvec, g32, dvec, dv32, lam, P, Jc,
                                   partials + (size_t)b * NACC_MAX, sw, delta);
             const unsigned long long tf1 = gtimer();
             t_factor += tf1 - tf0;
             // predicted decrease d.g + lam d.D.d (FP32 sums), finiteness, validity
             if (tid == 0) { s_pred[0] = 0.f; s_pred[1] = 0.f; }
             __syncthreads();
-            int fin_i = 1, valid_i = 1;
+            int fin_i = 1, valid_i = 1, small_i = 1;
             float dg_i = 0.f, dd_i = 0.f;
             if (ok && tid < P) {
                 const double di = delta[tid];
                 fin_i = isfinite(di);
+                // every step below xtol of its scale (|a|; w for centre and width)
+                double sc = (tid & 3) == 0 ? fabs(theta[tid]) : theta[(tid & ~3) + 3];
+                if (sc == 0.0) sc = 1.0;
+                small_i = fabs(di) < lmc.xtol * sc;
                 const float df = (float)di;
                 dg_i = df * g32[tid];
                 dd_i = dv32[tid] * df * df;
@@ -1212,6 +1260,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             }
             const int fin = __syncthreads_and(fin_i) && ok;
             const int valid = __syncthreads_and(valid_i);
+            const int small = __syncthreads_and(small_i);
             if (tid == 0) {
                 s_iters += 1;
                 s_go = 0;
@@ -1222,6 +1271,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     s_status = ASP_LM_CONVERGED; s_done = 1;
                 } else if (valid) {
                     s_go = 1;
+                    s_small = small;
                 } else {
                     s_lam *= lmc.lambda_up;
                     if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
