@@ -292,7 +292,7 @@ asp_status asp_launch_count(asp_ctx* ctx, int64_t* n);
  * and calls that overlap on the GPU (other threads or streams) race. */
 #define ASP_STATIC_KMAX 8
 #define ASP_STATIC_GRID_MAX 32
-#define ASP_STATIC_SCRATCH_BYTES 5944320
+#define ASP_STATIC_SCRATCH_BYTES 5960704
 asp_status asp_fit_static(const float* image_dev, int H, int W, const asp_gauss* init, int n, int n_old,
                           double omega_min, const asp_params* lm, asp_gauss* out, asp_fit_info* info,
                           void* stream);

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libasp.so")
 ASP_KMAX = 50
 ASP_STATIC_KMAX = 8
 ASP_STATIC_GRID_MAX = 32
-ASP_STATIC_SCRATCH_BYTES = 5944320
+ASP_STATIC_SCRATCH_BYTES = 5960704
 
 ASP_OK = 0
 STATUS_NAMES = {0: "ASP_OK", 1: "ASP_ERR_INVALID_ARG", 2: "ASP_ERR_CUDA", 3: "ASP_ERR_OOM", 4: "ASP_ERR_NAN",

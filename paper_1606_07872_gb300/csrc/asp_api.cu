@@ -466,7 +466,7 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     ctx->tpt = fit_tpt_for(ctx->p.k_max);
     int bps = 0;
     if (fit_configure(ctx->tpt, &bps) != cudaSuccess || bps < 1) return bail(ASP_ERR_CUDA);
-    ctx->g_max = ctx->num_sms * bps;
+    ctx->g_max = std::min(ctx->num_sms * bps, FIT_GRID_MAX);
 
     // device parameters
     ctx->dp.gain = ctx->p.gain;
@@ -1390,7 +1390,7 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
     b->px_per_cta = params->fit_px_per_cta;
     int bps = 0;
     if (fit_configure(b->tpt, &bps) != cudaSuccess || bps < 1) return bail(ASP_ERR_CUDA);
-    b->g_total = b->num_sms * bps;
+    b->g_total = std::min(b->num_sms * bps, FIT_GRID_MAX);
     if (n > b->g_total) return bail(ASP_ERR_UNSUPPORTED);
     if (cudaMalloc(&b->bars, sizeof(unsigned) * n) != cudaSuccess ||
         cudaMalloc(&b->dmap, sizeof(int) * (n + 1)) != cudaSuccess ||

@@ -14,7 +14,10 @@ constexpr int NAP_MAX = PMAX + 4;                  // [J | r] columns padded to 
 constexpr int NB_MAX = NAP_MAX / 4;                // 4x4 tiles per side
 constexpr int NTILES_MAX = NB_MAX * (NB_MAX + 1) / 2;
 constexpr int NACC_MAX = NTILES_MAX * 16;          // accumulator entries (tile order)
-constexpr int SUMS_DOUBLES = 3 * NACC_MAX;         // fit sums: two FP64 buffers, then their two FP32 copies
+constexpr int FIT_GRID_MAX = 1024;                 // CTAs of one fit group (at most)
+// fit sums: two FP64 buffers, their two FP32 copies, then each CTA's chi^2
+// partial pair (two buffers of FIT_GRID_MAX float2)
+constexpr int SUMS_DOUBLES = 3 * NACC_MAX + 2 * FIT_GRID_MAX;
 constexpr int MAX_TERMS = 2 * KMAX;                // subtraction terms per iteration
 constexpr int T1_SLACK_ROWS = 16;                  // zeroed rows behind the last subtraction term
 constexpr int MAX_SCALES = 8;                      // smoothing scales

@@ -832,6 +832,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     float* Jc = LARGE ? Ts + PX_SMEM : Ac32 + NACC_S;                          // union region
     float* red = Jc;
     float* sums32 = reinterpret_cast<float*>(sums + 2 * NACC_MAX);            // FP32 copies of both buffers
+    float2* chib = reinterpret_cast<float2*>(sums + 3 * NACC_MAX);            // chi^2 partials, 2 x FIT_GRID_MAX
 
     __shared__ FitDesc d;
     __shared__ MemberFrame fr[KMAX];
@@ -841,6 +842,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     __shared__ SolveWork sw;
     __shared__ double s_lam, s_chi2, s_chi2_init;
     __shared__ double s_lam_acc, s_lam_rej, s_thr;   // the decision's FP64 terms, computed during the pass
+    __shared__ double s_chi2_t;                       // chi^2 at the trial point
     __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc, s_small, s_rej_stall;
     __shared__ float s_pred[2];
 
@@ -917,6 +919,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     }
 
     unsigned epoch = 0;
+    int npass = 0;
     bool first = true;
     // phase clocks (CTA 0, thread 0): pass, CTA + cross-CTA reduction, LM logic + solves
     unsigned long long t_pass = 0, t_red = 0, t_solve = 0, t_factor = 0, t_subst = 0, t0 = gtimer(), t1;
@@ -936,6 +939,11 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         __syncthreads();
         const int nxt = 1 - s_cur;
         double* sums_nxt = sums + (size_t)nxt * NACC_MAX;
+        // this pass's chi^2 partials: buffers alternate, so a CTA's write two
+        // passes on follows every CTA's read (a grid barrier lies between)
+        float2* chib_p = chib + (npass & 1) * FIT_GRID_MAX;
+        const int chi_t = chi_idx >> 4, chi_e = chi_idx & 15;
+        ++npass;
         float* sums32_nxt = sums32 + (size_t)nxt * NACC_MAX;
         // the tiles in rounds of TPT per thread (one round unless the active
         // set is large), re-evaluating the J rows each round
@@ -1047,7 +1055,10 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     } else {
                         float2* dst = reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX) + t * 16;
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) dst[e] = make_float2(ks[q][e], -kc[q][e]);
+                        for (int e = 0; e < 16; ++e) {
+                            dst[e] = make_float2(ks[q][e], -kc[q][e]);
+                            if (t == chi_t && e == chi_e) chib_p[b] = make_float2(ks[q][e], -kc[q][e]);
+                        }
                     }
                 }
             }
@@ -1085,15 +1096,71 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     pair_add(sh, sl, h2, l2);
                 }
                 if (G == 1) { sums_nxt[e] = (double)sh + (double)sl; sums32_nxt[e] = sh + sl; }
-                else reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX)[e] = make_float2(sh, sl);
+                else {
+                    reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX)[e] = make_float2(sh, sl);
+                    if (e == chi_idx) chib_p[b] = make_float2(sh, sl);
+                }
             }
         }
 
-        // ---- cross-CTA reduction (fixed order -> identical in every CTA)
+        // ---- chi^2 at the trial point first: after a grid barrier every CTA
+        // combines the CTAs' chi^2 pairs (fixed order -> identical everywhere)
         if (G > 1) {
             ++epoch;
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
             if (s_err) return;
+            if (tid < 32) {
+                // lane l combines CTAs l, l + 32, ... (all loads in flight first)
+                float h = 0.f, l = 0.f;
+                for (int cb = tid; cb < G; cb += 8 * 32) {
+                    float2 v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int c = cb + 32 * k;
+                        v[k] = c < G ? __ldcg(chib_p + c) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) pair_add(h, l, v[k].x, v[k].y);
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const float hh = __shfl_down_sync(0xffffffffu, h, o);
+                    const float ll = __shfl_down_sync(0xffffffffu, l, o);
+                    pair_add(h, l, hh, ll);
+                }
+                if (tid == 0) s_chi2_t = (double)h + (double)l;
+            }
+        } else if (tid == 0) {
+            s_chi2_t = 0.0;
+        }
+        __syncthreads();
+        if (G == 1 && tid == 0) s_chi2_t = sums_nxt[chi_idx];
+        // ================= LM decision (identical in every CTA) =================
+        if (tid == 0) {
+            const double chi2_t = s_chi2_t;                      // FP64 acceptance test
+            s_passes += 1;
+            s_acc = 0;
+            if (first) {
+                s_cur = nxt;
+                s_chi2 = chi2_t;
+                s_chi2_init = chi2_t;
+            } else if (chi2_t < s_chi2) {
+                // relative decrease below rtol: (chi2 - chi2_t) < rtol chi2
+                const bool flat = !(s_chi2 - chi2_t >= s_thr) || !(s_chi2 > 0.0);
+                s_acc = 1;
+                s_cur = nxt;
+                s_chi2 = chi2_t;
+                s_lam = s_lam_acc;
+                if (flat || s_small) { s_status = ASP_LM_CONVERGED; s_done = 1; }
+            } else {
+                s_lam = s_lam_rej;
+                if (s_rej_stall) { s_status = ASP_LM_STALLED; s_done = 1; }
+            }
+        }
+        __syncthreads();
+        // ---- the full cross-CTA reduction, only when the point moves (a
+        // rejected step keeps the current point's sums)
+        if (G > 1 && s_cur == nxt) {
             // T lanes per entry (a power of two <= 32 and <= G, as many as the
             // grid's threads allow): lane (e_local, s) of a warp holds entry
             // e0 + e_local and combines the CTAs s, s + T, ... as four FP32
@@ -1146,33 +1213,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             ++epoch;
             grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
             if (s_err) return;
-        } else {
-            __syncthreads();
         }
-
         t1 = gtimer(); t_red += t1 - t0; t0 = t1;
-        // ================= LM decision (identical in every CTA) =================
-        if (tid == 0) {
-            const double chi2_t = __ldcg(sums_nxt + chi_idx);     // FP64 acceptance test
-            s_passes += 1;
-            s_acc = 0;
-            if (first) {
-                s_cur = nxt;
-                s_chi2 = chi2_t;
-                s_chi2_init = chi2_t;
-            } else if (chi2_t < s_chi2) {
-                // relative decrease below rtol: (chi2 - chi2_t) < rtol chi2
-                const bool flat = !(s_chi2 - chi2_t >= s_thr) || !(s_chi2 > 0.0);
-                s_acc = 1;
-                s_cur = nxt;
-                s_chi2 = chi2_t;
-                s_lam = s_lam_acc;
-                if (flat || s_small) { s_status = ASP_LM_CONVERGED; s_done = 1; }
-            } else {
-                s_lam = s_lam_rej;
-                if (s_rej_stall) { s_status = ASP_LM_STALLED; s_done = 1; }
-            }
-        }
         __syncthreads();
         if (s_acc && tid < P) theta[tid] = trial[tid];
         first = false;
