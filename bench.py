@@ -145,6 +145,18 @@ def _traffic_record():
     return out
 
 
+def _fit_phases(st) -> dict:
+    """The fit kernel's own phase clocks (CTA 0 of every fit, %globaltimer)
+    over the profiled step, per damped solve (LM iteration)."""
+    li = max(int(st["lm_iters"]), 1)
+    us = lambda k: 1e3 * float(st[k]) / li   # noqa: E731
+    return {"lm_iters": int(st["lm_iters"]), "passes": int(st["lm_passes"]),
+            "refinements": int(st["fit_refinements"]), "fp64_fallbacks": int(st["fit_fallbacks"]),
+            "us_per_lm_iter": {"pixel_pass": us("fit_pass_ms"), "chi2_decision_reduction": us("fit_reduce_ms"),
+                               "solve_total": us("fit_solve_ms"), "damped_solve": us("fit_factor_ms"),
+                               "post_solve_checks": us("fit_subst_ms")}}
+
+
 def _nvtx(push: bool):
     """NVTX range 'asp_timed' around the timed steps, so that a profiler can
     select exactly their launches (ncu --nvtx --nvtx-include asp_timed/)."""
@@ -495,6 +507,7 @@ def run_ours(a):
             "pixel_evals_per_s": pevals / (t_ms / 1e3),
             "fit_tflops": fit_flops / (t_ms / 1e3) / 1e12,
             "e2e": e2e, "gpu_launches": n_launch, "roofline": roof, "kernels": kernels,
+            "fit_phases": _fit_phases(prof_stats),
             "clocks": clk.summary()}
     weights = None
     if rank == 0 and not a.no_learned:
