@@ -836,7 +836,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
 
     __shared__ FitDesc d;
     __shared__ MemberFrame fr[KMAX];
-    __shared__ short2 ttab[NTILES_MAX];
+    __shared__ short2 ttab[NTILES_MAX];     // layout tile t -> (bi, bj), row-major upper triangle
+    __shared__ short tperm[NTILES_MAX];     // SYRK thread order -> layout tile
     __shared__ double theta[PMAX], trial[PMAX], delta[PMAX], gvec[PMAX], dvec[PMAX];
     __shared__ float g32[PMAX], dv32[PMAX], a32d[PMAX];
     __shared__ SolveWork sw;
@@ -875,6 +876,34 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         int bi = 0, rem = t;
         while (rem >= nb - bi) { rem -= nb - bi; ++bi; }
         ttab[t] = make_short2((short)bi, (short)(bi + rem));
+    }
+    // SYRK thread order: column blocks of 8 tile columns, rows ascending
+    // within a block, so the 32 lanes of a warp cover about 4 tile rows x 8
+    // tile columns and each pixel's two float4 J loads of a warp touch ~12
+    // distinct float4 (2 shared-memory wavefronts instead of ~5 in row order)
+    for (int t = tid; t < ntiles; t += blockDim.x) {
+        int k = t, c0 = 0, c1 = 0, full = 0, nfull = 0;
+        for (int C = 0;; ++C) {
+            c0 = 8 * C;
+            c1 = min(c0 + 7, nb - 1);
+            full = c1 - c0 + 1;                    // rows 0..c0 span the block's full width
+            nfull = c0 + 1;
+            const int cnt = nfull * full + (full - 1) * full / 2;   // rows c0+1..c1: widths full-1..1
+            if (k < cnt) break;
+            k -= cnt;
+        }
+        int bi, bj;
+        if (k < nfull * full) {
+            bi = k / full;
+            bj = c0 + k % full;
+        } else {
+            k -= nfull * full;
+            int w = full - 1;
+            bi = c0 + 1;
+            while (k >= w) { k -= w; --w; ++bi; }
+            bj = bi + k;
+        }
+        tperm[t] = (short)tile_index(bi, bj, nb);
     }
     int n_groups, my_group, my_tile0;
     if (ntiles >= (int)blockDim.x) {
@@ -1008,7 +1037,9 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     for (int q = 0; q < TPT; ++q) {
                         const int t = tbase + q * (int)blockDim.x;
                         if (t < ntiles) {
-                            const short2 bij = ttab[t];
+                            const short2 bij = ttab[tperm[t]];
+                            // unrolled so the next pixels' loads issue ahead of the FMAs
+#pragma unroll 4
                             for (int l = l0; l < l1; ++l) {
                                 const float4 av = *reinterpret_cast<const float4*>(Jc + l * JS + 4 * bij.x);
                                 const float4 bv = *reinterpret_cast<const float4*>(Jc + l * JS + 4 * bij.y);
@@ -1044,30 +1075,33 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             for (int q = 0; q < TPT; ++q) {
                 const int t = tbase + q * (int)blockDim.x;
                 if (my_group == 0 && t < ntiles) {
+                    const int slot = tperm[t];                // layout position of this tile
                     if (G == 1) {
-                        double* dst = sums_nxt + t * 16;
-                        float* dst32 = sums32_nxt + t * 16;
+                        double* dst = sums_nxt + slot * 16;
+                        float* dst32 = sums32_nxt + slot * 16;
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             dst[e] = (double)ks[q][e] - (double)kc[q][e];
                             dst32[e] = ks[q][e] - kc[q][e];
                         }
                     } else {
-                        float2* dst = reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX) + t * 16;
+                        float2* dst = reinterpret_cast<float2*>(partials + (size_t)b * NACC_MAX) + slot * 16;
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             dst[e] = make_float2(ks[q][e], -kc[q][e]);
-                            if (t == chi_t && e == chi_e) chib_p[b] = make_float2(ks[q][e], -kc[q][e]);
+                            if (slot == chi_t && e == chi_e) chib_p[b] = make_float2(ks[q][e], -kc[q][e]);
                         }
                     }
                 }
             }
         } else if (my_group >= 0) {
-            // several pixel groups per tile: park each group's leaf sums
+            // several pixel groups per tile: park each group's leaf sums at
+            // the tile's layout position
+            const int slot = tperm[my_tile0];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                red[(my_group * ntiles + my_tile0) * 16 + e] = ks[0][e];
-                red[(n_groups * ntiles + my_group * ntiles + my_tile0) * 16 + e] = kc[0][e];
+                red[(my_group * ntiles + slot) * 16 + e] = ks[0][e];
+                red[(n_groups * ntiles + my_group * ntiles + slot) * 16 + e] = kc[0][e];
             }
         }
         }   // rounds
