@@ -285,9 +285,9 @@ __device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ 
 __host__ __device__ constexpr int lp_offset(int P4) { return ((P4 + 1) * (P4 + 2) / 2 + 3) & ~3; }
 // Union region of S: the J chunk (rows x NAp floats, rows chosen to fit),
 // the FP32 factor of P4 <= PMAX_S with its 8-column panel, or the CTA's leaf
-// sums of several pixel groups (2 x FIT_THREADS x 16 floats).
+// sums of several pixel groups (2 x FIT_THREADS x 17 floats).
 constexpr int JC_FLOATS = lp_offset(PMAX_S) + 8 * (PMAX_S + 4);
-static_assert(JC_FLOATS >= 2 * FIT_THREADS * 16, "leaf sums must fit the union region");
+static_assert(JC_FLOATS >= 2 * FIT_THREADS * 17, "parked leaf sums (17 floats a tile) must fit the union region");
 static_assert(JC_FLOATS / (PMAX_S + 8) >= 64, "the J chunk of S must hold 64 rows");
 
 // Factor the PBxPB diagonal block at j0 (lower, packed in M) in registers,
@@ -1009,6 +1009,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 }
                 if (live) {
                     float model = 0.f;
+#pragma unroll 4
                     for (int k = 0; k < K; ++k) {
                         const MemberFrame& f = fr[k];
                         float dx = (float)(x - f.cx) - f.fx, dy = (float)(y - f.cy) - f.fy;
@@ -1096,35 +1097,39 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             }
         } else if (my_group >= 0) {
             // several pixel groups per tile: park each group's leaf sums at
-            // the tile's layout position
+            // the tile's layout position, 17 floats per tile so that the
+            // lanes' stores of one entry fall in distinct banks
             const int slot = tperm[my_tile0];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                red[(my_group * ntiles + slot) * 16 + e] = ks[0][e];
-                red[(n_groups * ntiles + my_group * ntiles + slot) * 16 + e] = kc[0][e];
+                red[(my_group * ntiles + slot) * 17 + e] = ks[0][e];
+                red[(n_groups * ntiles + my_group * ntiles + slot) * 17 + e] = kc[0][e];
             }
         }
         }   // rounds
         t1 = gtimer(); t_pass += t1 - t0; t0 = t1;
         if (n_groups > 1) {
             // the pixel groups' pairs combined error-free in FP32, in group order
+            // (entry e = 16 slot + q of group g parked at (g ntiles + slot) 17 + q)
+#define RS(g, e) red[((g) * ntiles + ((e) >> 4)) * 17 + ((e) & 15)]
+#define RC(g, e) red[((n_groups + (g)) * ntiles + ((e) >> 4)) * 17 + ((e) & 15)]
             __syncthreads();
             for (int e = tid; e < nacc; e += blockDim.x) {
                 // up to 4 groups in order; more as four chains (group g in
                 // chain g % 4) joined pairwise
                 float sh = 0.f, sl = 0.f;
                 if (n_groups <= 4) {
-                    for (int g = 0; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                    for (int g = 0; g < n_groups; ++g) pair_add(sh, sl, RS(g, e), -RC(g, e));
                 } else {
                     float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f;
                     int g = 0;
                     for (; g + 3 < n_groups; g += 4) {
-                        pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
-                        pair_add(h1, l1, red[(g + 1) * nacc + e], -red[(n_groups + g + 1) * nacc + e]);
-                        pair_add(h2, l2, red[(g + 2) * nacc + e], -red[(n_groups + g + 2) * nacc + e]);
-                        pair_add(h3, l3, red[(g + 3) * nacc + e], -red[(n_groups + g + 3) * nacc + e]);
+                        pair_add(sh, sl, RS(g, e), -RC(g, e));
+                        pair_add(h1, l1, RS(g + 1, e), -RC(g + 1, e));
+                        pair_add(h2, l2, RS(g + 2, e), -RC(g + 2, e));
+                        pair_add(h3, l3, RS(g + 3, e), -RC(g + 3, e));
                     }
-                    for (; g < n_groups; ++g) pair_add(sh, sl, red[g * nacc + e], -red[(n_groups + g) * nacc + e]);
+                    for (; g < n_groups; ++g) pair_add(sh, sl, RS(g, e), -RC(g, e));
                     pair_add(sh, sl, h1, l1);
                     pair_add(h2, l2, h3, l3);
                     pair_add(sh, sl, h2, l2);
@@ -1135,6 +1140,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     if (e == chi_idx) chib_p[b] = make_float2(sh, sl);
                 }
             }
+#undef RS
+#undef RC
         }
 
         // ---- chi^2 at the trial point first: after a grid barrier every CTA
