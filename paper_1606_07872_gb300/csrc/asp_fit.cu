@@ -683,6 +683,7 @@ constexpr float REFINE_INV_MAX = 10.0f;   // refine when some 1/L_jj of the scal
 
 struct SolveWork {              // shared-memory scratch of solve_damped
     double bt[PMAX], ud[PMAX], inv64[PMAX];
+    double rq[4][64];           // the refinement residual's column-quarter sums
     float sf[PMAX], mf[PMAX], xv[PMAX], zv[PMAX], cv[PMAX], inv32[PMAX];
     int flag, refinements, fallbacks, pad;
 };
@@ -749,21 +750,42 @@ __device__ bool solve_scaled_fp32(const AT& A, const TiledA32& A32, const double
         }
         __syncthreads();
         // refinement: c = (L L^T)^-1 (S g - S (A + lam D) S x), residual in
-        // FP64, one row per thread as four independent FMA chains
-        for (int i = tid; i < P4; i += blockDim.x) {
-            if (i >= P) { w.cv[i] = 0.f; continue; }
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int j = 0;
-            for (; j + 3 < P; j += 4) {          // unconditional loads, four chains
-                const double v0 = A(i, j), v1 = A(i, j + 1), v2 = A(i, j + 2), v3 = A(i, j + 3);
-                a0 = fma(v0, w.ud[j], a0);
-                a1 = fma(v1, w.ud[j + 1], a1);
-                a2 = fma(v2, w.ud[j + 2], a2);
-                a3 = fma(v3, w.ud[j + 3], a3);
+        // FP64.  Row i's columns are split in four quarters over the four
+        // thread groups of 64 (so the FP64 work spreads over all the SM's
+        // schedulers), each quarter as two FMA chains; the quarters are
+        // added in order.  P4 > 64 takes further rows in later rounds.
+        {
+            const int nq = (int)blockDim.x / 64;          // 4 column quarters
+            const int qi = tid / 64, ri = tid % 64;
+            const int qlen = (P + nq - 1) / nq;
+            const int ja = qi * qlen, jb = min(P, ja + qlen);
+            for (int i0 = 0; i0 < P4; i0 += 64) {
+                const int i = i0 + ri;
+                double part = 0.0;
+                if (i < P) {
+                    double a0 = 0.0, a1 = 0.0;
+                    int j = ja;
+                    for (; j + 1 < jb; j += 2) {
+                        const double v0 = A(i, j), v1 = A(i, j + 1);
+                        a0 = fma(v0, w.ud[j], a0);
+                        a1 = fma(v1, w.ud[j + 1], a1);
+                    }
+                    if (j < jb) a0 = fma(A(i, j), w.ud[j], a0);
+                    part = a0 + a1;
+                }
+                w.rq[qi][ri] = part;
+                __syncthreads();
+                if (tid < 64 && i < P4) {
+                    if (i >= P) {
+                        w.cv[i] = 0.f;
+                    } else {
+                        const double mx = ((w.rq[0][ri] + w.rq[1][ri]) + (w.rq[2][ri] + w.rq[3][ri])) +
+                                          lam * dv[i] * w.ud[i];
+                        w.cv[i] = (float)(w.bt[i] - (double)w.sf[i] * mx);
+                    }
+                }
+                __syncthreads();
             }
-            for (; j < P; ++j) a0 = fma(A(i, j), w.ud[j], a0);
-            const double mx = (a0 + a1) + (a2 + a3) + lam * dv[i] * w.ud[i];
-            w.cv[i] = (float)(w.bt[i] - (double)w.sf[i] * mx);
         }
         if (tid == 0) w.refinements += 1;
         __syncthreads();
