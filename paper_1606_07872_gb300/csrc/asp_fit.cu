@@ -9,13 +9,16 @@
 //   1. pixel pass (FP32): per pixel the K Gaussians, the residual r and the
 //      4K Jacobian entries, accumulated as the upper triangle of
 //      [J | r]^T [J | r] (J^T J, J^T r and r^T r) in 4x4 register tiles,
-//      leaf sums of <= 64 pixels, Kahan-compensated across leaves;
-//   2. CTA partials (FP32 hi/lo pairs) -> grid barrier -> error-free FP32
-//      pair reduction, each entry split over up to 32 lanes, one FP64 sum
-//      per entry -> grid barrier;
-//   3. every CTA redundantly runs the LM decision logic and the FP64
-//      Cholesky solve of (A + lambda diag A) delta = g, so no third barrier
-//      is needed to broadcast the next trial point.
+//      leaf sums of <= 64 pixels, Kahan-compensated across leaves; each CTA
+//      writes its partial sums as FP32 (sum, -compensation) pairs;
+//   2. grid barrier -> every CTA combines the CTAs' chi^2 pairs and takes the
+//      LM decision (all CTAs identically);
+//   3. accepted steps only: error-free FP32 pair reduction of every entry
+//      over the CTAs, one FP64 value (and its FP32 rounding) per entry ->
+//      grid barrier; a rejected step keeps the current point's sums;
+//   4. every CTA redundantly solves (A + lambda diag A) delta = g (scaled
+//      FP32 Cholesky, FP64 refinement when a pivot is small), so no further
+//      barrier is needed to broadcast the next trial point.
 // Grid barriers are bounded spins; on timeout the kernel records an error
 // and returns.
 #include "asp_dev.cuh"
