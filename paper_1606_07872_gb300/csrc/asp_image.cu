@@ -386,14 +386,21 @@ __device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int 
         const int x = cb * 32 + lane, y0 = rb * 64 + 8 * warp;
         if (x >= W || y0 >= H) continue;
         const float* col = S1 + ((long long)j * taps.s1rows + (y0 - m + taps.mpad)) * W + x;
+        // window rows u0 .. u0+15 in w, the next block's rows loaded ahead
+        // of this block's FMAs (the same rows as without the prefetch)
         float acc[8], w[16];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; w[i] = __ldg(col + (long long)i * W); }
+        for (int i = 0; i < 16; ++i) w[i] = __ldg(col + (long long)i * W);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
 #pragma unroll 1
         for (int u0 = 0; u0 < t8; u0 += 8) {
-            const float* c8 = col + (long long)(u0 + 8) * W;
+            float nx[8];
+            if (u0 + 8 < t8) {
+                const float* c16 = col + (long long)(u0 + 16) * W;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) w[8 + i] = __ldg(c8 + (long long)i * W);
+                for (int i = 0; i < 8; ++i) nx[i] = __ldg(c16 + (long long)i * W);
+            }
             const float4 ka = *reinterpret_cast<const float4*>(ktap + u0);
             const float4 kb = *reinterpret_cast<const float4*>(ktap + u0 + 4);
             const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
@@ -402,7 +409,7 @@ __device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int 
 #pragma unroll
                 for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+            for (int i = 0; i < 8; ++i) { w[i] = w[8 + i]; w[8 + i] = nx[i]; }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
