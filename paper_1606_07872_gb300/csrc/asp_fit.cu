@@ -870,7 +870,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     __shared__ double s_lam_acc, s_lam_rej, s_thr;   // the decision's FP64 terms, computed during the pass
     __shared__ double s_chi2_t;                       // chi^2 at the trial point
     __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc, s_small, s_rej_stall;
-    __shared__ float s_pred[2];
+    __shared__ float s_pred[2], s_thr32;   // predicted-decrease sums; rtol chi^2 of the current point
+    __shared__ unsigned s_flags;          // post-solve flags: finite, valid, small
 
     const int tid = threadIdx.x;
     {
@@ -1291,6 +1292,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         if (s_cur == nxt) {
             const double* sc = sums + (size_t)s_cur * NACC_MAX;
             const float* sc32 = sums32 + (size_t)s_cur * NACC_MAX;
+            if (tid == (int)blockDim.x - 1) s_thr32 = (float)(lmc.rtol * s_chi2);   // for the post-solve test
             if (!LARGE) {
 #pragma unroll 4
                 for (int e = tid; e < nacc; e += blockDim.x) {
@@ -1316,7 +1318,12 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
 
         // ---- propose the next trial point (solves without a pass loop here)
         while (!s_done) {
-            if (tid == 0 && s_iters >= lmc.max_iter) { s_status = ASP_LM_CAP; s_done = 1; }
+            if (tid == 0) {
+                if (s_iters >= lmc.max_iter) { s_status = ASP_LM_CAP; s_done = 1; }
+                s_pred[0] = 0.f;       // cleared here: the solve's barriers order them before the checks
+                s_pred[1] = 0.f;
+                s_flags = 7u;
+            }
             __syncthreads();
             if (s_done) break;
             const double lam = s_lam;
@@ -1335,8 +1342,6 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             const unsigned long long tf1 = gtimer();
             t_factor += tf1 - tf0;
             // predicted decrease d.g + lam d.D.d (FP32 sums), finiteness, validity
-            if (tid == 0) { s_pred[0] = 0.f; s_pred[1] = 0.f; }
-            __syncthreads();
             int fin_i = 1, valid_i = 1, small_i = 1;
             float dg_i = 0.f, dd_i = 0.f;
             if (ok && tid < P) {
@@ -1366,16 +1371,24 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 }
                 if ((tid & 31) == 0) { atomicAdd(&s_pred[0], dg_i); atomicAdd(&s_pred[1], dd_i); }
             }
-            const int fin = __syncthreads_and(fin_i) && ok;
-            const int valid = __syncthreads_and(valid_i);
-            const int small = __syncthreads_and(small_i);
+            // the three block-wide ANDs in one barrier: warp AND, then a shared atomic
+            {
+                unsigned f = (fin_i ? 1u : 0u) | (valid_i ? 2u : 0u) | (small_i ? 4u : 0u);
+                f = __reduce_and_sync(0xffffffffu, f);
+                if ((tid & 31) == 0) atomicAnd(&s_flags, f);
+            }
+            const float lam32 = tid == 0 ? (float)lam : 0.f;   // the test below runs on thread 0
+            __syncthreads();
+            const int fin = (s_flags & 1u) && ok;
+            const int valid = (s_flags & 2u) != 0u;
+            const int small = (s_flags & 4u) != 0u;
             if (tid == 0) {
                 s_iters += 1;
                 s_go = 0;
                 if (!fin) {
                     s_lam *= lmc.lambda_up;
                     if (s_lam > lmc.lambda_max) { s_status = ASP_LM_STALLED; s_done = 1; }
-                } else if ((double)s_pred[0] + lam * (double)s_pred[1] <= lmc.rtol * s_chi2) {
+                } else if (fmaf(lam32, s_pred[1], s_pred[0]) <= s_thr32) {   // FP32 sums against FP32 rtol chi^2
                     s_status = ASP_LM_CONVERGED; s_done = 1;
                 } else if (valid) {
                     s_go = 1;
