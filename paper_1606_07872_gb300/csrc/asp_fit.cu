@@ -266,25 +266,11 @@ __device__ void trsv_warp(const T* __restrict__ M, int P, const T* __restrict__ 
         if (lane + 32 * s < P) b[lane + 32 * s] = v[s];
 }
 
-// Low-latency Cholesky factorisation (FP32) of the packed lower matrix M,
-// columns 0..P-1 of rows 0..P (P a multiple of the panel width PB = 4 or 8;
-// row P carries a right-hand side b, which comes out as L^-1 b).  Blocked
-// right-looking with look-ahead, two block barriers per panel:
-//   A. one thread per row i below the panel's diagonal block: solve the
-//      row's PB panel entries against the already factored block, store
-//      them in M and column-major in Lp (ld LP_LD, conflict-free reads);
-//   B. warps 0..6: trailing rank-PB update of the rows below the next
-//      diagonal block, one row per warp, one column per lane;
-//      warp 7: the next diagonal block itself -- its rank-PB update, then
-//      its factorisation in registers (every lane redundantly), so the
-//      pivot chain of panel p+1 overlaps the update of panel p.
-// Narrow panels suit small P (fewer padded rows, shorter pivot chains on
-// the critical path), wide ones large P (half the barriers).
-// Every block is full (callers pad P with identity rows), so no load sits
-// behind a bounds test.  Returns false (uniformly) if a pivot is not
-// positive; *s_flag must be 0 on entry.
-// Lp (PB columns of ld lp_ld >= P + 1) sits behind the packed (P+1)-row
-// factor, at a 4-float-aligned offset.
+// The FP32 factor (packed lower, P4 + 1 rows with the right-hand side row;
+// P4 = P padded with identity rows to a multiple of the panel width, 4 for
+// P <= 32 and 8 above: narrow panels keep the pivot chain short for small
+// P, wide ones halve the barriers for large P) is followed by its panel Lp
+// (PB columns of ld lp_ld >= P + 1) at a 4-float-aligned offset.
 __host__ __device__ constexpr int lp_offset(int P4) { return ((P4 + 1) * (P4 + 2) / 2 + 3) & ~3; }
 // Union region of S: the J chunk (rows x NAp floats, rows chosen to fit),
 // the FP32 factor of P4 <= PMAX_S with its 8-column panel, or the CTA's leaf
@@ -293,55 +279,14 @@ constexpr int JC_FLOATS = lp_offset(PMAX_S) + 8 * (PMAX_S + 4);
 static_assert(JC_FLOATS >= 2 * FIT_THREADS * 17, "parked leaf sums (17 floats a tile) must fit the union region");
 static_assert(JC_FLOATS / (PMAX_S + 8) >= 64, "the J chunk of S must hold 64 rows");
 
-// Factor the PBxPB diagonal block at j0 (lower, packed in M) in registers,
-// every lane of the calling warp redundantly; lanes 0..PB-1 store row
-// j0+lane of the factor and its inverse pivot.  Returns false if a pivot
-// fails.
-template <int PB>
-__device__ __forceinline__ bool factor_diag(float* __restrict__ M, float* __restrict__ inv_diag, int j0, int lane) {
-    float d[PB][PB];
-#pragma unroll
-    for (int c = 0; c < PB; ++c)
-#pragma unroll
-        for (int t = 0; t <= c; ++t) d[c][t] = M[pidx(j0 + c, j0 + t)];
-    float inv[PB];
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < PB; ++c) {
-        float v = d[c][c];
-#pragma unroll
-        for (int t = 0; t < c; ++t) v = fmaf(-d[c][t], d[c][t], v);
-        ok = ok && v > 0.f && isfinite(v);
-        const float il = rsqrtf(v);
-        d[c][c] = v * il;
-        inv[c] = il;
-#pragma unroll
-        for (int r = c + 1; r < PB; ++r) {
-            float u = d[r][c];
-#pragma unroll
-            for (int t = 0; t < c; ++t) u = fmaf(-d[r][t], d[c][t], u);
-            d[r][c] = u * il;
-        }
-    }
-    __syncwarp();   // every lane has read the unfactored block
-#pragma unroll
-    for (int c = 0; c < PB; ++c)
-        if (c == lane) {
-#pragma unroll
-            for (int t = 0; t <= c; ++t) M[pidx(j0 + c, j0 + t)] = d[c][t];
-            inv_diag[j0 + c] = inv[c];
-        }
-    return ok;
-}
-
-// factor_diag with the panel's update folded in, right-looking: every lane
-// of the calling warp loads the PBxPB block at r0 and, if Lp is given, the
-// panel rows r0..r0+PB-1 (PB columns of ld LP_LD), subtracts their products
-// (panel columns in ascending order), then eliminates column by column with
-// the trailing entries updated at once, so the chain from one pivot to the
-// next is one multiply, one FMA and the reciprocal square root.  Same
-// operations in the same order as the separate update plus factor_diag, so
-// bitwise the same factor.
+// Factor the PBxPB diagonal block at r0 (lower, packed in M) in registers,
+// every lane of the calling warp redundantly; lane 0 stores the factor and
+// its inverse pivots.  If Lp is given, the panel rows r0..r0+PB-1 (PB columns
+// of ld LP_LD) are first subtracted (panel columns in ascending order).  The
+// elimination is right-looking, the trailing entries updated at once, so the
+// chain from one pivot to the next is one multiply, one FMA and the
+// reciprocal square root.  Returns false if a pivot is not positive and
+// finite.
 template <int PB>
 __device__ __forceinline__ bool factor_diag_rl(float* __restrict__ M, const float* __restrict__ Lp, int LP_LD,
                                                float* __restrict__ inv_diag, int r0, int lane) {
@@ -403,86 +348,20 @@ __device__ __forceinline__ bool factor_diag_rl(float* __restrict__ M, const floa
     return ok;
 }
 
-template <int PB>
-__device__ bool chol_lowlat(float* __restrict__ M, float* __restrict__ Lp, int P, float* __restrict__ inv_diag,
-                            int* s_flag, const int LP_LD) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int nrows = P + 1;
-    if (warp == 0 && !factor_diag<PB>(M, inv_diag, 0, lane) && lane == 0) *s_flag = 1;
-    __syncthreads();
-    if (*s_flag) return false;
-#pragma unroll 1
-    for (int j0 = 0; j0 < P; j0 += PB) {
-        const int r0 = j0 + PB;
-        // A: panel rows below the diagonal block
-        const int i = r0 + tid;
-        if (i < nrows) {
-            float a[PB], iv[PB];
-#pragma unroll
-            for (int c = 0; c < PB; ++c) { a[c] = M[pidx(i, j0 + c)]; iv[c] = inv_diag[j0 + c]; }
-            float l[PB][PB];
-#pragma unroll
-            for (int c = 1; c < PB; ++c)
-#pragma unroll
-                for (int t = 0; t < c; ++t) l[c][t] = M[pidx(j0 + c, j0 + t)];
-            // forward solve of the row against L_d, running updates
-#pragma unroll
-            for (int c = 0; c < PB; ++c) {
-                a[c] *= iv[c];
-#pragma unroll
-                for (int r = c + 1; r < PB; ++r) a[r] = fmaf(-l[r][c], a[c], a[r]);
-            }
-#pragma unroll
-            for (int c = 0; c < PB; ++c) {
-                M[pidx(i, j0 + c)] = a[c];
-                Lp[c * LP_LD + i] = a[c];
-            }
-        }
-        __syncthreads();
-        // B: trailing update (warps 0..nwarp-2) and look-ahead factor (last warp)
-        if (warp == nwarp - 1) {
-            if (r0 < P) {
-                // update the next diagonal block: PB(PB+1)/2 entries over the lanes
-                for (int e = lane; e < PB * (PB + 1) / 2; e += 32) {
-                    int rr = 0;
-                    while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-                    const int cc = e - rr * (rr + 1) / 2;
-                    float acc = M[pidx(r0 + rr, r0 + cc)];
-#pragma unroll
-                    for (int c = 0; c < PB; ++c) acc = fmaf(-Lp[c * LP_LD + r0 + rr], Lp[c * LP_LD + r0 + cc], acc);
-                    M[pidx(r0 + rr, r0 + cc)] = acc;
-                }
-                __syncwarp();
-                if (!factor_diag<PB>(M, inv_diag, r0, lane) && lane == 0) *s_flag = 1;
-            }
-        } else {
-            for (int ii = r0 + PB + warp; ii < nrows; ii += nwarp - 1) {
-                float li[PB];
-#pragma unroll
-                for (int c = 0; c < PB; ++c) li[c] = Lp[c * LP_LD + ii];
-                float* row = M + pidx(ii, 0);
-                const int kmax = min(ii, P - 1);
-                for (int k = r0 + lane; k <= kmax; k += 32) {
-                    float acc = row[k];
-#pragma unroll
-                    for (int c = 0; c < PB; ++c) acc = fmaf(-li[c], Lp[c * LP_LD + k], acc);
-                    row[k] = acc;
-                }
-            }
-        }
-        __syncthreads();
-        if (*s_flag) return false;
-    }
-    return true;
-}
-
-// The same factorisation as chol_lowlat (same operations in the same order,
-// so bitwise the same factor) with the trailing update register-tiled: each
-// thread of warps 0..nwarp-2 updates 4x4 tiles of the trailing matrix, two
-// 16-byte panel loads per panel column for 16 FMAs, where the row-per-warp
-// update needed one shared-memory load per FMA and was bound by the
-// shared-memory pipe.  Tiles cover rows r0 + 4 bi (bi >= PB / 4: the next
-// diagonal block is the last warp's) and columns r0 + 4 bj, bj <= bi.
+// Cholesky factorisation of the packed lower FP32 matrix M in place: rows
+// 0..P (row P carries a right-hand side b and comes out as L^-1 b, the
+// forward substitution fused into the factorisation), P a multiple of the
+// panel width PB.  Blocked right-looking with look-ahead; per panel:
+//   (A) one thread per row below the diagonal block solves its panel
+//       entries against the factored block, stored in place and column-major
+//       in Lp (PB columns of ld LP_LD, 16-byte aligned);
+//   (B) warps 0..nwarp-2 apply the trailing update on 4x4 register tiles
+//       (two 16-byte panel loads per panel column for 16 FMAs), rows
+//       r0 + 4 bi (bi >= PB / 4) and columns r0 + 4 bj, bj <= bi, while the
+//       last warp takes the next diagonal block with this panel's update and
+//       factors it (factor_diag_rl).
+// Two block barriers per panel.  *s_flag must be 0 on entry; returns false
+// if a pivot fails.
 template <int PB>
 __device__ bool chol_tiled(float* __restrict__ M, float* __restrict__ Lp, int P, float* __restrict__ inv_diag,
                            int* s_flag, const int LP_LD) {
@@ -566,7 +445,7 @@ __device__ bool chol_tiled(float* __restrict__ M, float* __restrict__ Lp, int P,
     return true;
 }
 
-// Back substitution L^T x = y with L from chol_lowlat (P a multiple of PB),
+// Back substitution L^T x = y with L from chol_tiled (P a multiple of PB),
 // all threads, PB-row blocks from the bottom, one block barrier per block:
 // every thread solves the block's 8 unknowns redundantly from the (already
 // updated) y entries, then thread i < jb removes them from y_i.  y is
@@ -801,17 +680,18 @@ __device__ bool solve_scaled_fp32(const AT& A, const TiledA32& A32, const double
     return false;
 }
 
-// Solve (A + lam diag(dv)) delta = g, A packed lower FP64 in shared memory,
-// all threads of the block.  With S = diag(A + lam D)^-1/2 rounded to FP32
+// Solve (A + lam diag(dv)) delta = g, all threads of the block; A is read
+// through the FP64 accessor (tile-ordered sums in shared memory or L2) and
+// its FP32 copy through A32.  With S = diag(A + lam D)^-1/2 rounded to FP32
 // (any diagonal scaling serves; an FP32 one is exact in FP64 below), the
 // matrix S (A + lam D) S, augmented by the row S g, is factored in FP32 (the
 // forward substitution comes out of the factorisation); one back
-// substitution gives x; one step of iterative refinement with the residual
+// substitution gives x; when a pivot of the unit-diagonal factor is below
+// 1e-2, one step of iterative refinement with the residual
 // S g - S (A + lam D) S x evaluated in FP64 corrects it; delta = S x.  If the
 // FP32 factor fails, an FP64 factor of the unscaled matrix is used, in m64
-// (P (P+1) / 2 doubles: shared memory for variant S, the CTA's partial row
-// in global memory for variant L).  Returns false when the damped matrix is
-// not positive definite.
+// (P (P+1) / 2 doubles: the CTA's partial row in global memory).  Returns
+// false when the damped matrix is not positive definite.
 template <class AT>
 __device__ bool solve_damped(const AT& A, const TiledA32& A32, const double* __restrict__ g, const float* __restrict__ g32,
                              const double* __restrict__ dv, const float* __restrict__ dv32, double lam, int P,
