@@ -33,9 +33,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "minor-cycle iterations/s (Asp-Clean2016, 1024x1024, active set <= 20)"
 UNIT = "iterations/s"
-FP32_LANES_PER_SM = 128
 
 
 def _args():
@@ -45,7 +43,13 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=0, help="minor-cycle iterations per step (0: the workload's 2000)")
-    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--size", type=int, default=0, help="image side (0: the workload's own)")
+    ap.add_argument("--config", type=int, choices=[2, 3], default=2,
+                    help="workload of the main line: 2 (1024^2, k_max 20) or 3 (4096^2, k_max 50)")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 4096^2 measurement beside config 2")
+    ap.add_argument("--config3-iters", type=int, default=0, help="iterations per config-3 step (0: its 5000)")
+    ap.add_argument("--config3-steps", type=int, default=2)
+    ap.add_argument("--config3-warmup", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batch comparison")
@@ -170,9 +174,11 @@ def _nvtx(push: bool):
         pass
 
 
-def _workload(size: int, seed: int):
+def _workload(config: int, size: int, seed: int):
     import synth
-    return synth.config2(seed, size=size)
+    if config == 3:
+        return synth.config3(seed, size=size or 4096)
+    return synth.config2(seed, size=size or 1024)
 
 
 def _dist():
@@ -198,14 +204,15 @@ def aggregate(t_ms: float, iters: int, pevals: int, device) -> tuple:
 
 # ---------------------------------------------------------------- cpu baseline (oracle)
 
-def _oracle_sample(size: int, budget_s: float, seed: int = 0, resume=None):
+def _oracle_sample(config: int, size: int, budget_s: float, seed: int = 0, resume=None):
     """Run the FP64 oracle's minor cycle on the same workload until budget_s
     has been spent (at least one iteration).  Returns (iterations, seconds,
     pixel_evals, state)."""
     import oracle as O
-    case = _workload(size, seed)
+    case = _workload(config, size, seed)
     if resume is None:
-        mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma))
+        mc = O.MinorCycle(case.dirty, case.psf, O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma,
+                                                            gain=case.gain))
     else:
         mc = resume
     n0, pe0 = mc.t, sum(h["fit"].pixel_evals for h in mc.history)
@@ -227,17 +234,101 @@ def _cpu_threads_env():
     return env
 
 
-def cpu_baseline(size: int, budget: float) -> dict:
-    """The oracle as it stands, single-threaded, in a child process."""
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; n, dt, pe, _ = bench._oracle_sample(%d, %f); "
-            "print(json.dumps([n, dt, pe]))" % (ROOT, size, budget))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_cpu_threads_env(),
-                       timeout=budget * 20 + 600)
-    n, dt, pe = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} minor-cycle iterations of the {size}x{size} workload from its dirty image "
-                      f"(FP64 NumPy oracle, 1 thread, {dt:.1f} s)",
-            "pixel_evals_per_s": pe / dt}
+def snapshot_states(asp, case, n_iter: int, n_snap: int, path: str):
+    """States of the workload's run at n_snap iterations spread uniformly
+    over [0, n_iter) (the GPU runs the cycle; each state is the residual,
+    the component list, the retained list, t and the switch statistics), so
+    that the oracle can be timed on iterations from the whole run."""
+    import numpy as np
+    import torch
+    ctx = asp.Context(torch.from_numpy(case.dirty).cuda(), torch.from_numpy(case.psf).cuda(), k_max=case.k_max,
+                      noise_sigma=case.noise_sigma, gain=case.gain, lm_max_iter=case.lm_max_iter)
+    ab, wb, _, _ = ctx.beam
+    data, t = {"beam": np.array([ab, wb])}, 0
+    for i in range(n_snap):
+        want = (i * n_iter) // n_snap
+        if want > t:
+            ctx.minor_cycle(want - t)
+            t = want
+        st = ctx.state()
+        data[f"R{i}"] = ctx.residual()
+        data[f"comps{i}"] = st["comps"]
+        data[f"ret{i}"] = np.asarray(st["retained"], dtype=np.int64)
+        data[f"meta{i}"] = np.array([st["t"], st["last_wi"], st["last_w0"]])
+    ctx.close()
+    np.savez(path, n=n_snap, **data)
+
+
+def _oracle_on_snapshots(config: int, size: int, path: str, idx, budget_s: float):
+    """Time the oracle's next iteration from each snapshot in idx (one
+    iteration each, in order, until budget_s is spent; at least one).
+    Returns (iterations, seconds, pixel_evals)."""
+    import numpy as np
+    import oracle as O
+    case = _workload(config, size, 0)
+    z = np.load(path)
+    ab, wb = z["beam"]
+    p = O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma, gain=case.gain)
+    n, dt, pe = 0, 0.0, 0
+    for i in idx:
+        mc = O.MinorCycle(case.dirty, case.psf, p, beam=(ab, wb))
+        comps = [O.Component(c[0], c[1], c[2], c[3], c[4], bool(c[5])) for c in z[f"comps{i}"]]
+        t, wi, w0 = z[f"meta{i}"]
+        mc.set_state(z[f"R{i}"].astype(np.float64), comps, list(z[f"ret{i}"]), int(t), wi, w0)
+        t0 = time.perf_counter()
+        rec = mc.step()
+        dt += time.perf_counter() - t0
+        if rec is not None:
+            n += 1
+            pe += rec["fit"].pixel_evals
+        if dt >= budget_s:
+            break
+    return n, dt, pe
+
+
+def cpu_baseline(asp, config: int, case, n_iter: int, budget: float) -> dict:
+    """The oracle as it stands, timed on iterations spread uniformly over the
+    workload's run (each restarted from the GPU's state at that point):
+    single-threaded until ``budget`` seconds, and on every host core at once
+    (one single-threaded process per core, each on its own snapshots)."""
+    n_cores = os.cpu_count() or 1
+    n_snap = max(16, n_cores)
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        snapshot_states(asp, case, n_iter, n_snap, path)
+        size = case.H
+
+        def child(idx, b):
+            code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                    "print(json.dumps(bench._oracle_on_snapshots(%d, %d, %r, %r, %f)))"
+                    % (ROOT, config, size, path, list(idx), b))
+            return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, text=True,
+                                    env=_cpu_threads_env())
+
+        # one thread: snapshots in an interleaved order (early and late
+        # iterations alike) until the budget
+        order = [i for k in range(4) for i in range(k, n_snap, 4)]
+        pr = child(order, budget)
+        out, _ = pr.communicate(timeout=budget * 30 + 900)
+        n1, dt1, pe1 = json.loads(out.strip().splitlines()[-1])
+        # all cores: every snapshot once, spread over the processes
+        t0 = time.perf_counter()
+        procs = [child(range(j, n_snap, n_cores), 1e9) for j in range(n_cores)]
+        res = [json.loads(q.communicate(timeout=budget * 60 + 1800)[0].strip().splitlines()[-1]) for q in procs]
+        wall = time.perf_counter() - t0
+        nA = sum(r[0] for r in res)
+        peA = sum(r[2] for r in res)
+    finally:
+        os.unlink(path)
+    return {"value": n1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n1} minor-cycle iterations of the {case.H}x{case.W} workload, each restarted from the GPU "
+                      f"run's state at one of {n_snap} points spread uniformly over its {n_iter} iterations (FP64 "
+                      f"NumPy oracle, 1 thread, {dt1:.1f} s)",
+            "pixel_evals_per_s": pe1 / dt1,
+            "all_cores": {"value": nA / wall, "unit": UNIT, "cores": n_cores,
+                          "sample": f"all {n_snap} snapshot iterations, {n_cores} single-threaded processes, "
+                                    f"{wall:.1f} s wall", "pixel_evals_per_s": peA / wall}}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -252,17 +343,17 @@ def run_reference(a):
     budget = max(2.0, min(a.cpu_budget, 15.0))
     # warm-up steps continue the same run (each step a bounded sample)
     for i in range(a.warmup + a.steps):
-        n, dt, pe, state = _oracle_sample(a.size, budget, resume=state)
+        n, dt, pe, state = _oracle_sample(a.config, a.size, budget, resume=state)
         if i >= a.warmup:
             n_total += n
             t_total += dt
             pe_total += pe
     value = n_total / t_total if t_total > 0 else 0.0
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
+    case = _workload(a.config, a.size, 0)
+    line = {"metric": _metric(case, a.config), "value": value, "unit": UNIT, "impl": "reference", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_total / max(a.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"config2 {a.size}x{a.size} Asp-Clean2016, k_max 20",
-                                            "global_batch": 1, "seq_len": None, "parallelism": "replicas"},
+            "data": "synthetic", "config": _config(case, a.config, a.iters or case.n_iter, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{n_total} consecutive minor-cycle iterations after {a.warmup} warm-up "
                                        f"samples, {budget:.0f} s per step, 1 thread"},
@@ -363,20 +454,12 @@ def learned_comparison(asp, n_train_images: int, seed: int = 0):
 
 # ---------------------------------------------------------------- our arm
 
-def run_ours(a):
-    import numpy as np
+def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush) -> dict:
+    """Device-timed steps (inputs resident in HBM), end-to-end steps through
+    the C-ABI with host buffers, and one profiled step (CUDA events around
+    every launch) of one workload on this rank."""
+    import ctypes as C
     import torch
-    import paper_1606_07872_gb300 as asp
-    from paper_1606_07872_gb300 import build as _b
-
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    _b.build()
-    case = _workload(a.size, rank)
-    n_iter = a.iters or case.n_iter
     dirty = torch.from_numpy(case.dirty).cuda()
     psf = torch.from_numpy(case.psf).cuda()
     stream = torch.cuda.Stream()
@@ -385,7 +468,6 @@ def run_ours(a):
     with torch.cuda.stream(stream):
         ctx = asp.Context(dirty, psf, params=params, stream=stream)
     L = asp.lib()
-    import ctypes as C
 
     def reset(d_ptr, on_host, p_ptr=None, p_host=0):
         asp._check(L.asp_reset(ctx.h, d_ptr, on_host, p_ptr, p_host), "asp_reset", ctx.h)
@@ -394,26 +476,23 @@ def run_ours(a):
         reset(dirty.data_ptr(), 0, psf.data_ptr(), 0)
         return asp.asp_minor_cycle(ctx.h, n_iter)
 
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    for _ in range(a.warmup):
-        step_device()
-    torch.cuda.synchronize()
-
     def launches():
         n = C.c_int64()
         L.asp_launch_count(ctx.h, C.byref(n))
         return n.value
 
+    for _ in range(warmup):
+        step_device()
+    torch.cuda.synchronize()
     # ---- timed region (device-resident inputs)
-    times, iters, pevals = [], 0, 0
-    fit_flops = sub_flops = 0.0
+    times, iters, pevals, fit_flops = [], 0, 0, 0.0
     l0 = launches()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     _nvtx(True)
     with ClockSampler(local) as clk:
-        for _ in range(a.steps):
+        for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -425,21 +504,16 @@ def run_ours(a):
             iters += st["iterations"]
             pevals += st["pixel_evals"]
             fit_flops += st["fit_flops"]
-            sub_flops += st["sub_flops"]
     torch.cuda.synchronize()
     _nvtx(False)
     n_launch = launches() - l0
-    t_ms = sum(times)
-    t_ms, iters, pevals = aggregate(t_ms, iters, pevals, "cuda")
-    value = iters / (t_ms / 1e3)
-
+    t_ms, iters, pevals = aggregate(sum(times), iters, pevals, "cuda")
     # ---- end to end through the C-ABI with host buffers
     dirty_h = torch.from_numpy(case.dirty).pin_memory()
     psf_h = torch.from_numpy(case.psf).pin_memory()
     res_h = torch.empty((case.H, case.W), dtype=torch.float32).pin_memory()
-    e2e_ms, e2e_iters = 0.0, 0
-    comps_bytes = 0
-    for _ in range(a.steps):
+    e2e_ms, e2e_iters, comps_bytes = 0.0, 0, 0
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -456,7 +530,6 @@ def run_ours(a):
     e2e = {"value": e2e_iters / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(case.dirty.nbytes + case.psf.nbytes),
            "d2h_bytes_per_step": int(res_h.numel() * 4 + comps_bytes)}
-
     # ---- per-kernel times (events around every launch, direct launches)
     L.asp_set_profiling(ctx.h, 1)
     step_device()
@@ -465,67 +538,147 @@ def run_ours(a):
     L.asp_get_kernel_times(ctx.h, kt, 16, C.byref(nk))
     prof_stats = asp.asp_get_stats(ctx.h)
     L.asp_set_profiling(ctx.h, 0)
+    ctx.close()
     kernels = {k.name.decode(): {"launches": k.launches, "total_ms": k.total_ms} for k in kt[: nk.value]}
-    dominant = max(kernels, key=lambda n: kernels[n]["total_ms"])
+    return {"t_ms": t_ms, "iters": iters, "pevals": pevals, "fit_flops": fit_flops, "n_launch": n_launch,
+            "e2e": e2e, "kernels": kernels, "prof": prof_stats, "clocks": clk.summary(), "n_iter": n_iter,
+            "steps": steps, "N": case.H * case.W}
 
-    peaks, peak_kind = _peaks()
-    props = torch.cuda.get_device_properties(local)
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+
+def rooflines(m: dict, peaks: dict, alu: dict) -> dict:
+    """Achieved rate of each kernel class against its bound, from the
+    profiled step: the method's algorithmic work (flops, exponentials,
+    bytes) over the class's event-timed launch time."""
+    k, st = m["kernels"], m["prof"]
+    hbm = float(peaks["hbm_gbs"])
+    fma = max(alu["fp32_fma_tflops"], alu["fp32_fma2_tflops"])
+    ex2 = alu["ex2_gops"]
+    out = {}
+    if "k_lm_fit" in k:
+        s = k["k_lm_fit"]["total_ms"] / 1e3
+        pass_s = st["fit_pass_ms"] / 1e3
+        out["k_lm_fit"] = {
+            "bound": "alu", "unit": "TFLOP/s", "peak": fma,
+            "achieved": st["fit_flops"] / s / 1e12, "frac": st["fit_flops"] / s / 1e12 / fma,
+            "pixel_pass_only": {"achieved": st["fit_flops"] / pass_s / 1e12 if pass_s else None,
+                                "frac": st["fit_flops"] / pass_s / 1e12 / fma if pass_s else None,
+                                "note": "pixel-pass phase clocks of the fit kernel's first CTA"},
+            "ex2": {"achieved_gops": st["fit_ex2"] / s / 1e9, "peak_gops": ex2, "frac": st["fit_ex2"] / s / 1e9 / ex2},
+            "avg_launch_ms": k["k_lm_fit"]["total_ms"] / max(k["k_lm_fit"]["launches"], 1)}
+    if "k_sub_h" in k and "k_sub_v_argmax" in k:
+        s = (k["k_sub_h"]["total_ms"] + k["k_sub_v_argmax"]["total_ms"]) / 1e3
+        out["k_sub_h+k_sub_v_argmax"] = {
+            "bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": st["sub_bytes"] / s / 1e9,
+            "frac": st["sub_bytes"] / s / 1e9 / hbm, "fp32_tflops": st["sub_flops"] / s / 1e12,
+            "fp32_frac": st["sub_flops"] / s / 1e12 / fma,
+            "bytes_note": "PSF regions read once + residual read and written once per iteration"}
+    if "k_smooth_h" in k and "k_smooth_v_argmax" in k:
+        s = (k["k_smooth_h"]["total_ms"] + k["k_smooth_v_argmax"]["total_ms"]) / 1e3
+        by = 4.0 * m["N"] * st["smooth_iters"]
+        out["k_smooth_h+k_smooth_v_argmax"] = {
+            "bound": "alu", "unit": "TFLOP/s", "peak": fma, "achieved": st["smooth_flops"] / s / 1e12,
+            "frac": st["smooth_flops"] / s / 1e12 / fma, "hbm_gbs": by / s / 1e9, "hbm_frac": by / s / 1e9 / hbm,
+            "bytes_note": "residual read once per smoothing iteration", "smoothing_iterations": st["smooth_iters"]}
+    if "k_argmax_abs" in k and k["k_argmax_abs"]["launches"]:
+        s = k["k_argmax_abs"]["total_ms"] / 1e3
+        by = 4.0 * m["N"] * k["k_argmax_abs"]["launches"]
+        out["k_argmax_abs"] = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": by / s / 1e9,
+                               "frac": by / s / 1e9 / hbm, "bytes_note": "residual read once per launch"}
+    return out
+
+
+def _metric(case, config: int) -> str:
+    return f"minor-cycle iterations/s (Asp-Clean2016, {case.H}x{case.W}, active set <= {case.k_max})"
+
+
+def _config(case, config: int, n_iter: int, world: int) -> dict:
+    return {"workload": f"config{config} {case.H}x{case.W} Asp-Clean2016 minor cycle, k_max {case.k_max}, "
+                        f"{n_iter} iterations/step, gain {case.gain}",
+            "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
+            "l2": "flushed (256 MB write) between steps, outside timing"}
+
+
+def workload_line(a, m: dict, case, world: int, peaks: dict, peak_kind: str, alu: dict, name: str) -> dict:
+    t_ms, iters = m["t_ms"], m["iters"]
+    k = m["kernels"]
+    dominant = max(k, key=lambda n: k[n]["total_ms"])
+    roofs = rooflines(m, peaks, alu)
     traffic = _traffic_record()
-    work = {"k_lm_fit": ("alu", prof_stats["fit_flops"]),
-            "k_sub_h": ("alu", None), "k_sub_v_argmax": ("alu", None)}
-    roof = None
-    kd = kernels[dominant]
-    if dominant == "k_lm_fit":
-        ach = prof_stats["fit_flops"] / (kd["total_ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "kernel": dominant, "avg_launch_ms": kd["total_ms"] / max(kd["launches"], 1),
-                "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"}
-    elif dominant in ("k_sub_h", "k_sub_v_argmax"):
-        # the subtraction's two passes together against HBM (algorithmic bytes)
-        ms = kernels["k_sub_h"]["total_ms"] + kernels["k_sub_v_argmax"]["total_ms"]
-        ach = prof_stats["sub_bytes"] / (ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": ach / float(peaks["hbm_gbs"]), "kernel": "k_sub_h+k_sub_v_argmax",
-                "avg_launch_ms": ms / max(kernels["k_sub_v_argmax"]["launches"], 1),
-                "flops_tflops": prof_stats["sub_flops"] / (ms / 1e3) / 1e12}
+    if dominant in ("k_sub_h", "k_sub_v_argmax"):
+        key = "k_sub_h+k_sub_v_argmax"
+    elif dominant in ("k_smooth_h", "k_smooth_v_argmax"):
+        key = "k_smooth_h+k_smooth_v_argmax"
     else:
-        roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
-                "kernel": dominant}
-    roof["traffic"] = traffic.get(roof.get("kernel", ""), {}).get("bytes_per_launch")
-    roof["peak_source"] = peak_kind
-    _ = work
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        key = dominant
+    r = roofs.get(key, {})
+    roof = {"bound": r.get("bound"), "achieved": r.get("achieved"), "peak": r.get("peak"), "unit": r.get("unit"),
+            "frac": r.get("frac"), "kernel": key,
+            "traffic": traffic.get(key, {}).get("bytes_per_launch"),
+            "peak_source": ("measured by this run's own FP32 FMA microbenchmark (asp_measure_alu_peaks; the larger "
+                            "of scalar and packed two-lane FMA)") if r.get("unit") == "TFLOP/s" else
+                           f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
+    if key == "k_lm_fit":
+        roof["pixel_pass_only"] = r["pixel_pass_only"]
+        roof["ex2"] = r["ex2"]
+        roof["avg_launch_ms"] = r["avg_launch_ms"]
+    return {"metric": _metric(case, int(name[-1])),
+            "value": iters / (t_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": m["steps"],
+            "ms_per_step": t_ms / m["steps"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"config2 {case.H}x{case.W} Asp-Clean2016 minor cycle, k_max {case.k_max}, "
-                                   f"{n_iter} iterations/step, gain {case.gain}",
-                       "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
-                       "l2": "flushed (256 MB write) between steps, outside timing"},
-            "pixel_evals_per_s": pevals / (t_ms / 1e3),
-            "fit_tflops": fit_flops / (t_ms / 1e3) / 1e12,
-            "e2e": e2e, "gpu_launches": n_launch, "roofline": roof, "kernels": kernels,
-            "fit_phases": _fit_phases(prof_stats),
-            "clocks": clk.summary()}
+            "config": _config(case, int(name[-1]), m["n_iter"], world),
+            "pixel_evals_per_s": m["pevals"] / (t_ms / 1e3), "fit_tflops": m["fit_flops"] / (t_ms / 1e3) / 1e12,
+            "e2e": m["e2e"], "gpu_launches": m["n_launch"], "roofline": roof, "kernel_rooflines": roofs,
+            "kernels": k, "fit_phases": _fit_phases(m["prof"]), "clocks": m["clocks"]}
+
+
+def run_ours(a):
+    import torch
+    import paper_1606_07872_gb300 as asp
+    from paper_1606_07872_gb300 import build as _b
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    _b.build()
+    peaks, peak_kind = _peaks()
+    alu = asp.asp_measure_alu_peaks()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    main_cfg = a.config
+    case = _workload(main_cfg, a.size, rank)
+    n_iter = a.iters or case.n_iter
+    m = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush)
+    line = workload_line(a, m, case, world, peaks, peak_kind, alu, f"config{main_cfg}")
+    line["warmup"] = a.warmup
+    line["alu_peaks"] = dict(alu, note="own microbenchmark on this device, this run: one full wave of "
+                                       "independent FMA / ex2.approx chains, CUDA-event timed")
     weights = None
-    if rank == 0 and not a.no_learned:
+    if main_cfg == 2 and not a.no_config3:
+        try:
+            c3 = _workload(3, 4096, rank)
+            m3 = measure_workload(asp, c3, a.config3_iters or c3.n_iter, a.config3_steps, a.config3_warmup,
+                                  local, world, flush)
+            line["config3"] = workload_line(a, m3, c3, world, peaks, peak_kind, alu, "config3")
+            line["config3"]["warmup"] = a.config3_warmup
+            del c3
+        except Exception as e:   # report, never hide, a failed measurement
+            line["config3"] = {"error": repr(e)[:300]}
+    if rank == 0 and main_cfg == 2 and not a.no_learned:
         try:
             line["learned"], weights = learned_comparison(asp, a.learned_train_images)
         except Exception as e:   # report, never hide, a failed comparison
             line["learned"] = {"error": repr(e)[:300]}
-    if rank == 0 and not a.no_batched:
+    if rank == 0 and main_cfg == 2 and not a.no_batched:
         try:
             line["batched"] = batched_comparison(asp, a.batch_images, seed0=1000 * rank, weights=weights)
         except Exception as e:
             line["batched"] = {"error": repr(e)[:300]}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline(a.size, a.cpu_budget)
+            line["cpu_baseline"] = cpu_baseline(asp, main_cfg, case, n_iter, a.cpu_budget)
         except Exception as e:  # report, never hide, a failed baseline
             line["cpu_baseline"] = {"value": None, "error": repr(e)[:200]}
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

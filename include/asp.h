@@ -148,6 +148,8 @@ typedef struct {
     int64_t learned_fits;     /* fits started from the network's proposal */
     int64_t learned_refits;   /* of those, refitted from the plain start by the fallback rule */
     int64_t learned_kept;     /* of those, whose learned-start result was kept */
+    double fit_ex2;           /* exponentials the LM passes evaluate: K per pixel evaluation */
+    int64_t smooth_iters;     /* iterations whose initial values came from the smoothing search */
 } asp_cycle_stats;
 
 /* One minor-cycle iteration as recorded on the device. */
@@ -199,6 +201,26 @@ asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_
 asp_status asp_eval_normal_equations(asp_ctx* ctx, const asp_gauss* theta, int n, int n_old,
                                      int x0, int x1, int y0, int y1,
                                      double* A_host, double* g_host, double* chi2_host);
+
+/* Levenberg-Marquardt (Marquardt 1963, the minimiser of Eq. 6) restarted at
+ * any point of a fit: the fit of asp_fit_active_set defined by init, n and
+ * n_old (window = bounding box of the init members' boxes; target T = R +
+ * the last n_old members' init Gaussians; trial bounds), but LM starts at
+ * start (n rows, host; NULL: init) with damping lambda = lambda0 (> 0,
+ * finite) and stops after max_iter damped solves (>= 0).  Besides the kept
+ * point (out) and the outcome (info; info->lambda is the damping after the
+ * last decision, info->chi2_init chi^2 at start), it returns the last
+ * proposed trial point theta + delta of the last damped solve (trial_out, n
+ * rows, host; may be NULL) and chi^2 of the last pixel pass (chi2_trial,
+ * host; may be NULL), which is chi^2 at that trial point when it was
+ * evaluated (info->passes counts the passes: the start plus each evaluated
+ * trial).  With max_iter = 1 this is one Marquardt step from (theta,
+ * lambda): one damped solve, the trial pass and the accept decision -- the
+ * hook the step-by-step parity tests and measurements use.  Errors as
+ * asp_fit_active_set; ASP_ERR_INVALID_ARG for a bad start, lambda0 or
+ * max_iter. */
+asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, const asp_gauss* start, double lambda0,
+                      int max_iter, asp_gauss* out, asp_fit_info* info, asp_gauss* trial_out, double* chi2_trial);
 
 /* R -= B * (gain * sum_i c_i) with the full PSF (Sect. 2 step 3); c_i is
  * component i sampled on the grid (a flux-normalised Gaussian on the box
@@ -292,10 +314,30 @@ asp_status asp_launch_count(asp_ctx* ctx, int64_t* n);
  * and calls that overlap on the GPU (other threads or streams) race. */
 #define ASP_STATIC_KMAX 8
 #define ASP_STATIC_GRID_MAX 32
-#define ASP_STATIC_SCRATCH_BYTES 5960704
+#define ASP_STATIC_SCRATCH_BYTES 5963776
 asp_status asp_fit_static(const float* image_dev, int H, int W, const asp_gauss* init, int n, int n_old,
                           double omega_min, const asp_params* lm, asp_gauss* out, asp_fit_info* info,
                           void* stream);
+
+/* Measured issue rates of the two pipes the LM pixel pass (Eq. 6 model,
+ * Jacobian and normal equations) runs on, for its ALU roofline: FP32 fused
+ * multiply-add (scalar, and Blackwell's packed two-lane fma.rn.f32x2) and
+ * the MUFU ex2 unit, each from one full wave of independent dependency
+ * chains on every SM of the current device, timed by CUDA events on the
+ * legacy default stream (synchronised), with the SM clock each ran at
+ * (clock64 cycles over event time).  Allocates and frees a few bytes of
+ * scratch.  The paper has no counterpart: it is the measuring rod of the
+ * roofline fractions the benchmark reports. */
+typedef struct {
+    int32_t sms;
+    int32_t reserved;
+    double fp32_fma_tflops;    /* scalar FP32 FMA, 2 flops each, whole device */
+    double fp32_fma2_tflops;   /* packed two-lane FP32 FMA, 2 flops per lane */
+    double ex2_gops;           /* ex2.approx.ftz.f32 results per second (1e9) */
+    double sm_mhz_fma, sm_mhz_fma2, sm_mhz_ex2;     /* SM clock during each kernel */
+    double fma_per_sm_clk, fma2_per_sm_clk, ex2_per_sm_clk;   /* per SM and clock */
+} asp_alu_peaks;
+asp_status asp_measure_alu_peaks(asp_alu_peaks* out);
 
 /* Checkpoint the whole minor-cycle state (residual included) to a file, or
  * restore it into a context of the same size. */

@@ -106,6 +106,10 @@ class FitResult:
     lam: float
     status: int
     pixel_evals: int
+    # the last proposed point theta + delta (None if no solve succeeded) and
+    # chi^2 of the last pixel pass (at that point when it was evaluated)
+    trial: Optional[np.ndarray] = None
+    chi2_trial: float = float("nan")
 
 
 @dataclasses.dataclass
@@ -240,6 +244,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
     chi2_init = chi2
     passes, iters, lam = 1, 0, lm.lambda0
     status = LM_CAP
+    last_trial, last_pass_chi2 = None, chi2
     while True:
         if iters >= lm.max_iter:
             status = LM_CAP
@@ -252,6 +257,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
                 status = LM_STALLED
                 break
             continue
+        last_trial = theta + delta
         # predicted decrease 2 d.g - d.A.d of the linearised model; by the
         # damped normal equations (A + lam D) d = g it equals d.g + lam d.D.d
         dd = np.diag(A).copy()
@@ -260,7 +266,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
         if pred <= lm.rtol * chi2:
             status = LM_CONVERGED
             break
-        trial = theta + delta
+        trial = last_trial
         if not _valid(trial, box, omega_min):
             lam *= lm.lambda_up
             if lam > lm.lambda_max:
@@ -269,6 +275,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
             continue
         A2, g2, chi2_t = normal_equations(T, xs, ys, trial)
         passes += 1
+        last_pass_chi2 = chi2_t
         if chi2_t < chi2:
             rel = (chi2 - chi2_t) / chi2 if chi2 > 0 else 0.0
             scale = np.empty_like(theta)
@@ -288,7 +295,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
             if lam > lm.lambda_max:
                 status = LM_STALLED
                 break
-    return FitResult(theta, chi2_init, chi2, iters, passes, lam, status, passes * n)
+    return FitResult(theta, chi2_init, chi2, iters, passes, lam, status, passes * n, last_trial, last_pass_chi2)
 
 
 # --------------------------------------------------------------------------
@@ -670,12 +677,13 @@ class MinorCycle:
         return chosen, (x0, x1, y0, y1)
 
     # -- one iteration
-    def step(self):
-        if self.stopped:
-            return None
+    def prepare(self):
+        """Steps 1-4 of an iteration without changing the state: the stopping
+        test, the init mode, the initial values, the active set, the window
+        and the fit's target T and start theta0.  None when the noise
+        threshold stops the cycle."""
         pidx, pval = peak_simple(self.R)
         if abs(pval) < self.p.stop_ksigma * self.noise:
-            self.stopped = True
             return None
         mode = self.choose_mode()
         init = self.initial_values(mode)
@@ -690,7 +698,18 @@ class MinorCycle:
             G = self.G(k)
             T += gauss_model(G, xs, ys)
             theta0 += list(G)
-        theta0 = np.array(theta0)
+        return dict(peak_index=pidx, peak_value=pval, mode=mode, init=init, chosen=chosen, window=win,
+                    xs=xs, ys=ys, T=T, theta0=np.array(theta0))
+
+    def step(self):
+        if self.stopped:
+            return None
+        prep = self.prepare()
+        if prep is None:
+            self.stopped = True
+            return None
+        pidx, pval, mode, init = prep["peak_index"], prep["peak_value"], prep["mode"], prep["init"]
+        chosen, win, xs, ys, T, theta0 = (prep[k] for k in ("chosen", "window", "xs", "ys", "T", "theta0"))
         learned = None
         if self.mlp is not None:
             fit, learned = self._learned_fit(T, xs, ys, theta0, win, init)
@@ -730,7 +749,8 @@ class MinorCycle:
         self.last_wi = new.width
         self.last_w0 = init["w0"]
         rec = dict(t=self.t, mode=mode, peak_index=pidx, peak_value=pval, init=init,
-                   members=[new_index] + chosen, window=win, fit=fit, n_terms=len(terms), learned=learned)
+                   members=[new_index] + chosen, window=win, fit=fit, n_terms=len(terms), learned=learned,
+                   T=T, xs=xs, ys=ys, theta0=theta0)
         self.history.append(rec)
         self.t += 1
         return rec

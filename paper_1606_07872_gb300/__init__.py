@@ -23,7 +23,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "AspError", "lib", "default_params", "asp_init", "asp_init_host", "asp_destroy", "asp_get_beam",
-    "asp_find_peak", "asp_fit_active_set", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
+    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_measure_alu_peaks", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
@@ -149,6 +149,34 @@ def asp_fit_active_set(h, init, n_old: int = 0):
     _check(lib().asp_fit_active_set(h, arr, n, int(n_old), out, C.byref(info)), "asp_fit_active_set", h)
     res = np.array([[g.amp, g.x, g.y, g.width] for g in out])
     return res, {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_}
+
+
+def asp_fit_lm(h, init, n_old: int, lambda0: float, max_iter: int, start=None):
+    """The fit defined by ``init`` / ``n_old``, LM started at ``start``
+    (default ``init``) with damping ``lambda0``, at most ``max_iter`` damped
+    solves.  Returns (kept rows, info dict, last trial rows, chi^2 of the
+    last pass)."""
+    arr, n = _gauss_array(init)
+    sarr = None
+    if start is not None:
+        sarr, ns = _gauss_array(start)
+        if ns != n:
+            raise ValueError("start must have as many rows as init")
+    out = (asp_gauss * n)()
+    trial = (asp_gauss * n)()
+    info = asp_fit_info()
+    c2 = C.c_double()
+    _check(lib().asp_fit_lm(h, arr, n, int(n_old), sarr, float(lambda0), int(max_iter), out, C.byref(info), trial,
+                            C.byref(c2)), "asp_fit_lm", h)
+    rows = lambda a: np.array([[g.amp, g.x, g.y, g.width] for g in a])   # noqa: E731
+    return rows(out), {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_}, rows(trial), c2.value
+
+
+def asp_measure_alu_peaks() -> dict:
+    """Measured FP32 FMA and MUFU ex2 issue rates of the current device."""
+    out = _lib.asp_alu_peaks()
+    _check(lib().asp_measure_alu_peaks(C.byref(out)), "asp_measure_alu_peaks")
+    return {f: getattr(out, f) for f, _ in _lib.asp_alu_peaks._fields_ if f != "reserved"}
 
 
 def asp_eval_normal_equations(h, theta, n_old: int, window):
@@ -397,6 +425,9 @@ class Context:
 
     def fit(self, init, n_old=0):
         return asp_fit_active_set(self.h, init, n_old)
+
+    def fit_lm(self, init, n_old, lambda0, max_iter, start=None):
+        return asp_fit_lm(self.h, init, n_old, lambda0, max_iter, start)
 
     def normal_equations(self, theta, n_old, window):
         return asp_eval_normal_equations(self.h, theta, n_old, window)

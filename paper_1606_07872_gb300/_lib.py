@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libasp.so")
 ASP_KMAX = 50
 ASP_STATIC_KMAX = 8
 ASP_STATIC_GRID_MAX = 32
-ASP_STATIC_SCRATCH_BYTES = 5960704
+ASP_STATIC_SCRATCH_BYTES = 5963776
 
 ASP_OK = 0
 STATUS_NAMES = {0: "ASP_OK", 1: "ASP_ERR_INVALID_ARG", 2: "ASP_ERR_CUDA", 3: "ASP_ERR_OOM", 4: "ASP_ERR_NAN",
@@ -62,7 +62,7 @@ class asp_cycle_stats(C.Structure):
                 ("fit_pass_ms", C.c_double), ("fit_reduce_ms", C.c_double), ("fit_solve_ms", C.c_double),
                 ("fit_factor_ms", C.c_double), ("fit_subst_ms", C.c_double), ("fit_refinements", C.c_int64),
                 ("fit_fallbacks", C.c_int64), ("learned_fits", C.c_int64), ("learned_refits", C.c_int64),
-                ("learned_kept", C.c_int64)]
+                ("learned_kept", C.c_int64), ("fit_ex2", C.c_double), ("smooth_iters", C.c_int64)]
 
 
 class asp_iter_record(C.Structure):
@@ -77,6 +77,13 @@ class asp_iter_record(C.Structure):
 class asp_batch_tuning(C.Structure):
     _fields_ = [("px_per_cta", C.c_int32), ("share_policy", C.c_int32), ("n_candidates", C.c_int32),
                 ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+
+class asp_alu_peaks(C.Structure):
+    _fields_ = [("sms", C.c_int32), ("reserved", C.c_int32), ("fp32_fma_tflops", C.c_double),
+                ("fp32_fma2_tflops", C.c_double), ("ex2_gops", C.c_double), ("sm_mhz_fma", C.c_double),
+                ("sm_mhz_fma2", C.c_double), ("sm_mhz_ex2", C.c_double), ("fma_per_sm_clk", C.c_double),
+                ("fma2_per_sm_clk", C.c_double), ("ex2_per_sm_clk", C.c_double)]
 
 
 class asp_kernel_time(C.Structure):
@@ -97,6 +104,8 @@ SIGNATURES = {
                      C.POINTER(C.c_double)],
     "asp_find_peak": [_P, _I, C.POINTER(asp_peak)],
     "asp_fit_active_set": [_P, C.POINTER(asp_gauss), _I, _I, C.POINTER(asp_gauss), C.POINTER(asp_fit_info)],
+    "asp_fit_lm": [_P, C.POINTER(asp_gauss), _I, _I, C.POINTER(asp_gauss), C.c_double, _I, C.POINTER(asp_gauss),
+                   C.POINTER(asp_fit_info), C.POINTER(asp_gauss), C.POINTER(C.c_double)],
     "asp_eval_normal_equations": [_P, C.POINTER(asp_gauss), _I, _I, _I, _I, _I, _I, _P, _P, _P],
     "asp_subtract": [_P, C.POINTER(asp_component), _I, C.c_float],
     "asp_minor_cycle": [_P, _I, C.POINTER(asp_cycle_stats)],
@@ -119,6 +128,7 @@ SIGNATURES = {
     "asp_launch_count": [_P, C.POINTER(C.c_int64)],
     "asp_fit_static": [_P, _I, _I, C.POINTER(asp_gauss), _I, _I, C.c_double, C.POINTER(asp_params),
                        C.POINTER(asp_gauss), C.POINTER(asp_fit_info), _P],
+    "asp_measure_alu_peaks": [C.POINTER(asp_alu_peaks)],
     "asp_save_state": [_P, C.c_char_p],
     "asp_load_state": [_P, C.c_char_p],
     "asp_batch_create": [C.POINTER(asp_params), _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_P), C.POINTER(_P), _I,

@@ -93,6 +93,34 @@ struct asp_ctx {
 
 namespace {
 
+// The public totals of a control block.
+void fill_stats(const CycleState& h, asp_cycle_stats* out) {
+    memset(out, 0, sizeof(*out));
+    out->iterations = h.t;
+    out->components = h.n_comp;
+    out->pixel_evals = h.pixel_evals;
+    out->lm_iters = h.lm_iters;
+    out->lm_passes = h.lm_passes;
+    out->peak_abs = std::fabs((double)h.peak.val);
+    out->stop_reason = h.stop_reason;
+    out->fit_flops = h.fit_flops;
+    out->sub_flops = h.sub_flops;
+    out->sub_bytes = h.sub_bytes;
+    out->smooth_flops = h.smooth_flops;
+    out->fit_pass_ms = h.fit_ns_pass * 1e-6;
+    out->fit_reduce_ms = h.fit_ns_reduce * 1e-6;
+    out->fit_solve_ms = h.fit_ns_solve * 1e-6;
+    out->fit_factor_ms = h.fit_ns_factor * 1e-6;
+    out->fit_subst_ms = h.fit_ns_subst * 1e-6;
+    out->fit_refinements = h.fit_refinements;
+    out->fit_fallbacks = h.fit_fallbacks;
+    out->learned_fits = h.learned_fits;
+    out->learned_refits = h.learned_refits;
+    out->learned_kept = h.learned_kept;
+    out->fit_ex2 = h.fit_ex2;
+    out->smooth_iters = h.smooth_iters;
+}
+
 asp_status fail(asp_ctx* c, asp_status s, const std::string& msg) {
     if (c) {
         c->err = msg;
@@ -629,7 +657,7 @@ asp_status asp_find_peak(asp_ctx* ctx, int mode, asp_peak* out) {
 }
 
 static asp_status run_fit(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, int x0, int x1, int y0, int y1,
-                          int max_iter, FitOut* fo) {
+                          int max_iter, FitOut* fo, double lambda0 = 0.0, const asp_gauss* start = nullptr) {
     FitDesc d;
     memset(&d, 0, sizeof(d));
     d.K = n;
@@ -646,9 +674,17 @@ static asp_status run_fit(asp_ctx* ctx, const asp_gauss* init, int n, int n_old,
         d.theta0[4 * k + 1] = init[k].x;
         d.theta0[4 * k + 2] = init[k].y;
         d.theta0[4 * k + 3] = init[k].width;
+        if (start) {
+            d.start[4 * k] = start[k].amp;
+            d.start[4 * k + 1] = start[k].x;
+            d.start[4 * k + 2] = start[k].y;
+            d.start[4 * k + 3] = start[k].width;
+        }
     }
+    d.has_start = start != nullptr;
     LMConst lmc = ctx->dp.lm;
     if (max_iter >= 0) lmc.max_iter = max_iter;
+    if (lambda0 > 0.0) lmc.lambda0 = lambda0;
     int smem_ok = 1;
     d.grid = fit_grid((long long)d.ww * d.wh, n, lmc.px_per_cta, ctx->g_max, &smem_ok);
     d.smem_ok = smem_ok;
@@ -670,10 +706,13 @@ static bool gauss_ok(const asp_gauss& g) {
     return std::isfinite(g.amp) && std::isfinite(g.x) && std::isfinite(g.y) && std::isfinite(g.width) && g.width > 0;
 }
 
-asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, asp_gauss* out,
-                              asp_fit_info* info) {
-    CHECK_CTX();
+static asp_status fit_common(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, const asp_gauss* start,
+                             double lambda0, int max_iter, asp_gauss* out, asp_fit_info* info, asp_gauss* trial,
+                             double* chi2_trial) {
     if (!init || !out || n < 1 || n > ctx->p.k_max || n_old < 0 || n_old > n) return ASP_ERR_INVALID_ARG;
+    if (start)
+        for (int k = 0; k < n; ++k)
+            if (!gauss_ok(start[k])) return ASP_ERR_INVALID_ARG;
     long long wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0;
     for (int k = 0; k < n; ++k) {
         if (!gauss_ok(init[k])) return ASP_ERR_INVALID_ARG;
@@ -687,14 +726,21 @@ asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_
     wx1 = std::min(wx1, (long long)ctx->W - 1); wy1 = std::min(wy1, (long long)ctx->H - 1);
     if (wx0 > wx1 || wy0 > wy1) return ASP_ERR_INVALID_ARG;
     FitOut fo;
-    asp_status s = run_fit(ctx, init, n, n_old, (int)wx0, (int)wx1, (int)wy0, (int)wy1, -1, &fo);
+    asp_status s = run_fit(ctx, init, n, n_old, (int)wx0, (int)wx1, (int)wy0, (int)wy1, max_iter, &fo, lambda0, start);
     if (s != ASP_OK) return s;
     for (int k = 0; k < n; ++k) {
         out[k].amp = fo.theta[4 * k];
         out[k].x = fo.theta[4 * k + 1];
         out[k].y = fo.theta[4 * k + 2];
         out[k].width = fo.theta[4 * k + 3];
+        if (trial) {
+            trial[k].amp = fo.trial[4 * k];
+            trial[k].x = fo.trial[4 * k + 1];
+            trial[k].y = fo.trial[4 * k + 2];
+            trial[k].width = fo.trial[4 * k + 3];
+        }
     }
+    if (chi2_trial) *chi2_trial = fo.chi2_trial;
     if (info) {
         info->iters = fo.iters;
         info->passes = fo.passes;
@@ -707,6 +753,19 @@ asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_
         info->pixel_evals = fo.pixel_evals;
     }
     return ASP_OK;
+}
+
+asp_status asp_fit_active_set(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, asp_gauss* out,
+                              asp_fit_info* info) {
+    CHECK_CTX();
+    return fit_common(ctx, init, n, n_old, nullptr, 0.0, -1, out, info, nullptr, nullptr);
+}
+
+asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, const asp_gauss* start, double lambda0,
+                      int max_iter, asp_gauss* out, asp_fit_info* info, asp_gauss* trial_out, double* chi2_trial) {
+    CHECK_CTX();
+    if (!(lambda0 > 0.0) || !std::isfinite(lambda0) || max_iter < 0) return ASP_ERR_INVALID_ARG;
+    return fit_common(ctx, init, n, n_old, start, lambda0, max_iter, out, info, trial_out, chi2_trial);
 }
 
 asp_status asp_eval_normal_equations(asp_ctx* ctx, const asp_gauss* theta, int n, int n_old, int x0, int x1, int y0,
@@ -797,30 +856,7 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         if (me) return fail(ctx, ASP_ERR_TIMEOUT, "network inference: tensor-core wait timed out");
     }
     if (h.error == ASP_ERR_NAN || h.nonfinite) return fail(ctx, ASP_ERR_NAN, "non-finite value in the residual");
-    if (out) {
-        out->iterations = h.t;
-        out->components = h.n_comp;
-        out->pixel_evals = h.pixel_evals;
-        out->lm_iters = h.lm_iters;
-        out->lm_passes = h.lm_passes;
-        out->peak_abs = std::fabs((double)h.peak.val);
-        out->stop_reason = h.stop_reason;
-        out->reserved = 0;
-        out->fit_flops = h.fit_flops;
-        out->sub_flops = h.sub_flops;
-        out->sub_bytes = h.sub_bytes;
-        out->smooth_flops = h.smooth_flops;
-        out->fit_pass_ms = h.fit_ns_pass * 1e-6;
-        out->fit_reduce_ms = h.fit_ns_reduce * 1e-6;
-        out->fit_solve_ms = h.fit_ns_solve * 1e-6;
-        out->fit_factor_ms = h.fit_ns_factor * 1e-6;
-        out->fit_subst_ms = h.fit_ns_subst * 1e-6;
-        out->fit_refinements = h.fit_refinements;
-        out->fit_fallbacks = h.fit_fallbacks;
-        out->learned_fits = h.learned_fits;
-        out->learned_refits = h.learned_refits;
-        out->learned_kept = h.learned_kept;
-    }
+    if (out) fill_stats(h, out);
     if (h.stop_reason == ASP_STOP_CAPACITY) return fail(ctx, ASP_ERR_CAPACITY, "component list full");
     return ASP_OK;
 }
@@ -831,28 +867,7 @@ asp_status asp_get_stats(asp_ctx* ctx, asp_cycle_stats* out) {
     CycleState h;
     asp_status s = read_state(ctx, &h);
     if (s != ASP_OK) return s;
-    out->iterations = h.t;
-    out->components = h.n_comp;
-    out->pixel_evals = h.pixel_evals;
-    out->lm_iters = h.lm_iters;
-    out->lm_passes = h.lm_passes;
-    out->peak_abs = std::fabs((double)h.peak.val);
-    out->stop_reason = h.stop_reason;
-    out->reserved = 0;
-    out->fit_flops = h.fit_flops;
-    out->sub_flops = h.sub_flops;
-    out->sub_bytes = h.sub_bytes;
-    out->smooth_flops = h.smooth_flops;
-    out->fit_pass_ms = h.fit_ns_pass * 1e-6;
-    out->fit_reduce_ms = h.fit_ns_reduce * 1e-6;
-    out->fit_solve_ms = h.fit_ns_solve * 1e-6;
-    out->fit_factor_ms = h.fit_ns_factor * 1e-6;
-    out->fit_subst_ms = h.fit_ns_subst * 1e-6;
-    out->fit_refinements = h.fit_refinements;
-    out->fit_fallbacks = h.fit_fallbacks;
-    out->learned_fits = h.learned_fits;
-    out->learned_refits = h.learned_refits;
-    out->learned_kept = h.learned_kept;
+    fill_stats(h, out);
     return ASP_OK;
 }
 
@@ -980,7 +995,8 @@ asp_status asp_set_state(asp_ctx* ctx, const asp_component* comps, int n_comp, c
     h.stopped = 0;
     h.stop_reason = 0;
     h.pixel_evals = h.lm_iters = h.lm_passes = 0;
-    h.fit_flops = h.sub_flops = h.sub_bytes = h.smooth_flops = 0.0;
+    h.fit_flops = h.sub_flops = h.sub_bytes = h.smooth_flops = h.fit_ex2 = 0.0;
+    h.smooth_iters = 0;
     h.fit_ns_pass = h.fit_ns_reduce = h.fit_ns_solve = h.fit_ns_factor = h.fit_ns_subst = 0;
     h.fit_refinements = h.fit_fallbacks = 0;
     CK(cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
@@ -1463,29 +1479,7 @@ asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stat
         if ((h.error == ASP_ERR_NAN || h.nonfinite) && first_err == ASP_OK) first_err = ASP_ERR_NAN;
         if (h.stop_reason == ASP_STOP_CAPACITY && first_err == ASP_OK) first_err = ASP_ERR_CAPACITY;
         if (stats) {
-            asp_cycle_stats& o = stats[i];
-            memset(&o, 0, sizeof(o));
-            o.iterations = h.t;
-            o.components = h.n_comp;
-            o.pixel_evals = h.pixel_evals;
-            o.lm_iters = h.lm_iters;
-            o.lm_passes = h.lm_passes;
-            o.peak_abs = std::fabs((double)h.peak.val);
-            o.stop_reason = h.stop_reason;
-            o.fit_flops = h.fit_flops;
-            o.sub_flops = h.sub_flops;
-            o.sub_bytes = h.sub_bytes;
-            o.smooth_flops = h.smooth_flops;
-            o.fit_pass_ms = h.fit_ns_pass * 1e-6;
-            o.fit_reduce_ms = h.fit_ns_reduce * 1e-6;
-            o.fit_solve_ms = h.fit_ns_solve * 1e-6;
-            o.fit_factor_ms = h.fit_ns_factor * 1e-6;
-            o.fit_subst_ms = h.fit_ns_subst * 1e-6;
-            o.fit_refinements = h.fit_refinements;
-            o.fit_fallbacks = h.fit_fallbacks;
-            o.learned_fits = h.learned_fits;
-            o.learned_refits = h.learned_refits;
-            o.learned_kept = h.learned_kept;
+            fill_stats(h, &stats[i]);
         }
     }
     return first_err;

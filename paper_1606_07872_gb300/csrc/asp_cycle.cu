@@ -146,7 +146,7 @@ __device__ __forceinline__ void cycle_begin_body(CycleState* st, Params p, int H
                     ? ASP_PEAK_SIMPLE : ASP_PEAK_SMOOTH;
     st->mode = mode;
     st->skip_smooth = mode != ASP_PEAK_SMOOTH;
-    if (mode == ASP_PEAK_SMOOTH) st->smooth_flops += smooth_flops;
+    if (mode == ASP_PEAK_SMOOTH) { st->smooth_flops += smooth_flops; st->smooth_iters += 1; }
     if (mode == ASP_PEAK_SIMPLE) {
         const long long idx = st->peak.idx;
         st->init[0] = st->peak.val;
@@ -222,6 +222,7 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
     wx1 = min(wx1, (long long)W - 1); wy1 = min(wy1, (long long)H - 1);
     f.K = K;
     f.n_old = K - 1;
+    f.has_start = 0;
     f.wx0 = (int)wx0; f.wy0 = (int)wy0;
     f.ww = (int)(wx1 - wx0 + 1); f.wh = (int)(wy1 - wy0 + 1);
     f.use_mask = 0;
@@ -331,6 +332,7 @@ __device__ __forceinline__ void update_body(CycleState* st, asp_component* comps
         st->last_w0 = st->init[3];
         st->pixel_evals += fo.pixel_evals;
         st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
+        st->fit_ex2 += (double)fo.pixel_evals * K;
         st->lm_iters += fo.iters;
         st->fit_ns_pass += fo.ns_pass;
         st->fit_ns_reduce += fo.ns_reduce;
@@ -416,6 +418,7 @@ __global__ void k_reset_state(CycleState* st) {
     st->last_wi = 0.0; st->last_w0 = 0.0;
     st->pixel_evals = 0; st->lm_iters = 0; st->lm_passes = 0;
     st->fit_flops = 0.0; st->sub_flops = 0.0; st->sub_bytes = 0.0; st->smooth_flops = 0.0;
+    st->fit_ex2 = 0.0; st->smooth_iters = 0;
     st->fit_ns_pass = 0; st->fit_ns_reduce = 0; st->fit_ns_solve = 0; st->fit_ns_factor = 0; st->fit_ns_subst = 0;
     st->fit_refinements = 0; st->fit_fallbacks = 0;
     st->nonfinite = 0;
@@ -538,6 +541,7 @@ __device__ void copy_words(void* dst, const void* src, int bytes) {
 __device__ void account_fit(CycleState* st, const FitOut& fo, int K) {
     st->pixel_evals += fo.pixel_evals;
     st->fit_flops += (double)fo.pixel_evals * pixel_eval_flops(K);
+    st->fit_ex2 += (double)fo.pixel_evals * K;
     st->lm_iters += fo.iters;
     st->lm_passes += fo.passes;
     st->fit_ns_pass += fo.ns_pass;

@@ -38,8 +38,8 @@ struct LMConst {
 };
 
 // One joint fit: K members, the trailing n_old of which are added back into
-// the target.  Window in source-image coordinates.
-struct FitDesc {
+// the target (at their theta0 values).  Window in source-image coordinates.
+struct FitDescHead {
     int K, n_old;
     int wx0, wy0, ww, wh;
     int use_mask, grid;
@@ -48,6 +48,14 @@ struct FitDesc {
     double bx0, bx1, by0, by1;     // trial centres must stay inside this box
     int active, smem_ok;
     double theta0[PMAX];
+};
+// The fit's description plus an optional LM start other than theta0 (which
+// still defines the added-back members' images in the target, the window
+// and the trial bounds): restarting LM from any point of a fit.  The fit
+// kernel keeps only the head in shared memory and reads the start once.
+struct FitDesc : FitDescHead {
+    int has_start, pad_start;
+    double start[PMAX];
 };
 
 struct FitOut {
@@ -58,6 +66,8 @@ struct FitOut {
     long long ns_pass, ns_reduce, ns_solve;   // time split of the fit (CTA 0)
     long long ns_factor, ns_subst;            // parts of ns_solve: damped solves, LM logic
     int refinements, fallbacks;               // FP64 refinement steps, FP64-factor fallbacks
+    double trial[PMAX];                       // the last proposed point (theta + delta of the last solve)
+    double chi2_trial;                        // chi^2 of the last pixel pass (at the last evaluated point)
 };
 
 // A separable subtraction term: image value scale * wx[i] * wy[j] at
@@ -104,6 +114,8 @@ struct CycleState {
     int members[KMAX];             // component index of each fit member (-1: new)
     long long pixel_evals, lm_iters, lm_passes;
     double fit_flops, sub_flops, sub_bytes, smooth_flops;   // algorithmic work totals
+    double fit_ex2;                                         // exponentials of the LM passes (K per pixel evaluation)
+    long long smooth_iters;                                 // iterations that ran the smoothing peak search
     long long fit_ns_pass, fit_ns_reduce, fit_ns_solve;     // fit time split
     long long fit_ns_factor, fit_ns_subst;
     long long fit_refinements, fit_fallbacks;

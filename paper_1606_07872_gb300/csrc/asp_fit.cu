@@ -739,7 +739,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     float* sums32 = reinterpret_cast<float*>(sums + 2 * NACC_MAX);            // FP32 copies of both buffers
     float2* chib = reinterpret_cast<float2*>(sums + 3 * NACC_MAX);            // chi^2 partials, 2 x FIT_GRID_MAX
 
-    __shared__ FitDesc d;
+    __shared__ FitDescHead d;
     __shared__ MemberFrame fr[KMAX];
     __shared__ short2 ttab[NTILES_MAX];     // layout tile t -> (bi, bj), row-major upper triangle
     __shared__ short tperm[NTILES_MAX];     // SYRK thread order -> layout tile
@@ -757,7 +757,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     {
         const int* srcw = reinterpret_cast<const int*>(descp);
         int* dstw = reinterpret_cast<int*>(&d);
-        for (int i = tid; i < (int)(sizeof(FitDesc) / sizeof(int)); i += blockDim.x) dstw[i] = srcw[i];
+        for (int i = tid; i < (int)(sizeof(FitDescHead) / sizeof(int)); i += blockDim.x) dstw[i] = srcw[i];
     }
     __syncthreads();
     if (!d.active) return;
@@ -835,13 +835,14 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         }
         if (in_smem) Ts[i] = v; else Tg[gi] = v;
     }
+    const bool has_start = descp->has_start != 0;
     if (tid == 0) {
-        for (int i = 0; i < P; ++i) theta[i] = d.theta0[i];
+        for (int i = 0; i < P; ++i) theta[i] = has_start ? descp->start[i] : d.theta0[i];
         s_lam = lmc.lambda0; s_cur = 0; s_iters = 0; s_passes = 0; s_status = ASP_LM_CAP;
         s_done = 0; s_err = 0; s_flag = 0;
         sw.refinements = 0; sw.fallbacks = 0;
     }
-    for (int i = tid; i < P; i += blockDim.x) trial[i] = d.theta0[i];
+    for (int i = tid; i < P; i += blockDim.x) trial[i] = has_start ? descp->start[i] : d.theta0[i];
     __syncthreads();
 
     // pixel coordinates of this thread's J row in the first chunk (the only
@@ -1303,6 +1304,8 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         out->passes = s_passes;
         out->status = s_status;
         out->pixel_evals = (long long)s_passes * Wn;
+        for (int i = 0; i < P; ++i) out->trial[i] = trial[i];
+        out->chi2_trial = s_chi2_t;
     }
 }
 

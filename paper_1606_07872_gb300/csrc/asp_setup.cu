@@ -52,6 +52,7 @@ __global__ void k_beam_init(FitDesc* d, const float* __restrict__ B, int H, int 
     const int y0 = max(0, H - r), y1 = min(2 * H - 1, H + r);
     d->K = 1;
     d->n_old = 0;
+    d->has_start = 0;
     d->wx0 = x0; d->wy0 = y0; d->ww = x1 - x0 + 1; d->wh = y1 - y0 + 1;
     d->use_mask = 1;
     d->mcx = W; d->mcy = H; d->mr2 = (double)r * r;

@@ -16,6 +16,7 @@
 // a device shares it and it keeps the last call's contents, so the entry
 // point clears what must start at zero (the grid-barrier counter and the fit
 // output) on each call; calls that overlap on the GPU race on it.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -96,7 +97,10 @@ extern "C" asp_status asp_fit_static(const float* image_dev, int H, int W, const
     long long wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0;
     for (int k = 0; k < n; ++k) {
         const asp_gauss& g = init[k];
-        if (!(g.width > 0) || g.width != g.width || g.amp != g.amp || g.x != g.x || g.y != g.y)
+        // finite values and a positive width, as asp_fit_active_set requires
+        // (an infinite centre or width would reach member_box's integer casts)
+        if (!std::isfinite(g.amp) || !std::isfinite(g.x) || !std::isfinite(g.y) || !std::isfinite(g.width) ||
+            !(g.width > 0))
             return ASP_ERR_INVALID_ARG;
         long long b[4];
         member_box(g.x, g.y, g.width, b);
@@ -161,7 +165,9 @@ extern "C" asp_status asp_fit_static(const float* image_dev, int H, int W, const
     FitOut fo;
     if (cudaMemcpyAsync(&fo, out_dev, sizeof(FitOut), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ASP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return ASP_ERR_CUDA;
-    if (fo.error) return ASP_ERR_TIMEOUT;
+    // FitOut.error carries the asp_status the kernel recorded (a bounded
+    // grid-barrier wait that gave up sets ASP_ERR_TIMEOUT)
+    if (fo.error) return fo.error > ASP_OK && fo.error <= ASP_ERR_CAPACITY ? (asp_status)fo.error : ASP_ERR_CUDA;
     for (int k = 0; k < n; ++k) {
         out[k].amp = fo.theta[4 * k];
         out[k].x = fo.theta[4 * k + 1];

@@ -52,9 +52,9 @@ def test_struct_sizes_match_header(libpath):
 #include <stdio.h>
 #include "asp.h"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(asp_gauss), sizeof(asp_component), sizeof(asp_peak),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(asp_gauss), sizeof(asp_component), sizeof(asp_peak),
          sizeof(asp_fit_info), sizeof(asp_params), sizeof(asp_cycle_stats), sizeof(asp_iter_record),
-         sizeof(asp_batch_tuning), sizeof(asp_kernel_time));
+         sizeof(asp_batch_tuning), sizeof(asp_kernel_time), sizeof(asp_alu_peaks));
   return 0;
 }}
 """
@@ -67,7 +67,7 @@ int main(void) {{
         sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (_lib.asp_gauss, _lib.asp_component, _lib.asp_peak, _lib.asp_fit_info,
                                        _lib.asp_params, _lib.asp_cycle_stats, _lib.asp_iter_record,
-                                       _lib.asp_batch_tuning, _lib.asp_kernel_time)]
+                                       _lib.asp_batch_tuning, _lib.asp_kernel_time, _lib.asp_alu_peaks)]
     assert sizes == mine
 
 
@@ -89,3 +89,14 @@ def test_null_and_bad_arguments_rejected_without_gpu(libpath):
     assert L.asp_init(ctypes.byref(p), 8, 8, 1, 1, None, ctypes.byref(h)) == 8
     assert L.asp_destroy(None) == 1
     assert L.asp_minor_cycle(None, 1, None) == 1
+
+
+def test_binding_constants_match_header():
+    """Every #define of include/asp.h that the binding mirrors has the same
+    value there."""
+    from paper_1606_07872_gb300 import _lib
+    defs = dict(re.findall(r"#define\s+(ASP_[A-Z_0-9]+)\s+(\d+)", open(HEADER).read()))
+    assert defs, "no numeric #define found"
+    for name, val in defs.items():
+        assert hasattr(_lib, name), name
+        assert getattr(_lib, name) == int(val), name

@@ -62,3 +62,28 @@ def test_fit_phases_per_lm_iteration():
     # no fit ran: no division by zero
     zero = dict(st, lm_iters=0, fit_pass_ms=0.0)
     assert bench._fit_phases(zero)["us_per_lm_iter"]["pixel_pass"] == 0.0
+
+
+def test_rooflines_from_algorithmic_work():
+    """Each kernel class's achieved rate is the method's algorithmic work over
+    its event-timed launch time, against the measured peak of its bound."""
+    import bench
+    m = {"N": 1024 * 1024,
+         "kernels": {"k_lm_fit": {"launches": 10, "total_ms": 100.0}, "k_sub_h": {"launches": 10, "total_ms": 3.0},
+                     "k_sub_v_argmax": {"launches": 10, "total_ms": 1.0},
+                     "k_smooth_h": {"launches": 10, "total_ms": 4.0},
+                     "k_smooth_v_argmax": {"launches": 10, "total_ms": 4.0},
+                     "k_argmax_abs": {"launches": 2, "total_ms": 0.01}},
+         "prof": {"fit_flops": 4e12, "fit_pass_ms": 40.0, "fit_ex2": 1e11, "sub_bytes": 8e9, "sub_flops": 4e10,
+                  "smooth_flops": 8e10, "smooth_iters": 100}}
+    alu = {"fp32_fma_tflops": 76.0, "fp32_fma2_tflops": 80.0, "ex2_gops": 10000.0}
+    r = bench.rooflines(m, {"hbm_gbs": 6800.0}, alu)
+    f = r["k_lm_fit"]
+    assert f["peak"] == 80.0 and f["achieved"] == pytest.approx(40.0) and f["frac"] == pytest.approx(0.5)
+    assert f["pixel_pass_only"]["achieved"] == pytest.approx(100.0)
+    assert f["ex2"]["achieved_gops"] == pytest.approx(1000.0) and f["ex2"]["frac"] == pytest.approx(0.1)
+    s = r["k_sub_h+k_sub_v_argmax"]
+    assert s["achieved"] == pytest.approx(2000.0) and s["frac"] == pytest.approx(2000.0 / 6800.0)
+    sm = r["k_smooth_h+k_smooth_v_argmax"]
+    assert sm["achieved"] == pytest.approx(10.0) and sm["hbm_gbs"] == pytest.approx(4.0 * 1024 * 1024 * 100 / 8e-3 / 1e9)
+    assert r["k_argmax_abs"]["achieved"] == pytest.approx(4.0 * 1024 * 1024 * 2 / 1e-5 / 1e9)

@@ -11,6 +11,8 @@ import pytest
 
 import oracle as O
 import synth
+from tests import fp32_bounds as FB
+from tests import teacher
 
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
@@ -172,26 +174,13 @@ def test_normal_equations_within_fp32_bound(asp, K, n_old):
     old = theta[K - n_old:].ravel()
     if n_old:
         T = T + O.gauss_model(old, xs, ys)
-    Ao, go, co = O.normal_equations(T, xs, ys, theta.ravel())
-    model, J = O.model_and_jacobian(theta.ravel(), xs, ys)
-    r = T - model
-    n = xs.size
-    # FP32 error model: a Jacobian entry of member k carries a relative error
-    # (8 + 2 |arg_k|) u32 (exponent argument rounding grows with r^2 / 2w^2,
-    # plus ex2 and the products); r carries 8 u32 (|T| + sum |g_k|) plus the
-    # members' own evaluation errors; the sums add (64 + log2 n + 16) u32 of
-    # sum |terms| (leaf + Kahan + trees).
-    th = theta.reshape(-1, 4)
-    eps = np.stack([(8 + 2 * ((xs - x0) ** 2 + (ys - y0) ** 2) / (2 * w * w)) * U32 for _, x0, y0, w in th], 1)
-    aJ = np.abs(J)
-    EJ = np.repeat(eps, 4, axis=1) * aJ
-    scale_r = np.abs(T) + O.gauss_model(np.abs(theta.ravel()), xs, ys)     # |T| + sum_k |g_k|
-    Er = 8 * U32 * scale_r + (aJ[:, 0::4] * eps * np.abs(th[:, 0])).sum(1)
-    c = 64 + np.log2(n) + 16
-    tiny = 4 * n * 2.0 ** -149          # FP32 absolute underflow floor per accumulated product
-    bA = EJ.T @ aJ + aJ.T @ EJ + c * U32 * (aJ.T @ aJ) + tiny
-    bg = EJ.T @ np.abs(r) + aJ.T @ Er + c * U32 * (aJ.T @ np.abs(r)) + tiny
-    bc = 2 * float(np.abs(r) @ Er) + c * U32 * float(r @ r) + tiny
+    # the FP32 error model of the pass (tests/fp32_bounds.py): Jacobian
+    # entries (8 + 2 |arg_k|) u32 relative, residual 8 u32 (|T| + sum |g_k|)
+    # plus the members' evaluation errors, sums (64 + log2 n + 16) u32 of
+    # sum |terms|; the oracle's FP64 sums are the reference
+    pb = FB.pass_bounds(T, xs, ys, theta.ravel())
+    Ao, go, co = pb["A"], pb["g"], pb["chi2"]
+    bA, bg, bc = pb["bA"], pb["bg"], pb["bc"]
     assert np.all(np.abs(A - Ao) <= bA + 1e-300), np.max(np.abs(A - Ao) / (bA + 1e-300))
     assert np.all(np.abs(g - go) <= bg + 1e-300), np.max(np.abs(g - go) / (bg + 1e-300))
     assert abs(chi2 - co) <= bc, (chi2, co, bc)
@@ -252,76 +241,39 @@ def test_large_window_multi_cta_fit(asp):
 # ----------------------------------------------------------------- minor cycle (a2-a10)
 
 def _oracle_from_gpu_state(ctx, case, p, beam):
-    st = ctx.state()
-    mc = O.MinorCycle(case.dirty, case.psf, p, beam=beam)
-    comps = [O.Component(c[0], c[1], c[2], c[3], c[4], bool(c[5])) for c in st["comps"]]
-    mc.set_state(ctx.residual().astype(np.float64), comps, st["retained"], st["t"], st["last_wi"],
-                 st["last_w0"])
-    return mc
+    return teacher.oracle_from_state(ctx, case, p, beam)[0]
 
 
 TIGHT = dict(lm_max_iter=300, lm_rtol=1e-12, lm_xtol=1e-10)
 
 
 @pytest.mark.parametrize("k_max", [1, 3, 5])
-def test_teacher_forced_minor_cycle_steps(asp, k_max):
-    """Each iteration starts both sides from the GPU's state: the discrete
-    decisions (mode, window, active set) must agree exactly; where the fit
-    converged, the GPU's chi^2 is the oracle optimum's within 1e-5 (the FP32
-    evaluation floor) and every parameter agrees with the optimum within
-    1e-4, or within the extent of the chi^2 valley at that floor where the
-    valley is wider (flat directions of joint fits); the residual update
-    agrees within 3e-4 relative L2.  Both sides run LM to the optimum (tight
-    tolerances; the GPU ends at its FP32 floor)."""
+def test_teacher_forced_minor_cycle_steps(asp, k_max, capsys):
+    """Each iteration starts both sides from the GPU's state (tests/teacher.py):
+    the discrete decisions agree exactly; the GPU's residual update is the
+    oracle's subtraction of the GPU's fitted components within 1e-5
+    relative L2; where the fits converged, every parameter is within 1e-4
+    of its scale of the oracle's optimum, or within twice the first-order
+    FP32 floor |A^-1| dg where that is larger.  Both sides run LM to the
+    optimum (tight tolerances; the GPU ends at its FP32 floor)."""
     case = synth.small_case(96, 104, seed=11, n_points=3, n_gauss=2, sigma_range=(2.5, 6))
     ctx = _ctx(asp, case, k_max=k_max, **TIGHT)
     ab, wb, _, _ = ctx.beam
     p = O.AspParams(k_max=k_max, noise_sigma=case.noise_sigma, lm=O.lm_exact())
-    checked = 0
+    stats = teacher.Stats()
     for it in range(12):
-        mc = _oracle_from_gpu_state(ctx, case, p, (ab, wb))
+        mc, st = teacher.oracle_from_state(ctx, case, p, (ab, wb))
         R_before = mc.R.copy()
-        G_pre = {k: mc.G(k) for k in mc.retained}
         rec = mc.step()
         if rec is None:
             break
         ctx.minor_cycle(1)
-        h = ctx.history()[-1]
-        assert h["mode"] == rec["mode"]
-        assert (h["x0"], h["x1"], h["y0"], h["y1"]) == tuple(rec["window"])
-        assert h["k"] == len(rec["members"])
-        fit = rec["fit"]
-        if fit.status != O.LM_CONVERGED or h["status"] == O.LM_CAP:
-            continue            # trajectories of capped fits are not unique
-        th_gpu, _ = ctx.last_fit()
-        th_orc = fit.theta.reshape(-1, 4)
-        # chi^2 of the GPU's fit, evaluated by the oracle on the same target,
-        # is the optimum's up to the FP32 evaluation floor
-        x0, x1, y0, y1 = rec["window"]
-        yy, xx = np.mgrid[y0:y1 + 1, x0:x1 + 1]
-        xx, yy = xx.ravel().astype(float), yy.ravel().astype(float)
-        T = R_before[y0:y1 + 1, x0:x1 + 1].ravel().copy()
-        for k in rec["members"][1:]:
-            T += O.gauss_model(G_pre[k], xx, yy)
-        chi2_gpu = float(np.sum((T - O.gauss_model(th_gpu.ravel(), xx, yy)) ** 2))
-        assert chi2_gpu <= fit.chi2 * (1 + 1e-5) + 1e-12
-        # parameters: the 1e-4 bar, widened along directions where chi^2 is
-        # flatter than the FP32 evaluation floor: |d theta_i| may reach the
-        # valley's extent sqrt(2 dchi2 (A^-1)_ii) at dchi2 = 1e-5 chi^2, with A
-        # the oracle's J^T J at its optimum
-        A, _, _ = O.normal_equations(T, xx, yy, fit.theta)
-        cov = np.linalg.pinv(A)
-        valley = np.sqrt(np.maximum(2 * 1e-5 * fit.chi2 * np.diag(cov), 0.0)).reshape(-1, 4)
-        for m in range(len(rec["members"])):
-            a, x, y, w = th_orc[m]
-            tol = np.maximum([1e-4 * abs(a), 1e-4 * max(1.0, w), 1e-4 * max(1.0, w), 1e-4 * w], 2 * valley[m])
-            assert np.all(np.abs(th_gpu[m] - th_orc[m]) <= tol), (m, th_gpu[m], th_orc[m], tol)
-        R = ctx.residual().astype(np.float64)
-        # the update follows the fitted components: 3e-4 for a single member,
-        # 1e-2 where a joint fit may sit elsewhere in its flat valley
-        assert _rel_l2(R - R_before, mc.R - R_before) < (3e-4 if len(rec["members"]) == 1 else 1e-2)
-        checked += 1
-    assert checked >= 3
+        teacher.check_iteration(ctx, case, rec, R_before, st, stats)
+    assert stats.fits >= 3 and stats.updates >= 10
+    with capsys.disabled():
+        print(f"\nk_max {k_max}: {stats.fits} converged fits, {stats.params_beyond_1e4}/{stats.params} parameters "
+              f"beyond 1e-4 (within the FP32 floor), max |dtheta|/scale {stats.max_rel_param:.2e}; "
+              f"residual updates max rel L2 {stats.max_rel_update:.2e}")
     ctx.close()
 
 
@@ -450,14 +402,16 @@ def test_config2_full_size_sampled(asp):
     pk = ctx.find_peak(asp.ASP_PEAK_SIMPLE)
     idx, val = O.peak_simple(R)
     assert pk["index"] == idx
-    # one teacher-forced iteration at full size
+    # teacher-forced iterations at full size (tests/teacher.py), with the
+    # run's own LM settings: decisions, the residual update (1e-5), and the
+    # parameters of converged fits (1e-4 or the FP32 floor)
     p = O.AspParams(k_max=case.k_max, noise_sigma=case.noise_sigma)
-    mc = _oracle_from_gpu_state(ctx, case, p, (ab, wb))
-    R0 = mc.R.copy()
-    rec = mc.step()
-    ctx.minor_cycle(1)
-    h = ctx.history()[-1]
-    assert h["mode"] == rec["mode"] and h["k"] == len(rec["members"])
-    if rec["fit"].status == O.LM_CONVERGED and h["status"] == O.LM_CONVERGED:
-        assert _rel_l2(ctx.residual() - R0, mc.R - R0) < 1e-3
+    stats = teacher.Stats()
+    for it in range(3):
+        mc, st = teacher.oracle_from_state(ctx, case, p, (ab, wb))
+        R_before = mc.R.copy()
+        rec = mc.step()
+        ctx.minor_cycle(1)
+        teacher.check_iteration(ctx, case, rec, R_before, st, stats)
+    assert stats.updates == 3
     ctx.close()

@@ -427,3 +427,76 @@ def test_minor_cycle_recovers_total_flux_and_reaches_noise():
     assert st["residual_max"] < 3 * case.noise_sigma
     assert st["model_flux"] == pytest.approx(case.sky.sum(), rel=0.01)
     assert st["residual_rms"] == pytest.approx(case.noise_sigma, rel=0.1)
+
+
+# ----------------------------------------------------------------- noise level, init switch, boxes (readings)
+
+def test_mad_sigma_hand_computed_and_normal_consistency():
+    """1.4826 x MAD: hand-computed medians on small arrays (odd and even
+    length, an outlier), and the estimator's defining property -- on a
+    normal sample it estimates the standard deviation, since the median of
+    |N(0, s^2)| is s times the 0.75 quantile of N(0, 1), 0.674490 (so
+    1.4826 = 1 / 0.674490 to five digits)."""
+    assert O.mad_sigma([1.0, 2.0, 3.0, 4.0, 100.0]) == pytest.approx(1.4826, rel=1e-15)   # med 3, |dev| med 1
+    assert O.mad_sigma([1.0, 2.0, 3.0, 4.0]) == pytest.approx(1.4826, rel=1e-15)          # med 2.5, |dev| med 1
+    assert O.mad_sigma([[5.0, 5.0], [5.0, 9.0]]) == 0.0                                     # med 5, |dev| med 0
+    assert O.mad_sigma([-2.0, 0.0, 0.0, 0.0, 6.0]) == 0.0
+    assert 1.0 / 1.4826 == pytest.approx(0.6744897501960817, rel=1e-4)                      # Phi^-1(3/4)
+    rng = np.random.default_rng(12)
+    for s in (1e-3, 2.5):
+        x = rng.normal(0.7, s, 1_000_000)
+        assert O.mad_sigma(x) == pytest.approx(s, rel=0.01)
+
+
+def _mc_with_last(t, last_wi, last_w0, area_frac=0.05, init_mode="auto"):
+    c = synth.small_case(24, 24, seed=0, n_points=1, n_gauss=0)
+    mc = O.MinorCycle(c.dirty, c.psf, O.AspParams(area_frac=area_frac, init_mode=init_mode, noise_sigma=1e-3),
+                      beam=(1.0, 1.5))
+    mc.t, mc.last_wi, mc.last_w0 = t, last_wi, last_w0
+    return mc
+
+
+def test_choose_mode_five_percent_area_rule():
+    """Sect. 3: the simple method iff the area of the last optimal component
+    is below 5 % of the area of the last initial guess (area ~ width^2).
+    Constructed cases: the first iteration has no history (smoothing); a
+    point component (omega_i = 0) means the simple method; areas just below
+    and above 5 %; a width ratio of 0.1 is an area ratio of 0.01; exact
+    equality is not 'below' (area_frac 1/4 and widths 1 and 2 make it exact
+    in binary)."""
+    assert _mc_with_last(0, 0.0, 1.5).choose_mode() == O.MODE_SMOOTH
+    assert _mc_with_last(3, 0.0, 1.5).choose_mode() == O.MODE_SIMPLE
+    assert _mc_with_last(3, 0.2236, 1.0).choose_mode() == O.MODE_SIMPLE      # area ratio 0.049997
+    assert _mc_with_last(3, 0.2237, 1.0).choose_mode() == O.MODE_SMOOTH      # area ratio 0.050042
+    assert _mc_with_last(3, 0.1, 1.0).choose_mode() == O.MODE_SIMPLE
+    assert _mc_with_last(3, 1.0, 2.0, area_frac=0.25).choose_mode() == O.MODE_SMOOTH
+    assert _mc_with_last(3, 0.999, 2.0, area_frac=0.25).choose_mode() == O.MODE_SIMPLE
+    assert _mc_with_last(3, 5.0, 1.0, init_mode="simple").choose_mode() == O.MODE_SIMPLE
+    assert _mc_with_last(3, 0.0, 1.0, init_mode="smooth").choose_mode() == O.MODE_SMOOTH
+
+
+def test_member_box_half_width_and_rounding():
+    """Member box: half-width max(5, ceil(4 omega)) around the centre
+    rounded half up; values worked by hand."""
+    assert O.member_box(10.0, 20.0, 1.0) == (5, 15, 15, 25)          # 4 omega = 4 < 5
+    assert O.member_box(10.0, 20.0, 1.25) == (5, 15, 15, 25)         # ceil(5.0) = 5
+    assert O.member_box(10.0, 20.0, 1.26) == (4, 16, 14, 26)         # ceil(5.04) = 6
+    assert O.member_box(2.5, 3.49, 2.0) == (-5, 11, -5, 11)          # 2.5 -> 3, 3.49 -> 3, h = 8
+    assert O.member_box(-0.5, -1.5, 0.5) == (-5, 5, -6, 4)           # -0.5 -> 0, -1.5 -> -1
+    assert O.member_box(7.5, 8.5, 30.0) == (-112, 128, -111, 129)    # h = 120
+
+
+def test_window_is_clipped_bounding_box_of_member_boxes():
+    """The joint window: bounding box of the members' boxes clipped to the
+    image, worked by hand for a new member at a corner and one retained
+    member reaching past the opposite edge."""
+    c = synth.small_case(40, 50, seed=0, n_points=1, n_gauss=0)
+    mc = O.MinorCycle(c.dirty, c.psf, O.AspParams(k_max=3, noise_sigma=1e-3), beam=(1.0, 1.5))
+    # retained member: flux 1, width 3 -> omega_ic = sqrt(9 + 2.25) = 3.354, h = ceil(13.42) = 14
+    mc.comps = [O.Component(1.0, 1.0 / (2 * math.pi * 9.0), 8.4, 33.2, 3.0, False)]
+    mc.retained = [0]
+    chosen, win = mc.select(dict(a0=1.0, x0=2.0, y0=37.0, w0=1.5))   # new box: h = 6, (-4, 8, 31, 43)
+    assert chosen == [0]                                              # 6.4^2 + 3.8^2 > 3.354^2
+    assert win == (0, 22, 19, 39)                                     # (-6, 22, 19, 47) clipped to 50 x 40
+    chosen, win = mc.select(dict(a0=1.0, x0=49.0, y0=0.0, w0=1.5))   # far corner: no overlap
+    assert chosen == [] and win == (43, 49, 0, 6)

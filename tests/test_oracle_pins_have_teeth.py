@@ -97,3 +97,70 @@ def test_gain_on_wrong_side_is_caught(monkeypatch):
     monkeypatch.setattr(OA.MinorCycle, "_component_from_fit", bad)
     with pytest.raises(AssertionError):
         pins.test_first_iteration_on_point_source_gaussian_psf()
+
+
+def test_mad_without_normal_factor_is_caught(monkeypatch):
+    def bad(img):
+        v = np.asarray(img, dtype=np.float64).ravel()
+        return float(np.median(np.abs(v - np.median(v))))
+
+    _patch(monkeypatch, "mad_sigma", bad)
+    with pytest.raises(AssertionError):
+        pins.test_mad_sigma_hand_computed_and_normal_consistency()
+
+
+def test_mad_as_mean_deviation_is_caught(monkeypatch):
+    def bad(img):
+        v = np.asarray(img, dtype=np.float64).ravel()
+        return 1.4826 * float(np.mean(np.abs(v - np.median(v))))
+
+    _patch(monkeypatch, "mad_sigma", bad)
+    with pytest.raises(AssertionError):
+        pins.test_mad_sigma_hand_computed_and_normal_consistency()
+
+
+def test_switch_on_widths_instead_of_areas_is_caught(monkeypatch):
+    def bad(self):
+        if self.t > 0 and self.last_wi < self.p.area_frac * self.last_w0:
+            return O.MODE_SIMPLE
+        return O.MODE_SMOOTH
+
+    monkeypatch.setattr(OA.MinorCycle, "choose_mode", bad)
+    with pytest.raises(AssertionError):
+        pins.test_choose_mode_five_percent_area_rule()
+
+
+def test_switch_with_non_strict_threshold_is_caught(monkeypatch):
+    def bad(self):
+        if self.t > 0 and self.last_wi ** 2 <= self.p.area_frac * self.last_w0 ** 2:
+            return O.MODE_SIMPLE
+        return O.MODE_SMOOTH
+
+    monkeypatch.setattr(OA.MinorCycle, "choose_mode", bad)
+    with pytest.raises(AssertionError):
+        pins.test_choose_mode_five_percent_area_rule()
+
+
+def test_member_box_with_half_even_rounding_is_caught(monkeypatch):
+    def bad(x, y, w):
+        h = max(5, int(math.ceil(4.0 * w)))
+        rx, ry = int(round(x)), int(round(y))       # Python rounds halves to even
+        return (rx - h, rx + h, ry - h, ry + h)
+
+    _patch(monkeypatch, "member_box", bad)
+    with pytest.raises(AssertionError):
+        pins.test_member_box_half_width_and_rounding()
+
+
+def test_window_without_clipping_is_caught(monkeypatch):
+    orig = OA.MinorCycle.select
+
+    def bad(self, init):
+        chosen, _ = orig(self, init)
+        boxes = [OA.member_box(init["x0"], init["y0"], init["w0"])] + [OA.member_box(*self.G(k)[1:4]) for k in chosen]
+        return chosen, (min(b[0] for b in boxes), max(b[1] for b in boxes), min(b[2] for b in boxes),
+                        max(b[3] for b in boxes))
+
+    monkeypatch.setattr(OA.MinorCycle, "select", bad)
+    with pytest.raises(AssertionError):
+        pins.test_window_is_clipped_bounding_box_of_member_boxes()

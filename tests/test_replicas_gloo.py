@@ -61,12 +61,12 @@ def test_aggregate_single_process_is_identity():
 
 def test_replicas_are_distinct_images():
     import bench
-    a = bench._workload(64, 0)
-    b = bench._workload(64, 1)
+    a = bench._workload(2, 64, 0)
+    b = bench._workload(2, 64, 1)
     assert a.dirty.shape == b.dirty.shape
     assert abs(a.dirty - b.dirty).max() > 0.0
     # same seed, same image: a rank's workload is reproducible
-    c = bench._workload(64, 0)
+    c = bench._workload(2, 64, 0)
     assert (a.dirty == c.dirty).all() and (a.psf == c.psf).all()
 
 

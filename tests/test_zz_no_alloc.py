@@ -46,8 +46,13 @@ def _close(a, b):
 
 def test_static_fit_matches_context_fit_on_two_calls(asp):
     import torch
-    case = synth.small_case(120, 128, seed=31, n_points=3, n_gauss=2, sigma_range=(2.5, 5.0))
-    img = torch.from_numpy(case.dirty).cuda()
+    case = synth.small_case(160, 168, seed=31, n_points=3, n_gauss=2, sigma_range=(2.5, 5.0))
+    # two known Gaussians (one broad) under the large-window call below, so
+    # that its joint fit is well determined
+    ys, xs = np.mgrid[0:160, 0:168].astype(np.float64)
+    extra = (0.5 * np.exp(-((xs - 84.3) ** 2 + (ys - 79.6) ** 2) / (2 * 8.0 ** 2))
+             + 0.3 * np.exp(-((xs - 78.2) ** 2 + (ys - 86.1) ** 2) / (2 * 3.0 ** 2)))
+    img = torch.from_numpy((case.dirty + extra).astype(np.float32)).cuda()
     psf = torch.from_numpy(case.psf).cuda()
     ctx = asp.Context(img, psf, k_max=4, noise_sigma=case.noise_sigma, lm_max_iter=200, lm_rtol=1e-10,
                       lm_xtol=1e-9)
@@ -57,9 +62,20 @@ def test_static_fit_matches_context_fit_on_two_calls(asp):
     calls = [
         ([[pk["a0"], pk["x0"], pk["y0"], pk["w0"]]], 0),                             # one member
         ([[0.3, 40.0, 52.0, 3.0], [0.2, 46.5, 55.0, 2.5], [0.1, 37.0, 48.0, 2.0]], 2),  # three, two added back
+        # a window of 65 x 65 pixels: more than the static entry point's 32
+        # CTAs cover at the context's tile of 96 pixels, so the two split the
+        # sums differently (FP32 summation order only)
+        ([[0.45, 84.0, 80.0, 7.5], [0.25, 78.0, 86.0, 3.2]], 0),
     ]
-    for init, n_old in calls:
-        ref, ref_info = ctx.fit(init, n_old)
+    refs = [ctx.fit(init, n_old) for init, n_old in calls]
+    assert (refs[2][1]["x1"] - refs[2][1]["x0"] + 1) * (refs[2][1]["y1"] - refs[2][1]["y0"] + 1) > 32 * 96
+    # one warm-up call (module and kernel attributes loaded, scratch address
+    # looked up), then device memory must not change over the later calls
+    rc, _, _ = _static_fit(asp, img, calls[0][0], calls[0][1], 0.25 * wb, params)
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for (init, n_old), (ref, ref_info) in zip(calls, refs):
         rc, got, info = _static_fit(asp, img, init, n_old, 0.25 * wb, params)
         assert rc == 0, asp._lib.STATUS_NAMES.get(rc, rc)
         assert (info.x0, info.x1, info.y0, info.y1) == (ref_info["x0"], ref_info["x1"], ref_info["y0"],
@@ -67,6 +83,9 @@ def test_static_fit_matches_context_fit_on_two_calls(asp):
         assert info.status == ref_info["status"]
         _close(got, ref)
         assert info.chi2_final == pytest.approx(ref_info["chi2_final"], rel=1e-5)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
     ctx.close()
 
 
@@ -81,3 +100,7 @@ def test_static_fit_rejects_sizes_beyond_its_limits(asp):
     big = torch.zeros((2048, 2048), dtype=torch.float32, device="cuda")
     rc, _, _ = _static_fit(asp, big, [[1.0, 1024.0, 1024.0, 400.0]], 0, 0.3, params)
     assert rc == 8                                           # window beyond the scratch's shared memory
+    for bad in ([1.0, 30.0, 30.0, float("inf")], [1.0, float("inf"), 30.0, 2.0], [float("-inf"), 30.0, 30.0, 2.0],
+                [1.0, 30.0, float("nan"), 2.0]):
+        rc, _, _ = _static_fit(asp, img, [bad], 0, 0.3, params)
+        assert rc == 1                                       # ASP_ERR_INVALID_ARG
