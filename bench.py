@@ -530,6 +530,13 @@ def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush) -> d
     e2e = {"value": e2e_iters / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(case.dirty.nbytes + case.psf.nbytes),
            "d2h_bytes_per_step": int(res_h.numel() * 4 + comps_bytes)}
+    # the run's outcome (the trajectory of discrete decisions depends on the
+    # FP32 summation order, so the work per iteration is reported with it)
+    import numpy as np
+    res = res_h.numpy().astype(np.float64)
+    outcome = {"final_residual_rms": float(np.sqrt(np.mean(res ** 2))), "components": int(comps.shape[0]),
+               "model_flux": float(comps[:, 0].sum()) if comps.shape[0] else 0.0,
+               "lm_iters_per_step": int(st["lm_iters"]), "pixel_evals_per_step": int(st["pixel_evals"])}
     # ---- per-kernel times (events around every launch, direct launches)
     L.asp_set_profiling(ctx.h, 1)
     step_device()
@@ -541,7 +548,8 @@ def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush) -> d
     ctx.close()
     kernels = {k.name.decode(): {"launches": k.launches, "total_ms": k.total_ms} for k in kt[: nk.value]}
     return {"t_ms": t_ms, "iters": iters, "pevals": pevals, "fit_flops": fit_flops, "n_launch": n_launch,
-            "e2e": e2e, "kernels": kernels, "prof": prof_stats, "clocks": clk.summary(), "n_iter": n_iter,
+            "e2e": e2e, "outcome": outcome, "kernels": kernels, "prof": prof_stats, "clocks": clk.summary(),
+            "n_iter": n_iter,
             "steps": steps, "N": case.H * case.W}
 
 
@@ -627,7 +635,8 @@ def workload_line(a, m: dict, case, world: int, peaks: dict, peak_kind: str, alu
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(case, int(name[-1]), m["n_iter"], world),
             "pixel_evals_per_s": m["pevals"] / (t_ms / 1e3), "fit_tflops": m["fit_flops"] / (t_ms / 1e3) / 1e12,
-            "e2e": m["e2e"], "gpu_launches": m["n_launch"], "roofline": roof, "kernel_rooflines": roofs,
+            "e2e": m["e2e"], "outcome": m["outcome"], "gpu_launches": m["n_launch"], "roofline": roof,
+            "kernel_rooflines": roofs,
             "kernels": k, "fit_phases": _fit_phases(m["prof"]), "clocks": m["clocks"]}
 
 

@@ -495,7 +495,7 @@ __global__ void k_fit_map_b(const ImgDesc* __restrict__ imgs, int n, int g_total
             FitDesc& f = imgs[i].st->fit;
             const long long Wn = (long long)f.ww * f.wh;
             f.grid = req[i];
-            f.smem_ok = ((Wn + req[i] - 1) / req[i]) <= PX_SMEM;
+            f.smem_ok = fit_smem_ok(Wn, req[i]);
         }
         acc += req[i];
     }

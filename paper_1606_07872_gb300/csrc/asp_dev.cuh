@@ -213,6 +213,18 @@ __device__ __host__ inline int fit_tiles(int K) {
 // is latency-bound (grid barriers and the serial solve dominate), so the
 // accumulation phase is spread as thin as the barriers allow; windows below
 // one tile run on a single CTA without grid barriers.
+// CTAs of a fit group of G that hold window pixels: with three or more,
+// the last one holds none and solves the damped system speculatively (the
+// step a rejected trial asks for next) while the others run the pass.
+__device__ __host__ inline int fit_pixel_ctas(int G) { return G >= 3 ? G - 1 : G; }
+
+// Whether the window's pixel slices (split over the group's pixel CTAs) fit
+// each CTA's shared-memory target buffer.
+__device__ __host__ inline int fit_smem_ok(long long Wn, int G) {
+    const long long gp = fit_pixel_ctas(G);
+    return ((Wn + gp - 1) / gp) <= PX_SMEM;
+}
+
 __device__ __host__ inline int fit_grid(long long Wn, int K, int px_per_cta, int g_max, int* smem_ok) {
     (void)K;   // one tile size serves every active-set size (measured)
     long long target = px_per_cta > 0 ? px_per_cta : FIT_PX_PER_CTA;
@@ -221,7 +233,7 @@ __device__ __host__ inline int fit_grid(long long Wn, int K, int px_per_cta, int
     long long g = (Wn + target - 1) / target;
     if (g < 1) g = 1;
     if (g > g_max) g = g_max;
-    *smem_ok = ((Wn + g - 1) / g) <= PX_SMEM;
+    *smem_ok = fit_smem_ok(Wn, (int)g);
     return (int)g;
 }
 

@@ -40,6 +40,14 @@ constexpr int PMAX_S = 4 * KMAX_S;
 constexpr int NB_S = (PMAX_S + 4) / 4;
 constexpr int NACC_S = NB_S * (NB_S + 1) / 2 * 16;            // cached sums of S, tile order (FP64 and FP32)
 constexpr int UNI_L_FLOATS = ((PMAX + 1) * (PMAX + 2) / 2 + 3) / 4 * 4 + 8 * (PMAX + 4);
+// Speculation block in the speculating CTA's partial row (doubles from
+// SPEC_OFF): two broadcast records of the pixel CTAs' LM state (8 doubles
+// each), then two speculative steps (lambda, ok, delta[PMAX]).  Above the
+// FP64 fallback factor the same row can hold (P (P+1) / 2 doubles).
+constexpr int SPEC_BC = 8;
+constexpr int SPEC_STEP = PMAX + 8;
+constexpr int SPEC_OFF = NACC_MAX - 2 * SPEC_BC - 2 * SPEC_STEP;
+static_assert(SPEC_OFF >= PMAX * (PMAX + 1) / 2, "the speculation block must not overlap the FP64 fallback factor");
 static_assert(UNI_L_FLOATS >= CH_XL * (NAP_MAX + 4), "J chunk of the large variant must fit its union region");
 
 struct MemberFrame {
@@ -752,6 +760,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     __shared__ int s_cur, s_iters, s_passes, s_status, s_done, s_err, s_flag, s_go, s_acc, s_small, s_rej_stall;
     __shared__ float s_pred[2], s_thr32;   // predicted-decrease sums; rtol chi^2 of the current point
     __shared__ unsigned s_flags;          // post-solve flags: finite, valid, small
+    __shared__ int s_use_spec;            // this solve takes the speculating CTA's step
 
     const int tid = threadIdx.x;
     {
@@ -763,12 +772,20 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     if (!d.active) return;
     const int G = d.grid;
     if (b >= G) return;
+    // Speculation.  With three or more CTAs the last one holds no pixels: it
+    // solves the damped system at lambda_up x lambda, the step a rejected
+    // trial asks for next, while the others run the trial's pixel pass, so a
+    // rejected step costs no solve.  Gp CTAs split the window.
+    const int Gp = fit_pixel_ctas(G);
+    const bool spec_on = Gp != G;
+    const bool is_spec = spec_on && b == Gp;
+    double* const spec_blk = spec_on ? partials + (size_t)Gp * NACC_MAX + SPEC_OFF : nullptr;
 
     const int K = d.K, P = 4 * K, NA = P + 1, NAp = (NA + 3) & ~3, nb = NAp / 4;
     const int ntiles = nb * (nb + 1) / 2;
     const int nacc = ntiles * 16;
     const long long Wn = (long long)d.ww * d.wh;
-    const long long s0 = Wn * b / G, s1 = Wn * (b + 1) / G;
+    const long long s0 = is_spec ? Wn : Wn * b / Gp, s1 = is_spec ? Wn : Wn * (b + 1) / Gp;
     const int slen = (int)(s1 - s0);
     const bool in_smem = d.smem_ok != 0;
     // J rows: stride of an odd number of float4s, so the row-per-thread
@@ -839,7 +856,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     if (tid == 0) {
         for (int i = 0; i < P; ++i) theta[i] = has_start ? descp->start[i] : d.theta0[i];
         s_lam = lmc.lambda0; s_cur = 0; s_iters = 0; s_passes = 0; s_status = ASP_LM_CAP;
-        s_done = 0; s_err = 0; s_flag = 0;
+        s_done = 0; s_err = 0; s_flag = 0; s_use_spec = 0; s_small = 0;
         sw.refinements = 0; sw.fallbacks = 0;
     }
     for (int i = tid; i < P; i += blockDim.x) trial[i] = has_start ? descp->start[i] : d.theta0[i];
@@ -871,6 +888,13 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             s_lam_rej = s_lam * lmc.lambda_up;
             s_rej_stall = s_lam_rej > lmc.lambda_max;
             s_thr = lmc.rtol * s_chi2;
+        }
+        if (spec_on && b == 0 && tid == (int)blockDim.x - 1) {
+            // the LM state the decision after this pass reads, for the
+            // speculating CTA (which did not see this fit's solves)
+            double* bc = spec_blk + (npass & 1) * SPEC_BC;
+            bc[0] = s_lam; bc[1] = s_lam_acc; bc[2] = s_lam_rej; bc[3] = s_rej_stall;
+            bc[4] = s_small; bc[5] = 0.0;
         }
         __syncthreads();
         const int nxt = 1 - s_cur;
@@ -978,7 +1002,9 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         // CTA partials stay FP32 pairs (hi, lo) = (Kahan sum, -compensation):
         // every FP64 operation or conversion costs the narrow FP64 pipe;
         // only a single-CTA fit writes its FP64 sums here
-        if (n_groups == 1) {
+        if (is_spec) {
+            // no pixels, no partial sums
+        } else if (n_groups == 1) {
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
                 const int t = tbase + q * (int)blockDim.x;
@@ -1015,7 +1041,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         }
         }   // rounds
         t1 = gtimer(); t_pass += t1 - t0; t0 = t1;
-        if (n_groups > 1) {
+        if (n_groups > 1 && !is_spec) {
             // the pixel groups' pairs combined error-free in FP32, in group order
             // (entry e = 16 slot + q of group g parked at (g ntiles + slot) 17 + q)
 #define RS(g, e) red[((g) * ntiles + ((e) >> 4)) * 17 + ((e) & 15)]
@@ -1060,12 +1086,12 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             if (tid < 32) {
                 // lane l combines CTAs l, l + 32, ... (all loads in flight first)
                 float h = 0.f, l = 0.f;
-                for (int cb = tid; cb < G; cb += 8 * 32) {
+                for (int cb = tid; cb < Gp; cb += 8 * 32) {
                     float2 v[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int c = cb + 32 * k;
-                        v[k] = c < G ? __ldcg(chib_p + c) : make_float2(0.f, 0.f);
+                        v[k] = c < Gp ? __ldcg(chib_p + c) : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) pair_add(h, l, v[k].x, v[k].y);
@@ -1083,6 +1109,17 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         }
         __syncthreads();
         if (G == 1 && tid == 0) s_chi2_t = sums_nxt[chi_idx];
+        if (is_spec && tid == 0) {
+            const double* bc = spec_blk + ((npass - 1) & 1) * SPEC_BC;
+            s_lam = __ldcg(bc + 0); s_lam_acc = __ldcg(bc + 1); s_lam_rej = __ldcg(bc + 2);
+            s_rej_stall = __ldcg(bc + 3) != 0.0; s_small = __ldcg(bc + 4) != 0.0;
+            s_thr = lmc.rtol * s_chi2;
+            if (__ldcg(bc + 5) != 0.0) s_done = 1;    // the fit ended in the pixel CTAs' solve loop
+        }
+        if (is_spec) {
+            __syncthreads();
+            if (s_done) break;
+        }
         // ================= LM decision (identical in every CTA) =================
         if (tid == 0) {
             const double chi2_t = s_chi2_t;                      // FP64 acceptance test
@@ -1104,6 +1141,13 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 s_lam = s_lam_rej;
                 if (s_rej_stall) { s_status = ASP_LM_STALLED; s_done = 1; }
             }
+            // a rejected trial asks for the step at the new lambda on the same
+            // A: the speculating CTA solved it during this pass
+            s_use_spec = 0;
+            if (spec_on && !is_spec && !first && !s_acc && !s_done) {
+                const double* st = spec_blk + 2 * SPEC_BC + ((npass - 1) & 1) * SPEC_STEP;
+                s_use_spec = __ldcg(st + 0) == s_lam && __ldcg(st + 1) != 0.0;
+            }
         }
         __syncthreads();
         // ---- the full cross-CTA reduction, only when the point moves (a
@@ -1116,7 +1160,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             // tree.  Same order in every CTA and every launch.
             const int nwarp = (int)blockDim.x >> 5, lane = tid & 31;
             int T = 1;
-            while (T < 32 && 2 * T <= G && (long long)G * (int)blockDim.x >= (long long)nacc * 2 * T) T *= 2;
+            while (T < 32 && 2 * T <= Gp && (long long)G * (int)blockDim.x >= (long long)nacc * 2 * T) T *= 2;
             const int E = 32 / T;
             const int el = lane & (E - 1), s0 = lane / E;
             const float2* pbase = reinterpret_cast<const float2*>(partials);
@@ -1129,12 +1173,12 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                     // (chain k % 4); absent CTAs load nothing and add zero
                     constexpr int RB = 16;
                     const float2* pe = pbase + e;
-                    for (int cb = s0; cb < G; cb += RB * T) {
+                    for (int cb = s0; cb < Gp; cb += RB * T) {
                         float2 v[RB];
 #pragma unroll
                         for (int k = 0; k < RB; ++k) {
                             const int c = cb + k * T;
-                            v[k] = c < G ? __ldcg(pe + (size_t)c * stride) : make_float2(0.f, 0.f);
+                            v[k] = c < Gp ? __ldcg(pe + (size_t)c * stride) : make_float2(0.f, 0.f);
                         }
 #pragma unroll
                         for (int k = 0; k < RB; k += 4) {
@@ -1197,7 +1241,26 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             __syncthreads();
         }
 
+        // ---- the speculating CTA: the step at lambda_up x lambda on the
+        // current A (what a rejected trial asks for next), published before
+        // it meets the others at the next pass's barrier
+        if (is_spec) {
+            if (s_done) break;
+            const double lam_s = s_lam * lmc.lambda_up;
+            const bool ok =
+                LARGE ? solve_damped(TileA{sums + (size_t)s_cur * NACC_MAX, nb},
+                                     TiledA32{sums32 + (size_t)s_cur * NACC_MAX, ttab, a32d, nacc, true}, gvec, g32,
+                                     dvec, dv32, lam_s, P, Jc, partials + (size_t)b * NACC_MAX, sw, delta)
+                      : solve_damped(SmemTileA{Ac, nb}, TiledA32{Ac32, ttab, a32d, nacc, false}, gvec, g32, dvec,
+                                     dv32, lam_s, P, Jc, partials + (size_t)b * NACC_MAX, sw, delta);
+            double* st = spec_blk + 2 * SPEC_BC + (npass & 1) * SPEC_STEP;
+            for (int i = tid; i < P; i += blockDim.x) st[2 + i] = delta[i];
+            if (tid == 0) { st[0] = lam_s; st[1] = ok ? 1.0 : 0.0; }
+            __syncthreads();
+            continue;
+        }
         // ---- propose the next trial point (solves without a pass loop here)
+        const int done_before = s_done;
         while (!s_done) {
             if (tid == 0) {
                 if (s_iters >= lmc.max_iter) { s_status = ASP_LM_CAP; s_done = 1; }
@@ -1212,7 +1275,14 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             bool ok;
             // the FP64 fallback factor goes to this CTA's partial row (consumed
             // by the reduction, rewritten by the next pass)
-            if (LARGE)
+            if (s_use_spec) {
+                // after a rejected trial: the speculating CTA's step at this lambda
+                const double* st = spec_blk + 2 * SPEC_BC + ((npass - 1) & 1) * SPEC_STEP;
+                for (int i = tid; i < P; i += blockDim.x) delta[i] = __ldcg(st + 2 + i);
+                ok = true;
+                __syncthreads();
+                if (tid == 0) s_use_spec = 0;
+            } else if (LARGE)
                 ok = solve_damped(TileA{sums + (size_t)s_cur * NACC_MAX, nb},
                                   TiledA32{sums32 + (size_t)s_cur * NACC_MAX, ttab, a32d, nacc, true}, gvec, g32,
                                   dvec, dv32, lam, P, Jc,
@@ -1285,7 +1355,17 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         }
         __syncthreads();
         t1 = gtimer(); t_solve += t1 - t0; t0 = t1;
-        if (s_done) break;
+        if (s_done) {
+            if (spec_on && !done_before) {
+                // the fit ended in the solve loop: the speculating CTA waits at
+                // the next pass's barrier and learns it there
+                if (b == 0 && tid == 0) spec_blk[(npass & 1) * SPEC_BC + 5] = 1.0;
+                ++epoch;
+                grid_barrier(bar, epoch * (unsigned)G, &s_err, &out->error);
+                if (s_err) return;
+            }
+            break;
+        }
     }
 
     if (b == 0 && tid == 0) {
