@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--config3-iters", type=int, default=0, help="iterations per config-3 step (0: its 5000)")
     ap.add_argument("--config3-steps", type=int, default=2)
     ap.add_argument("--config3-warmup", type=int, default=3)
+    ap.add_argument("--fit-px", type=int, default=0, help="LM fit tile: window pixels per CTA (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batch comparison")
@@ -454,7 +455,7 @@ def learned_comparison(asp, n_train_images: int, seed: int = 0):
 
 # ---------------------------------------------------------------- our arm
 
-def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush) -> dict:
+def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_px=0) -> dict:
     """Device-timed steps (inputs resident in HBM), end-to-end steps through
     the C-ABI with host buffers, and one profiled step (CUDA events around
     every launch) of one workload on this rank."""
@@ -464,7 +465,7 @@ def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush) -> d
     psf = torch.from_numpy(case.psf).cuda()
     stream = torch.cuda.Stream()
     params = asp.default_params(k_max=case.k_max, noise_sigma=case.noise_sigma, gain=case.gain,
-                                lm_max_iter=case.lm_max_iter)
+                                lm_max_iter=case.lm_max_iter, fit_px_per_cta=fit_px)
     with torch.cuda.stream(stream):
         ctx = asp.Context(dirty, psf, params=params, stream=stream)
     L = asp.lib()
@@ -657,7 +658,7 @@ def run_ours(a):
     main_cfg = a.config
     case = _workload(main_cfg, a.size, rank)
     n_iter = a.iters or case.n_iter
-    m = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush)
+    m = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush, a.fit_px)
     line = workload_line(a, m, case, world, peaks, peak_kind, alu, f"config{main_cfg}")
     line["warmup"] = a.warmup
     line["alu_peaks"] = dict(alu, note="own microbenchmark on this device, this run: one full wave of "

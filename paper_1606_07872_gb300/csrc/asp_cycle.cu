@@ -35,6 +35,13 @@ __device__ void gauss_of(const asp_component& c, double ab, double wb, double* g
 
 // Eqs. 7-8 through the flux F = a_ic w_ic^2 / (alpha_b omega_b^2); a point
 // when w_ic^2 <= omega_b^2 (1 + 1e-3).
+// Word copy by the 32 lanes of a warp (bytes a multiple of 4).
+__device__ __forceinline__ void copy_words_warp(void* dst, const void* src, int bytes, int lane) {
+    int* d = reinterpret_cast<int*>(dst);
+    const int* q = reinterpret_cast<const int*>(src);
+    for (int i = lane; i < bytes / 4; i += 32) d[i] = q[i];
+}
+
 __device__ asp_component deconvolve(double a, double x, double y, double w, double ab, double wb, double gain) {
     asp_component c;
     double F = a * w * w / (ab * wb * wb);
@@ -93,12 +100,14 @@ __device__ bool make_term(const asp_component& c, double s, int H, int W, int sl
 // passes.  Also the algorithmic work of R -= B * dC: per extended term
 // 2 nx (H + ny - 1) W + 2 ny H W flops, per deposit 2 H W, plus 2 H W for the
 // update; bytes: each term's PSF region read once, R read and written once.
-__device__ void finish_terms(CycleState* st, int H, int W) {
+// terms: the n_terms descriptors being built (in shared memory, so this
+// single-thread loop does not wait on a global round trip per field).
+__device__ void finish_terms(CycleState* st, TermDesc* terms, int n_terms, int H, int W) {
     long long off = 0;
     double fl = 0.0, by = 8.0 * (double)H * W;
     int nd = 0;
-    for (int t = 0; t < st->n_terms; ++t) {
-        TermDesc& td = st->terms[t];
+    for (int t = 0; t < n_terms; ++t) {
+        TermDesc& td = terms[t];
         if (td.bilinear) {
             const double fx0 = floor(td.cx), fy0 = floor(td.cy);
             const double fx = td.cx - fx0, fy = td.cy - fy0;
@@ -132,29 +141,37 @@ __device__ void finish_terms(CycleState* st, int H, int W) {
 
 __device__ __forceinline__ void cycle_begin_body(CycleState* st, Params p, int H, int W, double smooth_flops) {
     if (threadIdx.x != 0) return;
+    // every field read first, so the loads go out together instead of one
+    // L2 round trip per test
+    const int stopped = st->stopped;
+    const unsigned nonfinite = st->nonfinite;
+    const int t = st->t, t_stop = st->t_stop, n_comp = st->n_comp, cap_comp = st->cap_comp;
+    const float pval = st->peak.val;
+    const long long pidx = st->peak.idx;
+    const double thr = st->thr, last_wi = st->last_wi, last_w0 = st->last_w0, omega_b = st->omega_b;
     st->fit.active = 0;
     st->skip_smooth = 1;
-    if (st->stopped) return;
-    if (st->nonfinite) { st->stopped = 1; st->error = ASP_ERR_NAN; return; }
-    if (st->t >= st->t_stop) { st->stopped = 1; st->stop_reason = ASP_STOP_ITER; return; }
-    if (fabs((double)st->peak.val) < st->thr) { st->stopped = 1; st->stop_reason = ASP_STOP_NOISE; return; }
-    if (st->n_comp >= st->cap_comp) { st->stopped = 1; st->stop_reason = ASP_STOP_CAPACITY; return; }
+    if (stopped) return;
+    if (nonfinite) { st->stopped = 1; st->error = ASP_ERR_NAN; return; }
+    if (t >= t_stop) { st->stopped = 1; st->stop_reason = ASP_STOP_ITER; return; }
+    if (fabs((double)pval) < thr) { st->stopped = 1; st->stop_reason = ASP_STOP_NOISE; return; }
+    if (n_comp >= cap_comp) { st->stopped = 1; st->stop_reason = ASP_STOP_CAPACITY; return; }
     int mode;
     if (p.init_mode == ASP_INIT_SIMPLE) mode = ASP_PEAK_SIMPLE;
     else if (p.init_mode == ASP_INIT_SMOOTH) mode = ASP_PEAK_SMOOTH;
-    else mode = (st->t > 0 && st->last_wi * st->last_wi < (double)p.area_frac * st->last_w0 * st->last_w0)
+    else mode = (t > 0 && last_wi * last_wi < (double)p.area_frac * last_w0 * last_w0)
                     ? ASP_PEAK_SIMPLE : ASP_PEAK_SMOOTH;
     st->mode = mode;
     st->skip_smooth = mode != ASP_PEAK_SMOOTH;
     if (mode == ASP_PEAK_SMOOTH) { st->smooth_flops += smooth_flops; st->smooth_iters += 1; }
     if (mode == ASP_PEAK_SIMPLE) {
-        const long long idx = st->peak.idx;
-        st->init[0] = st->peak.val;
+        const long long idx = pidx;
+        st->init[0] = pval;
         st->init[1] = (double)(idx % W);
         st->init[2] = (double)(idx / W);
-        st->init[3] = st->omega_b;
+        st->init[3] = omega_b;
         st->init_scale = -1;
-        st->init_value = st->peak.val;
+        st->init_value = pval;
         st->init_s = 0.f;
     }
 }
@@ -168,10 +185,12 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32) return;
-    if (st->stopped) return;
-    FitDesc& f = st->fit;
+    // the fields read before the first branch, so their loads go out together
+    const int stopped = st->stopped, n_ret_ = st->n_ret;
     const double ab = st->alpha_b, wb = st->omega_b;
     const double ix = st->init[1], iy = st->init[2], iw = st->init[3];
+    if (stopped) return;
+    FitDesc& f = st->fit;
     long long nb[4];
     member_box(ix, iy, iw, nb);
     long long wx0 = nb[0], wx1 = nb[1], wy0 = nb[2], wy1 = nb[3];
@@ -180,7 +199,7 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
         st->members[0] = -1;
     }
     int K = 1;
-    const int n_ret = st->n_ret;
+    const int n_ret = n_ret_;
     for (int base = 0; base < n_ret && K < p.k_max; base += 32) {
         const int r = base + lane;
         double g[4] = {0, 0, 0, 0};
@@ -261,8 +280,10 @@ __device__ __forceinline__ void update_body(CycleState* st, asp_component* comps
     const int K = f.K;
     const int ni = st->n_comp;
     // refit members in parallel: retention test (tau) and the deconvolved new value
+    __shared__ int s_member[KMAX];
     for (int m = 1 + lane; m < K; m += 32) {
         const int k = st->members[m];
+        s_member[m] = k;
         const double* g0 = &f.theta0[4 * m];
         const double* g1 = &fo.theta[4 * m];
         const double tau = p.tau;
@@ -273,23 +294,28 @@ __device__ __forceinline__ void update_body(CycleState* st, asp_component* comps
         s_new[m] = deconvolve(g1[0], g1[1], g1[2], g1[3], ab, wb, 1.0);
     }
     __syncwarp();
+    __shared__ TermDesc s_terms[MAX_TERMS];
+    __shared__ int s_nt;
     if (lane == 0) {
         int nt = 0;
         // new component with the loop gain (Sect. 3, after Eq. 8)
         const asp_component cn = deconvolve(fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], ab, wb, (double)p.gain);
         comps[ni] = cn;
         st->n_comp = ni + 1;
-        if (make_term(cn, cn.flux, H, W, nt, st->terms[nt])) ++nt;
+        if (make_term(cn, cn.flux, H, W, nt, s_terms[nt])) ++nt;
         // old members are replaced by their refit values
         for (int m = 1; m < K; ++m) {
-            comps[st->members[m]] = s_new[m];
-            if (make_term(s_new[m], s_new[m].flux, H, W, nt, st->terms[nt])) ++nt;
-            if (make_term(s_old[m], -s_old[m].flux, H, W, nt, st->terms[nt])) ++nt;
+            comps[s_member[m]] = s_new[m];
+            if (make_term(s_new[m], s_new[m].flux, H, W, nt, s_terms[nt])) ++nt;
+            if (make_term(s_old[m], -s_old[m].flux, H, W, nt, s_terms[nt])) ++nt;
         }
         st->n_terms = nt;
-        finish_terms(st, H, W);
+        finish_terms(st, s_terms, nt, H, W);
         st->last_wi = cn.width;
+        s_nt = nt;
     }
+    __syncwarp();
+    copy_words_warp(st->terms, s_terms, s_nt * (int)sizeof(TermDesc), lane);
     // retained list: new first, then the previous list minus members whose
     // fit moved no parameter by more than tau (order kept)
     const int n_old = st->n_ret;
@@ -355,7 +381,7 @@ __global__ void k_terms_from_components(CycleState* st, const asp_component* __r
     for (int i = 0; i < n && nt < MAX_TERMS; ++i)
         if (make_term(comps[i], (double)gain * comps[i].flux, H, W, nt, st->terms[nt])) ++nt;
     st->n_terms = nt;
-    finish_terms(st, H, W);
+    finish_terms(st, st->terms, nt, H, W);
 }
 
 // Axis weights of every term: sampled Gaussian normalised to unit sum over the
@@ -367,7 +393,7 @@ __device__ __forceinline__ void build_weights_body(const CycleState* __restrict_
     if (t >= st->n_terms) return;
     const TermDesc td = st->terms[t];
     if (td.bilinear) return;          // applied as deposits, no axis weights
-    __shared__ double red[256];
+    __shared__ float red[256];
     for (int axis = 0; axis < 2; ++axis) {
         const double c = axis == 0 ? td.cx : td.cy;
         const int q0 = axis == 0 ? td.qx0 : td.qy0;
@@ -376,27 +402,35 @@ __device__ __forceinline__ void build_weights_body(const CycleState* __restrict_
         const int u1 = axis == 0 ? td.ux1 : td.uy1;
         float* out = wbuf + (axis == 0 ? td.woff_x : td.woff_y);
         {
-            const double iw = 1.0 / (2.0 * td.w * td.w);
-            double s = 0.0;
+            // FP32 samples exp(-dq^2 / 2 w^2) with dq = (q - q_c) - f, the
+            // integer and fractional parts of the centre apart (no
+            // cancellation); the normalising sum as per-thread partials and
+            // a fixed tree (error ~ (taps / 256 + 8) u32, far inside the
+            // subtraction's 1e-5 bar)
+            const float iw = (float)(1.0 / (2.0 * td.w * td.w));
+            const double cq = floor(c);
+            const float fr = (float)(c - cq);
+            const long long icq = (long long)cq;
+            float sum = 0.f;
             for (long long q = (long long)u0 + threadIdx.x; q <= u1; q += blockDim.x) {
-                const double dq = (double)q - c;
-                s += exp(-dq * dq * iw);
+                const float dq = (float)(q - icq) - fr;
+                sum += expf(-dq * dq * iw);
             }
-            red[threadIdx.x] = s;
+            red[threadIdx.x] = sum;
             __syncthreads();
             for (int o = 128; o > 0; o >>= 1) {
                 if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
                 __syncthreads();
             }
-            const double inv = 1.0 / red[0];
+            const float inv = 1.0f / red[0];
             __syncthreads();
             // reversed (tap i at n - 1 - i) and zero-padded to a multiple of 8
             const int n8 = (n + 7) & ~7;
             for (int i = threadIdx.x; i < n8; i += blockDim.x) {
                 float v = 0.f;
                 if (i < n) {
-                    const double dq = (double)(q0 + i) - c;
-                    v = (float)(exp(-dq * dq * iw) * inv);
+                    const float dq = (float)((long long)(q0 + i) - icq) - fr;
+                    v = expf(-dq * dq * iw) * inv;
                 }
                 out[i < n ? n - 1 - i : i] = v;
             }

@@ -19,7 +19,7 @@ constexpr int FIT_GRID_MAX = 1024;                 // CTAs of one fit group (at 
 // partial pair (two buffers of FIT_GRID_MAX float2)
 constexpr int SUMS_DOUBLES = 3 * NACC_MAX + 2 * FIT_GRID_MAX;
 constexpr int MAX_TERMS = 2 * KMAX;                // subtraction terms per iteration
-constexpr int T1_SLACK_ROWS = 16;                  // zeroed rows behind the last subtraction term
+constexpr int T1_SLACK_ROWS = 32;                  // rows behind the last subtraction term (the column pass's prefetch)
 constexpr int MAX_SCALES = 8;                      // smoothing scales
 constexpr int FIT_THREADS = 256;
 constexpr int PX_SMEM = 12288;                     // target pixels one CTA keeps in smem

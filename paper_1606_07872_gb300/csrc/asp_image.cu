@@ -105,6 +105,33 @@ k_argmax_abs(const float* __restrict__ R, long long N, ArgRes* part, unsigned* t
 // so the 32 lanes of a warp hit 32 different banks.
 __device__ __forceinline__ int spad(int q) { return q + (q >> 3); }
 
+// 8 outputs x 8 taps of a correlation: acc[i] += sum_d k[d] x[i + d], the 16
+// inputs x[0..15] given as two 8-register banks (lo, hi).
+__device__ __forceinline__ void conv8k(float (&acc)[8], const float (&lo)[8], const float (&hi)[8],
+                                       const float4 ka, const float4 kb) {
+    const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[d], i + d < 8 ? lo[i + d] : hi[i + d - 8], acc[i]);
+}
+// The same with the taps read from 8 consecutive floats of a 16-byte
+// aligned, zero-padded weight row in global memory (L1-cached).
+__device__ __forceinline__ void conv8(float (&acc)[8], const float (&lo)[8], const float (&hi)[8],
+                                      const float* __restrict__ k8) {
+    conv8k(acc, lo, hi, __ldg(reinterpret_cast<const float4*>(k8)), __ldg(reinterpret_cast<const float4*>(k8 + 4)));
+}
+// ... in shared memory.
+__device__ __forceinline__ void conv8s(float (&acc)[8], const float (&lo)[8], const float (&hi)[8], const float* k8) {
+    conv8k(acc, lo, hi, *reinterpret_cast<const float4*>(k8), *reinterpret_cast<const float4*>(k8 + 4));
+}
+
+// 8 consecutive rows of one column (row stride W) into a register bank.
+__device__ __forceinline__ void load_rows8(float (&b)[8], const float* __restrict__ p, int W) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = __ldg(p + (long long)i * W);
+}
+
 // ------------------------------------------------------------------ subtraction
 // R -= B * dC (Sect. 2 step 3) with dC a sum of separable sampled terms:
 // for term t with axis weights wx (nx taps from column qx0) and wy (ny taps
@@ -164,22 +191,20 @@ __device__ __forceinline__ void sub_h_body(const float* __restrict__ B, int H, i
         const int x0 = xs + 8 * lt;
         if (!live || x0 >= W) continue;
         const float* wxr = wbuf + td.woff_x;
-        float acc[8], w[16];
+        // the 16-entry window lives in two 8-register banks whose roles swap
+        // every 8 taps (the loop is unrolled by two), so no register moves
+        float acc[8], wa[8], wb[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; w[i] = buf[spad(8 * lt + i)]; }
+        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; wa[i] = buf[spad(8 * lt + i)]; }
 #pragma unroll 1
-        for (int u0 = 0; u0 < nx8; u0 += 8) {
+        for (int u0 = 0; u0 < nx8; u0 += 16) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) w[8 + i] = buf[spad(8 * lt + u0 + 8 + i)];
-            const float4 ka = __ldg(reinterpret_cast<const float4*>(wxr + u0));
-            const float4 kb = __ldg(reinterpret_cast<const float4*>(wxr + u0 + 4));
-            const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+            for (int i = 0; i < 8; ++i) wb[i] = buf[spad(8 * lt + u0 + 8 + i)];
+            conv8(acc, wa, wb, wxr + u0);
+            if (u0 + 8 >= nx8) break;
 #pragma unroll
-            for (int du = 0; du < 8; ++du)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+            for (int i = 0; i < 8; ++i) wa[i] = buf[spad(8 * lt + u0 + 16 + i)];
+            conv8(acc, wb, wa, wxr + u0 + 8);
         }
         float* out = T1 + td.t1off + (long long)r * W + x0;
         if (x0 + 8 <= W && (W & 3) == 0) {
@@ -233,23 +258,29 @@ __device__ __forceinline__ void sub_v_body(float* __restrict__ R, int H, int W, 
             const int ny8 = (td.ny + 7) & ~7;
             const float* wyr = wbuf + td.woff_y;
             const float* col = T1 + td.t1off + (long long)py0 * W + px;
-            float s[8], w[16];
+            // three 8-row register banks rotate (the loop is unrolled by
+            // three): each step computes on two and loads the next 8 rows
+            // into the third, a full step before they are used, so the L2
+            // latency of the column loads hides behind the FMAs.  The
+            // prefetch reads up to 23 rows past a term's last tap (zero
+            // taps; T1 keeps T1_SLACK_ROWS rows behind the last term).
+            float s[8], b0[8], b1[8], b2[8];
 #pragma unroll
-            for (int o = 0; o < 8; ++o) { s[o] = 0.f; w[o] = __ldg(col + (long long)o * W); }
+            for (int o = 0; o < 8; ++o) {
+                s[o] = 0.f;
+                b0[o] = __ldg(col + (long long)o * W);
+                b1[o] = __ldg(col + (long long)(8 + o) * W);
+            }
 #pragma unroll 1
-            for (int k0 = 0; k0 < ny8; k0 += 8) {
-                const float* c8 = col + (long long)(k0 + 8) * W;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) w[8 + i] = __ldg(c8 + (long long)i * W);
-                const float4 ka = __ldg(reinterpret_cast<const float4*>(wyr + k0));
-                const float4 kb = __ldg(reinterpret_cast<const float4*>(wyr + k0 + 4));
-                const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
-#pragma unroll
-                for (int dk = 0; dk < 8; ++dk)
-#pragma unroll
-                    for (int o = 0; o < 8; ++o) s[o] = fmaf(kk[dk], w[o + dk], s[o]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+            for (int k0 = 0; k0 < ny8; k0 += 24) {
+                load_rows8(b2, col + (long long)(k0 + 16) * W, W);
+                conv8(s, b0, b1, wyr + k0);
+                if (k0 + 8 >= ny8) break;
+                load_rows8(b0, col + (long long)(k0 + 24) * W, W);
+                conv8(s, b1, b2, wyr + k0 + 8);
+                if (k0 + 16 >= ny8) break;
+                load_rows8(b1, col + (long long)(k0 + 32) * W, W);
+                conv8(s, b2, b0, wyr + k0 + 16);
             }
 #pragma unroll
             for (int o = 0; o < 8; ++o) acc[o] = fmaf(td.scale, s[o], acc[o]);
@@ -324,22 +355,19 @@ __device__ __forceinline__ void smooth_h_body(const float* __restrict__ R, int H
         __syncthreads();
         const int x0 = xs + 8 * lt;
         if (!live || x0 >= W) continue;
-        float acc[8], w[16];
+        // two 8-register window banks swap roles every 8 taps (no moves)
+        float acc[8], wa[8], wb[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; w[i] = buf[spad(8 * lt + i)]; }
+        for (int i = 0; i < 8; ++i) { acc[i] = 0.f; wa[i] = buf[spad(8 * lt + i)]; }
 #pragma unroll 1
-        for (int u0 = 0; u0 < t8; u0 += 8) {
+        for (int u0 = 0; u0 < t8; u0 += 16) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) w[8 + i] = buf[spad(8 * lt + u0 + 8 + i)];
-            const float4 ka = *reinterpret_cast<const float4*>(ktap + u0);
-            const float4 kb = *reinterpret_cast<const float4*>(ktap + u0 + 4);
-            const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+            for (int i = 0; i < 8; ++i) wb[i] = buf[spad(8 * lt + u0 + 8 + i)];
+            conv8s(acc, wa, wb, ktap + u0);
+            if (u0 + 8 >= t8) break;
 #pragma unroll
-            for (int du = 0; du < 8; ++du)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) w[i] = w[8 + i];
+            for (int i = 0; i < 8; ++i) wa[i] = buf[spad(8 * lt + u0 + 16 + i)];
+            conv8s(acc, wb, wa, ktap + u0 + 8);
         }
         float* out = S1 + ((long long)j * taps.s1rows + y + taps.mpad) * W + x0;
         if (x0 + 8 <= W && (W & 3) == 0) {
@@ -386,30 +414,27 @@ __device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int 
         const int x = cb * 32 + lane, y0 = rb * 64 + 8 * warp;
         if (x >= W || y0 >= H) continue;
         const float* col = S1 + ((long long)j * taps.s1rows + (y0 - m + taps.mpad)) * W + x;
-        // window rows u0 .. u0+15 in w, the next block's rows loaded ahead
-        // of this block's FMAs (the same rows as without the prefetch)
-        float acc[8], w[16];
+        // three 8-row register banks rotate (the loop is unrolled by three):
+        // each step computes on two and loads the next 8 rows into the
+        // third a step ahead -- only rows the window will use, the same
+        // rows as without the prefetch
+        float acc[8], b0[8], b1[8], b2[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) w[i] = __ldg(col + (long long)i * W);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+        for (int i = 0; i < 8; ++i) {
+            acc[i] = 0.f;
+            b0[i] = __ldg(col + (long long)i * W);
+            b1[i] = __ldg(col + (long long)(8 + i) * W);
+        }
 #pragma unroll 1
-        for (int u0 = 0; u0 < t8; u0 += 8) {
-            float nx[8];
-            if (u0 + 8 < t8) {
-                const float* c16 = col + (long long)(u0 + 16) * W;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) nx[i] = __ldg(c16 + (long long)i * W);
-            }
-            const float4 ka = *reinterpret_cast<const float4*>(ktap + u0);
-            const float4 kb = *reinterpret_cast<const float4*>(ktap + u0 + 4);
-            const float kk[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
-#pragma unroll
-            for (int du = 0; du < 8; ++du)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc[i] = fmaf(kk[du], w[i + du], acc[i]);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { w[i] = w[8 + i]; w[8 + i] = nx[i]; }
+        for (int u0 = 0; u0 < t8; u0 += 24) {
+            if (u0 + 8 < t8) load_rows8(b2, col + (long long)(u0 + 16) * W, W);
+            conv8s(acc, b0, b1, ktap + u0);
+            if (u0 + 8 >= t8) break;
+            if (u0 + 16 < t8) load_rows8(b0, col + (long long)(u0 + 24) * W, W);
+            conv8s(acc, b1, b2, ktap + u0 + 8);
+            if (u0 + 16 >= t8) break;
+            if (u0 + 24 < t8) load_rows8(b1, col + (long long)(u0 + 32) * W, W);
+            conv8s(acc, b2, b0, ktap + u0 + 16);
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
