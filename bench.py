@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--config3-steps", type=int, default=2)
     ap.add_argument("--config3-warmup", type=int, default=3)
     ap.add_argument("--fit-px", type=int, default=0, help="LM fit tile: window pixels per CTA (0: library default)")
+    ap.add_argument("--no-split", action="store_true", help="skip the minor/major split comparison")
+    ap.add_argument("--split-every", type=int, default=50, help="minor iterations per major cycle in the split")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batch comparison")
@@ -455,7 +457,7 @@ def learned_comparison(asp, n_train_images: int, seed: int = 0):
 
 # ---------------------------------------------------------------- our arm
 
-def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_px=0) -> dict:
+def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_px=0, major_every=0) -> dict:
     """Device-timed steps (inputs resident in HBM), end-to-end steps through
     the C-ABI with host buffers, and one profiled step (CUDA events around
     every launch) of one workload on this rank."""
@@ -465,7 +467,7 @@ def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_
     psf = torch.from_numpy(case.psf).cuda()
     stream = torch.cuda.Stream()
     params = asp.default_params(k_max=case.k_max, noise_sigma=case.noise_sigma, gain=case.gain,
-                                lm_max_iter=case.lm_max_iter, fit_px_per_cta=fit_px)
+                                lm_max_iter=case.lm_max_iter, fit_px_per_cta=fit_px, major_every=major_every)
     with torch.cuda.stream(stream):
         ctx = asp.Context(dirty, psf, params=params, stream=stream)
     L = asp.lib()
@@ -641,6 +643,16 @@ def workload_line(a, m: dict, case, world: int, peaks: dict, peak_kind: str, alu
             "kernels": k, "fit_phases": _fit_phases(m["prof"]), "clocks": m["clocks"]}
 
 
+def split_summary(m: dict, exact_line: dict) -> dict:
+    """The minor/major split against the exact-subtraction run of the same
+    workload: rate, the final (exact) residual RMS and the kernel times."""
+    t = m["t_ms"]
+    return {"value": m["iters"] / (t / 1e3), "unit": UNIT, "e2e": m["e2e"], "outcome": m["outcome"],
+            "speedup_vs_exact": (m["iters"] / (t / 1e3)) / exact_line["value"],
+            "rms_ratio_vs_exact": m["outcome"]["final_residual_rms"] / exact_line["outcome"]["final_residual_rms"],
+            "kernels": m["kernels"], "clocks": m["clocks"]}
+
+
 def run_ours(a):
     import torch
     import paper_1606_07872_gb300 as asp
@@ -674,6 +686,18 @@ def run_ours(a):
             del c3
         except Exception as e:   # report, never hide, a failed measurement
             line["config3"] = {"error": repr(e)[:300]}
+    if main_cfg == 2 and not a.no_split:
+        try:
+            ms = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush, a.fit_px, a.split_every)
+            line["split"] = {"major_every": a.split_every, "config2": split_summary(ms, line)}
+            if isinstance(line.get("config3"), dict) and "value" in line["config3"]:
+                c3 = _workload(3, 4096, rank)
+                m3 = measure_workload(asp, c3, a.config3_iters or c3.n_iter, a.config3_steps, a.config3_warmup,
+                                      local, world, flush, 0, a.split_every)
+                line["split"]["config3"] = split_summary(m3, line["config3"])
+                del c3
+        except Exception as e:   # report, never hide, a failed measurement
+            line["split"] = {"error": repr(e)[:300]}
     if rank == 0 and main_cfg == 2 and not a.no_learned:
         try:
             line["learned"], weights = learned_comparison(asp, a.learned_train_images)

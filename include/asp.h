@@ -119,6 +119,15 @@ typedef struct {
                                (0: 96; clamped to [32, 12288]); changes the
                                grid and so the FP32 summation order, not the
                                method */
+    int32_t major_every;    /* 0: every iteration subtracts with the full PSF
+                               (Sect. 2 step 3).  n > 0: minor/major split in
+                               the manner of Clark CLEAN (Sect. 1, Sect. 3):
+                               minor iterations subtract each component's
+                               single-Gaussian-beam image (Eqs. 7-8 inverted)
+                               locally, and after every n of them, and at the
+                               end of each asp_minor_cycle call, the residual
+                               is recomputed exactly as D - B * M by an FFT
+                               convolution.  Contexts only (not batches). */
 } asp_params;
 
 /* Totals of asp_minor_cycle since asp_init (or the last asp_set_state). */
@@ -229,9 +238,21 @@ asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, con
  * ASP_KMAX. */
 asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float gain);
 
+/* R -= gain * sum_i b_i: component i through the PSF's single-Gaussian
+ * approximation (alpha_b, omega_b) -- the Gaussian (alpha_b omega_b^2 F_i /
+ * omega_ic^2, x_i, y_i, omega_ic), omega_ic^2 = omega_i^2 + omega_b^2
+ * (Eqs. 7-8 inverted) -- on the box |q - centre|_inf <= ceil(5 omega_ic) +
+ * 1, clipped: the minor cycle's update when asp_params.major_every > 0.
+ * Components whose own sampling box lies outside the image are skipped, as
+ * in asp_subtract.  n <= 2 x ASP_KMAX.  Finds the next peak. */
+asp_status asp_subtract_beam(asp_ctx* ctx, const asp_component* comps, int n, float gain);
+
 /* Run up to n_iter minor-cycle iterations (Sect. 2 steps 1-4 with the
  * Sect. 3 objective, deconvolution and initial-value switch); the loop stops
- * early when max|R| < stop_ksigma * noise_sigma.  Totals to out (may be NULL). */
+ * early when max|R| < stop_ksigma * noise_sigma.  Totals to out (may be NULL).
+ * With asp_params.major_every = m > 0 a major cycle (the exact residual D -
+ * B * M) follows every m iterations of the call and ends the call, so the
+ * residual is exact on return. */
 asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out);
 
 /* Multi-scale smoothed residual S_j (unit-L2 Gaussian of scale s_j, zero

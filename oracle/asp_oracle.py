@@ -38,7 +38,7 @@ __all__ = [
     "halfmax_width", "beam_fit", "peak_simple", "smoothing_scales", "smoothing_kernel_1d",
     "smooth_separable", "smooth_definition", "peak_smooth",
     "deconvolve", "gauss_approx", "component_terms", "terms_to_image",
-    "subtract_terms", "subtract_definition",
+    "subtract_terms", "subtract_definition", "beam_image_box", "subtract_beam_images",
     "member_box", "boxes_overlap", "MinorCycle", "mad_sigma",
 ]
 
@@ -93,6 +93,7 @@ class AspParams:
     init_mode: str = "auto"          # auto | simple | smooth
     tau: float = 1e-3                # active-set retention threshold
     retained_cap_factor: int = 8     # retained list capped at factor * k_max
+    major_every: int = 0             # 0: full-PSF subtraction every iteration; n: minor/major split
     lm: LMParams = dataclasses.field(default_factory=LMParams)
 
 
@@ -536,6 +537,37 @@ def subtract_terms(R, B, terms):
     return R
 
 
+def beam_image_box(x, y, w, alpha_b, omega_b, H, W):
+    """Reading of the minor cycle's approximate subtraction (the Clark-style
+    split): a component of flux 1 and width w through the single-Gaussian
+    beam is the Gaussian (a_ic, w_ic) of :func:`gauss_approx`, evaluated on
+    the box |q - centre|_inf <= ceil(5 w_ic) + 1 (clipped to the image).
+    Returns (qx0, qy0, image) or None."""
+    a_ic, w_ic = gauss_approx(1.0, w, alpha_b, omega_b)
+    h = math.ceil(5.0 * w_ic) + 1
+    x0, x1 = max(math.ceil(x - h), 0), min(math.floor(x + h), W - 1)
+    y0, y1 = max(math.ceil(y - h), 0), min(math.floor(y + h), H - 1)
+    if x0 > x1 or y0 > y1:
+        return None
+    ys, xs = np.mgrid[y0: y1 + 1, x0: x1 + 1].astype(np.float64)
+    return x0, y0, a_ic * np.exp(-((xs - x) ** 2 + (ys - y) ** 2) / (2.0 * w_ic * w_ic))
+
+
+def subtract_beam_images(R, items, alpha_b, omega_b):
+    """``R -= sum_i F_i * beam image of component i`` for items (F, x, y,
+    w): the minor cycle's update with the PSF approximated by its fitted
+    Gaussian.  Returns the new image."""
+    R = np.array(R, dtype=np.float64)
+    H, W = R.shape
+    for F, x, y, w in items:
+        b = beam_image_box(x, y, w, alpha_b, omega_b, H, W)
+        if b is None:
+            continue
+        x0, y0, img = b
+        R[y0: y0 + img.shape[0], x0: x0 + img.shape[1]] -= F * img
+    return R
+
+
 def subtract_definition(R, B, dC):
     """Brute-force 2-D direct form: ``R(p) -= sum_q dC(q) B(p - q + (H, W))``
     over every nonzero model pixel q and every image pixel p."""
@@ -615,6 +647,8 @@ class MinorCycle:
             ab, wb = beam
         self.alpha_b, self.omega_b = float(ab), float(wb)
         self.noise = params.noise_sigma if params.noise_sigma > 0 else mad_sigma(self.R)
+        self.D = self.R.copy()          # the dirty image (the major cycle's start)
+        self.since_major = 0
         self.comps: list[Component] = []
         self.retained: list[int] = []
         self.t = 0
@@ -724,8 +758,10 @@ class MinorCycle:
         if t is not None:
             terms.append(t)
         still = []
+        old_comps = {}
         for m, k in enumerate(chosen, start=1):
             old = self.comps[k]
+            old_comps[m] = old
             G0 = theta0[4 * m: 4 * m + 4]
             a, x, y, w = th[4 * m: 4 * m + 4]
             tau = self.p.tau
@@ -745,7 +781,17 @@ class MinorCycle:
         self.retained = [new_index] + [k for k in self.retained if k not in dropped]
         cap = self.p.retained_cap_factor * self.p.k_max
         self.retained = self.retained[:cap]
-        self.R = subtract_terms(self.R, self.B, terms)
+        if self.p.major_every > 0:
+            # minor/major split: each term's single-Gaussian-beam image
+            items = [(new.flux, new.x, new.y, new.width)]
+            for m, k in enumerate(chosen, start=1):
+                nc = self.comps[k]
+                items.append((nc.flux, nc.x, nc.y, nc.width))
+                items.append((-old_comps[m].flux, old_comps[m].x, old_comps[m].y, old_comps[m].width))
+            self.R = subtract_beam_images(self.R, items, self.alpha_b, self.omega_b)
+            self.since_major += 1
+        else:
+            self.R = subtract_terms(self.R, self.B, terms)
         self.last_wi = new.width
         self.last_w0 = init["w0"]
         rec = dict(t=self.t, mode=mode, peak_index=pidx, peak_value=pval, init=init,
@@ -795,10 +841,30 @@ class MinorCycle:
         info["kept"] = True
         return fit_l, info
 
+    def major(self):
+        """The major cycle of the minor/major split: the exact residual
+        ``R = D - B * M`` (Sect. 2 step 3 with the full PSF) of the whole
+        component list, each component sampled as in the per-iteration
+        subtraction."""
+        terms = []
+        for c in self.comps:
+            t = component_terms(c.flux, c.x, c.y, c.width, c.is_point, self.H, self.W)
+            if t is not None:
+                terms.append(t)
+        self.R = subtract_terms(self.D, self.B, terms)
+        self.since_major = 0
+
     def run(self, n_iter):
+        """Up to n_iter iterations; with the minor/major split a major cycle
+        follows every major_every iterations and ends the run."""
         for _ in range(n_iter):
-            if self.step() is None:
+            rec = self.step()
+            if rec is None:
                 break
+            if self.p.major_every > 0 and self.since_major >= self.p.major_every:
+                self.major()
+        if self.p.major_every > 0 and self.since_major > 0:
+            self.major()
         return self
 
     # -- state exchange (teacher forcing)

@@ -23,7 +23,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "AspError", "lib", "default_params", "asp_init", "asp_init_host", "asp_destroy", "asp_get_beam",
-    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_measure_alu_peaks", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
+    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
@@ -203,6 +203,12 @@ def asp_subtract(h, comps, gain: float = 1.0):
     """R -= B * (gain * sum of components); rows (flux, amp, x, y, width, is_point)."""
     arr, n = _component_array(comps)
     _check(lib().asp_subtract(h, arr, n, float(gain)), "asp_subtract", h)
+
+
+def asp_subtract_beam(h, comps, gain: float = 1.0):
+    """R -= gain * sum of the components' single-Gaussian-beam images."""
+    arr, n = _component_array(comps)
+    _check(lib().asp_subtract_beam(h, arr, n, float(gain)), "asp_subtract_beam", h)
 
 
 def _stats_dict(s: asp_cycle_stats) -> dict:
@@ -434,6 +440,9 @@ class Context:
 
     def subtract(self, comps, gain=1.0):
         asp_subtract(self.h, comps, gain)
+
+    def subtract_beam(self, comps, gain=1.0):
+        asp_subtract_beam(self.h, comps, gain)
 
     def minor_cycle(self, n_iter):
         return asp_minor_cycle(self.h, n_iter)

@@ -51,7 +51,7 @@ class asp_params(C.Structure):
                 ("noise_sigma", C.c_float), ("stop_ksigma", C.c_float), ("n_scales", C.c_int32),
                 ("area_frac", C.c_float), ("init_mode", C.c_int32), ("tau", C.c_double),
                 ("retained_cap", C.c_int32), ("max_components", C.c_int32),
-                ("fit_px_per_cta", C.c_int32)]
+                ("fit_px_per_cta", C.c_int32), ("major_every", C.c_int32)]
 
 
 class asp_cycle_stats(C.Structure):
@@ -108,6 +108,7 @@ SIGNATURES = {
                    C.POINTER(asp_fit_info), C.POINTER(asp_gauss), C.POINTER(C.c_double)],
     "asp_eval_normal_equations": [_P, C.POINTER(asp_gauss), _I, _I, _I, _I, _I, _I, _P, _P, _P],
     "asp_subtract": [_P, C.POINTER(asp_component), _I, C.c_float],
+    "asp_subtract_beam": [_P, C.POINTER(asp_component), _I, C.c_float],
     "asp_minor_cycle": [_P, _I, C.POINTER(asp_cycle_stats)],
     "asp_smooth": [_P, _I, _P],
     "asp_num_scales": [_P, C.POINTER(_I), _P],

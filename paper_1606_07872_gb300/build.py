@@ -83,7 +83,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if err.strip():
                 print(f"--- {os.path.basename(obj)}\n{err}", file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static",
+    # cuFFT (the major cycle's convolution) from the toolkit this nvcc
+    # belongs to, found at run time through an rpath to that toolkit
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-cudart", "static", "-lcufft",
+           "-Xlinker", "-rpath", "-Xlinker", cuda_lib,
            "-Xlinker", "--no-undefined"]   # a missing definition fails here, not at load time
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -18,11 +18,13 @@ using namespace aspd;
 // Kernel classes timed by asp_set_profiling.
 enum KernelClass {
     KC_BEGIN, KC_SMOOTH_H, KC_SMOOTH_V, KC_SELECT, KC_FIT, KC_UPDATE, KC_WEIGHTS, KC_SUB_H, KC_SUB_V, KC_ARGMAX,
-    KC_MLP, KC_LEARNED, KC_HARVEST, KC_COUNT
+    KC_MLP, KC_LEARNED, KC_HARVEST, KC_SUB_GAUSS, KC_MAJOR, KC_COUNT
 };
 static const char* const KC_NAMES[KC_COUNT] = {
     "k_cycle_begin", "k_smooth_h", "k_smooth_v_argmax", "k_select", "k_lm_fit", "k_update", "k_build_weights",
-    "k_sub_h", "k_sub_v_argmax", "k_argmax_abs", "mlp_infer (tcgen05)", "k_learned_*", "k_harvest"};
+    "k_sub_h", "k_sub_v_argmax", "k_argmax_abs", "mlp_infer (tcgen05)", "k_learned_*", "k_harvest",
+    "k_sub_gauss", "major cycle (FFT)"};
+static const int MAJOR_KERNELS = 8;   // launches of one major cycle (5 kernels, 2 FFTs, argmax)
 static const int KERNELS_PER_ITER = 9;   // kernels one minor-cycle iteration enqueues
 
 struct ProfMark {
@@ -72,7 +74,7 @@ struct asp_ctx {
     double prof_ms[KC_COUNT] = {};
     long long prof_n[KC_COUNT] = {};
     long long launches = 0;
-    int iter_kernels = KERNELS_PER_ITER;   // kernels one captured iteration holds
+    int graph_kernels = 8 * KERNELS_PER_ITER;   // kernels one graph replay launches
     // learned initial values
     int learned = 0;
     float* mlpP = nullptr;                 // FP32 parameter vector
@@ -86,6 +88,16 @@ struct asp_ctx {
     float* harvest_p = nullptr;
     float* harvest_t = nullptr;
     int harvest_cap = 0;
+    // minor/major split (asp_params.major_every > 0): the dirty image, the
+    // PSF's transform, FFT buffers and plans, per-component normalisations
+    float* D = nullptr;
+    float* fft_in = nullptr;
+    float* fft_out = nullptr;
+    cufftComplex* fft_work = nullptr;
+    cufftComplex* bhat = nullptr;
+    float2* norms = nullptr;
+    cufftHandle r2c = 0, c2r = 0;
+    bool plans = false;
     int broken = 0;
     std::string err;
     std::vector<void*> allocs;
@@ -175,7 +187,7 @@ asp_status validate_params(const asp_params* p) {
     if (p->k_max > ASP_KMAX) return ASP_ERR_UNSUPPORTED;
     if (p->lm_max_iter < 0 || p->n_scales < 1 || p->n_scales > MAX_SCALES) return ASP_ERR_INVALID_ARG;
     if (!(p->lm_lambda0 > 0) || !(p->lm_rtol >= 0) || !(p->lm_xtol >= 0)) return ASP_ERR_INVALID_ARG;
-    if (p->fit_px_per_cta < 0) return ASP_ERR_INVALID_ARG;
+    if (p->fit_px_per_cta < 0 || p->major_every < 0) return ASP_ERR_INVALID_ARG;
     if (p->init_mode < 0 || p->init_mode > 2) return ASP_ERR_INVALID_ARG;
     if (p->retained_cap < 0 || p->retained_cap > RET_MAX) return ASP_ERR_UNSUPPORTED;
     if (p->max_components < 0) return ASP_ERR_INVALID_ARG;
@@ -292,11 +304,36 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
         Mark m(ctx, KC_HARVEST);
         CK(launch_harvest(st, ctx->R, H, W, ctx->harvest_p, ctx->harvest_t, ctx->harvest_cap, s));
     }
+    if (ctx->p.major_every > 0) {
+        // minor/major split: the terms' single-Gaussian-beam images, then the
+        // next peak of the (approximate) residual
+        { Mark m(ctx, KC_SUB_GAUSS); CK(launch_sub_gauss(ctx->R, H, W, st, ctx->grid_img, s)); }
+        { Mark m(ctx, KC_ARGMAX);
+          CK(launch_argmax(ctx->R, ctx->N, ctx->grid_img, ctx->part, ctx->ticket, &st->peak, &st->nonfinite,
+                           &st->stopped, s)); }
+        return ASP_OK;
+    }
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(st, &st->stopped, ctx->wbuf, s)); }
     { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->taps, s)); }
     { Mark m(ctx, KC_SUB_V);
       CK(launch_sub_v(ctx->R, ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part, ctx->ticket,
                       s)); }
+    return ASP_OK;
+}
+
+// The major cycle: R = D - B * M exactly (FFT convolution), applied if a
+// minor iteration ran since the last one, then the next peak.
+asp_status enqueue_major(asp_ctx* ctx) {
+    CycleState* st = ctx->st;
+    {
+        Mark m(ctx, KC_MAJOR);
+        ctx->launches += MAJOR_KERNELS - 2;
+        CK(launch_major(ctx->comps, ctx->norms, st, ctx->H, ctx->W, ctx->fft_in, ctx->fft_work, ctx->bhat,
+                        ctx->fft_out, ctx->R, ctx->D, ctx->r2c, ctx->c2r, ctx->grid_img, ctx->stream));
+    }
+    { Mark m(ctx, KC_ARGMAX);
+      CK(launch_argmax(ctx->R, ctx->N, ctx->grid_img, ctx->part, ctx->ticket, &st->peak, &st->nonfinite,
+                       &st->major_skip, ctx->stream)); }
     return ASP_OK;
 }
 
@@ -313,10 +350,11 @@ asp_status build_graph(asp_ctx* ctx) {
     const long long launches_before = ctx->launches;
     if (ok) {
         for (int i = 0; i < ctx->graph_unroll && s == ASP_OK; ++i) s = enqueue_iteration(ctx);
+        if (s == ASP_OK && ctx->p.major_every > 0) s = enqueue_major(ctx);
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         ok = (s == ASP_OK) && e == cudaSuccess && g != nullptr;
     }
-    ctx->iter_kernels = (int)((ctx->launches - launches_before) / std::max(ctx->graph_unroll, 1));
+    ctx->graph_kernels = (int)(ctx->launches - launches_before);
     ctx->stream = saved;
     ctx->launches = launches_before;
     ctx->broken = 0;
@@ -504,6 +542,7 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     ctx->dp.retained_cap = ctx->p.retained_cap;
     ctx->dp.n_scales = ctx->p.n_scales;
     ctx->dp.tau = ctx->p.tau;
+    ctx->dp.major_every = ctx->p.major_every;
     ctx->dp.lm = lmconst_from(ctx->p);
 
     const long long N = ctx->N;
@@ -536,6 +575,25 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
         cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream) != cudaSuccess)
         return bail(ASP_ERR_CUDA);
 
+    if (ctx->p.major_every > 0) {
+        // the minor/major split's buffers, the FFT plans of the 2H x 2W
+        // grid and the PSF's transform
+        const size_t nc = (size_t)(2 * H) * (W + 1);
+        if (dalloc(ctx, &ctx->D, (size_t)N) != cudaSuccess || dalloc(ctx, &ctx->fft_in, (size_t)4 * N) != cudaSuccess ||
+            dalloc(ctx, &ctx->fft_out, (size_t)4 * N) != cudaSuccess || dalloc(ctx, &ctx->fft_work, nc) != cudaSuccess ||
+            dalloc(ctx, &ctx->bhat, nc) != cudaSuccess || dalloc(ctx, &ctx->norms, (size_t)cap) != cudaSuccess)
+            return bail(ASP_ERR_OOM);
+        if (cufftPlan2d(&ctx->r2c, 2 * H, 2 * W, CUFFT_R2C) != CUFFT_SUCCESS) return bail(ASP_ERR_CUDA);
+        if (cufftPlan2d(&ctx->c2r, 2 * H, 2 * W, CUFFT_C2R) != CUFFT_SUCCESS) {
+            cufftDestroy(ctx->r2c);
+            return bail(ASP_ERR_CUDA);
+        }
+        ctx->plans = true;
+        if (cudaMemcpyAsync(ctx->D, ctx->R, N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+            compute_psf_transform(ctx->B, H, W, ctx->fft_in, ctx->bhat, ctx->r2c, ctx->stream) != cudaSuccess)
+            return bail(ASP_ERR_CUDA);
+        ctx->graph_unroll = ctx->p.major_every;
+    }
     s = fit_beam(ctx);
     if (s != ASP_OK) return bail(s);
     s = setup_taps(ctx);
@@ -593,6 +651,7 @@ asp_status asp_destroy(asp_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->plans) { cufftDestroy(ctx->r2c); cufftDestroy(ctx->c2r); }
     collect_marks(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (void* q : ctx->allocs) cudaFree(q);
@@ -820,6 +879,21 @@ asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float g
     return ASP_OK;
 }
 
+asp_status asp_subtract_beam(asp_ctx* ctx, const asp_component* comps, int n, float gain) {
+    CHECK_CTX();
+    if (!comps || n < 0 || n > MAX_TERMS || !std::isfinite(gain)) return ASP_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(comps[i].flux) || !std::isfinite(comps[i].x) || !std::isfinite(comps[i].y) ||
+            !std::isfinite(comps[i].width) || comps[i].width < 0)
+            return ASP_ERR_INVALID_ARG;
+    if (n == 0) return ASP_OK;
+    CK(cudaMemcpyAsync(ctx->comp_stage, comps, n * sizeof(asp_component), cudaMemcpyHostToDevice, ctx->stream));
+    { Mark m(ctx, KC_UPDATE); CK(launch_terms_from_components(ctx->st, ctx->comp_stage, n, gain, ctx->H, ctx->W, ctx->stream)); }
+    { Mark m(ctx, KC_SUB_GAUSS); CK(launch_sub_gauss(ctx->R, ctx->H, ctx->W, ctx->st, ctx->grid_img, ctx->stream)); }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return refresh_peak(ctx);
+}
+
 asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
     CHECK_CTX();
     if (n_iter < 0) return ASP_ERR_INVALID_ARG;
@@ -837,11 +911,16 @@ asp_status asp_minor_cycle(asp_ctx* ctx, int n_iter, asp_cycle_stats* out) {
         if (ctx->graph_state == 1 && !ctx->profiling) {
             const int reps = (n_iter + ctx->graph_unroll - 1) / ctx->graph_unroll;
             for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-            ctx->launches += (long long)reps * ctx->graph_unroll * ctx->iter_kernels;
+            ctx->launches += (long long)reps * ctx->graph_kernels;
         } else {
+            const int me = ctx->p.major_every;
             for (int i = 0; i < n_iter; ++i) {
                 s = enqueue_iteration(ctx);
                 if (s != ASP_OK) return s;
+                if (me > 0 && ((i + 1) % me == 0 || i + 1 == n_iter)) {
+                    s = enqueue_major(ctx);
+                    if (s != ASP_OK) return s;
+                }
             }
         }
     }
@@ -1050,6 +1129,10 @@ asp_status asp_reset(asp_ctx* ctx, const float* dirty, int dirty_on_host, const 
     }
     CK(cudaMemcpyAsync(ctx->R, dirty, ctx->N * sizeof(float),
                        dirty_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->p.major_every > 0) {
+        CK(cudaMemcpyAsync(ctx->D, ctx->R, ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+        if (psf) CK(compute_psf_transform(ctx->B, ctx->H, ctx->W, ctx->fft_in, ctx->bhat, ctx->r2c, ctx->stream));
+    }
     { Mark m(ctx, KC_BEGIN); CK(launch_reset_state(ctx->st, ctx->stream)); }
     return refresh_peak(ctx);
 }
@@ -1380,6 +1463,7 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
     if (!out) return ASP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!params || n < 1 || n > MAX_BATCH || !H || !W || !dirty || !psf) return ASP_ERR_INVALID_ARG;
+    if (params->major_every != 0) return ASP_ERR_UNSUPPORTED;   // the minor/major split is per context
     for (int i = 0; i < n; ++i)
         if (H[i] < 1 || W[i] < 1 || !dirty[i] || !psf[i]) return ASP_ERR_INVALID_ARG;
     asp_batch* b = new asp_batch();

@@ -310,7 +310,9 @@ __device__ __forceinline__ void update_body(CycleState* st, asp_component* comps
             if (make_term(s_old[m], -s_old[m].flux, H, W, nt, s_terms[nt])) ++nt;
         }
         st->n_terms = nt;
-        finish_terms(st, s_terms, nt, H, W);
+        // the separable full-PSF passes' layout and work; the minor/major
+        // split subtracts the terms' beam images instead (k_sub_gauss)
+        if (p.major_every == 0) finish_terms(st, s_terms, nt, H, W);
         st->last_wi = cn.width;
         s_nt = nt;
     }
@@ -369,6 +371,7 @@ __device__ __forceinline__ void update_body(CycleState* st, asp_component* comps
         st->fit_fallbacks += fo.fallbacks;
         st->lm_passes += fo.passes;
         st->t += 1;
+        st->since_major += 1;
     }
 }
 
@@ -453,6 +456,7 @@ __global__ void k_reset_state(CycleState* st) {
     st->pixel_evals = 0; st->lm_iters = 0; st->lm_passes = 0;
     st->fit_flops = 0.0; st->sub_flops = 0.0; st->sub_bytes = 0.0; st->smooth_flops = 0.0;
     st->fit_ex2 = 0.0; st->smooth_iters = 0;
+    st->since_major = 0; st->major_skip = 1; st->major_cycles = 0;
     st->fit_ns_pass = 0; st->fit_ns_reduce = 0; st->fit_ns_solve = 0; st->fit_ns_factor = 0; st->fit_ns_subst = 0;
     st->fit_refinements = 0; st->fit_fallbacks = 0;
     st->nonfinite = 0;

@@ -135,11 +135,16 @@ struct CycleState {
     int learned_px, learned_py;    // the plain peak pixel
     int learned_used, need_plain;
     long long learned_fits, learned_refits, learned_kept;
+    // minor/major split: minor iterations since the last exact residual,
+    // whether the current major cycle is skipped, major cycles applied
+    int since_major, major_skip;
+    long long major_cycles;
 };
 
 struct Params {                    // device copy of asp_params plus derived values
     float gain, area_frac;
     int k_max, init_mode, retained_cap, n_scales;
+    int major_every, pad_p;
     double tau;
     LMConst lm;
 };

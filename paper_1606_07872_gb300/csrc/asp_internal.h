@@ -1,6 +1,7 @@
 // Host-side launchers shared between the translation units of libasp.
 #pragma once
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include "asp_dev.cuh"
 
@@ -73,6 +74,14 @@ cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps
                             float* S1, int grid, cudaStream_t s);
 cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
                             int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
+
+// asp_major.cu (minor/major split)
+cudaError_t launch_sub_gauss(float* R, int H, int W, CycleState* st, int grid, cudaStream_t s);
+cudaError_t launch_major(const asp_component* comps, float2* norms, CycleState* st, int H, int W, float* pad_in,
+                         cufftComplex* work, const cufftComplex* bhat, float* conv_out, float* R, const float* D,
+                         cufftHandle r2c, cufftHandle c2r, int grid, cudaStream_t s);
+cudaError_t compute_psf_transform(const float* B, int H, int W, float* pad_in, cufftComplex* bhat, cufftHandle r2c,
+                                  cudaStream_t s);
 
 // asp_cycle.cu
 cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, double smooth_flops, cudaStream_t s);

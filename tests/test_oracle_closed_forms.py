@@ -500,3 +500,49 @@ def test_window_is_clipped_bounding_box_of_member_boxes():
     assert win == (0, 22, 19, 39)                                     # (-6, 22, 19, 47) clipped to 50 x 40
     chosen, win = mc.select(dict(a0=1.0, x0=49.0, y0=0.0, w0=1.5))   # far corner: no overlap
     assert chosen == [] and win == (43, 49, 0, 6)
+
+
+# ----------------------------------------------------------------- minor/major split (reading of the Clark comparison)
+
+@pytest.mark.parametrize("F,x,y,w", [(1.3, 20.4, 18.7, 2.5), (-0.6, 15.0, 22.0, 0.0), (0.8, 21.6, 19.1, 4.0)])
+def test_beam_image_is_full_psf_subtraction_through_a_gaussian_psf(F, x, y, w):
+    """Through a PSF that is itself the Gaussian (alpha_b, omega_b), the
+    minor cycle's beam image of a component is the exact subtraction of its
+    sampled image (Sect. 3: Gaussian * Gaussian is the Gaussian with widths
+    in quadrature and the amplitude of Eq. 8) -- up to the discrete
+    sampling's aliasing and the 5 omega_ic box; a point component (w = 0)
+    on a pixel is the beam itself (off a pixel the exact path deposits it
+    bilinearly, a reading of its own)."""
+    H, W = 40, 44
+    ab, wb = 0.9, 1.8
+    B = synth.gaussian_psf(H, W, wb, ab)
+    t = O.component_terms(F, x, y, w, w == 0.0, H, W)
+    exact = -O.subtract_terms(np.zeros((H, W)), B, [t])
+    approx = -O.subtract_beam_images(np.zeros((H, W)), [(F, x, y, w)], ab, wb)
+    scale = np.abs(exact).max()
+    assert np.abs(exact - approx).max() <= 2e-5 * scale
+
+
+def test_major_cycle_is_the_brute_force_exact_residual():
+    c = synth.small_case(24, 28, seed=4, n_points=1, n_gauss=1, sigma_range=(2.0, 3.0))
+    mc = O.MinorCycle(c.dirty, c.psf, O.AspParams(k_max=2, noise_sigma=c.noise_sigma, major_every=3))
+    for _ in range(2):
+        mc.step()
+    mc.major()
+    dC = O.terms_to_image([O.component_terms(k.flux, k.x, k.y, k.width, k.is_point, 24, 28) for k in mc.comps], 24, 28)
+    ref = O.subtract_definition(c.dirty, c.psf, dC)
+    np.testing.assert_allclose(mc.R, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_major_every_iteration_reproduces_the_exact_cycle():
+    """With a major cycle after every minor iteration the residual is exact
+    at every peak search: the run takes the exact cycle's decisions and ends
+    with its components."""
+    c = synth.small_case(48, 52, seed=6, n_points=2, n_gauss=1, sigma_range=(2.0, 4.0))
+    a = O.MinorCycle(c.dirty, c.psf, O.AspParams(k_max=3, noise_sigma=c.noise_sigma)).run(12)
+    b = O.MinorCycle(c.dirty, c.psf, O.AspParams(k_max=3, noise_sigma=c.noise_sigma, major_every=1)).run(12)
+    assert [h["window"] for h in a.history] == [h["window"] for h in b.history]
+    fa = np.array([[k.flux, k.x, k.y, k.width] for k in a.comps])
+    fb = np.array([[k.flux, k.x, k.y, k.width] for k in b.comps])
+    np.testing.assert_allclose(fa, fb, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(a.R, b.R, rtol=0, atol=1e-10)

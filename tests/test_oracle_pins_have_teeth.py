@@ -164,3 +164,18 @@ def test_window_without_clipping_is_caught(monkeypatch):
     monkeypatch.setattr(OA.MinorCycle, "select", bad)
     with pytest.raises(AssertionError):
         pins.test_window_is_clipped_bounding_box_of_member_boxes()
+
+
+def test_beam_image_with_widths_added_linearly_is_caught(monkeypatch):
+    def bad(x, y, w, alpha_b, omega_b, H, W):
+        w_ic = w + omega_b
+        a_ic = alpha_b * omega_b * omega_b / (w_ic * w_ic)
+        h = math.ceil(5.0 * w_ic) + 1
+        x0, x1 = max(math.ceil(x - h), 0), min(math.floor(x + h), W - 1)
+        y0, y1 = max(math.ceil(y - h), 0), min(math.floor(y + h), H - 1)
+        ys, xs = np.mgrid[y0: y1 + 1, x0: x1 + 1].astype(np.float64)
+        return x0, y0, a_ic * np.exp(-((xs - x) ** 2 + (ys - y) ** 2) / (2.0 * w_ic * w_ic))
+
+    _patch(monkeypatch, "beam_image_box", bad)
+    with pytest.raises(AssertionError):
+        pins.test_beam_image_is_full_psf_subtraction_through_a_gaussian_psf(1.3, 20.4, 18.7, 2.5)
