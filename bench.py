@@ -52,6 +52,7 @@ def _args():
     ap.add_argument("--config3-warmup", type=int, default=3)
     ap.add_argument("--fit-px", type=int, default=0, help="LM fit tile: window pixels per CTA (0: library default)")
     ap.add_argument("--no-split", action="store_true", help="skip the minor/major split comparison")
+    ap.add_argument("--no-2004", action="store_true", help="skip the Eq. 3 vs Eq. 6 per-iteration comparison")
     ap.add_argument("--split-every", type=int, default=50, help="minor iterations per major cycle in the split")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
@@ -643,6 +644,44 @@ def workload_line(a, m: dict, case, world: int, peaks: dict, peak_kind: str, alu
             "kernels": k, "fit_phases": _fit_phases(m["prof"]), "clocks": m["clocks"]}
 
 
+def asp2004_comparison(asp) -> dict:
+    """The paper's Table 3 per-iteration comparison, on this GPU: one LM fit
+    of the first component of a workload with Asp-Clean2004's objective
+    (Eq. 3: the full PSF applied by FFT in every evaluation, whole image)
+    and with Asp-Clean2016's (Eq. 6: the fitted Gaussian directly, local
+    window), from the same smoothed-peak start; wall time per LM iteration
+    (device-synchronised C-ABI calls, best of 3)."""
+    import math
+    import torch
+    import synth
+    out = {"paper_table3_per_iteration_ratio": {"uniform": 61.11, "natural": 101.21, "robust": 41.66,
+                                                "note": "Python + CASA on a CPU, M31 256x256 (context)"}}
+    for name, case in (("256x256 (config1)", synth.config1(0)), ("1024x1024 (config2)", synth.config2(0))):
+        ctx = asp.Context(torch.from_numpy(case.dirty).cuda(), torch.from_numpy(case.psf).cuda(), k_max=case.k_max,
+                          noise_sigma=case.noise_sigma)
+        ab, wb, _, _ = ctx.beam
+        pk = ctx.find_peak(asp.ASP_PEAK_SMOOTH)
+        init6 = [[pk["a0"], pk["x0"], pk["y0"], pk["w0"]]]
+        wi = math.sqrt(max(pk["w0"] ** 2 - wb * wb, 0.25))
+        init3 = [[pk["a0"] * pk["w0"] ** 2 / (2 * math.pi * ab * wb * wb * wi * wi), pk["x0"], pk["y0"], wi]]
+        res = {}
+        for kind, call in (("eq6", lambda: ctx.fit(init6, 0)), ("eq3", lambda: ctx.fit_2004(init3, 0, 0.1))):
+            best, info = None, None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, info = call()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            res[kind] = {"seconds": best, "lm_iters": info["iters"], "passes": info["passes"],
+                         "ms_per_lm_iter": 1e3 * best / max(info["iters"], 1)}
+        res["per_iteration_ratio_eq3_over_eq6"] = res["eq3"]["ms_per_lm_iter"] / res["eq6"]["ms_per_lm_iter"]
+        out[name] = res
+        ctx.close()
+    return out
+
+
 def split_summary(m: dict, exact_line: dict) -> dict:
     """The minor/major split against the exact-subtraction run of the same
     workload: rate, the final (exact) residual RMS and the kernel times."""
@@ -698,6 +737,11 @@ def run_ours(a):
                 del c3
         except Exception as e:   # report, never hide, a failed measurement
             line["split"] = {"error": repr(e)[:300]}
+    if rank == 0 and main_cfg == 2 and not a.no_2004:
+        try:
+            line["asp2004"] = asp2004_comparison(asp)
+        except Exception as e:   # report, never hide, a failed comparison
+            line["asp2004"] = {"error": repr(e)[:300]}
     if rank == 0 and main_cfg == 2 and not a.no_learned:
         try:
             line["learned"], weights = learned_comparison(asp, a.learned_train_images)

@@ -231,6 +231,24 @@ asp_status asp_eval_normal_equations(asp_ctx* ctx, const asp_gauss* theta, int n
 asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, const asp_gauss* start, double lambda0,
                       int max_iter, asp_gauss* out, asp_fit_info* info, asp_gauss* trial_out, double* chi2_trial);
 
+/* Asp-Clean2004's objective (Sect. 2, Eq. 3), the system the paper
+ * accelerates: Levenberg-Marquardt on chi^2 = || T - B * sum_k g_k ||^2 over
+ * the whole image, g_k the UNCONVOLVED component a exp(-r^2 / 2 w^2) of each
+ * member (rows of init: amplitude, centre, width of the component itself),
+ * B the full PSF applied by an FFT convolution on the 2H x 2W grid in every
+ * evaluation (cuFFT, FP32), T the residual with the last n_old members'
+ * init components added back through B.  The LM rules are
+ * asp_fit_active_set's (context LM settings; trial widths in (omega_min,
+ * max(H, W)], centres inside the image; a trial costs the model's
+ * convolution, an accepted point the 4n Jacobian convolutions).  With a
+ * Gaussian PSF its optimum maps to Eq. 6's through Eqs. 7-8.  The LM
+ * iterations run on the host, the images, FFTs and sums on the device.
+ * 1 <= n <= 8 (ASP_ERR_UNSUPPORTED beyond).  The first call allocates its
+ * buffers (33 zero-padded images of 2H x 2W, their transforms) and plans,
+ * kept until asp_destroy.  info->pixel_evals counts evaluations x H W. */
+asp_status asp_fit_2004(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, double omega_min, asp_gauss* out,
+                        asp_fit_info* info);
+
 /* R -= B * (gain * sum_i c_i) with the full PSF (Sect. 2 step 3); c_i is
  * component i sampled on the grid (a flux-normalised Gaussian on the box
  * |q - centre|_inf <= ceil(5 w) + 1 if w >= 0.5 px and not a point, else a

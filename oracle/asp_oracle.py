@@ -34,7 +34,7 @@ __all__ = [
     "LMParams", "AspParams", "FitResult", "Component", "lm_exact",
     "LM_CONVERGED", "LM_CAP", "LM_STALLED", "MODE_SIMPLE", "MODE_SMOOTH",
     "round_half_up", "gauss_model", "model_and_jacobian", "normal_equations", "lm_fit",
-    "cholesky_solve_damped",
+    "cholesky_solve_damped", "psf_convolve", "model_jac_2004", "lm_fit_2004",
     "halfmax_width", "beam_fit", "peak_simple", "smoothing_scales", "smoothing_kernel_1d",
     "smooth_separable", "smooth_definition", "peak_smooth",
     "deconvolve", "gauss_approx", "component_terms", "terms_to_image",
@@ -217,7 +217,7 @@ def _valid(theta, box, omega_min):
     return True
 
 
-def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> FitResult:
+def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None, model_jac=None) -> FitResult:
     """Levenberg-Marquardt minimisation of the Eq. 6 objective.
 
     ``T`` are the target values at pixel coordinates ``(xs, ys)``; ``box =
@@ -234,6 +234,10 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
     5. on an accepted step stop if the relative decrease is below rtol or
        every |delta_i| is below xtol of its scale; on a reject stop if
        lambda exceeds lambda_max; stop after max_iter solves.
+
+    ``model_jac(theta) -> (model, J)`` replaces the Eq. 6 model and Jacobian
+    (e.g. the Eq. 3 objective of :func:`model_jac_2004`); xs and ys then
+    only size the data.
     """
     lm = lm or LMParams()
     T = np.asarray(T, dtype=np.float64).ravel()
@@ -241,7 +245,14 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
     ys = np.asarray(ys, dtype=np.float64).ravel()
     theta = np.array(theta0, dtype=np.float64)
     n = T.size
-    A, g, chi2 = normal_equations(T, xs, ys, theta)
+    if model_jac is None:
+        ne = lambda th: normal_equations(T, xs, ys, th)   # noqa: E731
+    else:
+        def ne(th):
+            m, J = model_jac(th)
+            r = T - m
+            return J.T @ J, J.T @ r, float(r @ r)
+    A, g, chi2 = ne(theta)
     chi2_init = chi2
     passes, iters, lam = 1, 0, lm.lambda0
     status = LM_CAP
@@ -274,7 +285,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
                 status = LM_STALLED
                 break
             continue
-        A2, g2, chi2_t = normal_equations(T, xs, ys, trial)
+        A2, g2, chi2_t = ne(trial)
         passes += 1
         last_pass_chi2 = chi2_t
         if chi2_t < chi2:
@@ -297,6 +308,47 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None) -> 
                 status = LM_STALLED
                 break
     return FitResult(theta, chi2_init, chi2, iters, passes, lam, status, passes * n, last_trial, last_pass_chi2)
+
+
+# --------------------------------------------------------------------------
+# Asp-Clean2004's objective (Sect. 2, Eq. 3): the full PSF inside chi^2
+
+def psf_convolve(B, img):
+    """``(B * img)(p) = sum_q B(p - q + (H, W)) img(q)`` for H x W images
+    with the 2H x 2W PSF (zero lag at [H, W]), as an FP64 FFT product on
+    the 2H x 2W grid (no wrap-around: p - q + H lies in [1, 2H - 1])."""
+    B = np.asarray(B, dtype=np.float64)
+    img = np.asarray(img, dtype=np.float64)
+    H, W = img.shape
+    pad = np.zeros((2 * H, 2 * W))
+    pad[:H, :W] = img
+    out = np.fft.irfft2(np.fft.rfft2(pad) * np.fft.rfft2(B), s=(2 * H, 2 * W))
+    return out[H: 2 * H, W: 2 * W]
+
+
+def model_jac_2004(B, theta, H, W):
+    """The Eq. 3 model B * sum_k g_k over the whole image and its
+    Jacobian: g_k the *unconvolved* component a exp(-r^2 / 2 omega^2)
+    sampled at the pixel centres; each column is the PSF convolution of the
+    component's derivative image (Sect. 2: one FFT convolution per
+    evaluation).  Returns (model (N,), J (N, 4K))."""
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    m, Jimg = model_and_jacobian(theta, xs.ravel(), ys.ravel())
+    model = psf_convolve(B, m.reshape(H, W)).ravel()
+    J = np.stack([psf_convolve(B, Jimg[:, j].reshape(H, W)).ravel() for j in range(Jimg.shape[1])], 1)
+    return model, J
+
+
+def lm_fit_2004(T_img, B, theta0, omega_min, lm: Optional[LMParams] = None) -> FitResult:
+    """Levenberg-Marquardt on the Eq. 3 objective chi^2 = || T - B * sum_k
+    g_k ||^2 over the whole image (T: the residual with the fitted members'
+    previous contributions added back through B), with the same LM rules
+    as :func:`lm_fit`; trial centres must stay in the image."""
+    T_img = np.asarray(T_img, dtype=np.float64)
+    H, W = T_img.shape
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    return lm_fit(T_img.ravel(), xs.ravel(), ys.ravel(), theta0, (0, W - 1, 0, H - 1), omega_min, lm,
+                  model_jac=lambda th: model_jac_2004(B, th, H, W))
 
 
 # --------------------------------------------------------------------------

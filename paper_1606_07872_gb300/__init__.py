@@ -23,7 +23,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "AspError", "lib", "default_params", "asp_init", "asp_init_host", "asp_destroy", "asp_get_beam",
-    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
+    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_fit_2004", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
@@ -177,6 +177,17 @@ def asp_measure_alu_peaks() -> dict:
     out = _lib.asp_alu_peaks()
     _check(lib().asp_measure_alu_peaks(C.byref(out)), "asp_measure_alu_peaks")
     return {f: getattr(out, f) for f, _ in _lib.asp_alu_peaks._fields_ if f != "reserved"}
+
+
+def asp_fit_2004(h, init, n_old: int = 0, omega_min: float = 0.1):
+    """LM on Asp-Clean2004's Eq. 3 objective (unconvolved components through
+    the full PSF by FFT).  Returns (fitted rows, info dict)."""
+    arr, n = _gauss_array(init)
+    out = (asp_gauss * n)()
+    info = asp_fit_info()
+    _check(lib().asp_fit_2004(h, arr, n, int(n_old), float(omega_min), out, C.byref(info)), "asp_fit_2004", h)
+    return (np.array([[g.amp, g.x, g.y, g.width] for g in out]),
+            {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_})
 
 
 def asp_eval_normal_equations(h, theta, n_old: int, window):
@@ -431,6 +442,9 @@ class Context:
 
     def fit(self, init, n_old=0):
         return asp_fit_active_set(self.h, init, n_old)
+
+    def fit_2004(self, init, n_old=0, omega_min=0.1):
+        return asp_fit_2004(self.h, init, n_old, omega_min)
 
     def fit_lm(self, init, n_old, lambda0, max_iter, start=None):
         return asp_fit_lm(self.h, init, n_old, lambda0, max_iter, start)

@@ -107,6 +107,7 @@ SIGNATURES = {
     "asp_fit_lm": [_P, C.POINTER(asp_gauss), _I, _I, C.POINTER(asp_gauss), C.c_double, _I, C.POINTER(asp_gauss),
                    C.POINTER(asp_fit_info), C.POINTER(asp_gauss), C.POINTER(C.c_double)],
     "asp_eval_normal_equations": [_P, C.POINTER(asp_gauss), _I, _I, _I, _I, _I, _I, _P, _P, _P],
+    "asp_fit_2004": [_P, C.POINTER(asp_gauss), _I, _I, C.c_double, C.POINTER(asp_gauss), C.POINTER(asp_fit_info)],
     "asp_subtract": [_P, C.POINTER(asp_component), _I, C.c_float],
     "asp_subtract_beam": [_P, C.POINTER(asp_component), _I, C.c_float],
     "asp_minor_cycle": [_P, _I, C.POINTER(asp_cycle_stats)],

@@ -98,6 +98,7 @@ struct asp_ctx {
     float2* norms = nullptr;
     cufftHandle r2c = 0, c2r = 0;
     bool plans = false;
+    Fit2004Buffers* f2004 = nullptr;   // Asp-Clean2004's objective, allocated by its first call
     int broken = 0;
     std::string err;
     std::vector<void*> allocs;
@@ -652,6 +653,14 @@ asp_status asp_destroy(asp_ctx* ctx) {
     else cudaDeviceSynchronize();
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->plans) { cufftDestroy(ctx->r2c); cufftDestroy(ctx->c2r); }
+    if (ctx->f2004) {
+        Fit2004Buffers* fb = ctx->f2004;
+        if (fb->r2c1) cufftDestroy(fb->r2c1);
+        if (fb->c2r1) cufftDestroy(fb->c2r1);
+        if (fb->r2cN) cufftDestroy(fb->r2cN);
+        if (fb->c2rN) cufftDestroy(fb->c2rN);
+        delete fb;
+    }
     collect_marks(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (void* q : ctx->allocs) cudaFree(q);
@@ -825,6 +834,211 @@ asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, con
     CHECK_CTX();
     if (!(lambda0 > 0.0) || !std::isfinite(lambda0) || max_iter < 0) return ASP_ERR_INVALID_ARG;
     return fit_common(ctx, init, n, n_old, start, lambda0, max_iter, out, info, trial_out, chi2_trial);
+}
+
+// ---------------------------------------------------------------- Asp-Clean2004's objective (Eq. 3)
+
+static asp_status f2004_setup(asp_ctx* ctx, int K) {
+    const int H = ctx->H, W = ctx->W;
+    const int nb = 4 * K + 1;
+    if (!ctx->f2004) {
+        Fit2004Buffers* fb = new Fit2004Buffers();
+        ctx->f2004 = fb;
+        const size_t nimg = (size_t)4 * ctx->N, nc = (size_t)(2 * H) * (W + 1);
+        fb->grid = ctx->grid_img;
+        fb->ne_blocks = ctx->grid_img;
+        CK(dalloc(ctx, &fb->imgs, nimg * FIT2004_NA));
+        CK(dalloc(ctx, &fb->conv, nimg * FIT2004_NA));
+        CK(dalloc(ctx, &fb->work, nc * FIT2004_NA));
+        CK(dalloc(ctx, &fb->bhat, nc));
+        CK(dalloc(ctx, &fb->T, (size_t)ctx->N));
+        CK(dalloc(ctx, &fb->partials, (size_t)fb->ne_blocks * FIT2004_NACC));
+        CK(dalloc(ctx, &fb->sums, (size_t)FIT2004_NACC));
+        CK(dalloc(ctx, &fb->theta, (size_t)4 * FIT2004_KMAX));
+        CK(cudaMemsetAsync(fb->imgs, 0, sizeof(float) * nimg * FIT2004_NA, ctx->stream));
+        if (cufftPlan2d(&fb->r2c1, 2 * H, 2 * W, CUFFT_R2C) != CUFFT_SUCCESS ||
+            cufftPlan2d(&fb->c2r1, 2 * H, 2 * W, CUFFT_C2R) != CUFFT_SUCCESS)
+            return fail(ctx, ASP_ERR_CUDA, "cuFFT plan");
+        CK(psf_transform_2004(*fb, ctx->B, H, W, ctx->stream));
+    }
+    Fit2004Buffers* fb = ctx->f2004;
+    if (fb->nb != nb) {
+        if (fb->r2cN) { cufftDestroy(fb->r2cN); fb->r2cN = 0; }
+        if (fb->c2rN) { cufftDestroy(fb->c2rN); fb->c2rN = 0; }
+        int n[2] = {2 * H, 2 * W};
+        const int dist_r = 4 * H * W, dist_c = 2 * H * (W + 1);
+        if (cufftPlanMany(&fb->r2cN, 2, n, nullptr, 1, dist_r, nullptr, 1, dist_c, CUFFT_R2C, nb) != CUFFT_SUCCESS ||
+            cufftPlanMany(&fb->c2rN, 2, n, nullptr, 1, dist_c, nullptr, 1, dist_r, CUFFT_C2R, nb) != CUFFT_SUCCESS)
+            return fail(ctx, ASP_ERR_CUDA, "cuFFT batched plan");
+        fb->nb = nb;
+    }
+    return ASP_OK;
+}
+
+// One evaluation of Eq. 3 at theta (host, 4K values): with full, the packed
+// upper triangle of [J | r]^T [J | r] into A (K4 x K4, full), g and chi2;
+// else chi2 only.
+static asp_status f2004_eval(asp_ctx* ctx, const double* theta, int K, bool full, double* A, double* g, double* chi2) {
+    Fit2004Buffers* fb = ctx->f2004;
+    const int P = 4 * K, NA = full ? P + 1 : 1, nacc = NA * (NA + 1) / 2;
+    CK(cudaMemcpyAsync(fb->theta, theta, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+    CK(eval_2004(*fb, fb->theta, K, NA, ctx->H, ctx->W, ctx->R, false, ctx->stream));
+    std::vector<double> sums((size_t)nacc);
+    CK(cudaMemcpyAsync(sums.data(), fb->sums, sizeof(double) * nacc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    auto at = [&](int i, int j) {                       // packed upper triangle, row-major
+        if (i > j) std::swap(i, j);
+        return sums[(size_t)i * NA - (size_t)i * (i - 1) / 2 + (j - i)];
+    };
+    *chi2 = at(NA - 1, NA - 1);
+    if (full) {
+        for (int i = 0; i < P; ++i) {
+            g[i] = at(i, P);
+            for (int j = 0; j < P; ++j) A[(size_t)i * P + j] = at(i, j);
+        }
+    }
+    return ASP_OK;
+}
+
+// (A + lam diag(d)) delta = g by FP64 Cholesky, d_i = A_ii (1 where A_ii <=
+// 0); false if not positive definite.
+static bool f2004_solve(const std::vector<double>& A, const std::vector<double>& g, double lam, int P,
+                        std::vector<double>& delta) {
+    std::vector<double> L((size_t)P * P, 0.0);
+    for (int i = 0; i < P; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = A[(size_t)i * P + j];
+            if (i == j) {
+                const double d = A[(size_t)i * P + i] > 0 ? A[(size_t)i * P + i] : 1.0;
+                v += lam * d;
+            }
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * P + k] * L[(size_t)j * P + k];
+            if (i == j) {
+                if (!(v > 0) || !std::isfinite(v)) return false;
+                L[(size_t)i * P + i] = std::sqrt(v);
+            } else {
+                L[(size_t)i * P + j] = v / L[(size_t)j * P + j];
+            }
+        }
+    std::vector<double> z((size_t)P);
+    for (int i = 0; i < P; ++i) {
+        double v = g[i];
+        for (int k = 0; k < i; ++k) v -= L[(size_t)i * P + k] * z[k];
+        z[i] = v / L[(size_t)i * P + i];
+    }
+    delta.assign((size_t)P, 0.0);
+    for (int i = P - 1; i >= 0; --i) {
+        double v = z[i];
+        for (int k = i + 1; k < P; ++k) v -= L[(size_t)k * P + i] * delta[k];
+        delta[i] = v / L[(size_t)i * P + i];
+        if (!std::isfinite(delta[i])) return false;
+    }
+    return true;
+}
+
+asp_status asp_fit_2004(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, double omega_min, asp_gauss* out,
+                        asp_fit_info* info) {
+    CHECK_CTX();
+    if (!init || !out || n < 1 || n_old < 0 || n_old > n || !(omega_min >= 0.0)) return ASP_ERR_INVALID_ARG;
+    if (n > FIT2004_KMAX) return ASP_ERR_UNSUPPORTED;
+    for (int k = 0; k < n; ++k)
+        if (!gauss_ok(init[k])) return ASP_ERR_INVALID_ARG;
+    asp_status s = f2004_setup(ctx, n);
+    if (s != ASP_OK) return s;
+    Fit2004Buffers* fb = ctx->f2004;
+    const int H = ctx->H, W = ctx->W, P = 4 * n;
+    // target: the residual with the last n_old members added back through B
+    if (n_old > 0) {
+        std::vector<double> th_old((size_t)4 * n_old);
+        for (int k = 0; k < n_old; ++k) {
+            const asp_gauss& q = init[n - n_old + k];
+            th_old[4 * k] = q.amp; th_old[4 * k + 1] = q.x; th_old[4 * k + 2] = q.y; th_old[4 * k + 3] = q.width;
+        }
+        CK(cudaMemcpyAsync(fb->theta, th_old.data(), sizeof(double) * 4 * n_old, cudaMemcpyHostToDevice, ctx->stream));
+        CK(eval_2004(*fb, fb->theta, n_old, 1, H, W, ctx->R, true, ctx->stream));
+    } else {
+        CK(cudaMemcpyAsync(fb->T, ctx->R, sizeof(float) * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    const LMConst lm = ctx->dp.lm;
+    std::vector<double> theta((size_t)P), A((size_t)P * P), g((size_t)P), delta, trial((size_t)P);
+    for (int k = 0; k < n; ++k) {
+        theta[4 * k] = init[k].amp; theta[4 * k + 1] = init[k].x; theta[4 * k + 2] = init[k].y;
+        theta[4 * k + 3] = init[k].width;
+    }
+    double chi2 = 0.0;
+    s = f2004_eval(ctx, theta.data(), n, true, A.data(), g.data(), &chi2);
+    if (s != ASP_OK) return s;
+    const double chi2_init = chi2, omega_max = (double)std::max(H, W);
+    int passes = 1, iters = 0, status = ASP_LM_CAP;
+    double lam = lm.lambda0;
+    while (true) {
+        if (iters >= lm.max_iter) { status = ASP_LM_CAP; break; }
+        const bool ok = f2004_solve(A, g, lam, P, delta);
+        ++iters;
+        if (!ok) {
+            lam *= lm.lambda_up;
+            if (lam > lm.lambda_max) { status = ASP_LM_STALLED; break; }
+            continue;
+        }
+        // predicted decrease d.g + lam d.D.d of the damped step (Marquardt)
+        double pred = 0.0;
+        for (int i = 0; i < P; ++i) {
+            const double d = A[(size_t)i * P + i] > 0 ? A[(size_t)i * P + i] : 1.0;
+            pred += delta[i] * g[i] + lam * d * delta[i] * delta[i];
+        }
+        if (pred <= lm.rtol * chi2) { status = ASP_LM_CONVERGED; break; }
+        bool valid = true;
+        for (int i = 0; i < P; ++i) {
+            trial[i] = theta[i] + delta[i];
+            valid = valid && std::isfinite(trial[i]);
+        }
+        for (int k = 0; k < n && valid; ++k) {
+            const double x = trial[4 * k + 1], y = trial[4 * k + 2], w = trial[4 * k + 3];
+            valid = w > omega_min && !(w > omega_max) && x >= 0 && x <= W - 1 && y >= 0 && y <= H - 1;
+        }
+        if (!valid) {
+            lam *= lm.lambda_up;
+            if (lam > lm.lambda_max) { status = ASP_LM_STALLED; break; }
+            continue;
+        }
+        double chi2_t = 0.0;
+        s = f2004_eval(ctx, trial.data(), n, false, nullptr, nullptr, &chi2_t);
+        if (s != ASP_OK) return s;
+        ++passes;
+        if (chi2_t < chi2) {
+            const double rel = chi2 > 0 ? (chi2 - chi2_t) / chi2 : 0.0;
+            bool small = true;
+            for (int i = 0; i < P; ++i) {
+                double sc = (i & 3) == 0 ? std::fabs(theta[i]) : theta[(i & ~3) + 3];
+                if (sc == 0.0) sc = 1.0;
+                small = small && std::fabs(delta[i]) < lm.xtol * sc;
+            }
+            theta = trial;
+            s = f2004_eval(ctx, theta.data(), n, true, A.data(), g.data(), &chi2);
+            if (s != ASP_OK) return s;
+            lam = std::max(lam / lm.lambda_down, lm.lambda_min);
+            if (rel < lm.rtol || small) { status = ASP_LM_CONVERGED; break; }
+        } else {
+            lam *= lm.lambda_up;
+            if (lam > lm.lambda_max) { status = ASP_LM_STALLED; break; }
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        out[k].amp = theta[4 * k]; out[k].x = theta[4 * k + 1]; out[k].y = theta[4 * k + 2];
+        out[k].width = theta[4 * k + 3];
+    }
+    if (info) {
+        info->iters = iters;
+        info->passes = passes;
+        info->status = status;
+        info->k = n;
+        info->x0 = 0; info->x1 = W - 1; info->y0 = 0; info->y1 = H - 1;
+        info->chi2_init = chi2_init;
+        info->chi2_final = chi2;
+        info->lambda = lam;
+        info->pixel_evals = (int64_t)passes * ctx->N;
+    }
+    return ASP_OK;
 }
 
 asp_status asp_eval_normal_equations(asp_ctx* ctx, const asp_gauss* theta, int n, int n_old, int x0, int x1, int y0,
@@ -1133,6 +1347,7 @@ asp_status asp_reset(asp_ctx* ctx, const float* dirty, int dirty_on_host, const 
         CK(cudaMemcpyAsync(ctx->D, ctx->R, ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
         if (psf) CK(compute_psf_transform(ctx->B, ctx->H, ctx->W, ctx->fft_in, ctx->bhat, ctx->r2c, ctx->stream));
     }
+    if (psf && ctx->f2004) CK(psf_transform_2004(*ctx->f2004, ctx->B, ctx->H, ctx->W, ctx->stream));
     { Mark m(ctx, KC_BEGIN); CK(launch_reset_state(ctx->st, ctx->stream)); }
     return refresh_peak(ctx);
 }

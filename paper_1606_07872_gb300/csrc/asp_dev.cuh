@@ -30,6 +30,12 @@ constexpr unsigned SPIN_LIMIT = 1u << 22;          // bounded grid-barrier wait 
 
 constexpr double LOG2E = 1.4426950408889634074;
 
+// Asp-Clean2004's objective (asp_fit_2004): members per fit and the packed
+// upper triangle of [J | r]^T [J | r] at that size.
+constexpr int FIT2004_KMAX = 8;
+constexpr int FIT2004_NA = 4 * FIT2004_KMAX + 1;
+constexpr int FIT2004_NACC = FIT2004_NA * (FIT2004_NA + 1) / 2;
+
 // ---------------------------------------------------------------- structs
 struct LMConst {
     double lambda0, lambda_up, lambda_down, lambda_min, lambda_max, rtol, xtol;

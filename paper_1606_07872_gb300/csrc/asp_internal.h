@@ -83,6 +83,24 @@ cudaError_t launch_major(const asp_component* comps, float2* norms, CycleState* 
 cudaError_t compute_psf_transform(const float* B, int H, int W, float* pad_in, cufftComplex* bhat, cufftHandle r2c,
                                   cudaStream_t s);
 
+// asp_2004.cu (Asp-Clean2004's objective)
+struct Fit2004Buffers {
+    float* imgs = nullptr;          // FIT2004_NA zero-padded 2H x 2W images
+    float* conv = nullptr;          // their PSF convolutions (same layout)
+    cufftComplex* work = nullptr;   // FIT2004_NA transforms of 2H x (W + 1)
+    cufftComplex* bhat = nullptr;   // the PSF's transform
+    float* T = nullptr;             // target image H x W
+    float2* partials = nullptr;     // ne_blocks x FIT2004_NACC pairs
+    double* sums = nullptr;         // FIT2004_NACC
+    double* theta = nullptr;        // 4 FIT2004_KMAX
+    cufftHandle r2c1 = 0, c2r1 = 0, r2cN = 0, c2rN = 0;
+    int nb = 0;                     // batch of the N plans (4K + 1)
+    int grid = 0, ne_blocks = 0;
+};
+cudaError_t eval_2004(const Fit2004Buffers& fb, const double* theta_dev, int K, int n_img, int H, int W,
+                      const float* R, bool target_only, cudaStream_t s);
+cudaError_t psf_transform_2004(const Fit2004Buffers& fb, const float* B, int H, int W, cudaStream_t s);
+
 // asp_cycle.cu
 cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, double smooth_flops, cudaStream_t s);
 cudaError_t launch_select(CycleState* st, const asp_component* comps, const Params& p, int H, int W, int g_max,

@@ -546,3 +546,51 @@ def test_major_every_iteration_reproduces_the_exact_cycle():
     fb = np.array([[k.flux, k.x, k.y, k.width] for k in b.comps])
     np.testing.assert_allclose(fa, fb, rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(a.R, b.R, rtol=0, atol=1e-10)
+
+
+# ----------------------------------------------------------------- Asp-Clean2004 objective (Eq. 3)
+
+@pytest.mark.parametrize("H,W", [(9, 11), (16, 13)])
+def test_psf_convolve_is_the_direct_convolution(H, W):
+    rng = np.random.default_rng(H * W)
+    B = rng.normal(size=(2 * H, 2 * W))
+    img = rng.normal(size=(H, W))
+    np.testing.assert_allclose(O.psf_convolve(B, img), -O.subtract_definition(np.zeros((H, W)), B, img),
+                               rtol=0, atol=1e-12)
+
+
+def test_2004_jacobian_against_central_differences():
+    H, W = 20, 22
+    B = synth.small_case(H, W, seed=2).psf.astype(np.float64)
+    theta = np.array([0.8, 9.3, 10.6, 2.1, -0.4, 12.2, 8.8, 1.4])
+    _, J = O.model_jac_2004(B, theta, H, W)
+    for j in range(theta.size):
+        h = 1e-6 * max(1.0, abs(theta[j]))
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (O.model_jac_2004(B, tp, H, W)[0] - O.model_jac_2004(B, tm, H, W)[0]) / (2 * h)
+        assert np.max(np.abs(fd - J[:, j])) <= 1e-6 * max(np.max(np.abs(J[:, j])), 1e-12), j
+
+
+def test_eq3_optimum_maps_to_eq6_optimum_through_eqs7_8():
+    """Sect. 3's premise, made exact by a Gaussian PSF: fitting the
+    unconvolved component through B (Eq. 3) and fitting the convolved
+    Gaussian directly (Eq. 6) reach the same optimum, related by Eq. 7
+    (omega_ic^2 = omega_i^2 + omega_b^2) and Eq. 8 (alpha_ic = 2 pi alpha_i
+    alpha_b omega_i^2 omega_b^2 / omega_ic^2), with equal centres."""
+    H, W = 40, 44
+    ab, wb = 0.9, 1.8
+    B = synth.gaussian_psf(H, W, wb, ab)
+    truth = np.array([0.7, 21.3, 19.6, 2.6])
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    D = O.psf_convolve(B, O.gauss_model(truth, xs, ys)) + np.random.default_rng(1).normal(0, 1e-4, (H, W))
+    f3 = O.lm_fit_2004(D, B, truth * [1.1, 1, 1, 0.9] + [0, 0.2, -0.2, 0], 0.3, O.lm_exact())
+    f6 = O.lm_fit(D.ravel(), xs.ravel(), ys.ravel(), [1.0, 21.0, 20.0, 3.0], (0, W - 1, 0, H - 1), 0.3,
+                  O.lm_exact())
+    a, x, y, w = f3.theta
+    a_ic, x_ic, y_ic, w_ic = f6.theta
+    assert w_ic ** 2 == pytest.approx(w * w + wb * wb, rel=1e-9)
+    assert a_ic == pytest.approx(2 * math.pi * a * ab * w * w * wb * wb / w_ic ** 2, rel=1e-9)
+    assert x == pytest.approx(x_ic, abs=1e-9) and y == pytest.approx(y_ic, abs=1e-9)
+    assert f3.chi2 == pytest.approx(f6.chi2, rel=1e-9)

@@ -179,3 +179,25 @@ def test_beam_image_with_widths_added_linearly_is_caught(monkeypatch):
     _patch(monkeypatch, "beam_image_box", bad)
     with pytest.raises(AssertionError):
         pins.test_beam_image_is_full_psf_subtraction_through_a_gaussian_psf(1.3, 20.4, 18.7, 2.5)
+
+
+def test_2004_jacobian_without_the_psf_is_caught(monkeypatch):
+    def bad(B, theta, H, W):
+        ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+        m, J = OA.model_and_jacobian(theta, xs.ravel(), ys.ravel())
+        return OA.psf_convolve(B, m.reshape(H, W)).ravel(), J      # columns not convolved
+
+    _patch(monkeypatch, "model_jac_2004", bad)
+    with pytest.raises(AssertionError):
+        pins.test_2004_jacobian_against_central_differences()
+
+
+def test_psf_convolve_with_flipped_psf_is_caught(monkeypatch):
+    orig = OA.psf_convolve
+
+    def bad(B, img):
+        return orig(np.asarray(B)[::-1, ::-1], img)
+
+    _patch(monkeypatch, "psf_convolve", bad)
+    with pytest.raises(AssertionError):
+        pins.test_psf_convolve_is_the_direct_convolution(9, 11)
