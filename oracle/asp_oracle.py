@@ -854,16 +854,16 @@ class MinorCycle:
         return rec
 
     def _learned_fit(self, T, xs, ys, theta0, win, init):
-        """Learned initial values (reading of the fallback rule): the plain
-        method fixed p*, the members and the window; the network proposes the
-        new member's start from the 32 x 32 patch at p* (BF16 operands as on
-        the GPU).  A proposal that is not finite, has a zero amplitude, or
-        lies outside the window or the width bounds is not used.  Otherwise
-        LM runs from it; if that fit ends non-finite or at the width bound,
-        or ends above chi^2 at the plain start (a fit from the plain start
-        could only end lower), LM runs again from the plain start and the
-        lower chi^2 is kept.  Hitting the LM cap alone is no reason: plain
-        fits of joint active sets hit it as often."""
+        """Learned initial values (reading of the fallback rule: the plain
+        start stays as fallback whenever LM from the learned start converges
+        to a worse chi^2 than LM from the plain start): the plain method
+        fixed p*, the members and the window; the network proposes the new
+        member's start from the 32 x 32 patch at p* (BF16 operands as on the
+        GPU).  A proposal that is not finite, has a zero amplitude, or lies
+        outside the window or the width bounds is not used (the plain fit
+        alone).  Otherwise LM runs from both starts and the learned start's
+        result is kept when it is finite, above the width bound and its
+        chi^2 is not above the plain start's fit's."""
         from . import mlp_oracle as Mo
         omega_min = 0.25 * self.omega_b
         px, py = int(init["x0"]), int(init["y0"])
@@ -875,23 +875,20 @@ class MinorCycle:
         omega_max = max(x1b - x0b + 1, y1b - y0b + 1)
         ok = (np.all(np.isfinite(prop)) and prop[0] != 0 and prop[3] > omega_min and not prop[3] > omega_max
               and x0b <= prop[1] <= x1b and y0b <= prop[2] <= y1b)
-        info = dict(used=bool(ok), refit=False, kept=False, proposal=prop)
+        info = dict(used=bool(ok), refit=False, kept=False, proposal=prop, chi2_learned=None, chi2_plain=None)
         if not ok:
             return lm_fit(T, xs, ys, theta0, win, omega_min, self.p.lm), info
-        chi2_plain = float(np.sum((T - gauss_model(theta0, xs, ys)) ** 2))
         th_l = theta0.copy()
         th_l[0:4] = prop
         fit_l = lm_fit(T, xs, ys, th_l, win, omega_min, self.p.lm)
-        bad = not np.isfinite(fit_l.chi2) or not fit_l.theta[3] > omega_min or fit_l.chi2 > chi2_plain
-        if not bad:
+        fit_p = lm_fit(T, xs, ys, theta0, win, omega_min, self.p.lm)
+        info["chi2_learned"], info["chi2_plain"] = fit_l.chi2, fit_p.chi2
+        good = np.isfinite(fit_l.chi2) and fit_l.theta[3] > omega_min and fit_l.chi2 <= fit_p.chi2
+        if good:
             info["kept"] = True
             return fit_l, info
         info["refit"] = True
-        fit_p = lm_fit(T, xs, ys, theta0, win, omega_min, self.p.lm)
-        if fit_p.chi2 < fit_l.chi2 or not np.isfinite(fit_l.chi2):
-            return fit_p, info
-        info["kept"] = True
-        return fit_l, info
+        return fit_p, info
 
     def major(self):
         """The major cycle of the minor/major split: the exact residual

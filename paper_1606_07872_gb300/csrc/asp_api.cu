@@ -88,6 +88,11 @@ struct asp_ctx {
     float* harvest_p = nullptr;
     float* harvest_t = nullptr;
     int harvest_cap = 0;
+    // the plain start's fit beside the learned one (learned initial values)
+    double* partials2 = nullptr;
+    double* sums2 = nullptr;
+    unsigned* bar2 = nullptr;
+    float* Tg2 = nullptr;
     // minor/major split (asp_params.major_every > 0): the dirty image, the
     // PSF's transform, FFT buffers and plans, per-component normalisations
     float* D = nullptr;
@@ -274,31 +279,25 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
                          ctx->ticket, s)); }
     { Mark m(ctx, KC_SELECT); CK(launch_select(st, ctx->comps, ctx->dp, H, W, ctx->g_max, s)); }
     if (ctx->learned) {
-        // chi^2 at the plain start (one pass), then the network's proposal
-        LMConst lm0 = ctx->dp.lm;
-        lm0.max_iter = 0;
+        // the network's proposal, then the fits from the learned and the
+        // plain start side by side in one launch, and the lower chi^2 kept
         { Mark m(ctx, KC_LEARNED); CK(launch_learned_prep(st, ctx->R, H, W, ctx->Xinf, s)); }
-        { Mark m(ctx, KC_FIT);
-          CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit2, lm0, &st->fout2, ctx->partials, ctx->sums,
-                           ctx->bar, ctx->Tg, s)); }
         {
             Mark m(ctx, KC_MLP);
             ctx->launches += mlp_infer_kernels() - 1;
             CK(launch_mlp_infer(ctx->Xinf, ctx->W1b, ctx->W2b, ctx->mlpP, ctx->Z1, ctx->H1b, ctx->Z2, ctx->H2, ctx->Yinf,
                                 ctx->mlp_err, s));
         }
-        { Mark m(ctx, KC_LEARNED); CK(launch_learned_apply(st, ctx->Yinf, s)); }
-    }
-    { Mark m(ctx, KC_FIT);
-      CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit, ctx->dp.lm, &st->fout, ctx->partials, ctx->sums,
-                       ctx->bar, ctx->Tg, s)); }
-    if (ctx->learned) {
-        // fallback: refit from the plain start when the learned fit is worse
-        { Mark m(ctx, KC_LEARNED); CK(launch_learned_check(st, s)); }
+        { Mark m(ctx, KC_LEARNED); CK(launch_learned_apply(st, ctx->Yinf, ctx->g_max, s)); }
         { Mark m(ctx, KC_FIT);
-          CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit2, ctx->dp.lm, &st->fout2, ctx->partials, ctx->sums,
-                           ctx->bar, ctx->Tg, s)); }
+          CK(launch_lm_fit_pair(ctx->tpt, ctx->g_max, ctx->R, W, ctx->dp.lm, &st->fit, &st->fout, ctx->partials,
+                                ctx->sums, ctx->bar, ctx->Tg, &st->fit2, &st->fout2, ctx->partials2, ctx->sums2,
+                                ctx->bar2, ctx->Tg2, s)); }
         { Mark m(ctx, KC_LEARNED); CK(launch_learned_pick(st, s)); }
+    } else {
+        Mark m(ctx, KC_FIT);
+        CK(launch_lm_fit(ctx->tpt, ctx->g_max, ctx->R, W, &st->fit, ctx->dp.lm, &st->fout, ctx->partials, ctx->sums,
+                         ctx->bar, ctx->Tg, s));
     }
     { Mark m(ctx, KC_UPDATE); CK(launch_update(st, ctx->comps, ctx->hist, ctx->dp, H, W, s)); }
     if (ctx->harvest_p) {
@@ -1404,6 +1403,11 @@ asp_status asp_set_mlp(asp_ctx* ctx, const float* params_host, int enable) {
             AL(ctx->H2, 128 * 256);
             AL(ctx->Yinf, 128 * 4);
             AL(ctx->mlp_err, 1);
+            // the plain start's fit runs beside the learned one
+            AL(ctx->partials2, (size_t)ctx->g_max * NACC_MAX);
+            AL(ctx->sums2, SUMS_DOUBLES);
+            AL(ctx->bar2, 1);
+            AL(ctx->Tg2, 4 * ctx->N);
 #undef AL
             ctx->mlpP = P;
             ctx->W1b = w1;
@@ -1412,7 +1416,7 @@ asp_status asp_set_mlp(asp_ctx* ctx, const float* params_host, int enable) {
             ctx->H1b = h1;
             CK(cudaMemsetAsync(ctx->Xinf, 0, 128 * 1024 * sizeof(uint16_t), ctx->stream));
             CK(cudaMemsetAsync(ctx->mlp_err, 0, sizeof(unsigned), ctx->stream));
-            // the fallback's fit descriptor starts inactive
+            // the plain start's fit descriptor starts inactive
             CK(cudaMemsetAsync(&ctx->st->fit2, 0, sizeof(FitDesc), ctx->stream));
         }
         CK(cudaMemcpyAsync(ctx->mlpP, params_host, mlp_num_params() * sizeof(float), cudaMemcpyHostToDevice,
@@ -1577,16 +1581,14 @@ asp_status batch_enqueue_iteration(asp_batch* b, cudaStream_t s) {
     BK(launch_fit_map_b(b->d_desc, n, b->g_total, b->dmap, s));
     if (b->learned) {
         BK(launch_learned_b(b->d_desc, n, 0, s));
-        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s, 1, 0));   // chi^2 at the plain start
         BK(launch_mlp_infer(b->Xinf, b->W1b, b->W2b, b->mlpP, b->Z1, b->H1b, b->Z2, b->H2, b->Yinf, b->mlp_err, s,
                             b->mlp_rows));
         BK(launch_learned_b(b->d_desc, n, 1, s));
     }
     BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s));
     if (b->learned) {
+        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s, 1, -1));  // the plain start's fit
         BK(launch_learned_b(b->d_desc, n, 2, s));
-        BK(launch_lm_fit_batched(b->tpt, b->d_desc, b->dmap, n, b->g_total, b->bars, s, 1, -1));  // fallback refit
-        BK(launch_learned_b(b->d_desc, n, 3, s));
     }
     BK(launch_update_b(b->d_desc, n, s));
     BK(launch_build_weights_b(b->d_desc, n, s));

@@ -592,9 +592,9 @@ __device__ void account_fit(CycleState* st, const FitOut& fo, int K) {
 }
 }  // namespace
 
-// After k_select: keep the plain start, arm fit2 as the chi^2-only
-// evaluation at it, and write the input patch (divided by |R(p*)|, BF16) to
-// Xrow.  One block.
+// After k_select: keep the plain start (fit2 is the plain method's fit,
+// armed once the proposal is known), and write the input patch (divided by
+// |R(p*)|, BF16) to Xrow.  One block.
 __device__ __forceinline__ void learned_prep_body(CycleState* st, const float* __restrict__ R, int H, int W,
                                                   __nv_bfloat16* __restrict__ Xrow) {
     const bool live = !st->stopped && st->fit.active;
@@ -619,7 +619,7 @@ __device__ __forceinline__ void learned_prep_body(CycleState* st, const float* _
         st->learned_rp = rp;
         st->learned_px = px;
         st->learned_py = py;
-        st->fit2.active = 1;
+        st->fit2.active = 0;
         st->learned_used = 0;
         st->need_plain = 0;
     }
@@ -628,64 +628,50 @@ __global__ void k_learned_prep(CycleState* st, const float* __restrict__ R, int 
     learned_prep_body(st, R, H, W, Xrow);
 }
 
-// After the chi^2-only fit and the network: the learned start of the new
-// member (y = the network's 4 outputs), kept plain when it is not finite,
-// outside the window or not above the width bound.
-__device__ __forceinline__ void learned_apply_body(CycleState* st, const float* __restrict__ y) {
+// After the network: the learned start of the new member (y = the network's
+// 4 outputs), used when it is finite, inside the window and the width
+// bounds.  Then both fits run -- fit from the learned start, fit2 from the
+// plain one -- and the lower chi^2 is kept (k_learned_pick).  g_pair > 0
+// (a context, both fits in one launch): each fit's group is capped at half
+// of the g_pair co-resident CTAs.
+__device__ __forceinline__ void learned_apply_body(CycleState* st, const float* __restrict__ y, int g_pair) {
     if (threadIdx.x != 0) return;
-    if (!st->fit2.active) return;
-    st->fit2.active = 0;
-    account_fit(st, st->fout2, st->fit.K);          // the chi^2 evaluation pass
     FitDesc& f = st->fit;
+    if (st->stopped || !f.active) return;
     const double a0 = (double)y[0] * st->learned_rp;
     const double w0 = st->omega_b * exp((double)y[1]);
     const double x0 = st->learned_px + (double)y[2];
     const double y0 = st->learned_py + (double)y[3];
     const bool ok = isfinite(a0) && isfinite(w0) && isfinite(x0) && isfinite(y0) && a0 != 0.0 && w0 > f.omega_min &&
                     !(w0 > f.omega_max) && !(x0 < f.bx0) && !(x0 > f.bx1) && !(y0 < f.by0) && !(y0 > f.by1);
-    if (ok) {
-        f.theta0[0] = a0; f.theta0[1] = x0; f.theta0[2] = y0; f.theta0[3] = w0;
-        st->learned_used = 1;
-        st->learned_fits += 1;
+    if (!ok) return;                                   // the plain fit alone
+    f.theta0[0] = a0; f.theta0[1] = x0; f.theta0[2] = y0; f.theta0[3] = w0;
+    st->learned_used = 1;
+    st->learned_fits += 1;
+    FitDesc& f2 = st->fit2;
+    f2.active = 1;
+    st->need_plain = 1;
+    if (g_pair > 0) {
+        const long long Wn = (long long)f.ww * f.wh;
+        const int ga = g_pair / 2, gb = g_pair - ga;
+        if (f.grid > ga) { f.grid = ga; f.smem_ok = fit_smem_ok(Wn, ga); }
+        if (f2.grid > gb) { f2.grid = gb; f2.smem_ok = fit_smem_ok(Wn, gb); }
     }
 }
-__global__ void k_learned_apply(CycleState* st, const float* __restrict__ y) { learned_apply_body(st, y); }
-
-// After the fit from the learned start: the fallback rule.
-__device__ __forceinline__ void learned_check_body(CycleState* st) {
-    const bool go = st->fit.active && st->learned_used;
-    __syncthreads();
-    if (!go) {
-        if (threadIdx.x == 0) { st->fit2.active = 0; st->need_plain = 0; }
-        return;
-    }
-    const FitOut& fo = st->fout;
-    // a learned fit is redone from the plain start when it ended non-finite,
-    // at the width bound, or above chi^2 at the plain start (hitting the LM
-    // cap alone is no reason: plain joint fits hit it as often)
-    const bool bad = !isfinite(fo.chi2) || !(fo.theta[3] > st->fit.omega_min) || fo.chi2 > st->fout2.chi2_init;
-    if (!bad) {
-        if (threadIdx.x == 0) { st->learned_kept += 1; st->fit2.active = 0; st->need_plain = 0; }
-        return;
-    }
-    copy_words(&st->fit2, &st->fit, (int)sizeof(FitDesc));
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) st->fit2.theta0[i] = st->plain_theta[i];
-        st->fit2.active = 1;
-        st->need_plain = 1;
-        st->learned_refits += 1;
-    }
+__global__ void k_learned_apply(CycleState* st, const float* __restrict__ y, int g_pair) {
+    learned_apply_body(st, y, g_pair);
 }
-__global__ void k_learned_check(CycleState* st) { learned_check_body(st); }
 
-// After the refit: keep the better chi^2; the other fit's work is counted
-// here (the kept one is counted by k_update).
+// After both fits: the learned start's result is kept when it is finite,
+// above the width bound and its chi^2 is not above the plain start's fit's;
+// otherwise the plain fit is (the fallback).  The other fit's work is
+// counted here (the kept one by k_update).
 __device__ __forceinline__ void learned_pick_body(CycleState* st) {
     const bool go = st->need_plain != 0;
     __syncthreads();
     if (!go) return;
-    const bool plain_better = st->fout2.chi2 < st->fout.chi2 || !isfinite(st->fout.chi2);
+    const FitOut& fl = st->fout;
+    const bool plain_better = !isfinite(fl.chi2) || !(fl.theta[3] > st->fit.omega_min) || !(fl.chi2 <= st->fout2.chi2);
     __syncthreads();
     if (threadIdx.x == 0) account_fit(st, plain_better ? st->fout : st->fout2, st->fit.K);
     __syncthreads();
@@ -694,6 +680,7 @@ __device__ __forceinline__ void learned_pick_body(CycleState* st) {
     if (threadIdx.x == 0) {
         if (plain_better) {
             for (int i = 0; i < 4; ++i) st->fit.theta0[i] = st->plain_theta[i];
+            st->learned_refits += 1;
         } else {
             st->learned_kept += 1;
         }
@@ -740,9 +727,10 @@ __global__ void k_harvest(const CycleState* __restrict__ st, const float* __rest
 // 2 check, 3 pick.
 __global__ void k_learned_b(const ImgDesc* __restrict__ imgs, int step) {
     const ImgDesc& g = imgs[blockIdx.y];
+    // step 0: patch; 1: the learned start (both fits run as two launches,
+    // so no group caps); 2: keep the better fit
     if (step == 0) learned_prep_body(g.st, g.R, g.H, g.W, reinterpret_cast<__nv_bfloat16*>(g.Xrow));
-    else if (step == 1) learned_apply_body(g.st, g.Yrow);
-    else if (step == 2) learned_check_body(g.st);
+    else if (step == 1) learned_apply_body(g.st, g.Yrow, 0);
     else learned_pick_body(g.st);
 }
 cudaError_t launch_learned_b(const ImgDesc* imgs, int n, int step, cudaStream_t s) {
@@ -754,12 +742,8 @@ cudaError_t launch_learned_prep(CycleState* st, const float* R, int H, int W, vo
     k_learned_prep<<<1, 256, 0, s>>>(st, R, H, W, reinterpret_cast<__nv_bfloat16*>(Xrow));
     return cudaGetLastError();
 }
-cudaError_t launch_learned_apply(CycleState* st, const float* y, cudaStream_t s) {
-    k_learned_apply<<<1, 32, 0, s>>>(st, y);
-    return cudaGetLastError();
-}
-cudaError_t launch_learned_check(CycleState* st, cudaStream_t s) {
-    k_learned_check<<<1, 256, 0, s>>>(st);
+cudaError_t launch_learned_apply(CycleState* st, const float* y, int g_pair, cudaStream_t s) {
+    k_learned_apply<<<1, 32, 0, s>>>(st, y, g_pair);
     return cudaGetLastError();
 }
 cudaError_t launch_learned_pick(CycleState* st, cudaStream_t s) {

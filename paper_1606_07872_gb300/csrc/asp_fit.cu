@@ -1397,6 +1397,24 @@ k_lm_fit(const float* __restrict__ src, int src_w, const FitDesc* __restrict__ d
     lm_fit_body<TPT, LARGE>(src, src_w, descp, lmc, out, partials, sums, bar, Tg, blockIdx.x);
 }
 
+// Two fits of one image side by side in one cooperative launch: CTAs
+// [0, GA) run fit A (the learned start), [GA, GA + GB) fit B (the plain
+// start), each with its own partials, sums, barrier counter and target
+// buffer; G = 0 for an inactive fit.
+template <int TPT, bool LARGE>
+__global__ void __launch_bounds__(FIT_THREADS, 1)
+k_lm_fit_pair(const float* __restrict__ src, int src_w, const __grid_constant__ LMConst lmc,
+              const FitDesc* __restrict__ dA, FitOut* __restrict__ oA, double* __restrict__ pA, double* __restrict__ sA,
+              unsigned* __restrict__ bA, float* __restrict__ tA, const FitDesc* __restrict__ dB,
+              FitOut* __restrict__ oB, double* __restrict__ pB, double* __restrict__ sB, unsigned* __restrict__ bB,
+              float* __restrict__ tB) {
+    const int GA = dA->active ? dA->grid : 0;
+    const int GB = dB->active ? dB->grid : 0;
+    const int c = (int)blockIdx.x;
+    if (c < GA) lm_fit_body<TPT, LARGE>(src, src_w, dA, lmc, oA, pA, sA, bA, tA, c);
+    else if (c - GA < GB) lm_fit_body<TPT, LARGE>(src, src_w, dB, lmc, oB, pB, sB, bB, tB, c - GA);
+}
+
 // Batched: the fits of many images in one cooperative launch of g_total
 // CTAs.  Image i owns CTAs [dmap[i], dmap[i+1]) (written on the device each
 // iteration by k_fit_map_b); each group runs its own fit with its own
@@ -1443,11 +1461,18 @@ int fit_tpt_for(int k_max) {
     return k_max <= KMAX_S ? 3 : 4;
 }
 
+static const void* fit_kernel_pair_ptr(int variant) {
+    return variant == 1 ? (const void*)k_lm_fit_pair<1, false>
+                        : variant == 3 ? (const void*)k_lm_fit_pair<3, false> : (const void*)k_lm_fit_pair<3, true>;
+}
+
 cudaError_t fit_configure(int variant, int* blocks_per_sm) {
     const int smem = (int)fit_smem_bytes(variant);
     cudaError_t e = cudaFuncSetAttribute(fit_kernel_ptr(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fit_kernel_b_ptr(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fit_kernel_pair_ptr(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fit_kernel_ptr(variant), FIT_THREADS, smem);
 }
@@ -1469,6 +1494,33 @@ cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap,
     if (tpt == 1) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<1, false>, imgs, dmap, n, which, max_iter_override);
     if (tpt == 3) return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3, false>, imgs, dmap, n, which, max_iter_override);
     return cudaLaunchKernelEx(&cfg, k_lm_fit_b<3, true>, imgs, dmap, n, which, max_iter_override);
+}
+
+cudaError_t launch_lm_fit_pair(int tpt, int grid, const float* src, int src_w, const LMConst& lmc, const FitDesc* dA,
+                               FitOut* oA, double* pA, double* sA, unsigned* bA, float* tA, const FitDesc* dB,
+                               FitOut* oB, double* pB, double* sB, unsigned* bB, float* tB, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bA, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(bB, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(FIT_THREADS);
+    cfg.dynamicSmemBytes = fit_smem_bytes(tpt);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (tpt == 1)
+        return cudaLaunchKernelEx(&cfg, k_lm_fit_pair<1, false>, src, src_w, lmc, dA, oA, pA, sA, bA, tA, dB, oB, pB,
+                                  sB, bB, tB);
+    if (tpt == 3)
+        return cudaLaunchKernelEx(&cfg, k_lm_fit_pair<3, false>, src, src_w, lmc, dA, oA, pA, sA, bA, tA, dB, oB, pB,
+                                  sB, bB, tB);
+    return cudaLaunchKernelEx(&cfg, k_lm_fit_pair<3, true>, src, src_w, lmc, dA, oA, pA, sA, bA, tA, dB, oB, pB, sB,
+                              bB, tB);
 }
 
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,

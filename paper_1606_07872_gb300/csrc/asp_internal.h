@@ -60,6 +60,9 @@ int fit_tpt_for(int k_max);
 cudaError_t fit_configure(int tpt, int* blocks_per_sm);
 cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap, int n, int g_total, unsigned* bars,
                                   cudaStream_t s, int which = 0, int max_iter_override = -1);
+cudaError_t launch_lm_fit_pair(int tpt, int grid, const float* src, int src_w, const LMConst& lmc, const FitDesc* dA,
+                               FitOut* oA, double* pA, double* sA, unsigned* bA, float* tA, const FitDesc* dB,
+                               FitOut* oB, double* pB, double* sB, unsigned* bB, float* tB, cudaStream_t s);
 cudaError_t launch_lm_fit(int tpt, int grid, const float* src, int src_w, const FitDesc* desc, const LMConst& lmc,
                           FitOut* out, double* partials, double* sums, unsigned* bar, float* Tg, cudaStream_t s);
 
@@ -132,8 +135,7 @@ int mlp_infer_kernels();
 cudaError_t mlp_prepare(const float* P, void* W1b, void* W2b, cudaStream_t s);
 long long mlp_num_params();
 cudaError_t launch_learned_prep(CycleState* st, const float* R, int H, int W, void* Xrow, cudaStream_t s);
-cudaError_t launch_learned_apply(CycleState* st, const float* y, cudaStream_t s);
-cudaError_t launch_learned_check(CycleState* st, cudaStream_t s);
+cudaError_t launch_learned_apply(CycleState* st, const float* y, int g_pair, cudaStream_t s);
 cudaError_t launch_learned_pick(CycleState* st, cudaStream_t s);
 cudaError_t launch_harvest(const CycleState* st, const float* R, int H, int W, float* patches, float* targets,
                            int capacity, cudaStream_t s);
