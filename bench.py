@@ -47,11 +47,17 @@ def _args():
     ap.add_argument("--config", type=int, choices=[2, 3], default=2,
                     help="workload of the main line: 2 (1024^2, k_max 20) or 3 (4096^2, k_max 50)")
     ap.add_argument("--no-config3", action="store_true", help="skip the 4096^2 measurement beside config 2")
-    ap.add_argument("--config3-iters", type=int, default=0, help="iterations per config-3 step (0: its 5000)")
-    ap.add_argument("--config3-steps", type=int, default=2)
-    ap.add_argument("--config3-warmup", type=int, default=3)
+    ap.add_argument("--config3-iters", type=int, default=300,
+                    help="iterations per 4096^2 step beside config 2 (its first 300 of 5000; 0: all 5000)")
+    ap.add_argument("--config3-steps", type=int, default=1)
+    ap.add_argument("--config3-warmup", type=int, default=1)
+    ap.add_argument("--split-config3", action="store_true", help="also measure the split on the 4096^2 workload")
     ap.add_argument("--fit-px", type=int, default=0, help="LM fit tile: window pixels per CTA (0: library default)")
     ap.add_argument("--no-split", action="store_true", help="skip the minor/major split comparison")
+    ap.add_argument("--sub", choices=["auto", "direct", "fft"], default="auto",
+                    help="residual update form of the measured runs (auto: FFT from 512x512 pixels)")
+    ap.add_argument("--no-sub-forms", action="store_true",
+                    help="skip the comparison with the direct residual update")
     ap.add_argument("--no-2004", action="store_true", help="skip the Eq. 3 vs Eq. 6 per-iteration comparison")
     ap.add_argument("--split-every", type=int, default=50, help="minor iterations per major cycle in the split")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -458,7 +464,8 @@ def learned_comparison(asp, n_train_images: int, seed: int = 0):
 
 # ---------------------------------------------------------------- our arm
 
-def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_px=0, major_every=0) -> dict:
+def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_px=0, major_every=0,
+                     sub_mode=0) -> dict:
     """Device-timed steps (inputs resident in HBM), end-to-end steps through
     the C-ABI with host buffers, and one profiled step (CUDA events around
     every launch) of one workload on this rank."""
@@ -468,7 +475,8 @@ def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_
     psf = torch.from_numpy(case.psf).cuda()
     stream = torch.cuda.Stream()
     params = asp.default_params(k_max=case.k_max, noise_sigma=case.noise_sigma, gain=case.gain,
-                                lm_max_iter=case.lm_max_iter, fit_px_per_cta=fit_px, major_every=major_every)
+                                lm_max_iter=case.lm_max_iter, fit_px_per_cta=fit_px, major_every=major_every,
+                                sub_mode=sub_mode)
     with torch.cuda.stream(stream):
         ctx = asp.Context(dirty, psf, params=params, stream=stream)
     L = asp.lib()
@@ -544,9 +552,9 @@ def measure_workload(asp, case, n_iter, steps, warmup, local, world, flush, fit_
     # ---- per-kernel times (events around every launch, direct launches)
     L.asp_set_profiling(ctx.h, 1)
     step_device()
-    kt = (asp._lib.asp_kernel_time * 16)()
+    kt = (asp._lib.asp_kernel_time * 32)()
     nk = C.c_int()
-    L.asp_get_kernel_times(ctx.h, kt, 16, C.byref(nk))
+    L.asp_get_kernel_times(ctx.h, kt, 32, C.byref(nk))
     prof_stats = asp.asp_get_stats(ctx.h)
     L.asp_set_profiling(ctx.h, 0)
     ctx.close()
@@ -577,14 +585,27 @@ def rooflines(m: dict, peaks: dict, alu: dict) -> dict:
                                 "note": "pixel-pass phase clocks of the fit kernel's first CTA"},
             "ex2": {"achieved_gops": st["fit_ex2"] / s / 1e9, "peak_gops": ex2, "frac": st["fit_ex2"] / s / 1e9 / ex2},
             "avg_launch_ms": k["k_lm_fit"]["total_ms"] / max(k["k_lm_fit"]["launches"], 1)}
-    if "k_sub_h" in k and "k_sub_v_argmax" in k:
+    if k.get("k_sub_h", {}).get("launches") and k.get("k_sub_v_argmax", {}).get("launches"):
         s = (k["k_sub_h"]["total_ms"] + k["k_sub_v_argmax"]["total_ms"]) / 1e3
         out["k_sub_h+k_sub_v_argmax"] = {
             "bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": st["sub_bytes"] / s / 1e9,
             "frac": st["sub_bytes"] / s / 1e9 / hbm, "fp32_tflops": st["sub_flops"] / s / 1e12,
             "fp32_frac": st["sub_flops"] / s / 1e12 / fma,
             "bytes_note": "PSF regions read once + residual read and written once per iteration"}
-    if "k_smooth_h" in k and "k_smooth_v_argmax" in k:
+    if k.get("subtraction (FFT)", {}).get("launches"):
+        # one update: the forward transform's input (4N floats) and output
+        # (2H (W+1) complex ~ 4N floats) once, the product's three complex
+        # streams, the inverse transform's input and output once, R read and
+        # written and the convolution's image quarter read: 124 N bytes
+        kk = k["subtraction (FFT)"]
+        s = kk["total_ms"] / 1e3
+        by = 124.0 * m["N"] * kk["launches"]
+        out["subtraction (FFT)"] = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": by / s / 1e9,
+                                    "frac": by / s / 1e9 / hbm, "us_per_update": kk["total_ms"] * 1e3 / kk["launches"],
+                                    "bytes_note": "124 N bytes per update: each transform's input and output once, "
+                                                  "the product's three streams, R read and written, the "
+                                                  "convolution's image quarter read (cuFFT kernels included)"}
+    if k.get("k_smooth_h", {}).get("launches") and k.get("k_smooth_v_argmax", {}).get("launches"):
         s = (k["k_smooth_h"]["total_ms"] + k["k_smooth_v_argmax"]["total_ms"]) / 1e3
         by = 4.0 * m["N"] * st["smooth_iters"]
         out["k_smooth_h+k_smooth_v_argmax"] = {
@@ -682,6 +703,22 @@ def asp2004_comparison(asp) -> dict:
     return out
 
 
+SUB_MODES = {"auto": 0, "direct": 1, "fft": 2}
+
+
+def sub_form_summary(m: dict, line: dict) -> dict:
+    """The same workload with the direct residual update (separable passes)
+    beside the measured line's form: rate, final RMS, the update's time."""
+    t = m["t_ms"]
+    k = m["kernels"]
+    upd = lambda kk: sum(kk.get(n, {}).get("total_ms", 0.0) for n in ("k_sub_h", "k_sub_v_argmax", "subtraction (FFT)"))
+    return {"value": m["iters"] / (t / 1e3), "unit": UNIT,
+            "speedup_of_measured_form": line["value"] / (m["iters"] / (t / 1e3)),
+            "rms_ratio_measured_over_direct": line["outcome"]["final_residual_rms"] / m["outcome"]["final_residual_rms"],
+            "update_ms_per_step": {"direct": upd(k), "measured": upd(line.get("kernels", {}))},
+            "outcome": m["outcome"]}
+
+
 def split_summary(m: dict, exact_line: dict) -> dict:
     """The minor/major split against the exact-subtraction run of the same
     workload: rate, the final (exact) residual RMS and the kernel times."""
@@ -690,6 +727,13 @@ def split_summary(m: dict, exact_line: dict) -> dict:
             "speedup_vs_exact": (m["iters"] / (t / 1e3)) / exact_line["value"],
             "rms_ratio_vs_exact": m["outcome"]["final_residual_rms"] / exact_line["outcome"]["final_residual_rms"],
             "kernels": m["kernels"], "clocks": m["clocks"]}
+
+
+def _sub_form(asp, case, sub: int) -> str:
+    """The residual update form a context of this size takes."""
+    if sub == SUB_MODES["auto"]:
+        return "fft" if case.H * case.W >= asp.ASP_SUB_FFT_MIN_PIXELS else "direct"
+    return "fft" if sub == SUB_MODES["fft"] else "direct"
 
 
 def run_ours(a):
@@ -709,8 +753,10 @@ def run_ours(a):
     main_cfg = a.config
     case = _workload(main_cfg, a.size, rank)
     n_iter = a.iters or case.n_iter
-    m = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush, a.fit_px)
+    sub = SUB_MODES[a.sub]
+    m = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush, a.fit_px, 0, sub)
     line = workload_line(a, m, case, world, peaks, peak_kind, alu, f"config{main_cfg}")
+    line["config"]["residual_update"] = _sub_form(asp, case, sub)
     line["warmup"] = a.warmup
     line["alu_peaks"] = dict(alu, note="own microbenchmark on this device, this run: one full wave of "
                                        "independent FMA / ex2.approx chains, CUDA-event timed")
@@ -719,17 +765,29 @@ def run_ours(a):
         try:
             c3 = _workload(3, 4096, rank)
             m3 = measure_workload(asp, c3, a.config3_iters or c3.n_iter, a.config3_steps, a.config3_warmup,
-                                  local, world, flush)
+                                  local, world, flush, 0, 0, sub)
             line["config3"] = workload_line(a, m3, c3, world, peaks, peak_kind, alu, "config3")
             line["config3"]["warmup"] = a.config3_warmup
+            line["config3"]["config"]["residual_update"] = _sub_form(asp, c3, sub)
+            if not a.no_sub_forms and _sub_form(asp, c3, sub) == "fft":
+                md = measure_workload(asp, c3, a.config3_iters or c3.n_iter, 1, 1, local, world, flush, 0, 0,
+                                      SUB_MODES["direct"])
+                line["config3"]["direct_update"] = sub_form_summary(md, line["config3"])
             del c3
         except Exception as e:   # report, never hide, a failed measurement
             line["config3"] = {"error": repr(e)[:300]}
+    if not a.no_sub_forms and line["config"]["residual_update"] == "fft":
+        try:
+            md = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush, a.fit_px, 0,
+                                  SUB_MODES["direct"])
+            line["direct_update"] = sub_form_summary(md, line)
+        except Exception as e:   # report, never hide, a failed measurement
+            line["direct_update"] = {"error": repr(e)[:300]}
     if main_cfg == 2 and not a.no_split:
         try:
             ms = measure_workload(asp, case, n_iter, a.steps, a.warmup, local, world, flush, a.fit_px, a.split_every)
             line["split"] = {"major_every": a.split_every, "config2": split_summary(ms, line)}
-            if isinstance(line.get("config3"), dict) and "value" in line["config3"]:
+            if a.split_config3 and isinstance(line.get("config3"), dict) and "value" in line["config3"]:
                 c3 = _workload(3, 4096, rank)
                 m3 = measure_workload(asp, c3, a.config3_iters or c3.n_iter, a.config3_steps, a.config3_warmup,
                                       local, world, flush, 0, a.split_every)

@@ -52,6 +52,14 @@ typedef enum {
 typedef enum { ASP_INIT_AUTO = 0, ASP_INIT_SIMPLE = 1, ASP_INIT_SMOOTH = 2 } asp_init_mode;
 /* Peak-search modes for asp_find_peak. */
 typedef enum { ASP_PEAK_SIMPLE = 0, ASP_PEAK_SMOOTH = 1 } asp_peak_mode;
+/* Residual update form.  DIRECT: separable passes over the PSF rows and
+ * columns the terms need (cost ~ sum over terms of taps x image pixels).
+ * FFT: the iteration's change image dC convolved with B as one product on
+ * the zero-padded 2H x 2W grid (cuFFT, FP32; cost independent of the number
+ * and widths of the terms).  AUTO: FFT for images of at least
+ * ASP_SUB_FFT_MIN_PIXELS pixels, DIRECT below. */
+typedef enum { ASP_SUB_AUTO = 0, ASP_SUB_DIRECT = 1, ASP_SUB_FFT = 2 } asp_sub_mode;
+#define ASP_SUB_FFT_MIN_PIXELS 262144   /* 512 x 512 */
 /* Levenberg-Marquardt termination codes (asp_fit_info.status). */
 typedef enum { ASP_LM_CONVERGED = 0, ASP_LM_CAP = 1, ASP_LM_STALLED = 2 } asp_lm_status;
 /* Why a minor cycle stopped (asp_cycle_stats.stop_reason). */
@@ -128,6 +136,13 @@ typedef struct {
                                end of each asp_minor_cycle call, the residual
                                is recomputed exactly as D - B * M by an FFT
                                convolution.  Contexts only (not batches). */
+    int32_t sub_mode;       /* asp_sub_mode: how the per-iteration residual
+                               update R -= B * dC (Sect. 2 step 3, full PSF)
+                               is computed.  Both forms take the same terms
+                               with the same sampled axis weights and point
+                               deposits and differ only in rounding.  Unused
+                               with major_every > 0.  Batches always take the
+                               direct passes (FFT rejected). */
 } asp_params;
 
 /* Totals of asp_minor_cycle since asp_init (or the last asp_set_state). */

@@ -17,7 +17,8 @@ import numpy as np
 from . import _lib
 from ._lib import (  # noqa: F401
     ASP_INIT_AUTO, ASP_INIT_SIMPLE, ASP_INIT_SMOOTH, ASP_KMAX, ASP_LM_CAP, ASP_LM_CONVERGED, ASP_LM_STALLED,
-    ASP_PEAK_SIMPLE, ASP_PEAK_SMOOTH, ASP_STOP_CAPACITY, ASP_STOP_ITER, ASP_STOP_NOISE, ASP_STOP_NONE,
+    ASP_PEAK_SIMPLE, ASP_PEAK_SMOOTH, ASP_SUB_AUTO, ASP_SUB_DIRECT, ASP_SUB_FFT, ASP_SUB_FFT_MIN_PIXELS,
+    ASP_STOP_CAPACITY, ASP_STOP_ITER, ASP_STOP_NOISE, ASP_STOP_NONE,
     asp_component, asp_cycle_stats, asp_fit_info, asp_gauss, asp_iter_record, asp_params, asp_peak,
 )
 
@@ -463,6 +464,19 @@ class Context:
 
     def stats(self):
         return asp_get_stats(self.h)
+
+    def set_profiling(self, on: bool):
+        """CUDA events around every launch (direct launches, no graph)."""
+        _check(lib().asp_set_profiling(self.h, 1 if on else 0), "asp_set_profiling", self.h)
+
+    def kernel_times(self):
+        """Per kernel class since profiling was switched on: name, launches,
+        total milliseconds."""
+        kt = (_lib.asp_kernel_time * 32)()
+        nk = C.c_int()
+        _check(lib().asp_get_kernel_times(self.h, kt, 32, C.byref(nk)), "asp_get_kernel_times", self.h)
+        return [{"name": k.name.decode(), "launches": int(k.launches), "total_ms": float(k.total_ms)}
+                for k in kt[: nk.value]]
 
     def residual(self) -> np.ndarray:
         out = np.empty((self.H, self.W), dtype=np.float32)

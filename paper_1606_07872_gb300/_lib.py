@@ -19,6 +19,8 @@ STATUS_NAMES = {0: "ASP_OK", 1: "ASP_ERR_INVALID_ARG", 2: "ASP_ERR_CUDA", 3: "AS
                 9: "ASP_ERR_CAPACITY"}
 ASP_INIT_AUTO, ASP_INIT_SIMPLE, ASP_INIT_SMOOTH = 0, 1, 2
 ASP_PEAK_SIMPLE, ASP_PEAK_SMOOTH = 0, 1
+ASP_SUB_AUTO, ASP_SUB_DIRECT, ASP_SUB_FFT = 0, 1, 2
+ASP_SUB_FFT_MIN_PIXELS = 512 * 512
 ASP_LM_CONVERGED, ASP_LM_CAP, ASP_LM_STALLED = 0, 1, 2
 ASP_STOP_NONE, ASP_STOP_ITER, ASP_STOP_NOISE, ASP_STOP_CAPACITY = 0, 1, 2, 3
 
@@ -51,7 +53,8 @@ class asp_params(C.Structure):
                 ("noise_sigma", C.c_float), ("stop_ksigma", C.c_float), ("n_scales", C.c_int32),
                 ("area_frac", C.c_float), ("init_mode", C.c_int32), ("tau", C.c_double),
                 ("retained_cap", C.c_int32), ("max_components", C.c_int32),
-                ("fit_px_per_cta", C.c_int32), ("major_every", C.c_int32)]
+                ("fit_px_per_cta", C.c_int32), ("major_every", C.c_int32),
+                ("sub_mode", C.c_int32)]
 
 
 class asp_cycle_stats(C.Structure):

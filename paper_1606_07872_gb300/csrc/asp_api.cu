@@ -18,13 +18,14 @@ using namespace aspd;
 // Kernel classes timed by asp_set_profiling.
 enum KernelClass {
     KC_BEGIN, KC_SMOOTH_H, KC_SMOOTH_V, KC_SELECT, KC_FIT, KC_UPDATE, KC_WEIGHTS, KC_SUB_H, KC_SUB_V, KC_ARGMAX,
-    KC_MLP, KC_LEARNED, KC_HARVEST, KC_SUB_GAUSS, KC_MAJOR, KC_COUNT
+    KC_MLP, KC_LEARNED, KC_HARVEST, KC_SUB_GAUSS, KC_MAJOR, KC_SUB_FFT, KC_COUNT
 };
 static const char* const KC_NAMES[KC_COUNT] = {
     "k_cycle_begin", "k_smooth_h", "k_smooth_v_argmax", "k_select", "k_lm_fit", "k_update", "k_build_weights",
     "k_sub_h", "k_sub_v_argmax", "k_argmax_abs", "mlp_infer (tcgen05)", "k_learned_*", "k_harvest",
-    "k_sub_gauss", "major cycle (FFT)"};
-static const int MAJOR_KERNELS = 8;   // launches of one major cycle (5 kernels, 2 FFTs, argmax)
+    "k_sub_gauss", "major cycle (FFT)", "subtraction (FFT)"};
+static const int MAJOR_KERNELS = 6;     // own kernels of one major cycle (5 and the argmax; the 2 cuFFT calls not counted)
+static const int SUB_FFT_KERNELS = 3;   // own kernels of one FFT residual update (the 2 cuFFT calls not counted)
 static const int KERNELS_PER_ITER = 9;   // kernels one minor-cycle iteration enqueues
 
 struct ProfMark {
@@ -103,6 +104,7 @@ struct asp_ctx {
     float2* norms = nullptr;
     cufftHandle r2c = 0, c2r = 0;
     bool plans = false;
+    bool sub_fft = false;   // per-iteration residual update by FFT (asp_params.sub_mode)
     Fit2004Buffers* f2004 = nullptr;   // Asp-Clean2004's objective, allocated by its first call
     int broken = 0;
     std::string err;
@@ -194,6 +196,7 @@ asp_status validate_params(const asp_params* p) {
     if (p->lm_max_iter < 0 || p->n_scales < 1 || p->n_scales > MAX_SCALES) return ASP_ERR_INVALID_ARG;
     if (!(p->lm_lambda0 > 0) || !(p->lm_rtol >= 0) || !(p->lm_xtol >= 0)) return ASP_ERR_INVALID_ARG;
     if (p->fit_px_per_cta < 0 || p->major_every < 0) return ASP_ERR_INVALID_ARG;
+    if (p->sub_mode < ASP_SUB_AUTO || p->sub_mode > ASP_SUB_FFT) return ASP_ERR_INVALID_ARG;
     if (p->init_mode < 0 || p->init_mode > 2) return ASP_ERR_INVALID_ARG;
     if (p->retained_cap < 0 || p->retained_cap > RET_MAX) return ASP_ERR_UNSUPPORTED;
     if (p->max_components < 0) return ASP_ERR_INVALID_ARG;
@@ -314,6 +317,13 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
         return ASP_OK;
     }
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(st, &st->stopped, ctx->wbuf, s)); }
+    if (ctx->sub_fft) {
+        Mark m(ctx, KC_SUB_FFT);
+        ctx->launches += SUB_FFT_KERNELS - 1;
+        CK(launch_sub_fft(st, &st->stopped, ctx->wbuf, H, W, ctx->fft_in, ctx->fft_work, ctx->bhat, ctx->fft_out, ctx->R,
+                          ctx->r2c, ctx->c2r, ctx->grid_img, ctx->part, ctx->ticket, s));
+        return ASP_OK;
+    }
     { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->taps, s)); }
     { Mark m(ctx, KC_SUB_V);
       CK(launch_sub_v(ctx->R, ctx->B, H, W, st, &st->stopped, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part, ctx->ticket,
@@ -546,6 +556,8 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     ctx->dp.lm = lmconst_from(ctx->p);
 
     const long long N = ctx->N;
+    ctx->sub_fft = ctx->p.major_every == 0 &&
+                   (ctx->p.sub_mode == ASP_SUB_FFT || (ctx->p.sub_mode == ASP_SUB_AUTO && N >= ASP_SUB_FFT_MIN_PIXELS));
     ctx->terms_cap = std::max(2 * ctx->p.k_max - 1, 1);
     const int cap = ctx->p.max_components;
 #define AL(ptr, n) if (dalloc(ctx, &(ptr), (size_t)(n)) != cudaSuccess) return bail(ASP_ERR_OOM)
@@ -556,8 +568,11 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     AL(ctx->comp_stage, MAX_TERMS);
     AL(ctx->hist, cap);
     AL(ctx->wbuf, (size_t)MAX_TERMS * wslot_stride(W, H));
-    AL(ctx->T1, ((size_t)ctx->terms_cap * (2 * H - 1) + T1_SLACK_ROWS) * W);   // slack rows: see k_sub_v_argmax
-    if (cudaMemset(ctx->T1, 0, ((size_t)ctx->terms_cap * (2 * H - 1) + T1_SLACK_ROWS) * W * sizeof(float)) != cudaSuccess)
+    // the direct update's row-pass buffer (the FFT update needs none; slack
+    // rows: see k_sub_v_argmax)
+    const size_t t1_rows = (ctx->sub_fft ? 0 : (size_t)ctx->terms_cap * (2 * H - 1)) + T1_SLACK_ROWS;
+    AL(ctx->T1, t1_rows * W);
+    if (cudaMemset(ctx->T1, 0, t1_rows * W * sizeof(float)) != cudaSuccess)
         return bail(ASP_ERR_CUDA);
     AL(ctx->partials, (size_t)ctx->g_max * NACC_MAX);
     AL(ctx->sums, SUMS_DOUBLES);
@@ -575,13 +590,17 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
         cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream) != cudaSuccess)
         return bail(ASP_ERR_CUDA);
 
-    if (ctx->p.major_every > 0) {
-        // the minor/major split's buffers, the FFT plans of the 2H x 2W
-        // grid and the PSF's transform
+    if (ctx->p.major_every > 0 || ctx->sub_fft) {
+        // the FFT buffers and plans of the 2H x 2W grid and the PSF's
+        // transform; the minor/major split adds the dirty image and the
+        // components' normalisations
         const size_t nc = (size_t)(2 * H) * (W + 1);
-        if (dalloc(ctx, &ctx->D, (size_t)N) != cudaSuccess || dalloc(ctx, &ctx->fft_in, (size_t)4 * N) != cudaSuccess ||
+        if (dalloc(ctx, &ctx->fft_in, (size_t)4 * N) != cudaSuccess ||
             dalloc(ctx, &ctx->fft_out, (size_t)4 * N) != cudaSuccess || dalloc(ctx, &ctx->fft_work, nc) != cudaSuccess ||
-            dalloc(ctx, &ctx->bhat, nc) != cudaSuccess || dalloc(ctx, &ctx->norms, (size_t)cap) != cudaSuccess)
+            dalloc(ctx, &ctx->bhat, nc) != cudaSuccess)
+            return bail(ASP_ERR_OOM);
+        if (ctx->p.major_every > 0 &&
+            (dalloc(ctx, &ctx->D, (size_t)N) != cudaSuccess || dalloc(ctx, &ctx->norms, (size_t)cap) != cudaSuccess))
             return bail(ASP_ERR_OOM);
         if (cufftPlan2d(&ctx->r2c, 2 * H, 2 * W, CUFFT_R2C) != CUFFT_SUCCESS) return bail(ASP_ERR_CUDA);
         if (cufftPlan2d(&ctx->c2r, 2 * H, 2 * W, CUFFT_C2R) != CUFFT_SUCCESS) {
@@ -589,10 +608,11 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
             return bail(ASP_ERR_CUDA);
         }
         ctx->plans = true;
-        if (cudaMemcpyAsync(ctx->D, ctx->R, N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+        if ((ctx->D && cudaMemcpyAsync(ctx->D, ctx->R, N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream) !=
+                           cudaSuccess) ||
             compute_psf_transform(ctx->B, H, W, ctx->fft_in, ctx->bhat, ctx->r2c, ctx->stream) != cudaSuccess)
             return bail(ASP_ERR_CUDA);
-        ctx->graph_unroll = ctx->p.major_every;
+        if (ctx->p.major_every > 0) ctx->graph_unroll = ctx->p.major_every;
     }
     s = fit_beam(ctx);
     if (s != ASP_OK) return bail(s);
@@ -1082,11 +1102,18 @@ asp_status asp_subtract(asp_ctx* ctx, const asp_component* comps, int n, float g
     CK(cudaMemcpyAsync(ctx->comp_stage, comps, n * sizeof(asp_component), cudaMemcpyHostToDevice, ctx->stream));
     { Mark m(ctx, KC_UPDATE); CK(launch_terms_from_components(ctx->st, ctx->comp_stage, n, gain, ctx->H, ctx->W, ctx->stream)); }
     { Mark m(ctx, KC_WEIGHTS); CK(launch_build_weights(ctx->st, nullptr, ctx->wbuf, ctx->stream)); }
+    if (ctx->sub_fft) {
+        Mark m(ctx, KC_SUB_FFT);
+        ctx->launches += SUB_FFT_KERNELS - 1;
+        CK(launch_sub_fft(ctx->st, nullptr, ctx->wbuf, ctx->H, ctx->W, ctx->fft_in, ctx->fft_work, ctx->bhat,
+                          ctx->fft_out, ctx->R, ctx->r2c, ctx->c2r, ctx->grid_img, ctx->part, ctx->ticket, ctx->stream));
+    } else {
     { Mark m(ctx, KC_SUB_H); CK(launch_sub_h(ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->taps, ctx->stream)); }
     {
         Mark m(ctx, KC_SUB_V);
         CK(launch_sub_v(ctx->R, ctx->B, ctx->H, ctx->W, ctx->st, nullptr, ctx->wbuf, ctx->T1, ctx->grid_img, ctx->part,
                         ctx->ticket, ctx->stream));
+    }
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return ASP_OK;
@@ -1342,10 +1369,9 @@ asp_status asp_reset(asp_ctx* ctx, const float* dirty, int dirty_on_host, const 
     }
     CK(cudaMemcpyAsync(ctx->R, dirty, ctx->N * sizeof(float),
                        dirty_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream));
-    if (ctx->p.major_every > 0) {
+    if (ctx->p.major_every > 0)
         CK(cudaMemcpyAsync(ctx->D, ctx->R, ctx->N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
-        if (psf) CK(compute_psf_transform(ctx->B, ctx->H, ctx->W, ctx->fft_in, ctx->bhat, ctx->r2c, ctx->stream));
-    }
+    if (psf && ctx->plans) CK(compute_psf_transform(ctx->B, ctx->H, ctx->W, ctx->fft_in, ctx->bhat, ctx->r2c, ctx->stream));
     if (psf && ctx->f2004) CK(psf_transform_2004(*ctx->f2004, ctx->B, ctx->H, ctx->W, ctx->stream));
     { Mark m(ctx, KC_BEGIN); CK(launch_reset_state(ctx->st, ctx->stream)); }
     return refresh_peak(ctx);
@@ -1681,6 +1707,7 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
     *out = nullptr;
     if (!params || n < 1 || n > MAX_BATCH || !H || !W || !dirty || !psf) return ASP_ERR_INVALID_ARG;
     if (params->major_every != 0) return ASP_ERR_UNSUPPORTED;   // the minor/major split is per context
+    if (params->sub_mode == ASP_SUB_FFT) return ASP_ERR_UNSUPPORTED;   // batch iterations subtract directly
     for (int i = 0; i < n; ++i)
         if (H[i] < 1 || W[i] < 1 || !dirty[i] || !psf[i]) return ASP_ERR_INVALID_ARG;
     asp_batch* b = new asp_batch();
@@ -1690,10 +1717,12 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, b->dev) != cudaSuccess) return bail(ASP_ERR_CUDA);
     b->num_sms = prop.multiProcessorCount;
+    asp_params ip = *params;
+    ip.sub_mode = ASP_SUB_DIRECT;   // the images' contexts hold no FFT buffers
     for (int i = 0; i < n; ++i) {
         asp_ctx* c = nullptr;
-        asp_status s = on_host ? asp_init_host(params, H[i], W[i], dirty[i], psf[i], stream, &c)
-                               : asp_init(params, H[i], W[i], dirty[i], psf[i], stream, &c);
+        asp_status s = on_host ? asp_init_host(&ip, H[i], W[i], dirty[i], psf[i], stream, &c)
+                               : asp_init(&ip, H[i], W[i], dirty[i], psf[i], stream, &c);
         if (s != ASP_OK) return bail(s);
         b->imgs.push_back(c);
         float* d = nullptr;

@@ -145,6 +145,10 @@ struct CycleState {
     // whether the current major cycle is skipped, major cycles applied
     int since_major, major_skip;
     long long major_cycles;
+    // FFT residual update: the change image's box of the last update (the
+    // next one clears it) and of the current one (x0, x1, y0, y1; empty
+    // when x0 > x1)
+    int dbox[4], dbox_next[4];
 };
 
 struct Params {                    // device copy of asp_params plus derived values

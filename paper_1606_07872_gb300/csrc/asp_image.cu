@@ -311,6 +311,59 @@ k_sub_v_argmax(float* __restrict__ R, int H, int W, CycleState* st, const int* g
                const float* __restrict__ wbuf, const float* __restrict__ T1, const float* __restrict__ B,
                ArgRes* part, unsigned* ticket) { sub_v_body(R, H, W, st, gate, wbuf, T1, B, part, ticket); }
 
+// FFT residual update, last step: R -= conv(p + (H, W)) / (4 H W) (the
+// inverse transform of dC's product with the PSF's transform, unnormalised;
+// the PSF's zero lag at [H, W] puts image pixel p at p + (H, W) of the
+// 2H x 2W grid) with the next argmax fused in, as k_sub_v_argmax does.  The
+// block that finishes the argmax records dC's box for the next update.
+__global__ void __launch_bounds__(RED_THREADS)
+k_fft_sub_argmax(float* __restrict__ R, const float* __restrict__ conv, int H, int W, CycleState* st, const int* gate,
+                 ArgRes* part, unsigned* ticket) {
+    if (gate && *gate) return;
+    const float sc = 1.0f / (4.0f * (float)H * (float)W);
+    const long long N = (long long)H * W;
+    const long long W2 = 2LL * W;
+    float bv = 0.f;
+    long long bi = 0x7fffffffffffffffLL;
+    int bj = 0;
+    unsigned bad = 0;
+    if ((W & 3) == 0) {
+        // 4 consecutive pixels of one row per thread: both rows are 16-byte aligned
+        const long long nq = N >> 2;
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+            const long long p = q << 2;
+            const long long y = p / W, x = p - y * W;
+            const float4 c = __ldg(reinterpret_cast<const float4*>(conv + (y + H) * W2 + x + W));
+            float4 r = reinterpret_cast<const float4*>(R)[q];
+            r.x -= c.x * sc; r.y -= c.y * sc; r.z -= c.z * sc; r.w -= c.w * sc;
+            reinterpret_cast<float4*>(R)[q] = r;
+            const float v[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!isfinite(v[k])) bad = 1;
+                if (arg_better(v[k], 0, p + k, bv, 0, bi)) { bv = v[k]; bi = p + k; }
+            }
+        }
+    } else {
+        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+            const long long y = p / W, x = p - y * W;
+            const float v = R[p] - __ldg(conv + (y + H) * W2 + x + W) * sc;
+            R[p] = v;
+            if (!isfinite(v)) bad = 1;
+            if (arg_better(v, 0, p, bv, 0, bi)) { bv = v; bi = p; }
+        }
+    }
+    if (bad) atomicOr(&st->nonfinite, 1u);
+    block_arg_reduce(bv, bj, bi);
+    if (grid_arg_finish(bv, bj, bi, part, ticket, &st->peak) && threadIdx.x < 4) st->dbox[threadIdx.x] = st->dbox_next[threadIdx.x];
+}
+
+cudaError_t launch_fft_sub_argmax(float* R, const float* conv, int H, int W, CycleState* st, const int* gate, int grid,
+                                  ArgRes* part, unsigned* ticket, cudaStream_t s) {
+    k_fft_sub_argmax<<<grid, RED_THREADS, 0, s>>>(R, conv, H, W, st, gate, part, ticket);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ smoothing
 // Separable Gaussian smoothing at every scale s_j (Sect. 2 step 1), zero
 // padded at the image edges, as two register-blocked passes: each thread

@@ -80,6 +80,11 @@ cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& tap
 
 // asp_major.cu (minor/major split)
 cudaError_t launch_sub_gauss(float* R, int H, int W, CycleState* st, int grid, cudaStream_t s);
+cudaError_t launch_fft_sub_argmax(float* R, const float* conv, int H, int W, CycleState* st, const int* gate, int grid,
+                                  ArgRes* part, unsigned* ticket, cudaStream_t s);
+cudaError_t launch_sub_fft(CycleState* st, const int* gate, const float* wbuf, int H, int W, float* pad_in,
+                           cufftComplex* work, const cufftComplex* bhat, float* conv_out, float* R, cufftHandle r2c,
+                           cufftHandle c2r, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
 cudaError_t launch_major(const asp_component* comps, float2* norms, CycleState* st, int H, int W, float* pad_in,
                          cufftComplex* work, const cufftComplex* bhat, float* conv_out, float* R, const float* D,
                          cufftHandle r2c, cufftHandle c2r, int grid, cudaStream_t s);

@@ -251,6 +251,117 @@ __global__ void k_major_residual(float* __restrict__ R, const float* __restrict_
     }
 }
 
+// ------------------------------------------------------------------ FFT residual update
+// The per-iteration update of Sect. 2 step 3, R -= B * dC with the full PSF,
+// as one FFT convolution of the change image dC (sub_mode FFT) instead of
+// the direct separable passes: dC is the same sum of the same terms, each
+// extended term scale_t wx_t(x) wy_t(y) with the axis weights
+// k_build_weights samples, each point-like term its bilinear deposits, so
+// both forms compute one definition and differ only in rounding.
+//
+// k_delta_image writes dC into the image corner of the zero-padded 2H x 2W
+// FFT input.  dC is zero outside the terms' boxes, so only the 32 x 32
+// tiles meeting the union of this update's box and the previous update's
+// box are written (the previous terms' samples are overwritten, by zeros
+// where nothing of the new update lies).  Per tile the terms meeting it are
+// listed in index order (ballot compaction); each thread sums them for 4
+// pixels of one column, then adds the deposits in their order.
+__global__ void __launch_bounds__(256) k_delta_image(CycleState* st, const int* gate, const float* __restrict__ wbuf,
+                                                    int H, int W, float* __restrict__ pad) {
+    if (gate && *gate) return;
+    __shared__ int tq[MAX_TERMS][4];     // qx0, nx, qy0, ny (nx = ny = 0 for point-like terms)
+    __shared__ int tw[MAX_TERMS][2];     // woff_x, woff_y
+    __shared__ float ts[MAX_TERMS];      // scale
+    __shared__ Deposit sdep[MAX_DEPOSITS];
+    __shared__ int list[MAX_TERMS];
+    __shared__ int wcount[8];
+    __shared__ int ub[4], count;
+    const int nt = min(st->n_terms, MAX_TERMS), nd = min(st->n_dep, MAX_DEPOSITS);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = tid; t < nt; t += blockDim.x) {
+        const TermDesc& td = st->terms[t];
+        const bool ext = !td.bilinear;
+        tq[t][0] = td.qx0; tq[t][1] = ext ? td.nx : 0; tq[t][2] = td.qy0; tq[t][3] = ext ? td.ny : 0;
+        tw[t][0] = td.woff_x; tw[t][1] = td.woff_y;
+        ts[t] = td.scale;
+    }
+    for (int i = tid; i < nd; i += blockDim.x) sdep[i] = st->dep[i];
+    __syncthreads();
+    if (tid == 0) {
+        int x0 = W, x1 = -1, y0 = H, y1 = -1;
+        for (int t = 0; t < nt; ++t) {
+            if (tq[t][1] <= 0 || tq[t][3] <= 0) continue;
+            x0 = min(x0, tq[t][0]); x1 = max(x1, tq[t][0] + tq[t][1] - 1);
+            y0 = min(y0, tq[t][2]); y1 = max(y1, tq[t][2] + tq[t][3] - 1);
+        }
+        for (int d = 0; d < nd; ++d) {
+            x0 = min(x0, sdep[d].qx); x1 = max(x1, sdep[d].qx);
+            y0 = min(y0, sdep[d].qy); y1 = max(y1, sdep[d].qy);
+        }
+        if (blockIdx.x == 0) {
+            st->dbox_next[0] = x0; st->dbox_next[1] = x1; st->dbox_next[2] = y0; st->dbox_next[3] = y1;
+        }
+        const int p0 = st->dbox[0], p1 = st->dbox[1], q0 = st->dbox[2], q1 = st->dbox[3];
+        if (p0 <= p1 && q0 <= q1) {
+            x0 = min(x0, p0); x1 = max(x1, p1); y0 = min(y0, q0); y1 = max(y1, q1);
+        }
+        ub[0] = max(x0, 0); ub[1] = min(x1, W - 1); ub[2] = max(y0, 0); ub[3] = min(y1, H - 1);
+    }
+    __syncthreads();
+    if (ub[0] > ub[1] || ub[2] > ub[3]) return;
+    const int tx0 = ub[0] / MT, tx1 = ub[1] / MT, ty0 = ub[2] / MT, ty1 = ub[3] / MT;
+    const int ntx = tx1 - tx0 + 1, ntiles = ntx * (ty1 - ty0 + 1);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int px0 = (tx0 + tile % ntx) * MT, py0 = (ty0 + tile / ntx) * MT;
+        const int px1 = min(px0 + MT - 1, W - 1), py1 = min(py0 + MT - 1, H - 1);
+        // the terms meeting the tile, in index order (nt <= MAX_TERMS <= 4 warps)
+        bool hit = false;
+        if (tid < nt)
+            hit = tq[tid][1] > 0 && tq[tid][3] > 0 && tq[tid][0] <= px1 && tq[tid][0] + tq[tid][1] - 1 >= px0 &&
+                  tq[tid][2] <= py1 && tq[tid][2] + tq[tid][3] - 1 >= py0;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcount[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += wcount[w];
+        if (hit) list[off + __popc(bal & ((1u << lane) - 1u))] = tid;
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wcount[w];
+            count = tot;
+        }
+        __syncthreads();
+        const int x = px0 + lane;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (x <= px1) {
+            for (int k = 0; k < count; ++k) {
+                const int t = list[k];
+                const int qx0 = tq[t][0], nx = tq[t][1], qy0 = tq[t][2], ny = tq[t][3];
+                if (x < qx0 || x >= qx0 + nx) continue;
+                // weights are stored reversed: tap i (pixel q0 + i) at n - 1 - i
+                const float wx = ts[t] * __ldg(wbuf + tw[t][0] + (nx - 1 - (x - qx0)));
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int y = py0 + warp * 4 + r;
+                    if (y >= qy0 && y < qy0 + ny) acc[r] = fmaf(wx, __ldg(wbuf + tw[t][1] + (ny - 1 - (y - qy0))), acc[r]);
+                }
+            }
+            for (int d = 0; d < nd; ++d) {
+                if (sdep[d].qx != x) continue;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (sdep[d].qy == py0 + warp * 4 + r) acc[r] += sdep[d].w;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int y = py0 + warp * 4 + r;
+                if (y <= py1) pad[(long long)y * (2 * W) + x] = acc[r];
+            }
+        }
+        __syncthreads();   // list and count are rebuilt for the next tile
+    }
+}
+
 cudaError_t launch_sub_gauss(float* R, int H, int W, CycleState* st, int grid, cudaStream_t s) {
     k_sub_gauss<<<grid, 256, 0, s>>>(R, H, W, st);
     return cudaGetLastError();
@@ -274,6 +385,24 @@ cudaError_t launch_major(const asp_component* comps, float2* norms, CycleState* 
     if (cufftExecC2R(c2r, work, conv_out) != CUFFT_SUCCESS) return cudaErrorUnknown;
     k_major_residual<<<grid, 256, 0, s>>>(R, D, conv_out, H, W, st);
     return cudaGetLastError();
+}
+
+// FFT residual update: dC into the padded input, forward transform, product
+// with the PSF's transform, inverse transform, then R -= conv / (4 H W)
+// with the next argmax (k_fft_sub_argmax, asp_image.cu).  The transforms
+// run whether or not the gate is set (a stopped cycle transforms a stale
+// dC and discards it).
+cudaError_t launch_sub_fft(CycleState* st, const int* gate, const float* wbuf, int H, int W, float* pad_in,
+                           cufftComplex* work, const cufftComplex* bhat, float* conv_out, float* R, cufftHandle r2c,
+                           cufftHandle c2r, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
+    k_delta_image<<<grid, 256, 0, s>>>(st, gate, wbuf, H, W, pad_in);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (cufftSetStream(r2c, s) != CUFFT_SUCCESS || cufftSetStream(c2r, s) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    if (cufftExecR2C(r2c, pad_in, work) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    k_fft_mul<<<grid, 256, 0, s>>>(work, bhat, (long long)(2 * H) * (W + 1));
+    if (cufftExecC2R(c2r, work, conv_out) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    return launch_fft_sub_argmax(R, conv_out, H, W, st, gate, grid, part, ticket, s);
 }
 
 // The PSF's transform: B (2H x 2W) through the forward plan into bhat, with

@@ -87,3 +87,22 @@ def test_rooflines_from_algorithmic_work():
     sm = r["k_smooth_h+k_smooth_v_argmax"]
     assert sm["achieved"] == pytest.approx(10.0) and sm["hbm_gbs"] == pytest.approx(4.0 * 1024 * 1024 * 100 / 8e-3 / 1e9)
     assert r["k_argmax_abs"]["achieved"] == pytest.approx(4.0 * 1024 * 1024 * 2 / 1e-5 / 1e9)
+
+
+def test_fft_update_roofline_and_absent_classes():
+    """The FFT residual update's rate is 124 N bytes per update over its
+    event time; classes that did not launch get no entry (no division by
+    zero)."""
+    import bench
+    m = {"N": 1024 * 1024,
+         "kernels": {"k_lm_fit": {"launches": 10, "total_ms": 100.0}, "k_sub_h": {"launches": 0, "total_ms": 0.0},
+                     "k_sub_v_argmax": {"launches": 0, "total_ms": 0.0},
+                     "subtraction (FFT)": {"launches": 10, "total_ms": 0.5}},
+         "prof": {"fit_flops": 4e12, "fit_pass_ms": 40.0, "fit_ex2": 1e11, "sub_bytes": 0.0, "sub_flops": 0.0,
+                  "smooth_flops": 0.0, "smooth_iters": 0}}
+    alu = {"fp32_fma_tflops": 76.0, "fp32_fma2_tflops": 80.0, "ex2_gops": 10000.0}
+    r = bench.rooflines(m, {"hbm_gbs": 6800.0}, alu)
+    assert "k_sub_h+k_sub_v_argmax" not in r and "k_smooth_h+k_smooth_v_argmax" not in r
+    f = r["subtraction (FFT)"]
+    assert f["achieved"] == pytest.approx(124.0 * 1024 * 1024 * 10 / 5e-4 / 1e9)
+    assert f["us_per_update"] == pytest.approx(50.0)

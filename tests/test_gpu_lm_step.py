@@ -154,13 +154,20 @@ def test_lm_steps_match_oracle_at_full_size(asp, capsys):
     ctx.minor_cycle(SCAN)
     capped = [h["t"] for h in ctx.history() if h["status"] == O.LM_CAP and h["t"] > FIRST[-1]]
     assert len(capped) >= N_CAPPED, len(capped)
-    picks = [capped[(i * (len(capped) - 1)) // (N_CAPPED - 1)] for i in range(N_CAPPED)]
+    # twice as many candidates as needed, spread over the scan: a fit that
+    # capped in the scan run can converge when fitted again (its start comes
+    # back through the host's FP64 state, and the trajectory is chaotic in
+    # the last bits), so candidates are examined until N_CAPPED capped
+    n_cand = min(len(capped), 2 * N_CAPPED)
+    picks = [capped[(i * (len(capped) - 1)) // (n_cand - 1)] for i in range(n_cand)]
     iterations = sorted(set(FIRST) | set(picks))
     ctx.close()
     ctx = asp.Context(_t(case.dirty), _t(case.psf), k_max=case.k_max, noise_sigma=case.noise_sigma,
                       gain=case.gain, lm_max_iter=case.lm_max_iter)
     t = 0
     for it in iterations:
+        if it not in FIRST and tally.capped_fits >= N_CAPPED:
+            break
         if it > t:
             ctx.minor_cycle(it - t)
             t = it

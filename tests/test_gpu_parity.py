@@ -93,27 +93,50 @@ def test_degenerate_one_pixel_image_is_an_error(asp):
 
 # ----------------------------------------------------------------- subtraction (a9)
 
+@pytest.mark.parametrize("sub_mode", ["direct", "fft"])
 @pytest.mark.parametrize("H,W,seed", [(48, 40, 0), (97, 131, 1), (256, 256, 2)])
-def test_subtraction_matches_oracle(asp, H, W, seed):
+def test_subtraction_matches_oracle(asp, H, W, seed, sub_mode):
+    """Both forms of the residual update (direct separable passes; one FFT
+    product of the change image) against the oracle's direct sums.  A
+    second update elsewhere checks that the FFT form's change image holds
+    only the current terms (the previous box is cleared)."""
     case = synth.small_case(H, W, seed=seed)
     rng = np.random.default_rng(seed)
-    ctx = _ctx(asp, case, k_max=8)
-    comps = []
-    for i in range(6):
-        w = [0.0, 0.3, 1.4, 4.7, 9.0, 0.8][i]
-        comps.append([rng.normal(), 0.0, rng.uniform(-3, W + 2), rng.uniform(-3, H + 2), w, int(w == 0.0)])
-    gain = 0.7
-    ctx.subtract(comps, gain)
-    R = ctx.residual().astype(np.float64)
-    terms = [O.component_terms(gain * c[0], c[2], c[3], c[4], bool(c[5]), H, W) for c in comps]
-    ref = O.subtract_terms(case.dirty, case.psf, [t for t in terms if t is not None])
-    d_gpu, d_ref = R - case.dirty, ref - case.dirty
-    assert _rel_l2(d_gpu, d_ref) < 1e-5
-    assert _rel_l2(R, ref) < 1e-5
-    pk = ctx.find_peak(asp.ASP_PEAK_SIMPLE)
-    idx, _ = O.peak_simple(ctx.residual())
-    assert pk["index"] == idx
+    mode = asp.ASP_SUB_FFT if sub_mode == "fft" else asp.ASP_SUB_DIRECT
+    ctx = _ctx(asp, case, k_max=8, sub_mode=mode)
+    R0 = case.dirty.astype(np.float64)
+    for rnd in range(2):
+        comps = []
+        for i in range(6):
+            w = [0.0, 0.3, 1.4, 4.7, 9.0, 0.8][(i + 3 * rnd) % 6]
+            comps.append([rng.normal(), 0.0, rng.uniform(-3, W + 2), rng.uniform(-3, H + 2), w, int(w == 0.0)])
+        gain = 0.7
+        ctx.subtract(comps, gain)
+        R = ctx.residual().astype(np.float64)
+        terms = [O.component_terms(gain * c[0], c[2], c[3], c[4], bool(c[5]), H, W) for c in comps]
+        ref = O.subtract_terms(R0, case.psf, [t for t in terms if t is not None])
+        d_gpu, d_ref = R - R0, ref - R0
+        assert _rel_l2(d_gpu, d_ref) < 1e-5, rnd
+        assert _rel_l2(R, ref) < 1e-5, rnd
+        pk = ctx.find_peak(asp.ASP_PEAK_SIMPLE)
+        idx, _ = O.peak_simple(ctx.residual())
+        assert pk["index"] == idx
+        R0 = R
     ctx.close()
+
+
+def test_fft_update_is_the_default_from_its_size(asp):
+    """sub_mode AUTO takes the FFT form from ASP_SUB_FFT_MIN_PIXELS pixels:
+    a run's launches show which form ran."""
+    for H, W, fft in ((256, 256, False), (512, 512, True)):
+        case = synth.small_case(H, W, seed=4)
+        ctx = _ctx(asp, case, k_max=3)
+        ctx.set_profiling(True)
+        ctx.minor_cycle(2)
+        prof = {k["name"]: k for k in ctx.kernel_times()}
+        assert (prof["subtraction (FFT)"]["launches"] > 0) == fft
+        assert (prof["k_sub_v_argmax"]["launches"] > 0) == (not fft)
+        ctx.close()
 
 
 def test_subtraction_gaussian_psf_closed_form(asp):
@@ -247,8 +270,8 @@ def _oracle_from_gpu_state(ctx, case, p, beam):
 TIGHT = dict(lm_max_iter=300, lm_rtol=1e-12, lm_xtol=1e-10)
 
 
-@pytest.mark.parametrize("k_max", [1, 3, 5])
-def test_teacher_forced_minor_cycle_steps(asp, k_max, capsys):
+@pytest.mark.parametrize("k_max,sub_mode", [(1, "direct"), (3, "direct"), (5, "direct"), (5, "fft")])
+def test_teacher_forced_minor_cycle_steps(asp, k_max, sub_mode, capsys):
     """Each iteration starts both sides from the GPU's state (tests/teacher.py):
     the discrete decisions agree exactly; the GPU's residual update is the
     oracle's subtraction of the GPU's fitted components within 1e-5
@@ -257,7 +280,8 @@ def test_teacher_forced_minor_cycle_steps(asp, k_max, capsys):
     FP32 floor |A^-1| dg where that is larger.  Both sides run LM to the
     optimum (tight tolerances; the GPU ends at its FP32 floor)."""
     case = synth.small_case(96, 104, seed=11, n_points=3, n_gauss=2, sigma_range=(2.5, 6))
-    ctx = _ctx(asp, case, k_max=k_max, **TIGHT)
+    mode = asp.ASP_SUB_FFT if sub_mode == "fft" else asp.ASP_SUB_DIRECT
+    ctx = _ctx(asp, case, k_max=k_max, sub_mode=mode, **TIGHT)
     ab, wb, _, _ = ctx.beam
     p = O.AspParams(k_max=k_max, noise_sigma=case.noise_sigma, lm=O.lm_exact())
     stats = teacher.Stats()
@@ -271,7 +295,7 @@ def test_teacher_forced_minor_cycle_steps(asp, k_max, capsys):
         teacher.check_iteration(ctx, case, rec, R_before, st, stats)
     assert stats.fits >= 3 and stats.updates >= 10
     with capsys.disabled():
-        print(f"\nk_max {k_max}: {stats.fits} converged fits, {stats.params_beyond_1e4}/{stats.params} parameters "
+        print(f"\nk_max {k_max} ({sub_mode} update): {stats.fits} converged fits, {stats.params_beyond_1e4}/{stats.params} parameters "
               f"beyond 1e-4 (within the FP32 floor), max |dtheta|/scale {stats.max_rel_param:.2e}; "
               f"residual updates max rel L2 {stats.max_rel_update:.2e}")
     ctx.close()
