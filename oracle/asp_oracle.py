@@ -217,7 +217,20 @@ def _valid(theta, box, omega_min):
     return True
 
 
-def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None, model_jac=None) -> FitResult:
+def _step_scale(theta):
+    """Per-parameter scale of the xtol test: |a| (1 where a = 0) for the
+    amplitude, omega for centre and width."""
+    scale = np.empty_like(theta)
+    scale[0::4] = np.abs(theta[0::4])
+    scale[0::4][scale[0::4] == 0] = 1.0
+    scale[1::4] = theta[3::4]
+    scale[2::4] = theta[3::4]
+    scale[3::4] = theta[3::4]
+    return scale
+
+
+def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None, model_jac=None, valid=None,
+           step_scale=None) -> FitResult:
     """Levenberg-Marquardt minimisation of the Eq. 6 objective.
 
     ``T`` are the target values at pixel coordinates ``(xs, ys)``; ``box =
@@ -237,7 +250,10 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None, mod
 
     ``model_jac(theta) -> (model, J)`` replaces the Eq. 6 model and Jacobian
     (e.g. the Eq. 3 objective of :func:`model_jac_2004`); xs and ys then
-    only size the data.
+    only size the data.  ``valid(theta) -> bool`` and ``step_scale(theta)
+    -> scales`` replace the trial-point test and the xtol scales of the
+    four-parameter members (the elliptical members of
+    ``oracle.elliptical``).
     """
     lm = lm or LMParams()
     T = np.asarray(T, dtype=np.float64).ravel()
@@ -279,7 +295,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None, mod
             status = LM_CONVERGED
             break
         trial = last_trial
-        if not _valid(trial, box, omega_min):
+        if not (_valid(trial, box, omega_min) if valid is None else valid(trial)):
             lam *= lm.lambda_up
             if lam > lm.lambda_max:
                 status = LM_STALLED
@@ -290,12 +306,7 @@ def lm_fit(T, xs, ys, theta0, box, omega_min, lm: Optional[LMParams] = None, mod
         last_pass_chi2 = chi2_t
         if chi2_t < chi2:
             rel = (chi2 - chi2_t) / chi2 if chi2 > 0 else 0.0
-            scale = np.empty_like(theta)
-            scale[0::4] = np.abs(theta[0::4])
-            scale[0::4][scale[0::4] == 0] = 1.0
-            scale[1::4] = theta[3::4]
-            scale[2::4] = theta[3::4]
-            scale[3::4] = theta[3::4]
+            scale = _step_scale(theta) if step_scale is None else step_scale(theta)
             small = float(np.max(np.abs(delta) / scale)) < lm.xtol
             theta, A, g, chi2 = trial, A2, g2, chi2_t
             lam = max(lam / lm.lambda_down, lm.lambda_min)
