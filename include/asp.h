@@ -82,6 +82,29 @@ typedef struct {
     int32_t reserved;
 } asp_component;
 
+/* Elliptical variant (the paper's circular Gaussians of Sect. 3 with a 2 x 2
+ * shape): a exp(-(A dx^2 + 2 B dx dy + C dy^2) / 2), (dx, dy) the offset
+ * from (x, y) and P = [[A, B], [B, C]] (pxx, pxy, pyy) the precision matrix,
+ * i.e. the inverse covariance.  For a circle of width w: A = C = 1 / w^2,
+ * B = 0. */
+typedef struct { double amp, x, y, pxx, pxy, pyy; } asp_gauss_ell;
+
+/* A deconvolved elliptical component: covariances add under convolution,
+ * so Sigma_i = Sigma_ic - Sigma_beam (Eq. 7's analogue), and flux is
+ * conserved (Eq. 8's analogue): flux F = a_ic sqrt(det Sigma_ic) / (alpha_b
+ * sqrt(det Sigma_b)), amp = F / (2 pi sqrt(det Sigma_i)); (sxx, sxy, syy)
+ * the covariance Sigma_i.  A point (Sigma_i = 0, amp = F) when the smaller
+ * eigenvalue of Sigma_ic - Sigma_b is at most 1e-3 times the smaller
+ * eigenvalue of Sigma_b (for a circular beam exactly the circular rule). */
+typedef struct {
+    double flux, amp, x, y, sxx, sxy, syy;
+    int32_t is_point;
+    int32_t reserved;
+} asp_component_ell;
+
+/* Largest elliptical active set (6 parameters a member). */
+#define ASP_ELL_KMAX 33
+
 /* Peak-search result.  SIMPLE: the largest |R| (lowest index on ties), init
  * (R(p*), x*, y*, omega_b).  SMOOTH: the largest |S_j| over scales and pixels
  * (ties: lower scale, then lower index); init (S/(sqrt(pi) s), x*, y*,
@@ -263,6 +286,33 @@ asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, con
  * kept until asp_destroy.  info->pixel_evals counts evaluations x H W. */
 asp_status asp_fit_2004(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, double omega_min, asp_gauss* out,
                         asp_fit_info* info);
+
+/* Elliptical beam: the circular beam's fit region (the pixels within
+ * ceil(3 omega_init) of the PSF's zero lag, omega_init its half-maximum
+ * width), Levenberg-Marquardt on the elliptical model started from the
+ * circular beam (A = C = 1 / omega_b^2, B = 0); trial principal widths in
+ * (0.25 omega_init, region extent].  out: (alpha_b, x_b, y_b, A_b, B_b,
+ * C_b) on the 2H x 2W PSF grid (zero lag at (W, H)).  ASP_ERR_NAN if the
+ * fit ends without a positive-definite shape.  The minor cycle keeps its
+ * circular beam. */
+asp_status asp_fit_beam_elliptical(asp_ctx* ctx, asp_gauss_ell* out);
+
+/* Eq. 6 with elliptical members: as asp_fit_active_set (same window rule,
+ * from the major width 1 / sqrt(mu_min(P)); same LM rules and launch), the
+ * last n_old members of init added back to the residual as the target,
+ * trial points positive definite with principal widths in (0.25 omega_b,
+ * window extent] and centres in the window.  1 <= n <= ASP_ELL_KMAX
+ * (ASP_ERR_UNSUPPORTED beyond); ASP_ERR_INVALID_ARG for a non-finite value
+ * or a shape that is not positive definite. */
+asp_status asp_fit_elliptical(asp_ctx* ctx, const asp_gauss_ell* init, int n, int n_old, asp_gauss_ell* out,
+                              asp_fit_info* info);
+
+/* Eqs. 7-8 for elliptical shapes (see asp_component_ell) on the device, for
+ * n fitted (PSF-convolved) Gaussians in against the beam (alpha_b, P_b) in
+ * beam (e.g. from asp_fit_beam_elliptical).  n <= ASP_ELL_KMAX;
+ * ASP_ERR_INVALID_ARG for a shape that is not positive definite. */
+asp_status asp_deconvolve_elliptical(asp_ctx* ctx, const asp_gauss_ell* in, int n, const asp_gauss_ell* beam,
+                                     asp_component_ell* out);
 
 /* R -= B * (gain * sum_i c_i) with the full PSF (Sect. 2 step 3); c_i is
  * component i sampled on the grid (a flux-normalised Gaussian on the box

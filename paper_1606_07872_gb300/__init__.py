@@ -20,11 +20,13 @@ from ._lib import (  # noqa: F401
     ASP_PEAK_SIMPLE, ASP_PEAK_SMOOTH, ASP_SUB_AUTO, ASP_SUB_DIRECT, ASP_SUB_FFT, ASP_SUB_FFT_MIN_PIXELS,
     ASP_STOP_CAPACITY, ASP_STOP_ITER, ASP_STOP_NOISE, ASP_STOP_NONE,
     asp_component, asp_cycle_stats, asp_fit_info, asp_gauss, asp_iter_record, asp_params, asp_peak,
+    asp_gauss_ell, asp_component_ell, ASP_ELL_KMAX,
 )
 
 __all__ = [
     "AspError", "lib", "default_params", "asp_init", "asp_init_host", "asp_destroy", "asp_get_beam",
-    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_fit_2004", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
+    "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_fit_2004", "asp_fit_elliptical",
+    "asp_fit_beam_elliptical", "asp_deconvolve_elliptical", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
@@ -189,6 +191,45 @@ def asp_fit_2004(h, init, n_old: int = 0, omega_min: float = 0.1):
     _check(lib().asp_fit_2004(h, arr, n, int(n_old), float(omega_min), out, C.byref(info)), "asp_fit_2004", h)
     return (np.array([[g.amp, g.x, g.y, g.width] for g in out]),
             {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_})
+
+
+def _ell_array(rows):
+    rows = np.asarray(rows, dtype=np.float64).reshape(-1, 6)
+    arr = (asp_gauss_ell * len(rows))()
+    for i, r in enumerate(rows):
+        arr[i] = asp_gauss_ell(*[float(v) for v in r])
+    return arr, len(rows)
+
+
+def _ell_rows(arr):
+    return np.array([[g.amp, g.x, g.y, g.pxx, g.pxy, g.pyy] for g in arr])
+
+
+def asp_fit_elliptical(h, init, n_old: int = 0):
+    """Eq. 6 with elliptical members: rows (amp, x, y, A, B, C), the
+    precision matrix [[A, B], [B, C]].  Returns (fitted rows, info dict)."""
+    arr, n = _ell_array(init)
+    out = (asp_gauss_ell * n)()
+    info = asp_fit_info()
+    _check(lib().asp_fit_elliptical(h, arr, n, int(n_old), out, C.byref(info)), "asp_fit_elliptical", h)
+    return _ell_rows(out), {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_}
+
+
+def asp_fit_beam_elliptical(h):
+    """The elliptical beam (alpha_b, x_b, y_b, A_b, B_b, C_b) on the PSF grid."""
+    out = asp_gauss_ell()
+    _check(lib().asp_fit_beam_elliptical(h, C.byref(out)), "asp_fit_beam_elliptical", h)
+    return _ell_rows([out])[0]
+
+
+def asp_deconvolve_elliptical(h, rows, beam):
+    """Eqs. 7-8 for ellipses on the device: rows (flux, amp, x, y, sxx, sxy,
+    syy, is_point)."""
+    arr, n = _ell_array(rows)
+    b, _ = _ell_array(beam)
+    out = (asp_component_ell * max(n, 1))()
+    _check(lib().asp_deconvolve_elliptical(h, arr, n, b, out), "asp_deconvolve_elliptical", h)
+    return np.array([[c.flux, c.amp, c.x, c.y, c.sxx, c.sxy, c.syy, c.is_point] for c in out[:n]])
 
 
 def asp_eval_normal_equations(h, theta, n_old: int, window):
@@ -446,6 +487,15 @@ class Context:
 
     def fit_2004(self, init, n_old=0, omega_min=0.1):
         return asp_fit_2004(self.h, init, n_old, omega_min)
+
+    def fit_elliptical(self, init, n_old=0):
+        return asp_fit_elliptical(self.h, init, n_old)
+
+    def beam_elliptical(self):
+        return asp_fit_beam_elliptical(self.h)
+
+    def deconvolve_elliptical(self, rows, beam):
+        return asp_deconvolve_elliptical(self.h, rows, beam)
 
     def fit_lm(self, init, n_old, lambda0, max_iter, start=None):
         return asp_fit_lm(self.h, init, n_old, lambda0, max_iter, start)

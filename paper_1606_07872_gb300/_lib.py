@@ -21,6 +21,7 @@ ASP_INIT_AUTO, ASP_INIT_SIMPLE, ASP_INIT_SMOOTH = 0, 1, 2
 ASP_PEAK_SIMPLE, ASP_PEAK_SMOOTH = 0, 1
 ASP_SUB_AUTO, ASP_SUB_DIRECT, ASP_SUB_FFT = 0, 1, 2
 ASP_SUB_FFT_MIN_PIXELS = 512 * 512
+ASP_ELL_KMAX = 33
 ASP_LM_CONVERGED, ASP_LM_CAP, ASP_LM_STALLED = 0, 1, 2
 ASP_STOP_NONE, ASP_STOP_ITER, ASP_STOP_NOISE, ASP_STOP_CAPACITY = 0, 1, 2, 3
 
@@ -32,6 +33,17 @@ class asp_gauss(C.Structure):
 class asp_component(C.Structure):
     _fields_ = [("flux", C.c_double), ("amp", C.c_double), ("x", C.c_double), ("y", C.c_double),
                 ("width", C.c_double), ("is_point", C.c_int32), ("reserved", C.c_int32)]
+
+
+class asp_gauss_ell(C.Structure):
+    _fields_ = [("amp", C.c_double), ("x", C.c_double), ("y", C.c_double), ("pxx", C.c_double),
+                ("pxy", C.c_double), ("pyy", C.c_double)]
+
+
+class asp_component_ell(C.Structure):
+    _fields_ = [("flux", C.c_double), ("amp", C.c_double), ("x", C.c_double), ("y", C.c_double),
+                ("sxx", C.c_double), ("sxy", C.c_double), ("syy", C.c_double), ("is_point", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class asp_peak(C.Structure):
@@ -113,6 +125,10 @@ SIGNATURES = {
     "asp_fit_2004": [_P, C.POINTER(asp_gauss), _I, _I, C.c_double, C.POINTER(asp_gauss), C.POINTER(asp_fit_info)],
     "asp_subtract": [_P, C.POINTER(asp_component), _I, C.c_float],
     "asp_subtract_beam": [_P, C.POINTER(asp_component), _I, C.c_float],
+    "asp_fit_beam_elliptical": [_P, C.POINTER(asp_gauss_ell)],
+    "asp_fit_elliptical": [_P, C.POINTER(asp_gauss_ell), _I, _I, C.POINTER(asp_gauss_ell), C.POINTER(asp_fit_info)],
+    "asp_deconvolve_elliptical": [_P, C.POINTER(asp_gauss_ell), _I, C.POINTER(asp_gauss_ell),
+                                  C.POINTER(asp_component_ell)],
     "asp_minor_cycle": [_P, _I, C.POINTER(asp_cycle_stats)],
     "asp_smooth": [_P, _I, _P],
     "asp_num_scales": [_P, C.POINTER(_I), _P],

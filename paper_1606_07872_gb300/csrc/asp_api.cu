@@ -106,6 +106,7 @@ struct asp_ctx {
     bool plans = false;
     bool sub_fft = false;   // per-iteration residual update by FFT (asp_params.sub_mode)
     Fit2004Buffers* f2004 = nullptr;   // Asp-Clean2004's objective, allocated by its first call
+    unsigned char* ell_buf = nullptr;  // elliptical deconvolution in/out, allocated by its first call
     int broken = 0;
     std::string err;
     std::vector<void*> allocs;
@@ -853,6 +854,152 @@ asp_status asp_fit_lm(asp_ctx* ctx, const asp_gauss* init, int n, int n_old, con
     CHECK_CTX();
     if (!(lambda0 > 0.0) || !std::isfinite(lambda0) || max_iter < 0) return ASP_ERR_INVALID_ARG;
     return fit_common(ctx, init, n, n_old, start, lambda0, max_iter, out, info, trial_out, chi2_trial);
+}
+
+// ---------------------------------------------------------------- elliptical variant
+
+static bool gauss_ell_ok(const asp_gauss_ell& g) {
+    if (!(std::isfinite(g.amp) && std::isfinite(g.x) && std::isfinite(g.y) && std::isfinite(g.pxx) &&
+          std::isfinite(g.pxy) && std::isfinite(g.pyy)))
+        return false;
+    return g.pxx > 0 && g.pyy > 0 && g.pxx * g.pyy - g.pxy * g.pxy > 0;
+}
+
+// Major principal width 1 / sqrt(mu_min) of a positive-definite precision matrix.
+static double ell_sigma_max(const asp_gauss_ell& g) {
+    const double h = 0.5 * (g.pxx + g.pyy), r = std::hypot(0.5 * (g.pxx - g.pyy), g.pxy);
+    return 1.0 / std::sqrt(h - r);
+}
+
+// One elliptical fit launch: the fit variant for 6n parameters (that of
+// ceil(6n / 4) circular members), configured on first use, at most the
+// context's grid.
+static asp_status ell_variant(asp_ctx* ctx, int K, int* tpt, int* g_max) {
+    *tpt = fit_tpt_for((6 * K + 3) / 4);
+    int bps = 0;
+    if (fit_configure(*tpt, &bps) != cudaSuccess || bps < 1) return fail(ctx, ASP_ERR_CUDA, "fit variant");
+    *g_max = std::min(std::min(ctx->num_sms * bps, FIT_GRID_MAX), ctx->g_max);
+    return ASP_OK;
+}
+
+static asp_status run_fit_ell(asp_ctx* ctx, FitDesc& d, int K, const float* src, int src_w, FitOut* fo) {
+    int tpt = 1, g_max = 1;
+    asp_status vs = ell_variant(ctx, K, &tpt, &g_max);
+    if (vs != ASP_OK) return vs;
+    LMConst lmc = ctx->dp.lm;
+    if (d.active) {
+        int smem_ok = 1;
+        d.grid = fit_grid((long long)d.ww * d.wh, d.K, lmc.px_per_cta, g_max, &smem_ok);
+        d.smem_ok = smem_ok;
+        CK(cudaMemcpyAsync(&ctx->st->fit, &d, sizeof(d), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream));
+    {
+        Mark m(ctx, KC_FIT);
+        CK(launch_lm_fit(tpt, g_max, src, src_w, &ctx->st->fit, lmc, &ctx->st->fout, ctx->partials, ctx->sums,
+                         ctx->bar, ctx->Tg, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (fo->error) return fail(ctx, ASP_ERR_TIMEOUT, "fit: grid barrier timed out");
+    return ASP_OK;
+}
+
+asp_status asp_fit_elliptical(asp_ctx* ctx, const asp_gauss_ell* init, int n, int n_old, asp_gauss_ell* out,
+                              asp_fit_info* info) {
+    CHECK_CTX();
+    if (!init || !out || n < 1 || n_old < 0 || n_old > n) return ASP_ERR_INVALID_ARG;
+    if (n > ASP_ELL_KMAX) return ASP_ERR_UNSUPPORTED;
+    long long wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!gauss_ell_ok(init[k])) return ASP_ERR_INVALID_ARG;
+        long long b[4];
+        host_member_box(init[k].x, init[k].y, ell_sigma_max(init[k]), b);
+        if (k == 0) { wx0 = b[0]; wx1 = b[1]; wy0 = b[2]; wy1 = b[3]; }
+        wx0 = std::min(wx0, b[0]); wx1 = std::max(wx1, b[1]);
+        wy0 = std::min(wy0, b[2]); wy1 = std::max(wy1, b[3]);
+    }
+    wx0 = std::max(wx0, 0LL); wy0 = std::max(wy0, 0LL);
+    wx1 = std::min(wx1, (long long)ctx->W - 1); wy1 = std::min(wy1, (long long)ctx->H - 1);
+    if (wx0 > wx1 || wy0 > wy1) return ASP_ERR_INVALID_ARG;
+    FitDesc d;
+    memset(&d, 0, sizeof(d));
+    d.K = n;
+    d.n_old = n_old;
+    d.model = 1;
+    d.wx0 = (int)wx0; d.wy0 = (int)wy0;
+    d.ww = (int)(wx1 - wx0 + 1); d.wh = (int)(wy1 - wy0 + 1);
+    d.omega_min = 0.25 * ctx->omega_b;
+    d.omega_max = (double)std::max(d.ww, d.wh);
+    d.bx0 = (double)wx0; d.bx1 = (double)wx1; d.by0 = (double)wy0; d.by1 = (double)wy1;
+    for (int k = 0; k < n; ++k) {
+        double* t = d.theta0 + 6 * k;
+        t[0] = init[k].amp; t[1] = init[k].x; t[2] = init[k].y;
+        t[3] = init[k].pxx; t[4] = init[k].pxy; t[5] = init[k].pyy;
+    }
+    d.active = 1;
+    FitOut fo;
+    asp_status s = run_fit_ell(ctx, d, n, ctx->R, ctx->W, &fo);
+    if (s != ASP_OK) return s;
+    for (int k = 0; k < n; ++k) {
+        const double* t = fo.theta + 6 * k;
+        out[k] = asp_gauss_ell{t[0], t[1], t[2], t[3], t[4], t[5]};
+    }
+    if (info) {
+        info->iters = fo.iters;
+        info->passes = fo.passes;
+        info->status = fo.status;
+        info->k = n;
+        info->x0 = (int)wx0; info->x1 = (int)wx1; info->y0 = (int)wy0; info->y1 = (int)wy1;
+        info->chi2_init = fo.chi2_init;
+        info->chi2_final = fo.chi2;
+        info->lambda = fo.lambda;
+        info->pixel_evals = fo.pixel_evals;
+    }
+    return ASP_OK;
+}
+
+asp_status asp_fit_beam_elliptical(asp_ctx* ctx, asp_gauss_ell* out) {
+    CHECK_CTX();
+    if (!out) return ASP_ERR_INVALID_ARG;
+    // the circular beam's region and bounds (k_beam_init, its grid sized
+    // for the launch below), then the elliptical start from the circular beam
+    int tpt = 1, g_max = 1;
+    asp_status s = ell_variant(ctx, 1, &tpt, &g_max);
+    if (s != ASP_OK) return s;
+    CK(launch_beam_init(&ctx->st->fit, ctx->B, ctx->H, ctx->W, g_max, ctx->stream));
+    CK(launch_beam_ell_desc(&ctx->st->fit, ctx->alpha_b, ctx->xb, ctx->yb, ctx->omega_b, ctx->stream));
+    FitDesc d;
+    memset(&d, 0, sizeof(d));   // inactive: run_fit_ell keeps the device's descriptor
+    FitOut fo;
+    s = run_fit_ell(ctx, d, 1, ctx->B, 2 * ctx->W, &fo);
+    if (s != ASP_OK) return s;
+    const asp_gauss_ell g{fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], fo.theta[4], fo.theta[5]};
+    if (!gauss_ell_ok(g) || g.amp == 0.0)
+        return fail(ctx, ASP_ERR_NAN, "elliptical beam fit failed (no positive-definite main lobe)");
+    *out = g;
+    return ASP_OK;
+}
+
+asp_status asp_deconvolve_elliptical(asp_ctx* ctx, const asp_gauss_ell* in, int n, const asp_gauss_ell* beam,
+                                     asp_component_ell* out) {
+    CHECK_CTX();
+    if (!in || !beam || !out || n < 0) return ASP_ERR_INVALID_ARG;
+    if (n > ASP_ELL_KMAX) return ASP_ERR_UNSUPPORTED;
+    if (!gauss_ell_ok(*beam) || beam->amp == 0.0) return ASP_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k)
+        if (!gauss_ell_ok(in[k])) return ASP_ERR_INVALID_ARG;
+    if (n == 0) return ASP_OK;
+    const size_t in_bytes = sizeof(asp_gauss_ell) * (ASP_ELL_KMAX + 1);
+    if (!ctx->ell_buf) CK(dalloc(ctx, &ctx->ell_buf, in_bytes + sizeof(asp_component_ell) * ASP_ELL_KMAX));
+    asp_gauss_ell* din = reinterpret_cast<asp_gauss_ell*>(ctx->ell_buf);
+    asp_component_ell* dout = reinterpret_cast<asp_component_ell*>(ctx->ell_buf + in_bytes);
+    CK(cudaMemcpyAsync(din, beam, sizeof(asp_gauss_ell), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(din + 1, in, sizeof(asp_gauss_ell) * n, cudaMemcpyHostToDevice, ctx->stream));
+    { Mark m(ctx, KC_UPDATE); CK(launch_deconvolve_ell(din, n, dout, ctx->stream)); }
+    CK(cudaMemcpyAsync(out, dout, sizeof(asp_component_ell) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ASP_OK;
 }
 
 // ---------------------------------------------------------------- Asp-Clean2004's objective (Eq. 3)

@@ -242,6 +242,7 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
     f.K = K;
     f.n_old = K - 1;
     f.has_start = 0;
+    f.model = 0;
     f.wx0 = (int)wx0; f.wy0 = (int)wy0;
     f.ww = (int)(wx1 - wx0 + 1); f.wh = (int)(wy1 - wy0 + 1);
     f.use_mask = 0;
@@ -444,6 +445,50 @@ __device__ __forceinline__ void build_weights_body(const CycleState* __restrict_
 
 __global__ void __launch_bounds__(256)
 k_build_weights(const CycleState* __restrict__ st, const int* gate, float* __restrict__ wbuf) { build_weights_body(st, gate, wbuf); }
+
+// Eqs. 7-8 for elliptical shapes, one thread per component (FP64):
+// Sigma = P^-1 for the fitted Gaussian and the beam, Sigma_i = Sigma_ic -
+// Sigma_b, flux F = a_ic sqrt(det Sigma_ic) / (alpha_b sqrt(det Sigma_b)),
+// amp = F / (2 pi sqrt(det Sigma_i)); a point when the smaller eigenvalue of
+// Sigma_i is at most 1e-3 times the smaller eigenvalue of Sigma_b.
+// v[0] is the beam, v[1..n] the components.
+__global__ void k_deconvolve_ell(const asp_gauss_ell* __restrict__ v, int n, asp_component_ell* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const asp_gauss_ell b = v[0], g = v[1 + k];
+    auto cov = [](double A, double B, double C, double& sxx, double& sxy, double& syy, double& det) {
+        const double dp = A * C - B * B;
+        sxx = C / dp; sxy = -B / dp; syy = A / dp;
+        det = 1.0 / dp;
+    };
+    auto eig_min = [](double sxx, double sxy, double syy) {
+        return 0.5 * (sxx + syy) - hypot(0.5 * (sxx - syy), sxy);
+    };
+    double bxx, bxy, byy, bdet, cxx, cxy, cyy, cdet;
+    cov(b.pxx, b.pxy, b.pyy, bxx, bxy, byy, bdet);
+    cov(g.pxx, g.pxy, g.pyy, cxx, cxy, cyy, cdet);
+    asp_component_ell c;
+    c.x = g.x;
+    c.y = g.y;
+    c.reserved = 0;
+    c.flux = g.amp * sqrt(cdet) / (b.amp * sqrt(bdet));
+    const double ixx = cxx - bxx, ixy = cxy - bxy, iyy = cyy - byy;
+    if (eig_min(ixx, ixy, iyy) <= 1e-3 * eig_min(bxx, bxy, byy)) {
+        c.is_point = 1;
+        c.amp = c.flux;
+        c.sxx = c.sxy = c.syy = 0.0;
+    } else {
+        c.is_point = 0;
+        c.sxx = ixx; c.sxy = ixy; c.syy = iyy;
+        c.amp = c.flux / (TWO_PI * sqrt(ixx * iyy - ixy * ixy));
+    }
+    out[k] = c;
+}
+
+cudaError_t launch_deconvolve_ell(const asp_gauss_ell* beam_then_in, int n, asp_component_ell* out, cudaStream_t s) {
+    k_deconvolve_ell<<<(n + 63) / 64, 64, 0, s>>>(beam_then_in, n, out);
+    return cudaGetLastError();
+}
 
 // Clears the minor-cycle state (components, retained list, counters) while
 // keeping the beam, the noise threshold and the capacities.

@@ -53,6 +53,7 @@ struct FitDescHead {
     double omega_min, omega_max;   // trial widths must lie in (omega_min, omega_max]
     double bx0, bx1, by0, by1;     // trial centres must stay inside this box
     int active, smem_ok;
+    int model, pad_model;          // 0: circular members (a, x, y, omega); 1: elliptical (a, x, y, A, B, C)
     double theta0[PMAX];
 };
 // The fit's description plus an optional LM start other than theta0 (which

@@ -51,8 +51,10 @@ static_assert(SPEC_OFF >= PMAX * (PMAX + 1) / 2, "the speculation block must not
 static_assert(UNI_L_FLOATS >= CH_XL * (NAP_MAX + 4), "J chunk of the large variant must fit its union region");
 
 struct MemberFrame {
-    float a, c, iw2, iw3, fx, fy;   // c = log2(e) / (2 w^2)
+    float a, c, iw2, iw3, fx, fy;   // circular: c = log2(e) / (2 w^2); elliptical: c = log2(e) A / 2
     int cx, cy;
+    float cb, cc;                   // elliptical: log2(e) B, log2(e) C / 2 (exponent coefficients)
+    float pa, pb, pc;               // elliptical: A, B, C (Jacobian)
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -118,6 +120,31 @@ __device__ __forceinline__ void make_frame(const double* th, MemberFrame& f) {
     f.fy = (float)(y - cy);
     f.cx = (int)cx;
     f.cy = (int)cy;
+}
+
+// Elliptical member (a, x, y, A, B, C): a exp(-(A dx^2 + 2 B dx dy + C
+// dy^2) / 2) = a exp2(-(c dx^2 + cb dx dy + cc dy^2)), same centre frame.
+__device__ __forceinline__ void make_frame_ell(const double* th, MemberFrame& f) {
+    const double a = th[0], x = th[1], y = th[2], A = th[3], B = th[4], C = th[5];
+    const double cx = floor(x + 0.5), cy = floor(y + 0.5);
+    f.a = (float)a;
+    f.c = (float)(0.5 * LOG2E * A);
+    f.cb = (float)(LOG2E * B);
+    f.cc = (float)(0.5 * LOG2E * C);
+    f.pa = (float)A;
+    f.pb = (float)B;
+    f.pc = (float)C;
+    f.fx = (float)(x - cx);
+    f.fy = (float)(y - cy);
+    f.cx = (int)cx;
+    f.cy = (int)cy;
+}
+
+// Eigenvalues (mu-, mu+) of the precision matrix [[A, B], [B, C]].
+__device__ __forceinline__ void prec_eig(double A, double B, double C, double& mm, double& mp) {
+    const double h = 0.5 * (A + C), r = hypot(0.5 * (A - C), B);
+    mm = h - r;
+    mp = h + r;
 }
 
 // Pivot l = sqrt(d) and 1/l.  FP32 (the refined factor): rsqrtf, whose
@@ -781,7 +808,9 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     const bool is_spec = spec_on && b == Gp;
     double* const spec_blk = spec_on ? partials + (size_t)Gp * NACC_MAX + SPEC_OFF : nullptr;
 
-    const int K = d.K, P = 4 * K, NA = P + 1, NAp = (NA + 3) & ~3, nb = NAp / 4;
+    const bool ell = d.model == 1;
+    const int NPM = ell ? 6 : 4;          // parameters per member
+    const int K = d.K, P = NPM * K, NA = P + 1, NAp = (NA + 3) & ~3, nb = NAp / 4;
     const int ntiles = nb * (nb + 1) / 2;
     const int nacc = ntiles * 16;
     const long long Wn = (long long)d.ww * d.wh;
@@ -839,7 +868,10 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     }
 
     // ---- stage the target T = src + sum of the added-back members
-    if (tid < K) make_frame(&d.theta0[4 * tid], fr[tid]);
+    if (tid < K) {
+        if (ell) make_frame_ell(&d.theta0[NPM * tid], fr[tid]);
+        else make_frame(&d.theta0[NPM * tid], fr[tid]);
+    }
     __syncthreads();
     for (int i = tid; i < slen; i += blockDim.x) {
         long long gi = s0 + i;
@@ -848,7 +880,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         for (int m = K - d.n_old; m < K; ++m) {
             const MemberFrame& f = fr[m];
             float dx = (float)(x - f.cx) - f.fx, dy = (float)(y - f.cy) - f.fy;
-            v += f.a * exp2f(-(dx * dx + dy * dy) * f.c);
+            v += f.a * exp2f(ell ? -((f.c * dx + f.cb * dy) * dx + f.cc * dy * dy) : -(dx * dx + dy * dy) * f.c);
         }
         if (in_smem) Ts[i] = v; else Tg[gi] = v;
     }
@@ -878,7 +910,10 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     unsigned long long t_pass = 0, t_red = 0, t_solve = 0, t_factor = 0, t_subst = 0, t0 = gtimer(), t1;
     while (true) {
         // ================= pixel pass at trial[] =================
-        if (tid < K) make_frame(&trial[4 * tid], fr[tid]);
+        if (tid < K) {
+            if (ell) make_frame_ell(&trial[NPM * tid], fr[tid]);
+            else make_frame(&trial[NPM * tid], fr[tid]);
+        }
         if (tid == (int)blockDim.x - 1 && !first) {
             // the LM decision's FP64 arithmetic (a division among it), done
             // here by a thread without a J row so that it stays off the
@@ -938,7 +973,27 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         live = ddx * ddx + ddy * ddy <= d.mr2;
                     }
                 }
-                if (live) {
+                if (live && ell) {
+                    // elliptical members: d/da = E, d/dx0 = g (A dx + B dy),
+                    // d/dy0 = g (B dx + C dy), d/dA = -g dx^2 / 2,
+                    // d/dB = -g dx dy, d/dC = -g dy^2 / 2
+                    float model = 0.f;
+#pragma unroll 2
+                    for (int k = 0; k < K; ++k) {
+                        const MemberFrame& f = fr[k];
+                        const float dx = (float)(x - f.cx) - f.fx, dy = (float)(y - f.cy) - f.fy;
+                        const float e = exp2f(-((f.c * dx + f.cb * dy) * dx + f.cc * dy * dy));
+                        const float g = f.a * e, hg = -0.5f * g;
+                        model += g;
+                        float2* r2p = reinterpret_cast<float2*>(row + 6 * k);
+                        r2p[0] = make_float2(e, g * (f.pa * dx + f.pb * dy));
+                        r2p[1] = make_float2(g * (f.pb * dx + f.pc * dy), hg * dx * dx);
+                        r2p[2] = make_float2(-g * dx * dy, hg * dy * dy);
+                    }
+                    float t = in_smem ? Ts[c0 + tid] : Tg[s0 + c0 + tid];
+                    row[P] = t - model;
+                    for (int c = P + 1; c < NAp; ++c) row[c] = 0.f;
+                } else if (live) {
                     float model = 0.f;
 #pragma unroll 4
                     for (int k = 0; k < K; ++k) {
@@ -1298,8 +1353,23 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             if (ok && tid < P) {
                 const double di = delta[tid];
                 fin_i = isfinite(di);
-                // every step below xtol of its scale (|a|; w for centre and width)
-                double sc = (tid & 3) == 0 ? fabs(theta[tid]) : theta[(tid & ~3) + 3];
+                // every step below xtol of its scale: |a|; w for centre and
+                // width (circular); the major width for the centre and
+                // (A + C) / 2 for A, B, C (elliptical)
+                double sc;
+                if (ell) {
+                    const int j = tid % 6, base = tid - j;
+                    if (j == 0) {
+                        sc = fabs(theta[tid]);
+                    } else {
+                        const double A = theta[base + 3], C = theta[base + 5];
+                        double mm, mp;
+                        prec_eig(A, theta[base + 4], C, mm, mp);
+                        sc = j <= 2 ? 1.0 / sqrt(mm) : 0.5 * (A + C);
+                    }
+                } else {
+                    sc = (tid & 3) == 0 ? fabs(theta[tid]) : theta[(tid & ~3) + 3];
+                }
                 if (sc == 0.0) sc = 1.0;
                 small_i = fabs(di) < lmc.xtol * sc;
                 const float df = (float)di;
@@ -1307,7 +1377,19 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 dd_i = dv32[tid] * df * df;
                 trial[tid] = theta[tid] + di;
             }
-            if (ok && tid < K) {
+            if (ok && tid < K && ell) {
+                // positive definite, principal widths 1 / sqrt(mu) in
+                // (omega_min, omega_max], centre in the box
+                const int o = 6 * tid;
+                const double a = theta[o] + delta[o], x = theta[o + 1] + delta[o + 1], y = theta[o + 2] + delta[o + 2];
+                const double A = theta[o + 3] + delta[o + 3], B = theta[o + 4] + delta[o + 4];
+                const double C = theta[o + 5] + delta[o + 5];
+                double mm, mp;
+                prec_eig(A, B, C, mm, mp);
+                valid_i = isfinite(a) && isfinite(x) && isfinite(y) && isfinite(A) && isfinite(B) && isfinite(C) &&
+                          !(x < d.bx0) && !(x > d.bx1) && !(y < d.by0) && !(y > d.by1) && mm > 0.0 &&
+                          mp < 1.0 / (d.omega_min * d.omega_min) && mm >= 1.0 / (d.omega_max * d.omega_max);
+            } else if (ok && tid < K) {
                 const double a = theta[4 * tid] + delta[4 * tid];
                 const double x = theta[4 * tid + 1] + delta[4 * tid + 1];
                 const double y = theta[4 * tid + 2] + delta[4 * tid + 2];

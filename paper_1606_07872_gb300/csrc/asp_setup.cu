@@ -53,6 +53,7 @@ __global__ void k_beam_init(FitDesc* d, const float* __restrict__ B, int H, int 
     d->K = 1;
     d->n_old = 0;
     d->has_start = 0;
+    d->model = 0;
     d->wx0 = x0; d->wy0 = y0; d->ww = x1 - x0 + 1; d->wh = y1 - y0 + 1;
     d->use_mask = 1;
     d->mcx = W; d->mcy = H; d->mr2 = (double)r * r;
@@ -64,6 +65,21 @@ __global__ void k_beam_init(FitDesc* d, const float* __restrict__ B, int H, int 
     d->grid = fit_grid((long long)d->ww * d->wh, 1, 0, g_max, &smem_ok);
     d->smem_ok = smem_ok;
     d->active = 1;
+}
+
+// The elliptical beam's fit: the circular beam's region and bounds, the
+// elliptical model started from the circular beam (A = C = 1 / omega_b^2,
+// B = 0).
+__global__ void k_beam_ell_desc(FitDesc* d, double a, double x, double y, double w) {
+    if (threadIdx.x != 0) return;
+    d->model = 1;
+    d->theta0[0] = a; d->theta0[1] = x; d->theta0[2] = y;
+    d->theta0[3] = 1.0 / (w * w); d->theta0[4] = 0.0; d->theta0[5] = 1.0 / (w * w);
+}
+
+cudaError_t launch_beam_ell_desc(FitDesc* d, double a, double x, double y, double w, cudaStream_t s) {
+    k_beam_ell_desc<<<1, 32, 0, s>>>(d, a, x, y, w);
+    return cudaGetLastError();
 }
 
 __global__ void k_radix_reset(unsigned long long* ws, long long rank) {

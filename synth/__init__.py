@@ -27,6 +27,8 @@ from .sky import (  # noqa: F401
     config4,
     small_case,
     gaussian_psf,
+    elliptical_psf,
+    elliptical_field,
     rng_for,
 )
 from .mlp_init import mlp_init  # noqa: F401,E402  (initial weights of the learned-init network)

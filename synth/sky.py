@@ -74,6 +74,40 @@ def gaussian_psf(H: int, W: int, sigma: float, amp: float = 1.0) -> np.ndarray:
     return amp * analytic_psf(H, W, sigma, None)
 
 
+def _rotated_gaussian(xs, ys, a, x0, y0, s_major, s_minor, phi):
+    """``a exp(-(u^2 / s_major^2 + v^2 / s_minor^2) / 2)`` with (u, v) the
+    offset from (x0, y0) rotated by -phi (major axis at angle phi from +x)."""
+    c, s = np.cos(phi), np.sin(phi)
+    dx, dy = xs - x0, ys - y0
+    u = c * dx + s * dy
+    v = -s * dx + c * dy
+    return a * np.exp(-0.5 * (u * u / (s_major * s_major) + v * v / (s_minor * s_minor)))
+
+
+def elliptical_psf(H: int, W: int, s_major: float, s_minor: float, phi: float, amp: float = 1.0,
+                   ring_radius: Optional[float] = None, ring_level: float = 0.02) -> np.ndarray:
+    """Elliptical Gaussian main lobe (widths s_major, s_minor, major axis at
+    phi) plus an optional circular ring sidelobe, 2H x 2W, zero lag at
+    [H, W]."""
+    y = np.arange(2 * H, dtype=np.float64)[:, None]
+    x = np.arange(2 * W, dtype=np.float64)[None, :]
+    b = _rotated_gaussian(x, y, amp, float(W), float(H), s_major, s_minor, phi)
+    if ring_radius is not None and ring_level != 0.0:
+        r = np.sqrt((x - W) ** 2 + (y - H) ** 2)
+        b = b + amp * ring_level * np.exp(-((r - ring_radius) ** 2) / (2.0 * s_minor * s_minor))
+    return b
+
+
+def elliptical_field(H: int, W: int, sources, noise_sigma: float, seed: int) -> np.ndarray:
+    """Sum of rotated elliptical Gaussians (rows a, x0, y0, s_major,
+    s_minor, phi) on the H x W pixel grid plus seeded white noise, FP64."""
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = np.zeros((H, W))
+    for a, x0, y0, s1, s2, phi in sources:
+        img += _rotated_gaussian(xs, ys, a, x0, y0, s1, s2, phi)
+    return img + rng_for(200, seed).normal(0.0, noise_sigma, (H, W))
+
+
 def _halfmax_sigma(psf: np.ndarray) -> float:
     """Main-lobe width of a generated PSF from the area above half maximum.
 

@@ -52,9 +52,10 @@ def test_struct_sizes_match_header(libpath):
 #include <stdio.h>
 #include "asp.h"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(asp_gauss), sizeof(asp_component), sizeof(asp_peak),
-         sizeof(asp_fit_info), sizeof(asp_params), sizeof(asp_cycle_stats), sizeof(asp_iter_record),
-         sizeof(asp_batch_tuning), sizeof(asp_kernel_time), sizeof(asp_alu_peaks));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(asp_gauss), sizeof(asp_component),
+         sizeof(asp_peak), sizeof(asp_fit_info), sizeof(asp_params), sizeof(asp_cycle_stats),
+         sizeof(asp_iter_record), sizeof(asp_batch_tuning), sizeof(asp_kernel_time), sizeof(asp_alu_peaks),
+         sizeof(asp_gauss_ell), sizeof(asp_component_ell));
   return 0;
 }}
 """
@@ -67,7 +68,8 @@ int main(void) {{
         sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (_lib.asp_gauss, _lib.asp_component, _lib.asp_peak, _lib.asp_fit_info,
                                        _lib.asp_params, _lib.asp_cycle_stats, _lib.asp_iter_record,
-                                       _lib.asp_batch_tuning, _lib.asp_kernel_time, _lib.asp_alu_peaks)]
+                                       _lib.asp_batch_tuning, _lib.asp_kernel_time, _lib.asp_alu_peaks,
+                                       _lib.asp_gauss_ell, _lib.asp_component_ell)]
     assert sizes == mine
 
 

@@ -264,3 +264,14 @@ def test_planted_validity_without_positive_definiteness_is_caught(monkeypatch):
     _patch(monkeypatch, "ell_valid", bad)
     with pytest.raises(AssertionError):
         test_valid_rejects_non_positive_definite_and_out_of_range_widths()
+
+
+def test_precision_form_equals_the_rotated_axes_form():
+    """The precision-matrix model against the generator's independent
+    rotated-axes formula u^2/s1^2 + v^2/s2^2."""
+    import synth
+    src = [(1.0, 10.3, 9.7, 3.0, 1.5, 0.6), (-0.4, 5.2, 14.1, 2.2, 2.0, -1.3)]
+    img = synth.elliptical_field(20, 22, src, 0.0, 0)
+    ys, xs = np.mgrid[0:20, 0:22].astype(float)
+    th = np.concatenate([[a, x, y, *E.precision_from_axes(s1, s2, p)] for a, x, y, s1, s2, p in src])
+    np.testing.assert_allclose(E.ell_model(th, xs, ys), img, rtol=1e-12, atol=1e-15)
