@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -54,6 +55,7 @@ def _args():
     ap.add_argument("--split-config3", action="store_true", help="also measure the split on the 4096^2 workload")
     ap.add_argument("--fit-px", type=int, default=0, help="LM fit tile: window pixels per CTA (0: library default)")
     ap.add_argument("--no-split", action="store_true", help="skip the minor/major split comparison")
+    ap.add_argument("--no-elliptical", action="store_true", help="skip the elliptical-variant comparison")
     ap.add_argument("--sub", choices=["auto", "direct", "fft"], default="auto",
                     help="residual update form of the measured runs (auto: FFT from 512x512 pixels)")
     ap.add_argument("--no-sub-forms", action="store_true",
@@ -438,6 +440,56 @@ def batched_comparison(asp, n_images: int, seed0: int = 0, weights=None) -> dict
     return out
 
 
+def elliptical_comparison(asp, reps: int = 20) -> dict:
+    """The elliptical variant against the circular fit on one window of the
+    1024x1024 workload's size: 12 rotated elliptical sources (widths 3-6 by
+    1.5-2.9 px) over a ~150 px region, noise 1e-2; the same 12 members
+    fitted as ellipses (6 parameters each) and as circles (4 each) from the
+    same circular starts, each fit
+    repeated ``reps`` times through the C ABI (per call: the launch, the
+    device synchronisation and the result copy)."""
+    import numpy as np
+    import torch
+    import synth
+    H = W = 1024
+    rng = np.random.default_rng(4)
+    src = [(rng.uniform(0.3, 1.0) * rng.choice([-1, 1]), rng.uniform(450, 560), rng.uniform(450, 560),
+            rng.uniform(3.0, 6.0), rng.uniform(1.5, 2.9), rng.uniform(-1.5, 1.5)) for _ in range(12)]
+    dirty = synth.elliptical_field(H, W, src, 1e-2, 11).astype(np.float32)
+    psf = synth.small_case(H, W, seed=5).psf
+    ctx = asp.Context(torch.from_numpy(dirty).cuda(), torch.from_numpy(psf).cuda(), noise_sigma=1e-2, k_max=20)
+    # both fits start from the same circles (what the peak search
+    # proposes): width sqrt(s_major s_minor), so the ellipse fit has to find
+    # each shape and orientation
+    ell_init, circ_init = [], []
+    for a, x, y, s1, s2, phi in src:
+        w2 = s1 * s2
+        ell_init.append([a, x, y, 1.0 / w2, 0.0, 1.0 / w2])
+        circ_init.append([a, x, y, math.sqrt(w2)])
+    out = {}
+    for name, call, init, npm in (("elliptical", ctx.fit_elliptical, ell_init, 6), ("circular", ctx.fit, circ_init, 4)):
+        call(init, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = [call(init, 0)[1] for _ in range(reps)]
+        t = (time.perf_counter() - t0) / reps
+        it = infos[-1]["iters"]
+        P = npm * len(init)
+        pe = infos[-1]["pixel_evals"]
+        flops = pe * ((P + 1) * (P + 2) + 20.0 * len(init))
+        out[name] = {"ms_per_fit": t * 1e3, "lm_iters": it, "passes": infos[-1]["passes"], "pixel_evals": pe,
+                     "us_per_lm_iter": t * 1e6 / max(it, 1), "status": infos[-1]["status"],
+                     "chi2_final": infos[-1]["chi2_final"], "fp32_tflops": flops / t / 1e12,
+                     "window": [infos[-1]["x0"], infos[-1]["x1"], infos[-1]["y0"], infos[-1]["y1"]]}
+    ctx.close()
+    out["members"] = 12
+    out["us_per_lm_iter_ratio_ell_over_circ"] = out["elliptical"]["us_per_lm_iter"] / out["circular"]["us_per_lm_iter"]
+    out["chi2_ratio_ell_over_circ"] = out["elliptical"]["chi2_final"] / out["circular"]["chi2_final"]
+    out["note"] = ("fp32_tflops counts (P+1)(P+2) + 20 K flops per pixel evaluation (the SYRK's upper triangle as "
+                   "FMAs plus the members' model and Jacobian), P = 6K or 4K")
+    return out
+
+
 def learned_comparison(asp, n_train_images: int, seed: int = 0):
     """Learned initial values: harvest (patch, converged fit) pairs from
     GPU runs of config-1 and config-2-style images (seeds >= 10000), train
@@ -800,6 +852,11 @@ def run_ours(a):
             line["asp2004"] = asp2004_comparison(asp)
         except Exception as e:   # report, never hide, a failed comparison
             line["asp2004"] = {"error": repr(e)[:300]}
+    if rank == 0 and main_cfg == 2 and not a.no_elliptical:
+        try:
+            line["elliptical"] = elliptical_comparison(asp)
+        except Exception as e:   # report, never hide, a failed comparison
+            line["elliptical"] = {"error": repr(e)[:300]}
     if rank == 0 and main_cfg == 2 and not a.no_learned:
         try:
             line["learned"], weights = learned_comparison(asp, a.learned_train_images)
