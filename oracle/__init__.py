@@ -21,3 +21,4 @@ they carry a "reading" note in their docstrings.
 from .asp_oracle import *  # noqa: F401,F403
 from . import mlp_oracle  # noqa: F401,E402  (learned initial values: MLP, loss, optimiser)
 from . import elliptical  # noqa: F401,E402  (elliptical beam and components)
+from . import multichannel  # noqa: F401,E402  (joint multi-channel fits)
