@@ -418,7 +418,7 @@ asp_status asp_launch_count(asp_ctx* ctx, int64_t* n);
  * and calls that overlap on the GPU (other threads or streams) race. */
 #define ASP_STATIC_KMAX 8
 #define ASP_STATIC_GRID_MAX 32
-#define ASP_STATIC_SCRATCH_BYTES 5963776
+#define ASP_STATIC_SCRATCH_BYTES 5964032
 asp_status asp_fit_static(const float* image_dev, int H, int W, const asp_gauss* init, int n, int n_old,
                           double omega_min, const asp_params* lm, asp_gauss* out, asp_fit_info* info,
                           void* stream);
@@ -507,6 +507,25 @@ asp_status asp_batch_set_mlp(asp_batch* b, const float* params_host, int enable)
 asp_status asp_batch_image(asp_batch* b, int i, asp_ctx** ctx);
 /* Kernels the batch has launched (graph nodes counted per replay). */
 asp_status asp_batch_launch_count(asp_batch* b, int64_t* n);
+
+/* Joint wide-band fit: the batch's images as the C channels of one
+ * observation (the paper's data is multi-channel, Sect. 4; its fits are per
+ * image).  A joint member has a centre (x, y) and an intrinsic width s
+ * shared by every channel and an image-plane amplitude a_c per channel; in
+ * channel c it is Eq. 6's Gaussian a_c exp(-r^2 / (2 w_c^2)) with w_c^2 =
+ * s^2 + omega_b_c^2 (Eq. 7 with channel c's beam).  chi^2 is the sum over
+ * channels of Eq. 6 over one shared window (the union of the members' boxes
+ * of their widest convolved width), the target of channel c its residual
+ * with the last n_old members of init added back.  LM rules of
+ * asp_fit_active_set; trial centres inside the window and every w_c at most
+ * the window extent.  init and out (host): n rows of 3 + C doubles (x, y,
+ * s, a_1 .. a_C).  flux (host, may be NULL): n x C doubles, Eq. 8 per
+ * channel, F_c = a_c w_c^2 / (alpha_b_c omega_b_c^2); is_point (host, may
+ * be NULL): n ints, s^2 <= 1e-3 min_c omega_b_c^2.  Every image must have
+ * the same size; n (3 + C) <= 4 x ASP_KMAX (ASP_ERR_UNSUPPORTED beyond).
+ * The first call allocates its buffers (C x H x W floats of targets). */
+asp_status asp_batch_fit_joint(asp_batch* b, const double* init, int n, int n_old, double* out, double* flux,
+                               int* is_point, asp_fit_info* info);
 
 /* ---------------------------------------------------------------- learned initial values
  * A 1024-256-256-4 GELU network proposes a new component's starting point

@@ -26,7 +26,7 @@ from ._lib import (  # noqa: F401
 __all__ = [
     "AspError", "lib", "default_params", "asp_init", "asp_init_host", "asp_destroy", "asp_get_beam",
     "asp_find_peak", "asp_fit_active_set", "asp_fit_lm", "asp_fit_2004", "asp_fit_elliptical",
-    "asp_fit_beam_elliptical", "asp_deconvolve_elliptical", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
+    "asp_fit_beam_elliptical", "asp_deconvolve_elliptical", "asp_batch_fit_joint", "asp_measure_alu_peaks", "asp_subtract_beam", "asp_eval_normal_equations", "asp_subtract", "asp_minor_cycle",
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
@@ -230,6 +230,18 @@ def asp_deconvolve_elliptical(h, rows, beam):
     out = (asp_component_ell * max(n, 1))()
     _check(lib().asp_deconvolve_elliptical(h, arr, n, b, out), "asp_deconvolve_elliptical", h)
     return np.array([[c.flux, c.amp, c.x, c.y, c.sxx, c.sxy, c.syy, c.is_point] for c in out[:n]])
+
+
+def asp_batch_fit_joint(h, init, n_old: int, n_chan: int):
+    rows = np.ascontiguousarray(np.asarray(init, dtype=np.float64).reshape(-1, 3 + n_chan))
+    n = rows.shape[0]
+    out = np.empty_like(rows)
+    flux = np.empty((n, n_chan))
+    pt = np.empty(n, dtype=np.int32)
+    info = asp_fit_info()
+    _check(lib().asp_batch_fit_joint(h, rows.ctypes.data, n, int(n_old), out.ctypes.data, flux.ctypes.data,
+                                     pt.ctypes.data, C.byref(info)), "asp_batch_fit_joint")
+    return out, flux, pt.astype(bool), {f.rstrip("_"): getattr(info, f) for f, _ in asp_fit_info._fields_}
 
 
 def asp_eval_normal_equations(h, theta, n_old: int, window):
@@ -624,6 +636,12 @@ class Batch:
 
     def autotune(self, n_trial_iter: int = 16) -> dict:
         return asp_batch_autotune(self.h, n_trial_iter)
+
+    def fit_joint(self, init, n_old: int = 0):
+        """Joint wide-band fit over the batch's images as channels: rows
+        (x, y, s, a_1 .. a_C).  Returns (fitted rows, flux [n, C] by Eq. 8
+        per channel, is_point [n], info dict)."""
+        return asp_batch_fit_joint(self.h, init, n_old, self.n)
 
     def image(self, i: int) -> Context:
         H, W = self.shapes[i]

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libasp.so")
 ASP_KMAX = 50
 ASP_STATIC_KMAX = 8
 ASP_STATIC_GRID_MAX = 32
-ASP_STATIC_SCRATCH_BYTES = 5963776
+ASP_STATIC_SCRATCH_BYTES = 5964032
 
 ASP_OK = 0
 STATUS_NAMES = {0: "ASP_OK", 1: "ASP_ERR_INVALID_ARG", 2: "ASP_ERR_CUDA", 3: "ASP_ERR_OOM", 4: "ASP_ERR_NAN",
@@ -160,6 +160,7 @@ SIGNATURES = {
     "asp_batch_autotune": [_P, _I, C.POINTER(asp_batch_tuning)],
     "asp_batch_image": [_P, _I, C.POINTER(_P)],
     "asp_batch_launch_count": [_P, C.POINTER(C.c_int64)],
+    "asp_batch_fit_joint": [_P, _P, _I, _I, _P, _P, _P, C.POINTER(asp_fit_info)],
     "asp_batch_set_mlp": [_P, _P, _I],
     "asp_mlp_gemm": [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P],
     "asp_mlp_num_params": [C.POINTER(C.c_longlong)],

@@ -1697,6 +1697,12 @@ struct asp_batch {
     float *Z1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *Yinf = nullptr;
     unsigned* mlp_err = nullptr;
     std::vector<void*> mlp_allocs;
+    // joint wide-band fit (asp_batch_fit_joint): channel pointers, beams,
+    // targets, Eq. 8 output; allocated by its first call
+    const float** j_src = nullptr;
+    double* j_wb2 = nullptr;     // omega_b^2 then alpha_b per channel
+    float* j_T = nullptr;
+    double* j_flux = nullptr;    // PMAX fluxes then PMAX point flags (as doubles)
 };
 
 namespace {
@@ -1831,6 +1837,106 @@ asp_status batch_run(asp_batch* b, int n_iter) {
 
 extern "C" {
 
+asp_status asp_batch_fit_joint(asp_batch* b, const double* init, int n, int n_old, double* out, double* flux,
+                               int* is_point, asp_fit_info* info) {
+    if (!b || b->broken) return b ? ASP_ERR_STATE : ASP_ERR_INVALID_ARG;
+    const int C = (int)b->imgs.size();
+    if (!init || !out || n < 1 || n_old < 0 || n_old > n) return ASP_ERR_INVALID_ARG;
+    if ((long long)n * (3 + C) > PMAX) return ASP_ERR_UNSUPPORTED;
+    asp_ctx* c0 = b->imgs[0];
+    const int H = c0->H, W = c0->W;
+    for (asp_ctx* c : b->imgs)
+        if (c->H != H || c->W != W) return ASP_ERR_UNSUPPORTED;
+    const int NPM = 3 + C;
+    for (int i = 0; i < n * NPM; ++i)
+        if (!std::isfinite(init[i])) return ASP_ERR_INVALID_ARG;
+    if (cudaSetDevice(b->dev) != cudaSuccess) return ASP_ERR_CUDA;
+    if (!b->j_src) {
+        BK(cudaMalloc(&b->j_src, sizeof(float*) * C));
+        BK(cudaMalloc(&b->j_wb2, sizeof(double) * 2 * C));
+        BK(cudaMalloc(&b->j_T, sizeof(float) * (size_t)C * c0->N));
+        BK(cudaMalloc(&b->j_flux, sizeof(double) * 2 * PMAX));
+    }
+    std::vector<const float*> srcs(C);
+    std::vector<double> wb(2 * C);
+    double max_wb2 = 0.0;
+    for (int c = 0; c < C; ++c) {
+        srcs[c] = b->imgs[c]->R;
+        wb[c] = b->imgs[c]->omega_b * b->imgs[c]->omega_b;
+        wb[C + c] = b->imgs[c]->alpha_b;
+        max_wb2 = std::max(max_wb2, wb[c]);
+    }
+    // the shared window: member boxes of the widest convolved width
+    long long wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0;
+    for (int k = 0; k < n; ++k) {
+        const double* r = init + (size_t)k * NPM;
+        long long bx[4];
+        host_member_box(r[0], r[1], std::sqrt(r[2] * r[2] + max_wb2), bx);
+        if (k == 0) { wx0 = bx[0]; wx1 = bx[1]; wy0 = bx[2]; wy1 = bx[3]; }
+        wx0 = std::min(wx0, bx[0]); wx1 = std::max(wx1, bx[1]);
+        wy0 = std::min(wy0, bx[2]); wy1 = std::max(wy1, bx[3]);
+    }
+    wx0 = std::max(wx0, 0LL); wy0 = std::max(wy0, 0LL);
+    wx1 = std::min(wx1, (long long)W - 1); wy1 = std::min(wy1, (long long)H - 1);
+    if (wx0 > wx1 || wy0 > wy1) return ASP_ERR_INVALID_ARG;
+    FitDesc d;
+    memset(&d, 0, sizeof(d));
+    d.K = n;
+    d.n_old = n_old;
+    d.model = 2;
+    d.n_chan = C;
+    d.chan_src = b->j_src;
+    d.chan_wb2 = b->j_wb2;
+    d.max_wb2 = max_wb2;
+    d.wx0 = (int)wx0; d.wy0 = (int)wy0;
+    d.ww = (int)(wx1 - wx0 + 1); d.wh = (int)(wy1 - wy0 + 1);
+    d.omega_min = 0.0;
+    d.omega_max = (double)std::max(d.ww, d.wh);
+    d.bx0 = (double)wx0; d.bx1 = (double)wx1; d.by0 = (double)wy0; d.by1 = (double)wy1;
+    for (int i = 0; i < n * NPM; ++i) d.theta0[i] = init[i];
+    const int tpt = fit_tpt_for((n * NPM + 3) / 4);
+    int bps = 0;
+    if (fit_configure(tpt, &bps) != cudaSuccess || bps < 1) return batch_fail(b, ASP_ERR_CUDA);
+    const int g_max = std::min(std::min(b->num_sms * bps, FIT_GRID_MAX), c0->g_max);
+    LMConst lmc = c0->dp.lm;
+    int smem_ok = 1;
+    d.grid = fit_grid((long long)d.ww * d.wh * C, n, lmc.px_per_cta, g_max, &smem_ok);
+    d.smem_ok = smem_ok;
+    d.active = 1;
+    cudaStream_t s = b->stream;
+    BK(cudaMemcpyAsync(b->j_src, srcs.data(), sizeof(float*) * C, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(b->j_wb2, wb.data(), sizeof(double) * 2 * C, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(&c0->st->fit, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    BK(cudaMemsetAsync(&c0->st->fout, 0, sizeof(FitOut), s));
+    BK(launch_lm_fit(tpt, g_max, c0->R, W, &c0->st->fit, lmc, &c0->st->fout, c0->partials, c0->sums, c0->bar,
+                     b->j_T, s));
+    BK(launch_joint_flux(&c0->st->fout, n, C, b->j_wb2, b->j_flux, s));
+    b->launches += 2;
+    FitOut fo;
+    std::vector<double> fl(2 * PMAX);
+    BK(cudaMemcpyAsync(&fo, &c0->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, s));
+    BK(cudaMemcpyAsync(fl.data(), b->j_flux, sizeof(double) * 2 * PMAX, cudaMemcpyDeviceToHost, s));
+    BK(cudaStreamSynchronize(s));
+    if (fo.error) return batch_fail(b, ASP_ERR_TIMEOUT);
+    for (int i = 0; i < n * NPM; ++i) out[i] = fo.theta[i];
+    if (flux)
+        for (int i = 0; i < n * C; ++i) flux[i] = fl[i];
+    if (is_point)
+        for (int k = 0; k < n; ++k) is_point[k] = fl[PMAX + k] != 0.0;
+    if (info) {
+        info->iters = fo.iters;
+        info->passes = fo.passes;
+        info->status = fo.status;
+        info->k = n;
+        info->x0 = (int)wx0; info->x1 = (int)wx1; info->y0 = (int)wy0; info->y1 = (int)wy1;
+        info->chi2_init = fo.chi2_init;
+        info->chi2_final = fo.chi2;
+        info->lambda = fo.lambda;
+        info->pixel_evals = fo.pixel_evals;
+    }
+    return ASP_OK;
+}
+
 asp_status asp_batch_destroy(asp_batch* b) {
     if (!b) return ASP_ERR_INVALID_ARG;
     cudaSetDevice(b->dev);
@@ -1843,6 +1949,10 @@ asp_status asp_batch_destroy(asp_batch* b) {
     if (b->bars) cudaFree(b->bars);
     if (b->dmap) cudaFree(b->dmap);
     for (void* q : b->mlp_allocs) cudaFree(q);
+    if (b->j_src) cudaFree(b->j_src);
+    if (b->j_wb2) cudaFree(b->j_wb2);
+    if (b->j_T) cudaFree(b->j_T);
+    if (b->j_flux) cudaFree(b->j_flux);
     delete b;
     return ASP_OK;
 }

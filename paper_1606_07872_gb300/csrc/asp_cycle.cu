@@ -490,6 +490,29 @@ cudaError_t launch_deconvolve_ell(const asp_gauss_ell* beam_then_in, int n, asp_
     return cudaGetLastError();
 }
 
+// Eq. 8 per channel for a joint wide-band fit: member k's flux in channel c,
+// F = a_kc w_kc^2 / (alpha_b_c omega_b_c^2) with w_kc^2 = s_k^2 +
+// omega_b_c^2, and the point flag s_k^2 <= 1e-3 min_c omega_b_c^2.  wb
+// holds omega_b_c^2 then alpha_b_c; out: K x C fluxes, then PMAX flags.
+__global__ void k_joint_flux(const FitOut* __restrict__ fo, int K, int C, const double* __restrict__ wb,
+                             double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * C) return;
+    const int k = i / C, c = i - k * C, NPM = 3 + C;
+    const double sk = fo->theta[NPM * k + 2], wb2 = wb[c];
+    out[i] = fo->theta[NPM * k + 3 + c] * (sk * sk + wb2) / (wb[C + c] * wb2);
+    if (c == 0) {
+        double wmin = wb[0];
+        for (int q = 1; q < C; ++q) wmin = fmin(wmin, wb[q]);
+        out[PMAX + k] = sk * sk <= 1e-3 * wmin ? 1.0 : 0.0;
+    }
+}
+
+cudaError_t launch_joint_flux(const FitOut* fo, int K, int C, const double* wb, double* out, cudaStream_t s) {
+    k_joint_flux<<<(K * C + 127) / 128, 128, 0, s>>>(fo, K, C, wb, out);
+    return cudaGetLastError();
+}
+
 // Clears the minor-cycle state (components, retained list, counters) while
 // keeping the beam, the noise threshold and the capacities.
 __global__ void k_reset_state(CycleState* st) {

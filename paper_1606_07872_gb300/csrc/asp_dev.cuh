@@ -53,7 +53,12 @@ struct FitDescHead {
     double omega_min, omega_max;   // trial widths must lie in (omega_min, omega_max]
     double bx0, bx1, by0, by1;     // trial centres must stay inside this box
     int active, smem_ok;
-    int model, pad_model;          // 0: circular members (a, x, y, omega); 1: elliptical (a, x, y, A, B, C)
+    int model, pad_model;          // 0: circular members (a, x, y, omega); 1: elliptical (a, x, y, A, B, C);
+                                   // 2: joint over n_chan channels (x, y, s, a_1 .. a_C)
+    int n_chan, pad_chan;          // model 2: channels, each an image of the same size (row stride src_w)
+    const float* const* chan_src;  // model 2: the channels' images (device array of n_chan pointers)
+    const double* chan_wb2;        // model 2: omega_b^2 of each channel's beam (device)
+    double max_wb2;                // model 2: the largest of them
     double theta0[PMAX];
 };
 // The fit's description plus an optional LM start other than theta0 (which

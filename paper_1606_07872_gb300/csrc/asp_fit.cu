@@ -140,6 +140,19 @@ __device__ __forceinline__ void make_frame_ell(const double* th, MemberFrame& f)
     f.cy = (int)cy;
 }
 
+// Joint member (x, y, s, a_1 .. a_C): the centre frame only; the
+// per-channel amplitude and 1 / omega_kc^2 live in the pass's channel
+// tables.  pa carries s (the Jacobian's d/ds = g r^2 s / omega^4).
+__device__ __forceinline__ void make_frame_mc(const double* th, MemberFrame& f) {
+    const double x = th[0], y = th[1];
+    const double cx = floor(x + 0.5), cy = floor(y + 0.5);
+    f.pa = (float)th[2];
+    f.fx = (float)(x - cx);
+    f.fy = (float)(y - cy);
+    f.cx = (int)cx;
+    f.cy = (int)cy;
+}
+
 // Eigenvalues (mu-, mu+) of the precision matrix [[A, B], [B, C]].
 __device__ __forceinline__ void prec_eig(double A, double B, double C, double& mm, double& mp) {
     const double h = 0.5 * (A + C), r = hypot(0.5 * (A - C), B);
@@ -808,12 +821,14 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     const bool is_spec = spec_on && b == Gp;
     double* const spec_blk = spec_on ? partials + (size_t)Gp * NACC_MAX + SPEC_OFF : nullptr;
 
-    const bool ell = d.model == 1;
-    const int NPM = ell ? 6 : 4;          // parameters per member
+    const bool ell = d.model == 1, mch = d.model == 2;
+    const int NCH = mch ? d.n_chan : 1;   // channels of a joint fit
+    const int NPM = ell ? 6 : mch ? 3 + NCH : 4;   // parameters per member
     const int K = d.K, P = NPM * K, NA = P + 1, NAp = (NA + 3) & ~3, nb = NAp / 4;
     const int ntiles = nb * (nb + 1) / 2;
     const int nacc = ntiles * 16;
-    const long long Wn = (long long)d.ww * d.wh;
+    // a joint fit runs over the window of every channel, channel after channel
+    const long long Wn1 = (long long)d.ww * d.wh, Wn = Wn1 * NCH;
     const long long s0 = is_spec ? Wn : Wn * b / Gp, s1 = is_spec ? Wn : Wn * (b + 1) / Gp;
     const int slen = (int)(s1 - s0);
     const bool in_smem = d.smem_ok != 0;
@@ -867,20 +882,40 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         if (my_group >= n_groups) my_group = -1;
     }
 
+    // joint fits: per (member, channel) amplitude and 1 / omega_kc^2, FP32,
+    // in the step buffer's storage (free from the end of a solve loop to the
+    // next solve)
+    float* const mc_a = reinterpret_cast<float*>(delta);
+    float* const mc_iw2 = mc_a + PMAX;
+
     // ---- stage the target T = src + sum of the added-back members
     if (tid < K) {
         if (ell) make_frame_ell(&d.theta0[NPM * tid], fr[tid]);
+        else if (mch) make_frame_mc(&d.theta0[NPM * tid], fr[tid]);
         else make_frame(&d.theta0[NPM * tid], fr[tid]);
+    }
+    if (mch && tid < K * NCH) {
+        const int k = tid / NCH, c = tid - k * NCH;
+        const double sk = d.theta0[NPM * k + 2];
+        mc_iw2[tid] = (float)(1.0 / (sk * sk + d.chan_wb2[c]));
+        mc_a[tid] = (float)d.theta0[NPM * k + 3 + c];
     }
     __syncthreads();
     for (int i = tid; i < slen; i += blockDim.x) {
         long long gi = s0 + i;
+        int ch = 0;
+        if (mch) { ch = (int)(gi / Wn1); gi -= (long long)ch * Wn1; }
         int y = d.wy0 + (int)(gi / d.ww), x = d.wx0 + (int)(gi % d.ww);
-        float v = src[(long long)y * src_w + x];
+        float v = mch ? d.chan_src[ch][(long long)y * src_w + x] : src[(long long)y * src_w + x];
         for (int m = K - d.n_old; m < K; ++m) {
             const MemberFrame& f = fr[m];
             float dx = (float)(x - f.cx) - f.fx, dy = (float)(y - f.cy) - f.fy;
-            v += f.a * exp2f(ell ? -((f.c * dx + f.cb * dy) * dx + f.cc * dy * dy) : -(dx * dx + dy * dy) * f.c);
+            if (mch) {
+                const int q = m * NCH + ch;
+                v += mc_a[q] * exp2f(-(dx * dx + dy * dy) * (0.5f * (float)LOG2E) * mc_iw2[q]);
+            } else {
+                v += f.a * exp2f(ell ? -((f.c * dx + f.cb * dy) * dx + f.cc * dy * dy) : -(dx * dx + dy * dy) * f.c);
+            }
         }
         if (in_smem) Ts[i] = v; else Tg[gi] = v;
     }
@@ -896,9 +931,10 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
 
     // pixel coordinates of this thread's J row in the first chunk (the only
     // chunk when the slice fits one), computed once for all passes
-    int x_first = 0, y_first = 0;
+    int x_first = 0, y_first = 0, c_first = 0;
     if (tid < CH && tid < slen) {
-        const long long gi = s0 + tid;
+        long long gi = s0 + tid;
+        if (mch) { c_first = (int)(gi / Wn1); gi -= (long long)c_first * Wn1; }
         y_first = d.wy0 + (int)(gi / d.ww);
         x_first = d.wx0 + (int)(gi % d.ww);
     }
@@ -912,7 +948,14 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
         // ================= pixel pass at trial[] =================
         if (tid < K) {
             if (ell) make_frame_ell(&trial[NPM * tid], fr[tid]);
+            else if (mch) make_frame_mc(&trial[NPM * tid], fr[tid]);
             else make_frame(&trial[NPM * tid], fr[tid]);
+        }
+        if (mch && tid < K * NCH) {
+            const int k = tid / NCH, c = tid - k * NCH;
+            const double sk = trial[NPM * k + 2];
+            mc_iw2[tid] = (float)(1.0 / (sk * sk + d.chan_wb2[c]));
+            mc_a[tid] = (float)trial[NPM * k + 3 + c];
         }
         if (tid == (int)blockDim.x - 1 && !first) {
             // the LM decision's FP64 arithmetic (a division among it), done
@@ -958,13 +1001,15 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
             if (tid < CH) {
                 float* row = Jc + tid * JS;
                 bool live = tid < cn;
-                int x = 0, y = 0;
+                int x = 0, y = 0, ch = 0;
                 if (live) {
                     if (c0 == 0) {
                         x = x_first;
                         y = y_first;
+                        ch = c_first;
                     } else {
-                        const long long gi = s0 + c0 + tid;
+                        long long gi = s0 + c0 + tid;
+                        if (mch) { ch = (int)(gi / Wn1); gi -= (long long)ch * Wn1; }
                         y = d.wy0 + (int)(gi / d.ww);
                         x = d.wx0 + (int)(gi % d.ww);
                     }
@@ -973,7 +1018,29 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         live = ddx * ddx + ddy * ddy <= d.mr2;
                     }
                 }
-                if (live && ell) {
+                if (live && mch) {
+                    // joint members in channel ch: d/dx = g dx / w^2,
+                    // d/dy = g dy / w^2, d/ds = g r^2 s / w^4, d/da_k,ch = E;
+                    // every other channel's amplitude column is zero
+                    for (int c = 0; c < NAp; ++c) row[c] = 0.f;
+                    float model = 0.f;
+                    for (int k = 0; k < K; ++k) {
+                        const MemberFrame& f = fr[k];
+                        const int q = k * NCH + ch;
+                        const float dx = (float)(x - f.cx) - f.fx, dy = (float)(y - f.cy) - f.fy;
+                        const float r2 = dx * dx + dy * dy, iw2 = mc_iw2[q];
+                        const float e = exp2f(-r2 * (0.5f * (float)LOG2E) * iw2);
+                        const float g = mc_a[q] * e, giw = g * iw2;
+                        model += g;
+                        float* rk = row + NPM * k;
+                        rk[0] = giw * dx;
+                        rk[1] = giw * dy;
+                        rk[2] = giw * r2 * f.pa * iw2;
+                        rk[3 + ch] = e;
+                    }
+                    float t = in_smem ? Ts[c0 + tid] : Tg[s0 + c0 + tid];
+                    row[P] = t - model;
+                } else if (live && ell) {
                     // elliptical members: d/da = E, d/dx0 = g (A dx + B dy),
                     // d/dy0 = g (B dx + C dy), d/dA = -g dx^2 / 2,
                     // d/dB = -g dx dy, d/dC = -g dy^2 / 2
@@ -1357,7 +1424,11 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 // width (circular); the major width for the centre and
                 // (A + C) / 2 for A, B, C (elliptical)
                 double sc;
-                if (ell) {
+                if (mch) {
+                    // the widest convolved width for x, y, s; |a| for amplitudes
+                    const int j = tid % NPM, base = tid - j;
+                    sc = j < 3 ? sqrt(theta[base + 2] * theta[base + 2] + d.max_wb2) : fabs(theta[tid]);
+                } else if (ell) {
                     const int j = tid % 6, base = tid - j;
                     if (j == 0) {
                         sc = fabs(theta[tid]);
@@ -1377,7 +1448,13 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                 dd_i = dv32[tid] * df * df;
                 trial[tid] = theta[tid] + di;
             }
-            if (ok && tid < K && ell) {
+            if (ok && tid < K && mch) {
+                // centre in the box, every convolved width within the window
+                const int o = NPM * tid;
+                const double x = theta[o] + delta[o], y = theta[o + 1] + delta[o + 1], sv = theta[o + 2] + delta[o + 2];
+                valid_i = isfinite(x) && isfinite(y) && isfinite(sv) && !(x < d.bx0) && !(x > d.bx1) &&
+                          !(y < d.by0) && !(y > d.by1) && !(sv * sv + d.max_wb2 > d.omega_max * d.omega_max);
+            } else if (ok && tid < K && ell) {
                 // positive definite, principal widths 1 / sqrt(mu) in
                 // (omega_min, omega_max], centre in the box
                 const int o = 6 * tid;

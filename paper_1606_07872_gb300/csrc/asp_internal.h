@@ -146,6 +146,7 @@ cudaError_t launch_harvest(const CycleState* st, const float* R, int H, int W, f
                            int capacity, cudaStream_t s);
 cudaError_t launch_beam_init(FitDesc* desc, const float* B, int H, int W, int g_max, cudaStream_t s);
 cudaError_t launch_beam_ell_desc(FitDesc* d, double a, double x, double y, double w, cudaStream_t s);
+cudaError_t launch_joint_flux(const FitOut* fo, int K, int C, const double* wb, double* out, cudaStream_t s);
 cudaError_t launch_deconvolve_ell(const asp_gauss_ell* beam_then_in, int n, asp_component_ell* out, cudaStream_t s);
 cudaError_t launch_radix_median(const float* v, long long n, int absdev, double center, unsigned long long* ws,
                                 double* out, cudaStream_t s);
