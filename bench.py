@@ -56,6 +56,7 @@ def _args():
     ap.add_argument("--fit-px", type=int, default=0, help="LM fit tile: window pixels per CTA (0: library default)")
     ap.add_argument("--no-split", action="store_true", help="skip the minor/major split comparison")
     ap.add_argument("--no-elliptical", action="store_true", help="skip the elliptical-variant comparison")
+    ap.add_argument("--no-joint", action="store_true", help="skip the joint wide-band fit comparison")
     ap.add_argument("--sub", choices=["auto", "direct", "fft"], default="auto",
                     help="residual update form of the measured runs (auto: FFT from 512x512 pixels)")
     ap.add_argument("--no-sub-forms", action="store_true",
@@ -490,6 +491,60 @@ def elliptical_comparison(asp, reps: int = 20) -> dict:
     return out
 
 
+def joint_comparison(asp, C: int = 32, reps: int = 10) -> dict:
+    """The joint wide-band fit against per-channel fits: one field observed
+    in C = 32 channels (the paper's data has 32) of 256x256, each channel's
+    Gaussian PSF narrowing with frequency (sigma 2.0 .. 1.0 px), three
+    members with power-law spectra (index -1 .. 1), noise 5e-3.  Joint: one
+    fit of 3 (3 + C) parameters over all channels' windows.  Per channel:
+    C independent circular fits of the same members (4 parameters each).
+    Both from the same starts, each repeated ``reps`` times through the C
+    ABI; reported: time per fit, LM iterations, and the spread of the
+    members' fitted centres across channels (the joint fit shares one)."""
+    import numpy as np
+    import synth
+    H = W = 256
+    rng = np.random.default_rng(12)
+    nu = np.linspace(1.0, 2.0, C)
+    sig = 2.0 / nu
+    members = [[rng.uniform(110, 146), rng.uniform(110, 146), rng.uniform(1.0, 3.0),
+                *(rng.uniform(0.3, 1.0) * nu ** rng.uniform(-1, 1))] for _ in range(3)]
+    dirty, psf = [], []
+    for c in range(C):
+        src = [(m[3 + c], m[0], m[1], math.hypot(m[2], sig[c]), math.hypot(m[2], sig[c]), 0.0) for m in members]
+        dirty.append(synth.elliptical_field(H, W, src, 5e-3, 100 + c).astype(np.float32))
+        psf.append(synth.gaussian_psf(H, W, sig[c]).astype(np.float32))
+    b = asp.Batch(dirty, psf, noise_sigma=5e-3, k_max=5)
+    init = np.array(members, float)
+    init[:, 0] += 0.3
+    init[:, 1] -= 0.2
+    init[:, 2] *= 1.2
+    init[:, 3:] *= 0.9
+    b.fit_joint(init, 0)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out, flux, pt, info = b.fit_joint(init, 0)
+    t_joint = (time.perf_counter() - t0) / reps
+    views = [b.image(c) for c in range(C)]
+    starts = [[[m[3 + c], m[0], m[1], math.hypot(m[2], sig[c])] for m in init] for c in range(C)]
+    for c in range(C):
+        views[c].fit(starts[c], 0)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        per = [views[c].fit(starts[c], 0) for c in range(C)]
+    t_per = (time.perf_counter() - t0) / reps
+    xs = np.array([[r[1] for r in p[0]] for p in per])        # [C, K] centres of the per-channel fits
+    b.close()
+    return {"channels": C, "image": f"{H}x{W}", "members": len(members),
+            "joint": {"ms": t_joint * 1e3, "lm_iters": info["iters"], "parameters": int(init.size),
+                      "pixel_evals": info["pixel_evals"], "status": info["status"],
+                      "us_per_lm_iter": t_joint * 1e6 / max(info["iters"], 1)},
+            "per_channel": {"ms": t_per * 1e3, "fits": C, "lm_iters": int(sum(p[1]["iters"] for p in per)),
+                            "centre_spread_px": float(np.max(xs.std(axis=0)))},
+            "time_ratio_per_channel_over_joint": t_per / t_joint,
+            "true_centres_x": [float(m[0]) for m in members], "joint_centres_x": [float(r[0]) for r in out]}
+
+
 def learned_comparison(asp, n_train_images: int, seed: int = 0):
     """Learned initial values: harvest (patch, converged fit) pairs from
     GPU runs of config-1 and config-2-style images (seeds >= 10000), train
@@ -857,6 +912,11 @@ def run_ours(a):
             line["elliptical"] = elliptical_comparison(asp)
         except Exception as e:   # report, never hide, a failed comparison
             line["elliptical"] = {"error": repr(e)[:300]}
+    if rank == 0 and main_cfg == 2 and not a.no_joint:
+        try:
+            line["joint"] = joint_comparison(asp)
+        except Exception as e:   # report, never hide, a failed comparison
+            line["joint"] = {"error": repr(e)[:300]}
     if rank == 0 and main_cfg == 2 and not a.no_learned:
         try:
             line["learned"], weights = learned_comparison(asp, a.learned_train_images)
