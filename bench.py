@@ -420,7 +420,24 @@ def batched_comparison(asp, n_images: int, seed0: int = 0, weights=None) -> dict
            "pixel_evals_per_s": sum(s["pixel_evals"] for s in bat) / t_bat,
            "sequential_pixel_evals_per_s": sum(s["pixel_evals"] for s in seq) / t_seq,
            "max_rms_ratio_batch_vs_sequential": max(x / y for x, y in zip(bat_rms, seq_rms)),
+           "mean_rms_ratio_batch_vs_sequential": float(np.mean([x / y for x, y in zip(bat_rms, seq_rms)])),
            "gpu_launches": launches, "autotune": tune}
+    # the work queue: every image's own minor cycle, images on CUDA streams
+    queue = []
+    for lanes, px in ((4, 0), (8, 0), (16, 0), (8, 768), (16, 768)):
+        b.reset()
+        b.run_queue(0, n_lanes=lanes, px_per_cta=px)          # graphs for this lane count and tile
+        t0 = time.perf_counter()
+        q = b.run_queue(n_iter, n_lanes=lanes, px_per_cta=px)
+        t_q = time.perf_counter() - t0
+        q_rms = [float(np.sqrt(np.mean(b.image(i).residual().astype(np.float64) ** 2))) for i in range(n_images)]
+        it_q = sum(x["iterations"] for x in q)
+        queue.append({"lanes": lanes, "px_per_cta": px, "iterations_per_s": it_q / t_q,
+                      "speedup_vs_sequential": (it_q / t_q) / (it_seq / t_seq),
+                      "mean_rms_ratio_vs_sequential": float(np.mean([x / y for x, y in zip(q_rms, seq_rms)])),
+                      "max_rms_ratio_vs_sequential": max(x / y for x, y in zip(q_rms, seq_rms))})
+    out["queue"] = {"runs": queue, "best": max(queue, key=lambda r: r["iterations_per_s"])}
+    b.run_queue(0, n_lanes=1, px_per_cta=0)                   # the images' uncapped defaults back
     if weights is not None:
         b.set_mlp(weights)
         b.reset()

@@ -508,6 +508,22 @@ asp_status asp_batch_image(asp_batch* b, int i, asp_ctx** ctx);
 /* Kernels the batch has launched (graph nodes counted per replay). */
 asp_status asp_batch_launch_count(asp_batch* b, int64_t* n);
 
+/* Work queue over the batch's images: every image runs n_iter iterations
+ * of its own minor cycle (its context's CUDA graph; the same kernels and
+ * the same per-image results as asp_minor_cycle), so images advance
+ * independently and a small image never waits for a large image's fits.
+ * The images go longest first (by pixels) onto the least-loaded of n_lanes
+ * CUDA streams, each lane running its images back to back; the call
+ * synchronises once.  Each image's fit grid is capped at ceil(SMs /
+ * n_lanes) CTAs so that the lanes' cooperative fits run side by side, and
+ * px_per_cta > 0 sets the images' fit window tile (0: their parameters');
+ * both change only the FP32 summation order of the fits, and stay set on
+ * the images' contexts until the next call with other values (n_lanes = 1
+ * and px_per_cta = 0 restore the uncapped defaults).  stats (host, n
+ * entries, may be NULL) as asp_batch_minor_cycle.  Not with learned
+ * initial values (ASP_ERR_UNSUPPORTED). */
+asp_status asp_batch_run_queue(asp_batch* b, int n_iter, int n_lanes, int px_per_cta, asp_cycle_stats* stats);
+
 /* Joint wide-band fit: the batch's images as the C channels of one
  * observation (the paper's data is multi-channel, Sect. 4; its fits are per
  * image).  A joint member has a centre (x, y) and an intrinsic width s

@@ -30,7 +30,7 @@ __all__ = [
     "asp_smooth", "asp_num_scales", "asp_copy_residual", "asp_set_residual", "asp_get_components",
     "asp_get_history", "asp_get_stats", "asp_get_state", "asp_set_state", "asp_save_state", "asp_load_state",
     "asp_get_last_fit", "asp_batch_create", "asp_batch_destroy", "asp_batch_reset", "asp_batch_minor_cycle",
-    "asp_batch_autotune", "asp_batch_image", "asp_batch_launch_count",
+    "asp_batch_autotune", "asp_batch_run_queue", "asp_batch_image", "asp_batch_launch_count",
     "Context", "Batch", "MLP", "mlp_pack", "mlp_unpack",
 ]
 
@@ -429,6 +429,12 @@ def asp_batch_minor_cycle(b, n_iter: int, n_images: int) -> list:
     return [_stats_dict(stats[i]) for i in range(n_images)]
 
 
+def asp_batch_run_queue(b, n_iter: int, n_lanes: int, px_per_cta: int, n_images: int) -> list:
+    stats = (asp_cycle_stats * n_images)()
+    _check(lib().asp_batch_run_queue(b, n_iter, n_lanes, px_per_cta, stats), "asp_batch_run_queue")
+    return [_stats_dict(stats[i]) for i in range(n_images)]
+
+
 def asp_batch_autotune(b, n_trial_iter: int) -> dict:
     t = _lib.asp_batch_tuning()
     _check(lib().asp_batch_autotune(b, n_trial_iter, C.byref(t)), "asp_batch_autotune")
@@ -636,6 +642,11 @@ class Batch:
 
     def autotune(self, n_trial_iter: int = 16) -> dict:
         return asp_batch_autotune(self.h, n_trial_iter)
+
+    def run_queue(self, n_iter: int, n_lanes: int = 8, px_per_cta: int = 0) -> list:
+        """Work queue: every image runs its own minor cycle, the images spread
+        over n_lanes CUDA streams (asp_batch_run_queue)."""
+        return asp_batch_run_queue(self.h, n_iter, n_lanes, px_per_cta, self.n)
 
     def fit_joint(self, init, n_old: int = 0):
         """Joint wide-band fit over the batch's images as channels: rows

@@ -157,6 +157,7 @@ SIGNATURES = {
     "asp_batch_destroy": [_P],
     "asp_batch_reset": [_P],
     "asp_batch_minor_cycle": [_P, _I, C.POINTER(asp_cycle_stats)],
+    "asp_batch_run_queue": [_P, _I, _I, _I, C.POINTER(asp_cycle_stats)],
     "asp_batch_autotune": [_P, _I, C.POINTER(asp_batch_tuning)],
     "asp_batch_image": [_P, _I, C.POINTER(_P)],
     "asp_batch_launch_count": [_P, C.POINTER(C.c_int64)],

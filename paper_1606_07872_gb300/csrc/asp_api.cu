@@ -66,6 +66,7 @@ struct asp_ctx {
     unsigned long long* hist256 = nullptr;
     double* dscalar = nullptr;
     int g_max = 1, tpt = 1, grid_img = 1;
+    int g_alloc = 1;   // fit CTAs the partial-sum buffer holds (g_max may be capped below it)
     cudaGraphExec_t gexec = nullptr;
     int graph_unroll = 8;
     int graph_state = 0;   // 0 untried, 1 usable, -1 unavailable (direct launches)
@@ -544,6 +545,7 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     int bps = 0;
     if (fit_configure(ctx->tpt, &bps) != cudaSuccess || bps < 1) return bail(ASP_ERR_CUDA);
     ctx->g_max = std::min(ctx->num_sms * bps, FIT_GRID_MAX);
+    ctx->g_alloc = ctx->g_max;
 
     // device parameters
     ctx->dp.gain = ctx->p.gain;
@@ -877,7 +879,7 @@ static double ell_sigma_max(const asp_gauss_ell& g) {
 static asp_status ell_variant(asp_ctx* ctx, int K, int* tpt, int* g_max) {
     *tpt = fit_tpt_for((6 * K + 3) / 4);
     int bps = 0;
-    if (fit_configure(*tpt, &bps) != cudaSuccess || bps < 1) return fail(ctx, ASP_ERR_CUDA, "fit variant");
+    if (fit_configure_model(1, *tpt, &bps) != cudaSuccess || bps < 1) return fail(ctx, ASP_ERR_CUDA, "fit variant");
     *g_max = std::min(std::min(ctx->num_sms * bps, FIT_GRID_MAX), ctx->g_max);
     return ASP_OK;
 }
@@ -896,8 +898,8 @@ static asp_status run_fit_ell(asp_ctx* ctx, FitDesc& d, int K, const float* src,
     CK(cudaMemsetAsync(&ctx->st->fout, 0, sizeof(FitOut), ctx->stream));
     {
         Mark m(ctx, KC_FIT);
-        CK(launch_lm_fit(tpt, g_max, src, src_w, &ctx->st->fit, lmc, &ctx->st->fout, ctx->partials, ctx->sums,
-                         ctx->bar, ctx->Tg, ctx->stream));
+        CK(launch_lm_fit_model(1, tpt, g_max, src, src_w, &ctx->st->fit, lmc, &ctx->st->fout, ctx->partials,
+                               ctx->sums, ctx->bar, ctx->Tg, ctx->stream));
     }
     CK(cudaMemcpyAsync(fo, &ctx->st->fout, sizeof(FitOut), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1703,6 +1705,10 @@ struct asp_batch {
     double* j_wb2 = nullptr;     // omega_b^2 then alpha_b per channel
     float* j_T = nullptr;
     double* j_flux = nullptr;    // PMAX fluxes then PMAX point flags (as doubles)
+    // work queue (asp_batch_run_queue): lane streams, the lane count and
+    // window tile the images' graphs were built for
+    std::vector<cudaStream_t> lanes;
+    int q_lanes = 0, q_px = -1;
 };
 
 namespace {
@@ -1896,7 +1902,7 @@ asp_status asp_batch_fit_joint(asp_batch* b, const double* init, int n, int n_ol
     for (int i = 0; i < n * NPM; ++i) d.theta0[i] = init[i];
     const int tpt = fit_tpt_for((n * NPM + 3) / 4);
     int bps = 0;
-    if (fit_configure(tpt, &bps) != cudaSuccess || bps < 1) return batch_fail(b, ASP_ERR_CUDA);
+    if (fit_configure_model(2, tpt, &bps) != cudaSuccess || bps < 1) return batch_fail(b, ASP_ERR_CUDA);
     const int g_max = std::min(std::min(b->num_sms * bps, FIT_GRID_MAX), c0->g_max);
     LMConst lmc = c0->dp.lm;
     int smem_ok = 1;
@@ -1908,8 +1914,8 @@ asp_status asp_batch_fit_joint(asp_batch* b, const double* init, int n, int n_ol
     BK(cudaMemcpyAsync(b->j_wb2, wb.data(), sizeof(double) * 2 * C, cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(&c0->st->fit, &d, sizeof(d), cudaMemcpyHostToDevice, s));
     BK(cudaMemsetAsync(&c0->st->fout, 0, sizeof(FitOut), s));
-    BK(launch_lm_fit(tpt, g_max, c0->R, W, &c0->st->fit, lmc, &c0->st->fout, c0->partials, c0->sums, c0->bar,
-                     b->j_T, s));
+    BK(launch_lm_fit_model(2, tpt, g_max, c0->R, W, &c0->st->fit, lmc, &c0->st->fout, c0->partials, c0->sums,
+                           c0->bar, b->j_T, s));
     BK(launch_joint_flux(&c0->st->fout, n, C, b->j_wb2, b->j_flux, s));
     b->launches += 2;
     FitOut fo;
@@ -1949,6 +1955,7 @@ asp_status asp_batch_destroy(asp_batch* b) {
     if (b->bars) cudaFree(b->bars);
     if (b->dmap) cudaFree(b->dmap);
     for (void* q : b->mlp_allocs) cudaFree(q);
+    for (cudaStream_t l : b->lanes) cudaStreamDestroy(l);
     if (b->j_src) cudaFree(b->j_src);
     if (b->j_wb2) cudaFree(b->j_wb2);
     if (b->j_T) cudaFree(b->j_T);
@@ -2068,6 +2075,89 @@ asp_status asp_batch_minor_cycle(asp_batch* b, int n_iter, asp_cycle_stats* stat
         if (stats) {
             fill_stats(h, &stats[i]);
         }
+    }
+    return first_err;
+}
+
+asp_status asp_batch_run_queue(asp_batch* b, int n_iter, int n_lanes, int px_per_cta, asp_cycle_stats* stats) {
+    if (!b || n_iter < 0 || n_lanes < 1 || n_lanes > 64 || px_per_cta < 0) return ASP_ERR_INVALID_ARG;
+    if (b->broken) return ASP_ERR_STATE;
+    if (b->learned) return ASP_ERR_UNSUPPORTED;   // the batch's network runs in the lock-step iteration
+    cudaSetDevice(b->dev);
+    const int n = (int)b->imgs.size();
+    // lane streams, and each image's fit grid capped so that the lanes'
+    // cooperative fits fit the GPU side by side; the graphs are rebuilt for
+    // the cap (and the window tile) once per configuration
+    while ((int)b->lanes.size() < n_lanes) {
+        cudaStream_t l = nullptr;
+        BK(cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking));
+        b->lanes.push_back(l);
+    }
+    if (b->q_lanes != n_lanes || b->q_px != px_per_cta) {
+        const int cap = std::max(1, (b->num_sms + n_lanes - 1) / n_lanes);
+        for (asp_ctx* c : b->imgs) {
+            c->g_max = std::min(c->g_alloc, cap);
+            c->dp.lm.px_per_cta = px_per_cta > 0 ? px_per_cta : c->p.fit_px_per_cta;
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            c->graph_state = 0;
+            asp_status gs = build_graph(c);
+            if (gs != ASP_OK) return gs;
+        }
+        b->q_lanes = n_lanes;
+        b->q_px = px_per_cta;
+    }
+    // lanes start after the batch stream's earlier work
+    cudaEvent_t ev0;
+    BK(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+    BK(cudaEventRecord(ev0, b->stream));
+    for (int l = 0; l < n_lanes; ++l) BK(cudaStreamWaitEvent(b->lanes[l], ev0, 0));
+    cudaEventDestroy(ev0);
+    // longest first onto the least-loaded lane (cost: image pixels)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->imgs[a]->N > b->imgs[c]->N; });
+    std::vector<long long> load(n_lanes, 0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[l] += b->imgs[i]->N;
+        asp_ctx* c = b->imgs[i];
+        cudaStream_t saved = c->stream;
+        c->stream = b->lanes[l];
+        asp_status es = ASP_OK;
+        if (launch_arm_b(b->d_desc + i, 1, n_iter, c->stream) != cudaSuccess) es = ASP_ERR_CUDA;
+        b->launches += 1;
+        if (es == ASP_OK && n_iter > 0) {
+            if (c->graph_state == 1) {
+                const int reps = (n_iter + c->graph_unroll - 1) / c->graph_unroll;
+                for (int r = 0; r < reps && es == ASP_OK; ++r)
+                    if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) es = ASP_ERR_CUDA;
+                b->launches += (long long)reps * c->graph_kernels;
+            } else {
+                const long long l0 = c->launches;
+                for (int it = 0; it < n_iter && es == ASP_OK; ++it) es = enqueue_iteration(c);
+                b->launches += c->launches - l0;
+            }
+        }
+        c->stream = saved;
+        if (es != ASP_OK) return batch_fail(b, es);
+    }
+    for (int l = 0; l < n_lanes; ++l) {
+        cudaEvent_t ev;
+        BK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        BK(cudaEventRecord(ev, b->lanes[l]));
+        BK(cudaStreamWaitEvent(b->stream, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    BK(cudaStreamSynchronize(b->stream));
+    asp_status first_err = ASP_OK;
+    for (int i = 0; i < n; ++i) {
+        CycleState h;
+        BK(cudaMemcpyAsync(&h, b->imgs[i]->st, sizeof(CycleState), cudaMemcpyDeviceToHost, b->stream));
+        BK(cudaStreamSynchronize(b->stream));
+        if (h.error == ASP_ERR_TIMEOUT) { b->broken = 1; return ASP_ERR_TIMEOUT; }
+        if ((h.error == ASP_ERR_NAN || h.nonfinite) && first_err == ASP_OK) first_err = ASP_ERR_NAN;
+        if (h.stop_reason == ASP_STOP_CAPACITY && first_err == ASP_OK) first_err = ASP_ERR_CAPACITY;
+        if (stats) fill_stats(h, &stats[i]);
     }
     return first_err;
 }

@@ -56,8 +56,14 @@ int sub_h_blen(int W, const SmoothTaps& geo);
 
 // asp_fit.cu
 size_t fit_smem_bytes();
+size_t fit_smem_bytes(int variant);
 int fit_tpt_for(int k_max);
 cudaError_t fit_configure(int tpt, int* blocks_per_sm);
+// the elliptical (model 1) and joint wide-band (model 2) fit kernels
+cudaError_t fit_configure_model(int model, int variant, int* blocks_per_sm);
+cudaError_t launch_lm_fit_model(int model, int tpt, int grid, const float* src, int src_w, const FitDesc* desc,
+                                const LMConst& lmc, FitOut* out, double* partials, double* sums, unsigned* bar,
+                                float* Tg, cudaStream_t s);
 cudaError_t launch_lm_fit_batched(int tpt, const ImgDesc* imgs, const int* dmap, int n, int g_total, unsigned* bars,
                                   cudaStream_t s, int which = 0, int max_iter_override = -1);
 cudaError_t launch_lm_fit_pair(int tpt, int grid, const float* src, int src_w, const LMConst& lmc, const FitDesc* dA,

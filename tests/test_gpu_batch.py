@@ -64,9 +64,10 @@ def test_batch_teacher_forced_per_image(asp):
     b.close()
 
 
-def _teacher_forced(b, cases, n_iter, tight, sample_px=None):
+def _teacher_forced(b, cases, n_iter, tight, sample_px=None, step=None):
     """Per-image teacher-forced checks of n_iter batch iterations (see
-    tests/teacher.py); returns the statistics."""
+    tests/teacher.py; step() advances every image by one, by default one
+    lock-step batch iteration); returns the statistics."""
     views = [b.image(i) for i in range(len(cases))]
     lm = O.lm_exact() if tight else O.LMParams()
     ps = [O.AspParams(k_max=c.k_max, noise_sigma=c.noise_sigma, lm=lm) for c in cases]
@@ -78,7 +79,10 @@ def _teacher_forced(b, cases, n_iter, tight, sample_px=None):
             ab, wb, _, _ = v.beam
             mc, st = teacher.oracle_from_state(v, c, p, (ab, wb))
             recs.append((teacher.oracle_iteration(mc), mc.R.copy(), st))
-        b.minor_cycle(1)
+        if step is None:
+            b.minor_cycle(1)
+        else:
+            step()
         for v, c, (rec, R0, st) in zip(views, cases, recs):
             if rec is None:
                 continue
@@ -160,4 +164,36 @@ def test_batch_learned_equals_single_contexts(asp):
             assert stats[i][k] == st[k], k
         np.testing.assert_array_equal(b.image(i).residual(), ctx.residual())
         ctx.close()
+    b.close()
+
+
+def test_work_queue_equals_each_images_own_run(asp):
+    """The work queue (images on 4 CUDA streams, each running its own minor
+    cycle) computes exactly what each image's context computes alone with
+    the same fit grid cap and window tile: the lanes share no state."""
+    cases = _cases([21, 22, 23, 24, 25, 26], sizes=(64, 96, 128, 256))
+    b = _batch(asp, cases)
+    stats = b.run_queue(30, n_lanes=4, px_per_cta=768)
+    res = [b.image(i).residual() for i in range(len(cases))]
+    comps = [b.image(i).components() for i in range(len(cases))]
+    b.reset()
+    for i in range(len(cases)):
+        st = b.image(i).minor_cycle(30)        # the image's own context, one after another
+        assert st["iterations"] == stats[i]["iterations"] and st["pixel_evals"] == stats[i]["pixel_evals"]
+        np.testing.assert_array_equal(b.image(i).residual(), res[i])
+        np.testing.assert_array_equal(b.image(i).components(), comps[i])
+    b.close()
+
+
+def test_work_queue_teacher_forced_large_images(asp):
+    """Queue mode at config-4 sizes (a 1024^2 and a 2048^2 image beside two
+    small ones, default LM settings): every image's iterations,
+    teacher-forced, agree with the oracle -- decisions exactly, residual
+    updates within 1e-5 relative L2 (the large images' at sampled pixels
+    against the brute-force direct subtraction)."""
+    cases = [synth.config4(s, sizes=(z,)) for s, z in ((31, 256), (32, 1024), (33, 2048), (34, 512))]
+    b = _batch(asp, cases)
+    b.run_queue(3, n_lanes=3)
+    stats = _teacher_forced(b, cases, 2, tight=False, sample_px=256, step=lambda: b.run_queue(1, n_lanes=3))
+    assert stats.updates >= 6
     b.close()

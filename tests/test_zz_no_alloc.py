@@ -73,8 +73,24 @@ def test_static_fit_matches_context_fit_on_two_calls(asp):
     # looked up), then device memory must not change over the later calls
     rc, _, _ = _static_fit(asp, img, calls[0][0], calls[0][1], 0.25 * wb, params)
     assert rc == 0
+    # earlier tests' tensors freed by the garbage collector mid-loop would
+    # move torch's count: collect first, and hold the collector meanwhile
+    import gc
+    gc.collect()
+    gc.disable()
     torch.cuda.synchronize()
     free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    try:
+        _static_calls(asp, img, calls, refs, wb, params)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+    finally:
+        gc.enable()
+    ctx.close()
+
+
+def _static_calls(asp, img, calls, refs, wb, params):
     for (init, n_old), (ref, ref_info) in zip(calls, refs):
         rc, got, info = _static_fit(asp, img, init, n_old, 0.25 * wb, params)
         assert rc == 0, asp._lib.STATUS_NAMES.get(rc, rc)
@@ -83,10 +99,6 @@ def test_static_fit_matches_context_fit_on_two_calls(asp):
         assert info.status == ref_info["status"]
         _close(got, ref)
         assert info.chi2_final == pytest.approx(ref_info["chi2_final"], rel=1e-5)
-    torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.cuda.memory_allocated() == alloc0
-    ctx.close()
 
 
 def test_static_fit_rejects_sizes_beyond_its_limits(asp):
