@@ -102,6 +102,88 @@ __device__ bool make_term(const asp_component& c, double s, int H, int W, int sl
 // update; bytes: each term's PSF region read once, R read and written once.
 // terms: the n_terms descriptors being built (in shared memory, so this
 // single-thread loop does not wait on a global round trip per field).
+// Warp-inclusive scan of a 64-bit count over the 32 lanes.
+__device__ __forceinline__ long long warp_scan_ll(long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// finish_terms by the 32 lanes of a warp: each lane takes terms t = lane,
+// lane + 32, ...; T1 offsets and deposit slots come from warp scans, in
+// term order, so the result is the serial loop's (deposits beyond
+// MAX_DEPOSITS dropped in the same order); the work totals are warp sums.
+__device__ void finish_terms_warp(CycleState* st, TermDesc* terms, int n_terms, int H, int W, int lane) {
+    long long off = 0;
+    int nd = 0;
+    double fl = 0.0, by = 0.0;
+    for (int t0 = 0; t0 < n_terms; t0 += 32) {
+        const int t = t0 + lane;
+        long long rows = 0;
+        int ndep = 0;
+        unsigned dmask = 0;
+        double qx[2] = {0, 0}, qy[2] = {0, 0}, wx[2] = {0, 0}, wy[2] = {0, 0};
+        if (t < n_terms) {
+            TermDesc& td = terms[t];
+            if (td.bilinear) {
+                const double fx0 = floor(td.cx), fy0 = floor(td.cy);
+                const double fx = td.cx - fx0, fy = td.cy - fy0;
+                for (int j = 0; j < 2; ++j)
+                    for (int i = 0; i < 2; ++i) {
+                        const long long ix = (long long)fx0 + i, iy = (long long)fy0 + j;
+                        if (ix < 0 || ix >= W || iy < 0 || iy >= H) continue;
+                        dmask |= 1u << (2 * j + i);
+                        ++ndep;
+                    }
+                qx[0] = fx0; qy[0] = fy0; wx[0] = 1.0 - fx; wx[1] = fx; wy[0] = 1.0 - fy; wy[1] = fy;
+            } else {
+                rows = (long long)(H + td.ny - 1) * W;
+                fl += 2.0 * td.nx * (double)(H + td.ny - 1) * W + 2.0 * td.ny * (double)H * W;
+                by += 4.0 * (double)(H + td.ny - 1) * (W + td.nx - 1);
+            }
+        }
+        const long long rows_incl = warp_scan_ll(rows, lane);
+        const long long dep_incl = warp_scan_ll(ndep, lane);
+        if (t < n_terms) {
+            TermDesc& td = terms[t];
+            if (td.bilinear) {
+                td.t1off = -1;
+                int slot = nd + (int)(dep_incl - ndep);
+                for (int q = 0; q < 4; ++q) {
+                    if (!(dmask & (1u << q))) continue;
+                    if (slot < MAX_DEPOSITS) {
+                        const int i = q & 1, j = q >> 1;
+                        st->dep[slot].qx = (int)((long long)qx[0] + i);
+                        st->dep[slot].qy = (int)((long long)qy[0] + j);
+                        st->dep[slot].w = (float)((double)td.scale * wx[i] * wy[j]);
+                        st->dep[slot].pad = 0;
+                        fl += 2.0 * (double)H * W;
+                        by += 4.0 * (double)H * W;
+                    }
+                    ++slot;
+                }
+            } else {
+                td.t1off = off + rows_incl - rows;
+            }
+        }
+        off += __shfl_sync(0xffffffffu, rows_incl, 31);
+        nd += (int)__shfl_sync(0xffffffffu, dep_incl, 31);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fl += __shfl_xor_sync(0xffffffffu, fl, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
+    }
+    if (lane == 0) {
+        st->n_dep = nd < MAX_DEPOSITS ? nd : MAX_DEPOSITS;
+        st->sub_flops += fl + 2.0 * (double)H * W;
+        st->sub_bytes += by + 8.0 * (double)H * W;
+    }
+}
+
 __device__ void finish_terms(CycleState* st, TermDesc* terms, int n_terms, int H, int W) {
     long long off = 0;
     double fl = 0.0, by = 8.0 * (double)H * W;
@@ -200,15 +282,31 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
     }
     int K = 1;
     const int n_ret = n_ret_;
+    // the retained components staged 256 at a time: the list entries, then
+    // their components, each batch of loads in flight together (two global
+    // round trips per 256 entries instead of two per 32)
+    constexpr int STG = 256;
+    __shared__ int s_rk[STG];
+    __shared__ asp_component s_rc[STG];
     for (int base = 0; base < n_ret && K < p.k_max; base += 32) {
+        if ((base & (STG - 1)) == 0) {
+            __syncwarp();
+            const int c1 = min(n_ret, base + STG);
+#pragma unroll 4
+            for (int r = base + lane; r < c1; r += 32) s_rk[r - base] = st->ret[r];
+            __syncwarp();
+#pragma unroll 4
+            for (int r = base + lane; r < c1; r += 32) s_rc[r - base] = comps[s_rk[r - base]];
+            __syncwarp();
+        }
         const int r = base + lane;
         double g[4] = {0, 0, 0, 0};
         long long b[4] = {0, 0, 0, 0};
         int k = -1;
         bool ok = false;
         if (r < n_ret) {
-            k = st->ret[r];
-            gauss_of(comps[k], ab, wb, g);
+            k = s_rk[r & (STG - 1)];
+            gauss_of(s_rc[r & (STG - 1)], ab, wb, g);
             member_box(g[1], g[2], g[3], b);
             const double dx = g[1] - ix, dy = g[2] - iy;
             const double mw = fmax(iw, g[3]);
@@ -294,31 +392,56 @@ __device__ __forceinline__ void update_body(CycleState* st, asp_component* comps
         s_old[m] = comps[k];
         s_new[m] = deconvolve(g1[0], g1[1], g1[2], g1[3], ab, wb, 1.0);
     }
-    __syncwarp();
-    __shared__ TermDesc s_terms[MAX_TERMS];
-    __shared__ int s_nt;
+    __shared__ asp_component s_cn;
     if (lane == 0) {
-        int nt = 0;
         // new component with the loop gain (Sect. 3, after Eq. 8)
-        const asp_component cn = deconvolve(fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], ab, wb, (double)p.gain);
-        comps[ni] = cn;
+        s_cn = deconvolve(fo.theta[0], fo.theta[1], fo.theta[2], fo.theta[3], ab, wb, (double)p.gain);
+        comps[ni] = s_cn;
         st->n_comp = ni + 1;
-        if (make_term(cn, cn.flux, H, W, nt, s_terms[nt])) ++nt;
-        // old members are replaced by their refit values
-        for (int m = 1; m < K; ++m) {
-            comps[s_member[m]] = s_new[m];
-            if (make_term(s_new[m], s_new[m].flux, H, W, nt, s_terms[nt])) ++nt;
-            if (make_term(s_old[m], -s_old[m].flux, H, W, nt, s_terms[nt])) ++nt;
-        }
-        st->n_terms = nt;
-        // the separable full-PSF passes' layout and work; the minor/major
-        // split subtracts the terms' beam images instead (k_sub_gauss)
-        if (p.major_every == 0) finish_terms(st, s_terms, nt, H, W);
-        st->last_wi = cn.width;
-        s_nt = nt;
+        st->last_wi = s_cn.width;
     }
     __syncwarp();
-    copy_words_warp(st->terms, s_terms, s_nt * (int)sizeof(TermDesc), lane);
+    // the terms in a fixed order -- the new component, then each refit
+    // member's new value and its old value negated -- one candidate per
+    // lane (u = 0; u = 2m - 1, 2m for member m), those whose support meets
+    // the image kept in order by a ballot; old members are replaced by their
+    // refit values
+    __shared__ TermDesc s_terms[MAX_TERMS];
+    const int n_cand = 2 * K - 1;
+    int nt = 0;
+    for (int u0 = 0; u0 < n_cand; u0 += 32) {
+        const int u = u0 + lane;
+        TermDesc td;
+        bool ok = false;
+        if (u < n_cand) {
+            if (u == 0) {
+                ok = make_term(s_cn, s_cn.flux, H, W, 0, td);
+            } else {
+                const int m = (u + 1) >> 1;
+                if (u & 1) {
+                    comps[s_member[m]] = s_new[m];
+                    ok = make_term(s_new[m], s_new[m].flux, H, W, 0, td);
+                } else {
+                    ok = make_term(s_old[m], -s_old[m].flux, H, W, 0, td);
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const int slot = nt + __popc(bal & ((1u << lane) - 1u));
+            td.woff_x = slot * wslot_stride(W, H);
+            td.woff_y = slot * wslot_stride(W, H) + wslot_x_len(W);
+            s_terms[slot] = td;
+        }
+        nt += __popc(bal);
+    }
+    __syncwarp();
+    if (lane == 0) st->n_terms = nt;
+    // the separable full-PSF passes' layout and work; the minor/major split
+    // subtracts the terms' beam images instead (k_sub_gauss)
+    if (p.major_every == 0) finish_terms_warp(st, s_terms, nt, H, W, lane);
+    __syncwarp();
+    copy_words_warp(st->terms, s_terms, nt * (int)sizeof(TermDesc), lane);
     // retained list: new first, then the previous list minus members whose
     // fit moved no parameter by more than tau (order kept)
     const int n_old = st->n_ret;
