@@ -282,31 +282,15 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
     }
     int K = 1;
     const int n_ret = n_ret_;
-    // the retained components staged 256 at a time: the list entries, then
-    // their components, each batch of loads in flight together (two global
-    // round trips per 256 entries instead of two per 32)
-    constexpr int STG = 256;
-    __shared__ int s_rk[STG];
-    __shared__ asp_component s_rc[STG];
     for (int base = 0; base < n_ret && K < p.k_max; base += 32) {
-        if ((base & (STG - 1)) == 0) {
-            __syncwarp();
-            const int c1 = min(n_ret, base + STG);
-#pragma unroll 4
-            for (int r = base + lane; r < c1; r += 32) s_rk[r - base] = st->ret[r];
-            __syncwarp();
-#pragma unroll 4
-            for (int r = base + lane; r < c1; r += 32) s_rc[r - base] = comps[s_rk[r - base]];
-            __syncwarp();
-        }
         const int r = base + lane;
         double g[4] = {0, 0, 0, 0};
         long long b[4] = {0, 0, 0, 0};
         int k = -1;
         bool ok = false;
         if (r < n_ret) {
-            k = s_rk[r & (STG - 1)];
-            gauss_of(s_rc[r & (STG - 1)], ab, wb, g);
+            k = st->ret[r];
+            gauss_of(comps[k], ab, wb, g);
             member_box(g[1], g[2], g[3], b);
             const double dx = g[1] - ix, dy = g[2] - iy;
             const double mw = fmax(iw, g[3]);
