@@ -939,11 +939,18 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     for (int i = tid; i < P; i += blockDim.x) trial[i] = has_start ? descp->start[i] : d.theta0[i];
     __syncthreads();
 
+    // phase A's threads per pixel row (circular members): the members of a
+    // pixel split over TPP adjacent lanes, a power of two with CH TPP <=
+    // the block, so chunks narrower than the block keep every thread busy
+    int TPP = 1;
+    if (!ell && !mch)
+        while (CH * TPP * 2 <= (int)blockDim.x) TPP *= 2;
+    const int lpix = tid / TPP, lq = tid - lpix * TPP;   // this thread's row and member offset
     // pixel coordinates of this thread's J row in the first chunk (the only
     // chunk when the slice fits one), computed once for all passes
     int x_first = 0, y_first = 0, c_first = 0;
-    if (tid < CH && tid < slen) {
-        long long gi = s0 + tid;
+    if (lpix < CH && lpix < slen) {
+        long long gi = s0 + lpix;
         if (mch) { c_first = (int)(gi / Wn1); gi -= (long long)c_first * Wn1; }
         y_first = d.wy0 + (int)(gi / d.ww);
         x_first = d.wx0 + (int)(gi % d.ww);
@@ -1007,10 +1014,10 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
 
         for (int c0 = 0; c0 < slen; c0 += CH) {
             const int cn = min(CH, slen - c0);
-            // phase A: one pixel row of [J | r] per thread
-            if (tid < CH) {
-                float* row = Jc + tid * JS;
-                bool live = tid < cn;
+            // phase A: one pixel row of [J | r] per TPP threads
+            if (lpix < CH) {
+                float* row = Jc + lpix * JS;
+                bool live = lpix < cn;
                 int x = 0, y = 0, ch = 0;
                 if (live) {
                     if (c0 == 0) {
@@ -1018,7 +1025,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         y = y_first;
                         ch = c_first;
                     } else {
-                        long long gi = s0 + c0 + tid;
+                        long long gi = s0 + c0 + lpix;
                         if (mch) { ch = (int)(gi / Wn1); gi -= (long long)ch * Wn1; }
                         y = d.wy0 + (int)(gi / d.ww);
                         x = d.wx0 + (int)(gi % d.ww);
@@ -1048,7 +1055,7 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         rk[2] = giw * r2 * f.pa * iw2;
                         rk[3 + ch] = e;
                     }
-                    float t = in_smem ? Ts[c0 + tid] : Tg[s0 + c0 + tid];
+                    float t = in_smem ? Ts[c0 + lpix] : Tg[s0 + c0 + lpix];
                     row[P] = t - model;
                 } else if (live && ell) {
                     // elliptical members: d/da = E, d/dx0 = g (A dx + B dy),
@@ -1067,13 +1074,16 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         r2p[1] = make_float2(g * (f.pb * dx + f.pc * dy), hg * dx * dx);
                         r2p[2] = make_float2(-g * dx * dy, hg * dy * dy);
                     }
-                    float t = in_smem ? Ts[c0 + tid] : Tg[s0 + c0 + tid];
+                    float t = in_smem ? Ts[c0 + lpix] : Tg[s0 + c0 + lpix];
                     row[P] = t - model;
                     for (int c = P + 1; c < NAp; ++c) row[c] = 0.f;
                 } else if (live) {
+                    // members lq, lq + TPP, ...; the TPP partial model sums
+                    // meet in a butterfly over the row's lanes (every lane
+                    // ends with the same value)
                     float model = 0.f;
 #pragma unroll 4
-                    for (int k = 0; k < K; ++k) {
+                    for (int k = lq; k < K; k += TPP) {
                         const MemberFrame& f = fr[k];
                         float dx = (float)(x - f.cx) - f.fx, dy = (float)(y - f.cy) - f.fy;
                         float r2 = dx * dx + dy * dy;
@@ -1083,11 +1093,17 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
                         float4 jr = make_float4(e, g * dx * f.iw2, g * dy * f.iw2, g * r2 * f.iw3);
                         *reinterpret_cast<float4*>(row + 4 * k) = jr;
                     }
-                    float t = in_smem ? Ts[c0 + tid] : Tg[s0 + c0 + tid];
-                    row[P] = t - model;
-                    for (int c = P + 1; c < NAp; ++c) row[c] = 0.f;
+                    if (TPP > 1) {
+                        const unsigned gm = ((1u << TPP) - 1u) << ((tid & 31) & ~(TPP - 1));
+                        for (int o = TPP >> 1; o > 0; o >>= 1) model += __shfl_xor_sync(gm, model, o);
+                    }
+                    if (lq == 0) {
+                        float t = in_smem ? Ts[c0 + lpix] : Tg[s0 + c0 + lpix];
+                        row[P] = t - model;
+                        for (int c = P + 1; c < NAp; ++c) row[c] = 0.f;
+                    }
                 } else {
-                    for (int c = 0; c < NAp; ++c) row[c] = 0.f;
+                    for (int c = lq; c < NAp; c += TPP) row[c] = 0.f;
                 }
             }
             __syncthreads();
