@@ -567,7 +567,7 @@ def learned_comparison(asp, n_train_images: int, seed: int = 0):
     GPU runs of config-1 and config-2-style images (seeds >= 10000), train
     the network on the GPU, then the equal-RMS protocol on the 1024x1024
     workload (plain for 2000 iterations gives RMS_p; learned until RMS <=
-    1.01 RMS_p or 2000 iterations)."""
+    1.01 RMS_p or 3000 iterations)."""
     from paper_1606_07872_gb300 import learned as L
     import synth
     t0 = time.perf_counter()

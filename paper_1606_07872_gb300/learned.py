@@ -114,12 +114,15 @@ def run_to_rms(case, weights: Optional[dict], target_rms: Optional[float], cap: 
     return out
 
 
-def compare_equal_rms(case, weights: dict, cap: Optional[int] = None, chunk: int = 50) -> dict:
+def compare_equal_rms(case, weights: dict, cap: Optional[int] = None, chunk: int = 50,
+                      learned_cap_factor: float = 1.5) -> dict:
     """The equal-RMS protocol: plain for the cap gives RMS_p; the learned run
-    goes until RMS <= 1.01 RMS_p (or the cap)."""
+    goes until RMS <= 1.01 RMS_p, or learned_cap_factor times the cap (a
+    learned run that needs more iterations than plain still gets its time to
+    equal RMS measured, and loses on it)."""
     cap = int(cap or case.n_iter)
     plain = run_to_rms(case, None, None, cap, chunk)
-    learned = run_to_rms(case, weights, 1.01 * plain["rms"], cap, chunk)
+    learned = run_to_rms(case, weights, 1.01 * plain["rms"], int(learned_cap_factor * cap), chunk)
     return dict(plain=plain, learned=learned,
                 reached=learned["rms"] <= 1.01 * plain["rms"],
                 time_ratio=plain["seconds"] / max(learned["seconds"], 1e-12),

@@ -250,7 +250,7 @@ def test_harvest_records(asp):
 
 def test_equal_rms_protocol_on_a_small_image(asp, capsys):
     """The equal-RMS protocol (the plain cycle for the cap gives RMS_p; the
-    learned one runs until RMS <= 1.01 RMS_p or the cap) on a 256^2 image of
+    learned one runs until RMS <= 1.01 RMS_p or 1.5 x the cap) on a 256^2 image of
     the 1024^2 workload's kind, with a network trained on the GPU from fits
     harvested on disjoint seeds.  The reported quantities must be
     consistent (every used proposal either kept or replaced by the plain
@@ -265,7 +265,7 @@ def test_equal_rms_protocol_on_a_small_image(asp, capsys):
     cap = 300
     res = L.compare_equal_rms(synth.config2(0, size=256), w, cap=cap)
     p, q = res["plain"], res["learned"]
-    assert 0 < p["iterations"] <= cap and 0 < q["iterations"] <= cap
+    assert 0 < p["iterations"] <= cap and 0 < q["iterations"] <= int(1.5 * cap)
     assert q["learned_fits"] > 0
     assert q["learned_kept"] + q["learned_refits"] == q["learned_fits"]
     assert res["reached"] == (q["rms"] <= 1.01 * p["rms"])
