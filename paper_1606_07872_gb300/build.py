@@ -25,6 +25,11 @@ LIB = os.path.join(HERE, "libasp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+# Per-file flags.  The scalar control kernels (deconvolution, terms, active
+# set) are instantiated for contexts and batches alike: without FMA
+# contraction their FP64 arithmetic is the same in every instantiation (and
+# rounds like the FP64 oracle's), whatever the compiler decides elsewhere.
+FILE_FLAGS = {"asp_cycle.cu": ["--fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -57,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     """Compile (if anything changed) and return the path of libasp.so."""
     nvcc = _nvcc()
     os.makedirs(BUILD_DIR, exist_ok=True)
-    hdr_digest = _digest(_headers(), " ".join(NVCC_FLAGS + ARCH))
+    hdr_digest = _digest(_headers(), " ".join(NVCC_FLAGS + ARCH) + repr(sorted(FILE_FLAGS.items())))
     stamp = os.path.join(BUILD_DIR, "stamp")
     srcs = _sources()
     want = _digest(srcs, hdr_digest)
@@ -68,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if ptxas_verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)

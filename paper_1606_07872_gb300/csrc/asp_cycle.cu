@@ -298,25 +298,25 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
             // the sum of their amplitudes determined)
             ok = b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3] && dx * dx + dy * dy > mw * mw;
         }
-        unsigned mask = __ballot_sync(FULL, ok);
-        while (mask != 0u && K < p.k_max) {
-            const int src = __ffs(mask) - 1;
-            double gs[4];
-            long long bs[4];
-            for (int i = 0; i < 4; ++i) {
-                gs[i] = __shfl_sync(FULL, g[i], src);
-                bs[i] = __shfl_sync(FULL, b[i], src);
-            }
-            const int ks = __shfl_sync(FULL, k, src);
-            if (lane == 0) {
-                for (int i = 0; i < 4; ++i) f.theta0[4 * K + i] = gs[i];
-                st->members[K] = ks;
-            }
-            wx0 = min(wx0, bs[0]); wx1 = max(wx1, bs[1]);
-            wy0 = min(wy0, bs[2]); wy1 = max(wy1, bs[3]);
-            ++K;
-            mask &= mask - 1u;
+        // the first k_max - K overlapping entries in list order: each taken
+        // lane writes its own member slot; the window grows by warp min/max
+        // reductions over the taken lanes' boxes (image coordinates fit int)
+        const unsigned mask = __ballot_sync(FULL, ok);
+        const int rank = __popc(mask & ((1u << lane) - 1u));
+        const bool take = ok && rank < p.k_max - K;
+        if (take) {
+            const int slot = K + rank;
+            for (int i = 0; i < 4; ++i) f.theta0[4 * slot + i] = g[i];
+            st->members[slot] = k;
         }
+        const int big = 0x3fffffff;
+        const int c0 = take ? (int)max(b[0], (long long)-big) : big, c1 = take ? (int)min(b[1], (long long)big) : -big;
+        const int c2 = take ? (int)max(b[2], (long long)-big) : big, c3 = take ? (int)min(b[3], (long long)big) : -big;
+        wx0 = min(wx0, (long long)__reduce_min_sync(FULL, c0));
+        wx1 = max(wx1, (long long)__reduce_max_sync(FULL, c1));
+        wy0 = min(wy0, (long long)__reduce_min_sync(FULL, c2));
+        wy1 = max(wy1, (long long)__reduce_max_sync(FULL, c3));
+        K += __popc(__ballot_sync(FULL, take));
     }
     if (lane != 0) return;
     wx0 = max(wx0, 0LL); wy0 = max(wy0, 0LL);
