@@ -395,14 +395,19 @@ cudaError_t launch_major(const asp_component* comps, float2* norms, CycleState* 
 cudaError_t launch_sub_fft(CycleState* st, const int* gate, const float* wbuf, int H, int W, float* pad_in,
                            cufftComplex* work, const cufftComplex* bhat, float* conv_out, float* R, cufftHandle r2c,
                            cufftHandle c2r, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
-    k_delta_image<<<grid, 256, 0, s>>>(st, gate, wbuf, H, W, pad_in);
+    // grid = 4 blocks per SM: the change image (often a few tiles) with one
+    // block per SM, so few blocks stage the terms for nothing; the residual
+    // pass with two per SM, several float4 per thread and fewer argmax
+    // partials for the last block to reduce
+    const int g_sm = grid >= 4 ? grid / 4 : 1, g_sub = grid >= 2 ? grid / 2 : 1;
+    k_delta_image<<<g_sm, 256, 0, s>>>(st, gate, wbuf, H, W, pad_in);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cufftSetStream(r2c, s) != CUFFT_SUCCESS || cufftSetStream(c2r, s) != CUFFT_SUCCESS) return cudaErrorUnknown;
     if (cufftExecR2C(r2c, pad_in, work) != CUFFT_SUCCESS) return cudaErrorUnknown;
     k_fft_mul<<<grid, 256, 0, s>>>(work, bhat, (long long)(2 * H) * (W + 1));
     if (cufftExecC2R(c2r, work, conv_out) != CUFFT_SUCCESS) return cudaErrorUnknown;
-    return launch_fft_sub_argmax(R, conv_out, H, W, st, gate, grid, part, ticket, s);
+    return launch_fft_sub_argmax(R, conv_out, H, W, st, gate, g_sub, part, ticket, s);
 }
 
 // The PSF's transform: B (2H x 2W) through the forward plan into bhat, with
