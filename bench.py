@@ -57,6 +57,9 @@ def _args():
     ap.add_argument("--no-split", action="store_true", help="skip the minor/major split comparison")
     ap.add_argument("--no-elliptical", action="store_true", help="skip the elliptical-variant comparison")
     ap.add_argument("--no-joint", action="store_true", help="skip the joint wide-band fit comparison")
+    ap.add_argument("--large-fit", type=int, default=0,
+                    help="only run one LM step of this many members over a ~950^2 window of a 2048^2 image "
+                         "(k_max 50: the large fit variant), for profiling, and print its outcome")
     ap.add_argument("--sub", choices=["auto", "direct", "fft"], default="auto",
                     help="residual update form of the measured runs (auto: FFT from 512x512 pixels)")
     ap.add_argument("--no-sub-forms", action="store_true",
@@ -958,8 +961,38 @@ def run_ours(a):
     return 0
 
 
+def large_fit_probe(K: int) -> dict:
+    """One LM step (the start's pass, one damped solve, the trial's pass) of
+    K members over a ~950^2 window: K circular sources of width 40 px
+    (synth.elliptical_field, seed 0, noise 1e-2) on a 2048^2 image with a
+    Gaussian PSF of width 2, context k_max 50; the start has the sources'
+    amplitudes x 0.9, centres shifted by half a pixel and width 42."""
+    import numpy as np
+    import torch
+    import paper_1606_07872_gb300 as asp
+    import synth
+    H = W = 2048
+    rng = np.random.default_rng(0)
+    src = [(rng.uniform(0.3, 1.0), rng.uniform(700, 1350), rng.uniform(700, 1350), 40.0, 40.0, 0.0)
+           for _ in range(K)]
+    dirty = synth.elliptical_field(H, W, src, 1e-2, 3).astype(np.float32)
+    psf = synth.gaussian_psf(H, W, 2.0).astype(np.float32)
+    ctx = asp.Context(torch.from_numpy(dirty).cuda(), torch.from_numpy(psf).cuda(), noise_sigma=1e-2, k_max=50)
+    init = [[a * 0.9, x + 0.5, y - 0.5, 42.0] for a, x, y, *_ in src]
+    t0 = time.perf_counter()
+    _, info = ctx.fit_lm(init, 0, 1e-3, 1)[:2]
+    t = time.perf_counter() - t0
+    ctx.close()
+    P = 4 * K
+    return {"members": K, "ms": t * 1e3, "info": info,
+            "tflops": info["pixel_evals"] * (15 * K + 1 + (P + 1) * (P + 2)) / t / 1e12}
+
+
 def main():
     a = _args()
+    if a.large_fit:
+        print(json.dumps(large_fit_probe(a.large_fit)))
+        return 0
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)
