@@ -997,6 +997,8 @@ def large_fit_probe(K: int) -> dict:
 def main():
     a = _args()
     if a.large_fit:
+        from paper_1606_07872_gb300 import build as _b
+        _b.build()
         print(json.dumps(large_fit_probe(a.large_fit)))
         return 0
     if a.impl == "reference":
