@@ -751,11 +751,15 @@ def _metric(case, config: int) -> str:
     return f"minor-cycle iterations/s (Asp-Clean2016, {case.H}x{case.W}, active set <= {case.k_max})"
 
 
-def _config(case, config: int, n_iter: int, world: int) -> dict:
+def _config(case, config: int, n_iter: int, world: int, sub: int = 0) -> dict:
+    """The workload's config block; `residual_update` names the update form
+    a default context of this size takes (the same in both arms, so that
+    their configs compare equal)."""
+    form = "fft" if (sub == 2 or (sub == 0 and case.H * case.W >= 512 * 512)) else "direct"
     return {"workload": f"config{config} {case.H}x{case.W} Asp-Clean2016 minor cycle, k_max {case.k_max}, "
                         f"{n_iter} iterations/step, gain {case.gain}",
             "global_batch": world, "seq_len": None, "parallelism": f"replicas x{world}",
-            "l2": "flushed (256 MB write) between steps, outside timing"}
+            "l2": "flushed (256 MB write) between steps, outside timing", "residual_update": form}
 
 
 def workload_line(a, m: dict, case, world: int, peaks: dict, peak_kind: str, alu: dict, name: str) -> dict:
