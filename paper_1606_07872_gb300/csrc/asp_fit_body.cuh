@@ -940,11 +940,15 @@ __device__ __forceinline__ void lm_fit_body(const float* __restrict__ src, int s
     __syncthreads();
 
     // phase A's threads per pixel row (circular members): the members of a
-    // pixel split over TPP adjacent lanes, a power of two with CH TPP <=
-    // the block, so chunks narrower than the block keep every thread busy
+    // pixel split over TPP adjacent lanes, a power of two (at most 8) with
+    // TPP times the rows a chunk holds (the slice's, if it is shorter than
+    // a chunk) within the block, so narrow chunks and short slices keep the
+    // threads busy
     int TPP = 1;
-    if (!ell && !mch)
-        while (CH * TPP * 2 <= (int)blockDim.x) TPP *= 2;
+    if (!ell && !mch) {
+        const int rows = max(1, min(CH, slen));   // rows a chunk of this slice fills
+        while (rows * TPP * 2 <= (int)blockDim.x && TPP < 8) TPP *= 2;
+    }
     const int lpix = tid / TPP, lq = tid - lpix * TPP;   // this thread's row and member offset
     // pixel coordinates of this thread's J row in the first chunk (the only
     // chunk when the slice fits one), computed once for all passes
