@@ -66,6 +66,8 @@ struct asp_ctx {
     unsigned long long* hist256 = nullptr;
     double* dscalar = nullptr;
     int g_max = 1, tpt = 1, grid_img = 1;
+    int grid_sh = 1, grid_sv = 1;   // smoothing passes: resident blocks (<= grid_img)
+    unsigned* sched = nullptr;      // smoothing task counters: row pass [0, 1], column pass [2, 3]
     int g_alloc = 1;   // fit CTAs the partial-sum buffer holds (g_max may be capped below it)
     cudaGraphExec_t gexec = nullptr;
     int graph_unroll = 8;
@@ -278,10 +280,10 @@ asp_status enqueue_iteration(asp_ctx* ctx) {
     CycleState* st = ctx->st;
     cudaStream_t s = ctx->stream;
     { Mark m(ctx, KC_BEGIN); CK(launch_cycle_begin(st, ctx->dp, H, W, ctx->smooth_flops, s)); }
-    { Mark m(ctx, KC_SMOOTH_H); CK(launch_smooth_h(ctx->R, H, W, ctx->taps, &st->skip_smooth, -1, ctx->S1, ctx->grid_img, s)); }
+    { Mark m(ctx, KC_SMOOTH_H); CK(launch_smooth_h(ctx->R, H, W, ctx->taps, &st->skip_smooth, -1, ctx->S1, ctx->grid_sh, ctx->sched, s)); }
     { Mark m(ctx, KC_SMOOTH_V);
-      CK(launch_smooth_v(ctx->S1, H, W, ctx->taps, st, &st->skip_smooth, -1, nullptr, ctx->grid_img, ctx->part,
-                         ctx->ticket, s)); }
+      CK(launch_smooth_v(ctx->S1, H, W, ctx->taps, st, &st->skip_smooth, -1, nullptr, ctx->grid_sv, ctx->part,
+                         ctx->ticket, ctx->sched + 2, s)); }
     { Mark m(ctx, KC_SELECT); CK(launch_select(st, ctx->comps, ctx->dp, H, W, ctx->g_max, s)); }
     if (ctx->learned) {
         // the network's proposal, then the fits from the learned and the
@@ -452,6 +454,8 @@ asp_status setup_taps(asp_ctx* ctx) {
         const int last = 8 * t.tpr + t.t8max + 7;          // largest staged index
         t.blen = last + (last >> 3) + 1;
     }
+    // the paired row pass doubles the taps and the segment buffers
+    t.pair_h = 2 * ((size_t)t.t8max + (size_t)t.rpb * t.blen) * sizeof(float) <= 48 * 1024;
     t.mpad = ((m_max + 7) & ~7) + 8;
     t.s1rows = (long long)H + 2LL * t.mpad + 8;
     if (taps.size() > ctx->taps_cap) {
@@ -469,8 +473,9 @@ asp_status setup_taps(asp_ctx* ctx) {
     }
     // the halo rows stay zero: only interior rows are ever written
     CK(cudaMemset(ctx->S1, 0, s1_need * sizeof(float)));
-    const size_t smem_h = ((size_t)t.t8max + (size_t)t.rpb * t.blen) * sizeof(float);
-    if (smem_h > 48 * 1024) return ASP_ERR_UNSUPPORTED;
+    if (smooth_h_smem(t) > 48 * 1024) return ASP_ERR_UNSUPPORTED;
+    ctx->grid_sh = smooth_grid_h(t, ctx->num_sms, ctx->grid_img);
+    ctx->grid_sv = smooth_grid_v(t, ctx->num_sms, ctx->grid_img);
     CK(cudaMemcpy(ctx->taps_dev, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice));
     t.k = ctx->taps_dev;
     ctx->taps = t;
@@ -583,6 +588,7 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     AL(ctx->Tg, 4 * N);   // window targets beyond shared memory (image or PSF windows)
     AL(ctx->part, std::max(ctx->grid_img, ctx->g_max));
     AL(ctx->ticket, 1);
+    AL(ctx->sched, 4);
     AL(ctx->hist256, 260);
     AL(ctx->dscalar, 4);
 #undef AL
@@ -590,7 +596,8 @@ static asp_status init_common(const asp_params* pin, int H, int W, const float* 
     if (cudaMemcpyAsync(ctx->R, dirty, N * sizeof(float), kind, ctx->stream) != cudaSuccess ||
         cudaMemcpyAsync(ctx->B, psf, 4 * N * sizeof(float), kind, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->st, 0, sizeof(CycleState), ctx->stream) != cudaSuccess ||
-        cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream) != cudaSuccess)
+        cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->sched, 0, 4 * sizeof(unsigned), ctx->stream) != cudaSuccess)
         return bail(ASP_ERR_CUDA);
 
     if (ctx->p.major_every > 0 || ctx->sub_fft) {
@@ -723,12 +730,12 @@ asp_status asp_find_peak(asp_ctx* ctx, int mode, asp_peak* out) {
     }
     {
         Mark m(ctx, KC_SMOOTH_H);
-        CK(launch_smooth_h(ctx->R, ctx->H, ctx->W, ctx->taps, nullptr, -1, ctx->S1, ctx->grid_img, ctx->stream));
+        CK(launch_smooth_h(ctx->R, ctx->H, ctx->W, ctx->taps, nullptr, -1, ctx->S1, ctx->grid_sh, ctx->sched, ctx->stream));
     }
     {
         Mark m(ctx, KC_SMOOTH_V);
-        CK(launch_smooth_v(ctx->S1, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, -1, nullptr, ctx->grid_img, ctx->part,
-                           ctx->ticket, ctx->stream));
+        CK(launch_smooth_v(ctx->S1, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, -1, nullptr, ctx->grid_sv, ctx->part,
+                           ctx->ticket, ctx->sched + 2, ctx->stream));
     }
     asp_status s = read_state(ctx, &h);
     if (s != ASP_OK) return s;
@@ -1353,12 +1360,13 @@ asp_status asp_smooth(asp_ctx* ctx, int scale_index, float* out_dev) {
     if (scale_index < 0 || scale_index >= ctx->taps.n || !out_dev) return ASP_ERR_INVALID_ARG;
     {
         Mark m(ctx, KC_SMOOTH_H);
-        CK(launch_smooth_h(ctx->R, ctx->H, ctx->W, ctx->taps, nullptr, scale_index, ctx->S1, ctx->grid_img, ctx->stream));
+        CK(launch_smooth_h(ctx->R, ctx->H, ctx->W, ctx->taps, nullptr, scale_index, ctx->S1, ctx->grid_sh, ctx->sched,
+                           ctx->stream));
     }
     {
         Mark m(ctx, KC_SMOOTH_V);
-        CK(launch_smooth_v(ctx->S1, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, scale_index, out_dev, ctx->grid_img,
-                           ctx->part, ctx->ticket, ctx->stream));
+        CK(launch_smooth_v(ctx->S1, ctx->H, ctx->W, ctx->taps, ctx->st, nullptr, scale_index, out_dev, ctx->grid_sv,
+                           ctx->part, ctx->ticket, ctx->sched + 2, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return ASP_OK;
@@ -2020,9 +2028,8 @@ asp_status asp_batch_create(const asp_params* params, int n, const int* H, const
         g.part = c->part; g.ticket = c->ticket;
         g.dp = c->dp;
         g.sub_blen = sub_h_blen(c->W, c->taps);
-        b->smem_smooth_h = std::max(b->smem_smooth_h,
-                                    ((size_t)c->taps.t8max + (size_t)c->taps.rpb * c->taps.blen) * sizeof(float));
-        b->smem_smooth_v = std::max(b->smem_smooth_v, (size_t)c->taps.t8max * sizeof(float));
+        b->smem_smooth_h = std::max(b->smem_smooth_h, smooth_h_smem(c->taps));
+        b->smem_smooth_v = std::max(b->smem_smooth_v, smooth_v_smem(c->taps));
         b->smem_sub_h = std::max(b->smem_sub_h, (size_t)c->taps.rpb * g.sub_blen * sizeof(float));
         n_max = std::max(n_max, c->N);
     }

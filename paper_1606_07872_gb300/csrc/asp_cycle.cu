@@ -11,7 +11,9 @@
 //                  component list / retained list updates, and the separable
 //                  subtraction terms dC = gain c_new + sum_old (c'_k - c_k);
 //   k_build_weights the sampled, flux-normalised axis weights of each term.
-// These are scalar control kernels: one thread (or one block per term).
+// These are control kernels: one thread, one warp or one block (k_select
+// scans the retained list with a block; k_build_weights takes a block per
+// term).
 #include <cuda_bf16.h>
 
 #include "asp_dev.cuh"
@@ -22,6 +24,7 @@ namespace aspd {
 namespace {
 
 constexpr double TWO_PI = 6.283185307179586477;
+constexpr int SELECT_THREADS = 256;   // k_select: retained members tested at once
 
 // Single-Gaussian image of a component: (alpha_b omega_b^2 F / w_ic^2, x, y,
 // w_ic) with w_ic^2 = w_i^2 + omega_b^2 (Eqs. 7-8 inverted).
@@ -262,11 +265,14 @@ __global__ void k_cycle_begin(CycleState* st, Params p, int H, int W, double smo
 
 __device__ __forceinline__ void select_body(CycleState* st, const asp_component* __restrict__ comps, Params p, int H, int W,
                          int g_max) {
-    // one warp: lanes test 32 retained members at a time; the first ones in
-    // list order (most recent first) are taken, as in a sequential scan
+    // the block's threads test blockDim.x retained members at a time; the
+    // first ones in list order (most recent first) are taken, as in a
+    // sequential scan: a member's rank is the number of overlapping members
+    // before it in the list (warp ballots plus the warps before it)
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x >= 32) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+    __shared__ int s_cnt[2][32];      // per warp: overlapping members, taken members
+    __shared__ int s_box[4][32];      // per warp: bounds of the taken members' boxes
     // the fields read before the first branch, so their loads go out together
     const int stopped = st->stopped, n_ret_ = st->n_ret;
     const double ab = st->alpha_b, wb = st->omega_b;
@@ -276,14 +282,14 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
     long long nb[4];
     member_box(ix, iy, iw, nb);
     long long wx0 = nb[0], wx1 = nb[1], wy0 = nb[2], wy1 = nb[3];
-    if (lane == 0) {
+    if (tid == 0) {
         for (int i = 0; i < 4; ++i) f.theta0[i] = st->init[i];
         st->members[0] = -1;
     }
     int K = 1;
     const int n_ret = n_ret_;
-    for (int base = 0; base < n_ret && K < p.k_max; base += 32) {
-        const int r = base + lane;
+    for (int base = 0; base < n_ret && K < p.k_max; base += blockDim.x) {
+        const int r = base + tid;
         double g[4] = {0, 0, 0, 0};
         long long b[4] = {0, 0, 0, 0};
         int k = -1;
@@ -298,11 +304,15 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
             // the sum of their amplitudes determined)
             ok = b[0] <= nb[1] && nb[0] <= b[1] && b[2] <= nb[3] && nb[2] <= b[3] && dx * dx + dy * dy > mw * mw;
         }
-        // the first k_max - K overlapping entries in list order: each taken
-        // lane writes its own member slot; the window grows by warp min/max
-        // reductions over the taken lanes' boxes (image coordinates fit int)
         const unsigned mask = __ballot_sync(FULL, ok);
-        const int rank = __popc(mask & ((1u << lane) - 1u));
+        if (lane == 0) s_cnt[0][warp] = __popc(mask);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += s_cnt[0][w];
+        // the first k_max - K overlapping entries in list order: each taken
+        // thread writes its own member slot; the window grows by min/max
+        // reductions over the taken threads' boxes (image coordinates fit int)
+        const int rank = before + __popc(mask & ((1u << lane) - 1u));
         const bool take = ok && rank < p.k_max - K;
         if (take) {
             const int slot = K + rank;
@@ -312,13 +322,24 @@ __device__ __forceinline__ void select_body(CycleState* st, const asp_component*
         const int big = 0x3fffffff;
         const int c0 = take ? (int)max(b[0], (long long)-big) : big, c1 = take ? (int)min(b[1], (long long)big) : -big;
         const int c2 = take ? (int)max(b[2], (long long)-big) : big, c3 = take ? (int)min(b[3], (long long)big) : -big;
-        wx0 = min(wx0, (long long)__reduce_min_sync(FULL, c0));
-        wx1 = max(wx1, (long long)__reduce_max_sync(FULL, c1));
-        wy0 = min(wy0, (long long)__reduce_min_sync(FULL, c2));
-        wy1 = max(wy1, (long long)__reduce_max_sync(FULL, c3));
-        K += __popc(__ballot_sync(FULL, take));
+        const int m0 = __reduce_min_sync(FULL, c0), m1 = __reduce_max_sync(FULL, c1);
+        const int m2 = __reduce_min_sync(FULL, c2), m3 = __reduce_max_sync(FULL, c3);
+        const int nt = __popc(__ballot_sync(FULL, take));
+        if (lane == 0) {
+            s_box[0][warp] = m0; s_box[1][warp] = m1; s_box[2][warp] = m2; s_box[3][warp] = m3;
+            s_cnt[1][warp] = nt;
+        }
+        __syncthreads();
+        for (int w = 0; w < nw; ++w) {
+            K += s_cnt[1][w];
+            wx0 = min(wx0, (long long)s_box[0][w]);
+            wx1 = max(wx1, (long long)s_box[1][w]);
+            wy0 = min(wy0, (long long)s_box[2][w]);
+            wy1 = max(wy1, (long long)s_box[3][w]);
+        }
+        __syncthreads();                  // s_cnt and s_box are rewritten by the next chunk
     }
-    if (lane != 0) return;
+    if (tid != 0) return;
     wx0 = max(wx0, 0LL); wy0 = max(wy0, 0LL);
     wx1 = min(wx1, (long long)W - 1); wy1 = min(wy1, (long long)H - 1);
     f.K = K;
@@ -724,7 +745,7 @@ cudaError_t launch_cycle_begin_b(const ImgDesc* imgs, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_select_b(const ImgDesc* imgs, int n, cudaStream_t s) {
-    k_select_b<<<dim3(1, n), 32, 0, s>>>(imgs);
+    k_select_b<<<dim3(1, n), SELECT_THREADS, 0, s>>>(imgs);
     return cudaGetLastError();
 }
 cudaError_t launch_update_b(const ImgDesc* imgs, int n, cudaStream_t s) {
@@ -938,7 +959,7 @@ cudaError_t launch_cycle_begin(CycleState* st, const Params& p, int H, int W, do
 
 cudaError_t launch_select(CycleState* st, const asp_component* comps, const Params& p, int H, int W, int g_max,
                           cudaStream_t s) {
-    k_select<<<1, 32, 0, s>>>(st, comps, p, H, W, g_max);
+    k_select<<<1, SELECT_THREADS, 0, s>>>(st, comps, p, H, W, g_max);
     return cudaGetLastError();
 }
 

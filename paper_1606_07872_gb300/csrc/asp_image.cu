@@ -105,6 +105,38 @@ k_argmax_abs(const float* __restrict__ R, long long N, ArgRes* part, unsigned* t
 // so the 32 lanes of a warp hit 32 different banks.
 __device__ __forceinline__ int spad(int q) { return q + (q >> 3); }
 
+// Task order of the smoothing passes.  Tasks are numbered scale by scale,
+// and a task's cost grows with its scale (20x from the first scale to the
+// sixth).  With a counter (sched[0]), thread 0 takes the next task,
+// costliest first, so a block that finishes early takes more and the SMs
+// end together.  The block that leaves last resets the counter and its exit
+// count (sched[1]) for the next launch.  Without a counter the blocks stride
+// over the tasks.  Both forms begin with the block barrier that orders the
+// previous task's shared-memory reads before the next task's writes.
+__device__ __forceinline__ long long next_task(unsigned* sched, long long r, long long total) {
+    __shared__ long long s_task;
+    __syncthreads();
+    if (sched == nullptr) {
+        const long long t = r * gridDim.x + blockIdx.x;
+        return t < total ? t : -1;
+    }
+    if (threadIdx.x == 0) {
+        const long long t = (long long)atomicAdd(sched, 1u);
+        s_task = t < total ? total - 1 - t : -1;
+    }
+    __syncthreads();
+    return s_task;
+}
+__device__ __forceinline__ void end_tasks(unsigned* sched) {
+    if (sched == nullptr || threadIdx.x != 0) return;
+    __threadfence();                                  // this block's last fetch before its exit count
+    if (atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+        __threadfence();
+        atomicExch(sched, 0u);
+        atomicExch(sched + 1, 0u);
+    }
+}
+
 // 8 outputs x 8 taps of a correlation: acc[i] += sum_d k[d] x[i + d], the 16
 // inputs x[0..15] given as two 8-register banks (lo, hi).
 __device__ __forceinline__ void conv8k(float (&acc)[8], const float (&lo)[8], const float (&hi)[8],
@@ -130,6 +162,33 @@ __device__ __forceinline__ void conv8s(float (&acc)[8], const float (&lo)[8], co
 __device__ __forceinline__ void load_rows8(float (&b)[8], const float* __restrict__ p, int W) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) b[i] = __ldg(p + (long long)i * W);
+}
+
+// conv8k for two independent output streams at once (two rows, or two
+// columns) with Blackwell's packed two-lane FP32 FMA.  Each lane rounds
+// like fmaf and the taps are applied in the same order, so every output has
+// the bits of the scalar pass, with half the FMA instructions.  k16 holds
+// the 8 taps each written twice (k0 k0 k1 k1 ...), 16-byte aligned.
+__device__ __forceinline__ void conv8k2(float2 (&acc)[8], const float2 (&lo)[8], const float2 (&hi)[8],
+                                        const float* k16) {
+    const float4* k4 = reinterpret_cast<const float4*>(k16);
+    float2 kk[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = k4[q];
+        kk[2 * q] = make_float2(v.x, v.y);
+        kk[2 * q + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = __ffma2_rn(kk[d], i + d < 8 ? lo[i + d] : hi[i + d - 8], acc[i]);
+}
+
+// 8 consecutive rows of two adjacent columns (8-byte aligned) into a bank.
+__device__ __forceinline__ void load_rows8x2(float2 (&b)[8], const float* __restrict__ p, int W) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = __ldg(reinterpret_cast<const float2*>(p + (long long)i * W));
 }
 
 // ------------------------------------------------------------------ subtraction
@@ -374,10 +433,10 @@ cudaError_t launch_fft_sub_argmax(float* R, const float* conv, int H, int W, Cyc
 // Row pass: S1_j[y + mpad][x] = sum_u k_j[u] R[y][x + u - m_j].  A block
 // task is rpb row segments of 8 tpr outputs each; the segment with its
 // halo is staged in shared memory.  Blocks loop over the tasks of every
-// scale (or only_scale).
-__device__ __forceinline__ void smooth_h_body(const float* __restrict__ R, int H, int W, const SmoothTaps& taps, const int* gate,
-           int only_scale, float* __restrict__ S1) {
-    if (gate && *gate) return;
+// scale (or only_scale).  This form takes one row per thread; the paired
+// form below (the default where its buffers fit) two.
+__device__ __forceinline__ void smooth_h_single(const float* __restrict__ R, int H, int W, const SmoothTaps& taps,
+                                                int only_scale, float* __restrict__ S1, unsigned* sched) {
     extern __shared__ __align__(16) float sm_h[];
     float* ktap = sm_h;
     const int tid = threadIdx.x;
@@ -387,14 +446,15 @@ __device__ __forceinline__ void smooth_h_body(const float* __restrict__ R, int H
     const int j0 = only_scale >= 0 ? only_scale : 0, nj = only_scale >= 0 ? 1 : taps.n;
     const long long rowtasks = (long long)H * nseg;
     const long long btasks = (rowtasks + rpb - 1) / rpb;
-    for (long long task = blockIdx.x; task < nj * btasks; task += gridDim.x) {
+    for (long long r = 0;; ++r) {
+        const long long task = next_task(sched, r, nj * btasks);
+        if (task < 0) break;
         const int j = j0 + (int)(task / btasks);
         const long long rt = (task % btasks) * rpb + sub;
         const int m = taps.m[j], t8 = taps.t8[j];
         const bool live = sub < rpb && rt < rowtasks;
         const int y = live ? (int)(rt / nseg) : 0;
         const int xs = live ? (int)(rt % nseg) * 8 * tpr : 0;
-        __syncthreads();                                     // previous task's reads are done
         const float* kj = taps.k + taps.off[j];
         for (int q = tid; q < t8; q += blockDim.x) ktap[q] = q < 2 * m + 1 ? kj[q] : 0.f;
         if (sub < rpb) {
@@ -434,33 +494,115 @@ __device__ __forceinline__ void smooth_h_body(const float* __restrict__ R, int H
     }
 }
 
-__global__ void __launch_bounds__(RED_THREADS)
+// Paired row pass: each thread takes the same 8 outputs of rows y and y + 1
+// (a row-pair task), the two rows staged interleaved as float2 so one
+// shared load feeds both lanes of a packed FMA.  Same sums, same order, so
+// the same bits as smooth_h_single.  Shared memory: the taps twice each
+// (2 t8max floats), then rpb buffers of 2 blen floats.  The float2 index
+// spad(q) puts a half-warp's 8-byte loads in distinct bank pairs.
+__device__ __forceinline__ void smooth_h_pair(const float* __restrict__ R, int H, int W, const SmoothTaps& taps,
+                                              int only_scale, float* __restrict__ S1, unsigned* sched) {
+    extern __shared__ __align__(16) float sm_h[];
+    float* ktap = sm_h;
+    const int tid = threadIdx.x;
+    const int tpr = taps.tpr, rpb = taps.rpb, nseg = taps.nseg;
+    const int sub = tid / tpr, lt = tid - sub * tpr;
+    float2* buf = reinterpret_cast<float2*>(sm_h + 2 * taps.t8max) + sub * taps.blen;
+    const int j0 = only_scale >= 0 ? only_scale : 0, nj = only_scale >= 0 ? 1 : taps.n;
+    const long long rowtasks = (long long)((H + 1) >> 1) * nseg;
+    const long long btasks = (rowtasks + rpb - 1) / rpb;
+    for (long long r = 0;; ++r) {
+        const long long task = next_task(sched, r, nj * btasks);
+        if (task < 0) break;
+        const int j = j0 + (int)(task / btasks);
+        const long long rt = (task % btasks) * rpb + sub;
+        const int m = taps.m[j], t8 = taps.t8[j];
+        const bool live = sub < rpb && rt < rowtasks;
+        const int y = live ? 2 * (int)(rt / nseg) : 0;
+        const bool live1 = live && y + 1 < H;
+        const int xs = live ? (int)(rt % nseg) * 8 * tpr : 0;
+        const float* kj = taps.k + taps.off[j];
+        for (int q = tid; q < t8; q += blockDim.x) {
+            const float v = q < 2 * m + 1 ? kj[q] : 0.f;
+            reinterpret_cast<float2*>(ktap)[q] = make_float2(v, v);
+        }
+        if (sub < rpb) {
+            const float* row = R + (long long)y * W;
+            const int len = 8 * tpr + t8 + 8;
+            for (int q = lt; q < len; q += tpr) {
+                const int x = xs - m + q;
+                const bool in = x >= 0 && x < W;
+                buf[spad(q)] = make_float2((live && in) ? __ldg(row + x) : 0.f, (live1 && in) ? __ldg(row + W + x) : 0.f);
+            }
+        }
+        __syncthreads();
+        const int x0 = xs + 8 * lt;
+        if (!live || x0 >= W) continue;
+        float2 acc[8], wa[8], wb[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { acc[i] = make_float2(0.f, 0.f); wa[i] = buf[spad(8 * lt + i)]; }
+#pragma unroll 1
+        for (int u0 = 0; u0 < t8; u0 += 16) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) wb[i] = buf[spad(8 * lt + u0 + 8 + i)];
+            conv8k2(acc, wa, wb, ktap + 2 * u0);
+            if (u0 + 8 >= t8) break;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) wa[i] = buf[spad(8 * lt + u0 + 16 + i)];
+            conv8k2(acc, wb, wa, ktap + 2 * u0 + 16);
+        }
+        float* out = S1 + ((long long)j * taps.s1rows + y + taps.mpad) * W + x0;
+        if (x0 + 8 <= W && (W & 3) == 0) {
+            reinterpret_cast<float4*>(out)[0] = make_float4(acc[0].x, acc[1].x, acc[2].x, acc[3].x);
+            reinterpret_cast<float4*>(out)[1] = make_float4(acc[4].x, acc[5].x, acc[6].x, acc[7].x);
+            if (live1) {
+                reinterpret_cast<float4*>(out + W)[0] = make_float4(acc[0].y, acc[1].y, acc[2].y, acc[3].y);
+                reinterpret_cast<float4*>(out + W)[1] = make_float4(acc[4].y, acc[5].y, acc[6].y, acc[7].y);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (x0 + i < W) {
+                    out[i] = acc[i].x;
+                    if (live1) out[W + i] = acc[i].y;
+                }
+        }
+    }
+}
+
+__device__ __forceinline__ void smooth_h_body(const float* __restrict__ R, int H, int W, const SmoothTaps& taps, const int* gate,
+                                              int only_scale, float* __restrict__ S1, unsigned* sched) {
+    if (gate && *gate) return;
+    if (taps.pair_h) smooth_h_pair(R, H, W, taps, only_scale, S1, sched);
+    else smooth_h_single(R, H, W, taps, only_scale, S1, sched);
+    end_tasks(sched);
+}
+
+__global__ void __launch_bounds__(RED_THREADS, 4)
 k_smooth_h(const float* __restrict__ R, int H, int W, const __grid_constant__ SmoothTaps taps, const int* gate,
-           int only_scale, float* __restrict__ S1) { smooth_h_body(R, H, W, taps, gate, only_scale, S1); }
+           int only_scale, float* __restrict__ S1, unsigned* sched) { smooth_h_body(R, H, W, taps, gate, only_scale, S1, sched); }
 
 // Column pass for every scale with the fused argmax of |S_j| over (j, p);
 // the last block turns the winner into the initial values
 // (S/(sqrt(pi) s), x*, y*, max(s, omega_b)).  out_S (optional) receives S_j.
 // A block task is 32 columns x 64 rows of one scale: lane = column, warp w
 // = rows 8w..8w+7.  The row-pass image has mpad zero rows above and below,
-// so the sliding window needs no bounds tests.
-__device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int H, int W, const SmoothTaps& taps, CycleState* st,
-                  const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket) {
-    if (gate && *gate) return;
+// so the sliding window needs no bounds tests.  This form serves odd W; the
+// paired form below (even W) is the default.
+__device__ __forceinline__ void smooth_v_single(const float* __restrict__ S1, int H, int W, const SmoothTaps& taps,
+                                                int j0, int nj, float* __restrict__ out_S, float& bv, int& bj,
+                                                long long& bi, unsigned* sched) {
     extern __shared__ __align__(16) float ktap[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int j0 = only_scale >= 0 ? only_scale : 0, nj = only_scale >= 0 ? 1 : taps.n;
     const int ncb = (W + 31) / 32, nrb = (H + 63) / 64;
     const long long per = (long long)ncb * nrb;
-    float bv = 0.f;
-    long long bi = 0x7fffffffffffffffLL;
-    int bj = 0x7fffffff;
-    for (long long task = blockIdx.x; task < nj * per; task += gridDim.x) {
+    for (long long r = 0;; ++r) {
+        const long long task = next_task(sched, r, nj * per);
+        if (task < 0) break;
         const int j = j0 + (int)(task / per);
         const int rem = (int)(task % per);
         const int rb = rem / ncb, cb = rem - rb * ncb;
         const int m = taps.m[j], t8 = taps.t8[j];
-        __syncthreads();
         const float* kj = taps.k + taps.off[j];
         for (int q = tid; q < t8; q += blockDim.x) ktap[q] = q < 2 * m + 1 ? kj[q] : 0.f;
         __syncthreads();
@@ -499,6 +641,77 @@ __device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int 
             }
         }
     }
+}
+
+// Paired column pass (even W): a block task is 64 columns x 64 rows, lane l
+// takes columns 2l and 2l + 1 with one 8-byte load per row and packed FMAs
+// (the taps written twice each in shared memory).  Same sums in the same
+// order as smooth_v_single, so the same S_j bits and the same winner
+// (arg_better is a total order, so the visiting order does not matter).
+__device__ __forceinline__ void smooth_v_pair(const float* __restrict__ S1, int H, int W, const SmoothTaps& taps,
+                                              int j0, int nj, float* __restrict__ out_S, float& bv, int& bj,
+                                              long long& bi, unsigned* sched) {
+    extern __shared__ __align__(16) float ktap[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncb = (W + 63) / 64, nrb = (H + 63) / 64;
+    const long long per = (long long)ncb * nrb;
+    for (long long r = 0;; ++r) {
+        const long long task = next_task(sched, r, nj * per);
+        if (task < 0) break;
+        const int j = j0 + (int)(task / per);
+        const int rem = (int)(task % per);
+        const int rb = rem / ncb, cb = rem - rb * ncb;
+        const int m = taps.m[j], t8 = taps.t8[j];
+        const float* kj = taps.k + taps.off[j];
+        for (int q = tid; q < t8; q += blockDim.x) {
+            const float v = q < 2 * m + 1 ? kj[q] : 0.f;
+            reinterpret_cast<float2*>(ktap)[q] = make_float2(v, v);
+        }
+        __syncthreads();
+        const int x = cb * 64 + 2 * lane, y0 = rb * 64 + 8 * warp;
+        if (x >= W || y0 >= H) continue;                     // W even: x + 1 < W as well
+        const float* col = S1 + ((long long)j * taps.s1rows + (y0 - m + taps.mpad)) * W + x;
+        float2 acc[8], b0[8], b1[8], b2[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
+        load_rows8x2(b0, col, W);
+        load_rows8x2(b1, col + (long long)8 * W, W);
+#pragma unroll 1
+        for (int u0 = 0; u0 < t8; u0 += 24) {
+            if (u0 + 8 < t8) load_rows8x2(b2, col + (long long)(u0 + 16) * W, W);
+            conv8k2(acc, b0, b1, ktap + 2 * u0);
+            if (u0 + 8 >= t8) break;
+            if (u0 + 16 < t8) load_rows8x2(b0, col + (long long)(u0 + 24) * W, W);
+            conv8k2(acc, b1, b2, ktap + 2 * u0 + 16);
+            if (u0 + 16 >= t8) break;
+            if (u0 + 24 < t8) load_rows8x2(b1, col + (long long)(u0 + 32) * W, W);
+            conv8k2(acc, b2, b0, ktap + 2 * u0 + 32);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int y = y0 + i;
+            if (y < H) {
+                const long long p = (long long)y * W + x;
+                if (out_S) { out_S[p] = acc[i].x; out_S[p + 1] = acc[i].y; }   // caller's buffer: 4-byte alignment
+                if (arg_better(acc[i].x, j, p, bv, bj, bi)) { bv = acc[i].x; bj = j; bi = p; }
+                if (arg_better(acc[i].y, j, p + 1, bv, bj, bi)) { bv = acc[i].y; bj = j; bi = p + 1; }
+            }
+        }
+    }
+}
+
+// Shared memory of the column pass: the taps written twice (paired form).
+__device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int H, int W, const SmoothTaps& taps, CycleState* st,
+                  const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket,
+                  unsigned* sched) {
+    if (gate && *gate) return;
+    const int j0 = only_scale >= 0 ? only_scale : 0, nj = only_scale >= 0 ? 1 : taps.n;
+    float bv = 0.f;
+    long long bi = 0x7fffffffffffffffLL;
+    int bj = 0x7fffffff;
+    if ((W & 1) == 0) smooth_v_pair(S1, H, W, taps, j0, nj, out_S, bv, bj, bi, sched);
+    else smooth_v_single(S1, H, W, taps, j0, nj, out_S, bv, bj, bi, sched);
+    end_tasks(sched);
     block_arg_reduce(bv, bj, bi);
     if (grid_arg_finish(bv, bj, bi, part, ticket, &st->speak) && threadIdx.x == 0 && only_scale < 0) {
         // the grid-wide winner (not this block's partial)
@@ -516,20 +729,21 @@ __device__ __forceinline__ void smooth_v_body(const float* __restrict__ S1, int 
     }
 }
 
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, 3)
 k_smooth_v_argmax(const float* __restrict__ S1, int H, int W, const __grid_constant__ SmoothTaps taps, CycleState* st,
-                  const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket) { smooth_v_body(S1, H, W, taps, st, gate, only_scale, out_S, part, ticket); }
+                  const int* gate, int only_scale, float* __restrict__ out_S, ArgRes* part, unsigned* ticket,
+                  unsigned* sched) { smooth_v_body(S1, H, W, taps, st, gate, only_scale, out_S, part, ticket, sched); }
 
 
 // ------------------------------------------------------------------ batched wrappers
 // grid.y = image; every image runs the same body with its own buffers.
 __global__ void __launch_bounds__(RED_THREADS) k_smooth_h_b(const ImgDesc* __restrict__ imgs) {
     const ImgDesc& g = imgs[blockIdx.y];
-    smooth_h_body(g.R, g.H, g.W, g.taps, &g.st->skip_smooth, -1, g.S1);
+    smooth_h_body(g.R, g.H, g.W, g.taps, &g.st->skip_smooth, -1, g.S1, nullptr);
 }
 __global__ void __launch_bounds__(RED_THREADS) k_smooth_v_b(const ImgDesc* __restrict__ imgs) {
     const ImgDesc& g = imgs[blockIdx.y];
-    smooth_v_body(g.S1, g.H, g.W, g.taps, g.st, &g.st->skip_smooth, -1, nullptr, g.part, g.ticket);
+    smooth_v_body(g.S1, g.H, g.W, g.taps, g.st, &g.st->skip_smooth, -1, nullptr, g.part, g.ticket, nullptr);
 }
 __global__ void __launch_bounds__(RED_THREADS) k_sub_h_b(const ImgDesc* __restrict__ imgs) {
     const ImgDesc& g = imgs[blockIdx.y];
@@ -585,17 +799,38 @@ cudaError_t launch_sub_v(float* R, const float* B, int H, int W, CycleState* st,
     return cudaGetLastError();
 }
 
+size_t smooth_h_smem(const SmoothTaps& t) {
+    const size_t nr = t.pair_h ? 2 : 1;
+    return nr * ((size_t)t.t8max + (size_t)t.rpb * t.blen) * sizeof(float);
+}
+size_t smooth_v_smem(const SmoothTaps& t) { return 2 * (size_t)t.t8max * sizeof(float); }
+
+// Blocks of the smoothing passes: as many as are resident at once (their
+// snake-ordered tasks balance only across co-resident blocks), at most cap.
+static int resident_grid(const void* fn, size_t smem, int num_sms, int cap) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RED_THREADS, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return std::max(1, std::min(cap, per_sm * num_sms));
+}
+int smooth_grid_h(const SmoothTaps& t, int num_sms, int cap) {
+    return resident_grid(reinterpret_cast<const void*>(&k_smooth_h), smooth_h_smem(t), num_sms, cap);
+}
+int smooth_grid_v(const SmoothTaps& t, int num_sms, int cap) {
+    return resident_grid(reinterpret_cast<const void*>(&k_smooth_v_argmax), smooth_v_smem(t), num_sms, cap);
+}
+
 cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
-                            float* S1, int grid, cudaStream_t s) {
-    const size_t smem = ((size_t)taps.t8max + (size_t)taps.rpb * taps.blen) * sizeof(float);
-    k_smooth_h<<<grid, RED_THREADS, smem, s>>>(R, H, W, taps, gate, only_scale, S1);
+                            float* S1, int grid, unsigned* sched, cudaStream_t s) {
+    k_smooth_h<<<grid, RED_THREADS, smooth_h_smem(taps), s>>>(R, H, W, taps, gate, only_scale, S1, sched);
     return cudaGetLastError();
 }
 
 cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
-                            int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s) {
-    k_smooth_v_argmax<<<grid, RED_THREADS, (size_t)taps.t8max * sizeof(float), s>>>(S1, H, W, taps, st, gate,
-                                                                                   only_scale, out_S, part, ticket);
+                            int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, unsigned* sched,
+                            cudaStream_t s) {
+    k_smooth_v_argmax<<<grid, RED_THREADS, smooth_v_smem(taps), s>>>(S1, H, W, taps, st, gate, only_scale, out_S,
+                                                                      part, ticket, sched);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ struct SmoothTaps {          // unit-L2 1-D smoothing kernels, passed by value
     int rpb;                 // row pass: row segments per block (256 / tpr)
     int nseg;                // row pass: segments per image row
     int blen;                // row pass: shared floats per segment buffer (bank-padded)
+    int pair_h;              // row pass takes two rows per thread (packed FMAs) when its buffers fit
     int mpad;                // zero halo rows above and below each scale's row-pass image
     long long s1rows;        // rows of each scale's row-pass image (H + 2 mpad + 8)
 };
@@ -53,6 +54,10 @@ struct ImgDesc {
 constexpr int MAX_BATCH = 256;
 
 int sub_h_blen(int W, const SmoothTaps& geo);
+size_t smooth_h_smem(const SmoothTaps& t);   // dynamic shared bytes of the row pass (its chosen form)
+size_t smooth_v_smem(const SmoothTaps& t);   // ... of the column pass
+int smooth_grid_h(const SmoothTaps& t, int num_sms, int cap);   // resident blocks of the row pass (<= cap)
+int smooth_grid_v(const SmoothTaps& t, int num_sms, int cap);   // ... of the column pass
 
 // asp_fit.cu
 size_t fit_smem_bytes();
@@ -79,10 +84,12 @@ cudaError_t launch_sub_h(const float* B, int H, int W, const CycleState* st, con
                           float* T1, int grid, const SmoothTaps& geo, cudaStream_t s);
 cudaError_t launch_sub_v(float* R, const float* B, int H, int W, CycleState* st, const int* gate, const float* wbuf,
                          const float* T1, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
+// sched: two zeroed unsigned task counters of this pass (nullptr: static order)
 cudaError_t launch_smooth_h(const float* R, int H, int W, const SmoothTaps& taps, const int* gate, int only_scale,
-                            float* S1, int grid, cudaStream_t s);
+                            float* S1, int grid, unsigned* sched, cudaStream_t s);
 cudaError_t launch_smooth_v(const float* S1, int H, int W, const SmoothTaps& taps, CycleState* st, const int* gate,
-                            int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, cudaStream_t s);
+                            int only_scale, float* out_S, int grid, ArgRes* part, unsigned* ticket, unsigned* sched,
+                            cudaStream_t s);
 
 // asp_major.cu (minor/major split)
 cudaError_t launch_sub_gauss(float* R, int H, int W, CycleState* st, int grid, cudaStream_t s);

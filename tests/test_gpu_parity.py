@@ -103,7 +103,7 @@ def test_subtraction_matches_oracle(asp, H, W, seed, sub_mode):
     case = synth.small_case(H, W, seed=seed)
     rng = np.random.default_rng(seed)
     mode = asp.ASP_SUB_FFT if sub_mode == "fft" else asp.ASP_SUB_DIRECT
-    ctx = _ctx(asp, case, k_max=8, sub_mode=mode)
+    ctx = _ctx(asp, case, k_max=k_max, sub_mode=mode)
     R0 = case.dirty.astype(np.float64)
     for rnd in range(2):
         comps = []
@@ -156,8 +156,10 @@ def test_subtraction_gaussian_psf_closed_form(asp):
 
 # ----------------------------------------------------------------- smoothing (a3)
 
-@pytest.mark.parametrize("H,W", [(64, 80), (256, 256)])
+@pytest.mark.parametrize("H,W", [(64, 80), (256, 256), (61, 75), (97, 130)])
 def test_smoothing_images_and_peak(asp, H, W):
+    """Even W takes the paired column pass, odd W the single one; odd H
+    leaves the paired row pass a last pair with one live row."""
     case = synth.small_case(H, W, seed=5, n_gauss=2, sigma_range=(3, 8))
     ctx = _ctx(asp, case)
     _, wb, _, _ = ctx.beam
