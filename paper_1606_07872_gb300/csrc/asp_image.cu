@@ -428,7 +428,10 @@ cudaError_t launch_fft_sub_argmax(float* R, const float* conv, int H, int W, Cyc
 // padded at the image edges, as two register-blocked passes: each thread
 // produces 8 consecutive outputs, keeping a 16-entry sliding window of the
 // input in registers, so 8 taps cost 8 loads, 2 broadcast tap loads and 64
-// FMAs.  Taps are zero-padded to a multiple of 8 (t8).
+// FMAs.  Taps are zero-padded to a multiple of 8 (t8).  The paired forms
+// give each thread two such output streams (two rows, or two columns) and
+// run both with packed two-lane FMAs: the same bits, half the FMA
+// instructions.
 
 // Row pass: S1_j[y + mpad][x] = sum_u k_j[u] R[y][x + u - m_j].  A block
 // task is rpb row segments of 8 tpr outputs each; the segment with its
