@@ -808,8 +808,9 @@ size_t smooth_h_smem(const SmoothTaps& t) {
 }
 size_t smooth_v_smem(const SmoothTaps& t) { return 2 * (size_t)t.t8max * sizeof(float); }
 
-// Blocks of the smoothing passes: as many as are resident at once (their
-// snake-ordered tasks balance only across co-resident blocks), at most cap.
+// Blocks of the smoothing passes: as many as are resident at once (blocks
+// that draw tasks from the counter balance only while they all run), at
+// most cap.
 static int resident_grid(const void* fn, size_t smem, int num_sms, int cap) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RED_THREADS, smem) != cudaSuccess || per_sm < 1)
