@@ -275,3 +275,23 @@ def test_precision_form_equals_the_rotated_axes_form():
     ys, xs = np.mgrid[0:20, 0:22].astype(float)
     th = np.concatenate([[a, x, y, *E.precision_from_axes(s1, s2, p)] for a, x, y, s1, s2, p in src])
     np.testing.assert_allclose(E.ell_model(th, xs, ys), img, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- member box and xtol scales
+
+def test_member_box_of_a_circle_is_the_circular_box():
+    for x, y, w in ((10.2, 7.5, 1.3), (40.5, 3.49, 2.6), (-3.5, 12.0, 0.7)):
+        assert E.ell_member_box(x, y, 1 / w ** 2, 0.0, 1 / w ** 2) == O.member_box(x, y, w)
+
+
+def test_member_box_follows_the_major_width():
+    A, B, C = E.precision_from_axes(3.2, 0.9, 0.6)
+    h = max(math.ceil(4 * 3.2), 5)                              # 13
+    assert E.ell_member_box(20.4, 30.6, A, B, C) == (20 - h, 20 + h, 31 - h, 31 + h)
+
+
+def test_xtol_scales_hand_values():
+    A, B, C = 1 / 9, 0.0, 1.0                                   # major width 3 along x, minor 1
+    sc = E.ell_step_scale(np.array([-0.4, 5.0, 6.0, A, B, C, 0.0, 1.0, 2.0, 0.25, 0.0, 0.25]))
+    np.testing.assert_allclose(sc, [0.4, 3.0, 3.0, 5 / 9, 5 / 9, 5 / 9, 1.0, 2.0, 2.0, 0.25, 0.25, 0.25],
+                               rtol=1e-14)

@@ -188,3 +188,27 @@ def test_planted_amplitudes_in_the_wrong_channel_are_caught(monkeypatch):
     monkeypatch.setattr(M, "mc_model_and_jacobian", bad)
     with pytest.raises(AssertionError):
         test_lm_recovers_noiseless_members_across_channels()
+
+
+# ---------------------------------------------------------------- trial test and xtol scales
+
+def test_trial_test_hand_cases():
+    wb2 = np.array([1.5, 2.0]) ** 2            # widest beam 2.0
+    box = (10, 29, 5, 20)                      # extent max(20, 16) = 20
+    ok = np.array([15.0, 12.0, 1.0, 0.5, 0.4])
+    assert M.mc_valid(ok, box, wb2)
+    assert M.mc_valid(np.array([15.0, 12.0, 0.0, 0.5, 0.4]), box, wb2)          # a point (s = 0)
+    assert M.mc_valid(np.array([10.0, 20.0, 1.0, 0.5, 0.4]), box, wb2)          # centre on the box edge
+    assert not M.mc_valid(np.array([9.99, 12.0, 1.0, 0.5, 0.4]), box, wb2)      # centre outside
+    assert not M.mc_valid(np.array([15.0, 20.01, 1.0, 0.5, 0.4]), box, wb2)
+    s_edge = math.sqrt(20.0 ** 2 - 4.0)                                          # s^2 + 4 = 20^2
+    assert M.mc_valid(np.array([15.0, 12.0, s_edge, 0.5, 0.4]), box, wb2)
+    assert not M.mc_valid(np.array([15.0, 12.0, s_edge * (1 + 1e-9), 0.5, 0.4]), box, wb2)
+    assert not M.mc_valid(np.array([15.0, 12.0, np.nan, 0.5, 0.4]), box, wb2)
+
+
+def test_xtol_scales_hand_values():
+    wb2 = np.array([1.5, 2.0]) ** 2
+    th = np.array([15.0, 12.0, 1.5, -0.5, 0.0])
+    w = math.sqrt(1.5 ** 2 + 4.0)
+    np.testing.assert_allclose(M.mc_step_scale(th, wb2), [w, w, w, 0.5, 1.0], rtol=1e-15)
