@@ -1,0 +1,104 @@
+"""The FP32 error model of tests/fp32_bounds.py against an FP32 evaluation
+of the same pixel pass (NumPy float32, on the CPU).
+
+The GPU's parity tests accept its normal equations and chi^2 within the
+bounds pass_bounds derives from the pass's operations.  Here those bounds
+are checked against an independent FP32 evaluation of the pass, in the
+GPU's order of operations: member frames rounded from FP64 (integer centre
+plus fractional offset, exponent constant 0.5 log2(e) / w^2, 1 / w^2,
+1 / w^3), per-pixel exp2 of the negated argument, the J row and residual in
+FP32, sums of J^T J, J^T r and r^2 in FP32 leaves of at most 64 pixels
+with compensated (Kahan) accumulation across leaves.  Every entry must lie
+within its bound, and the bounds must not be loose by orders of magnitude
+(a bound far above every error would pass any GPU result)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.fp32_bounds import pass_bounds
+
+F = np.float32
+LOG2E = 1.4426950408889634
+
+
+def _fp32_pass(T, xs, ys, theta):
+    """FP32 J rows and residuals, then FP32-leaf / Kahan sums."""
+    th = np.asarray(theta, dtype=np.float64).reshape(-1, 4)
+    px = xs.astype(np.int64)
+    py = ys.astype(np.int64)
+    n, K = xs.size, th.shape[0]
+    J = np.zeros((n, 4 * K), dtype=F)
+    model = np.zeros(n, dtype=F)
+    for k, (a, x, y, w) in enumerate(th):
+        cx, cy = math.floor(x + 0.5), math.floor(y + 0.5)
+        fx, fy = F(x - cx), F(y - cy)
+        iw = 1.0 / w
+        c, iw2, iw3 = F(0.5 * LOG2E * iw * iw), F(iw * iw), F(iw * iw * iw)
+        dx = (px - cx).astype(F) - fx
+        dy = (py - cy).astype(F) - fy
+        q = dx * dx + dy * dy
+        e = np.exp2(-(c * q)).astype(F)
+        gk = F(a) * e
+        J[:, 4 * k] = e
+        J[:, 4 * k + 1] = gk * dx * iw2
+        J[:, 4 * k + 2] = gk * dy * iw2
+        J[:, 4 * k + 3] = gk * q * iw3
+        model = model + gk
+    r = T.astype(F) - model
+    Jr = np.concatenate([J, r[:, None]], axis=1)
+    P1 = Jr.shape[1]
+    tot = np.zeros((P1, P1), dtype=F)
+    comp = np.zeros((P1, P1), dtype=F)
+    for s in range(0, n, 64):
+        blk = Jr[s: s + 64]
+        leaf = np.zeros((P1, P1), dtype=F)
+        for row in blk:                                  # FP32 products summed in FP32
+            leaf = leaf + np.outer(row, row).astype(F)
+        y = leaf - comp                                  # Kahan across leaves
+        t = tot + y
+        comp = (t - tot) - y
+        tot = t
+    S = tot.astype(np.float64)
+    return S[:-1, :-1], S[:-1, -1], float(S[-1, -1])
+
+
+def _case(seed, K, n_side):
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:n_side, 0:n_side].astype(np.float64)
+    xs, ys = xs.ravel(), ys.ravel()
+    truth = np.column_stack([rng.uniform(0.1, 1.0, K), rng.uniform(5, n_side - 5, K),
+                             rng.uniform(5, n_side - 5, K), rng.uniform(1.2, 6.0, K)]).ravel()
+    T = O.gauss_model(truth, xs, ys) + rng.normal(0, 1e-3, xs.size)
+    T = T.astype(F).astype(np.float64)                   # the GPU's target is FP32
+    theta = truth * np.tile([1.05, 1.0, 1.0, 0.95], K) + np.tile([0.0, 0.3, -0.2, 0.0], K)
+    return T, xs, ys, theta
+
+
+@pytest.mark.parametrize("seed,K,n_side", [(0, 1, 24), (1, 3, 32), (2, 6, 40), (3, 10, 48)])
+def test_fp32_pass_within_its_error_bounds(seed, K, n_side):
+    T, xs, ys, theta = _case(seed, K, n_side)
+    b = pass_bounds(T, xs, ys, theta)
+    A32, g32, c32 = _fp32_pass(T, xs, ys, theta)
+    iu = np.triu_indices(A32.shape[0])
+    errA, errg, errc = np.abs(A32 - b["A"])[iu], np.abs(g32 - b["g"]), abs(c32 - b["chi2"])
+    assert np.all(errA <= b["bA"][iu]), np.max(errA / b["bA"][iu])
+    assert np.all(errg <= b["bg"]), np.max(errg / b["bg"])
+    assert errc <= b["bc"], errc / b["bc"]
+    # not vacuous: the largest error reaches a visible fraction of its bound
+    ratio = max(np.max(errA / b["bA"][iu]), np.max(errg / b["bg"]), errc / b["bc"])
+    assert ratio > 1e-3, ratio
+
+
+def test_bounds_catch_a_real_fp32_mistake():
+    """The same FP32 pass evaluated at widths off by 2^-9 relative (about
+    what an 8-bit mantissa would keep) must leave the bounds: they are tight
+    enough to see an error that a correct FP32 evaluation does not make."""
+    T, xs, ys, theta = _case(4, 3, 32)
+    b = pass_bounds(T, xs, ys, theta)
+    th = np.asarray(theta, float).reshape(-1, 4).copy()
+    th[:, 3] *= 1.0 + 2.0 ** -9                          # a width off by 2^-9 relative
+    A32, g32, c32 = _fp32_pass(T, xs, ys, th.ravel())
+    iu = np.triu_indices(A32.shape[0])
+    assert np.any(np.abs(A32 - b["A"])[iu] > b["bA"][iu]) or np.any(np.abs(g32 - b["g"]) > b["bg"])
