@@ -102,3 +102,39 @@ def test_bounds_catch_a_real_fp32_mistake():
     A32, g32, c32 = _fp32_pass(T, xs, ys, th.ravel())
     iu = np.triu_indices(A32.shape[0])
     assert np.any(np.abs(A32 - b["A"])[iu] > b["bA"][iu]) or np.any(np.abs(g32 - b["g"]) > b["bg"])
+
+
+def _fp32_damped_solve(A, g, lam):
+    """The kernel's solve in FP32: FP32 copies of A and g, the scaled matrix
+    S (A + lam D) S with S = diag(A + lam D)^-1/2 (unit diagonal), its FP32
+    Cholesky factor and the two FP32 triangular solves, then delta = S x."""
+    import scipy.linalg
+    A32, g32 = A.astype(F), g.astype(F)
+    d = np.diag(A32).copy()
+    d[~(d > 0)] = F(1)
+    M = A32 + F(lam) * np.diag(d).astype(F)
+    s = (F(1) / np.sqrt(np.diag(M))).astype(F)
+    Ms = (s[:, None] * M * s[None, :]).astype(F)
+    L = scipy.linalg.cholesky(Ms, lower=True)
+    assert L.dtype == F
+    y = scipy.linalg.solve_triangular(L, (s * g32).astype(F), lower=True)
+    x = scipy.linalg.solve_triangular(L.T, y, lower=False)
+    assert x.dtype == F
+    return (s * x).astype(np.float64)
+
+
+@pytest.mark.parametrize("seed,K", [(5, 2), (6, 5), (7, 9)])
+def test_fp32_damped_solve_within_the_step_bound(seed, K):
+    from tests.fp32_bounds import marquardt_diag, step_backward, step_bound
+    T, xs, ys, theta = _case(seed, K, 40)
+    b = pass_bounds(T, xs, ys, theta)
+    A32, g32, _ = _fp32_pass(T, xs, ys, theta)              # the FP32 sums the solve starts from
+    for lam in (1e-6, 1e-3, 1.0):
+        M = b["A"] + lam * np.diag(marquardt_diag(b["A"]))
+        delta = np.linalg.solve(M, b["g"])
+        got = _fp32_damped_solve(A32, g32, lam)
+        bound, kappa = step_bound(b["A"], b["g"], lam, b["bA"], b["bg"], delta)
+        if kappa < 0.5:                                      # the first-order bound is meaningful
+            assert np.all(np.abs(got - delta) <= bound), np.max(np.abs(got - delta) / bound)
+        resid, allowed = step_backward(b["A"], b["g"], lam, b["bA"], b["bg"], got)
+        assert np.all(resid <= allowed), np.max(resid / allowed)
